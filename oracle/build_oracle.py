@@ -1,0 +1,34 @@
+"""Build the oracle's one C routine (order-exact pivot loop) in place.
+
+TEST INFRASTRUCTURE.  ``python oracle/build_oracle.py`` writes
+``oracle/_pivots.so``; the oracle's Python wrapper builds it on first use.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "pivots.c")
+OUT = os.path.join(HERE, "_pivots.so")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
+        return OUT
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", OUT + ".tmp", SRC, "-lm"]
+    # use the hardware fused multiply-add when the host has one (the result
+    # of fma() is the same correctly rounded value either way)
+    try:
+        flags = open("/proc/cpuinfo").read()
+        if " fma " in flags and " avx2 " in flags:
+            cmd[1:1] = ["-mfma", "-mavx2"]
+    except OSError:
+        pass
+    subprocess.check_call(cmd)
+    os.replace(OUT + ".tmp", OUT)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,356 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here compares the oracle with something other than itself: a
+closed form, a finite difference, a brute-force sum, an analytic integral,
+a linear-algebra identity, or the paper's pre-ISDF definitions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth import workloads as wl
+from oracle import orbitals, jastrow, pivots, fit, wbuild, xtc, energies
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    """3-atom H chain, one s shell per atom: 3 orbitals, 3 x 16 x 26 grid."""
+    w = wl.tiny_chain(n_atom=3, n_rad=16, n_ang=26, shells=(0,), n_mu=6, seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    return w, phi, dphi
+
+
+@pytest.fixture(scope="module")
+def h6():
+    w = wl.h6_chain()
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    return w, phi, dphi
+
+
+# ---------------------------------------------------------------- orbitals
+
+def test_single_primitive_closed_form():
+    """One normalised p_x primitive at a known point against its formula."""
+    b = wl.Basis(center=np.array([[0.1, -0.2, 0.3]]), powers=np.array([[1, 0, 0]], np.int32),
+                 exps=np.array([[0.7]]), coefs=np.array([[1.3]]), atom=np.zeros(1, np.int32))
+    r = np.array([[0.5, 0.4, -0.1]])
+    v, g = orbitals.eval_ao(b, r)
+    x, y, z = r[0] - b.center[0]
+    r2 = x * x + y * y + z * z
+    ref = 1.3 * x * math.exp(-0.7 * r2)
+    assert abs(v[0, 0] - ref) < 1e-15
+    # analytic derivative along x: (1 - 2 a x^2) exp(-a r^2)
+    assert abs(g[0, 0, 0] - 1.3 * (1 - 2 * 0.7 * x * x) * math.exp(-0.7 * r2)) < 1e-15
+    assert abs(g[1, 0, 0] - 1.3 * x * (-2 * 0.7 * y) * math.exp(-0.7 * r2)) < 1e-15
+
+
+def test_orbital_gradient_fd(h6):
+    w, phi, dphi = h6
+    rng = np.random.default_rng(0)
+    pts = w.grid_xyz[rng.choice(w.n_g, 40, replace=False)]
+    h = 1e-5
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        fp, _ = orbitals.eval_orbitals(w.basis, w.mo_coef, pts + e)
+        fm, _ = orbitals.eval_orbitals(w.basis, w.mo_coef, pts - e)
+        _, d = orbitals.eval_orbitals(w.basis, w.mo_coef, pts)
+        fd = (fp - fm) / (2 * h)
+        assert np.max(np.abs(fd - d[ax])) < 1e-7 * max(1.0, np.max(np.abs(d[ax])))
+
+
+def test_orbitals_match_analytic_overlap():
+    """Grid quadrature of phi_p phi_q reproduces the analytic L2 overlap used
+    to orthonormalise the orbitals (C^T S_AO C = I), on a fine one-atom grid."""
+    w = wl.tiny_chain(n_atom=1, n_rad=80, n_ang=302, shells=(0, 1), seed=3)
+    phi, _ = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    ov = (phi * w.grid_w[None, :]) @ phi.T
+    assert np.max(np.abs(ov - np.eye(w.n_orb))) < 2e-3
+
+
+# ---------------------------------------------------------------- Jastrow
+
+def test_radial_closed_form():
+    jas = wl.radial_jastrow(np.zeros((2, 3)))
+    ri = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, -0.5]])
+    rj = np.array([[0.3, -0.4, 1.2], [2.0, 0.0, 0.0]])
+    K = jastrow.kernels(ri, rj, jas)
+    for a in range(2):
+        for b in range(2):
+            dv = ri[a] - rj[b]
+            r = np.linalg.norm(dv)
+            up = 1.0 / (2.0 * (1.0 + r) ** 2)
+            assert np.allclose(K[:3, a, b], up * dv / r, rtol=1e-14, atol=0)
+            assert abs(K[3, a, b] - 1.0 / (4.0 * (1.0 + r) ** 4)) < 1e-15
+    u = jastrow.u_value(ri, rj, jas)
+    r = np.linalg.norm(ri[1] - rj[0])
+    assert abs(u[1, 0] - r / (2 * (1 + r))) < 1e-15
+
+
+@pytest.mark.parametrize("terms", [wl.BH_TERMS_C3, wl.bh_terms_c4()])
+def test_bh_gradient_fd(terms):
+    atoms, xyz = wl.benzene() if len(terms) == 10 else wl.h_chain(4, 1.8)
+    jas = wl.bh_jastrow(atoms, xyz, terms, np.random.default_rng(5), scale=0.3)
+    jas.b = np.linspace(0.8, 1.3, jas.n_types)
+    jas.d = 1.1
+    rng = np.random.default_rng(1)
+    ri = rng.normal(size=(7, 3)) * 2
+    rj = rng.normal(size=(5, 3)) * 2
+    g = jastrow.grad1_u(ri, rj, jas)
+    h = 1e-6
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        fd = (jastrow.u_value(ri + e, rj, jas) - jastrow.u_value(ri - e, rj, jas)) / (2 * h)
+        assert np.max(np.abs(fd - g[ax])) < 1e-8
+
+
+def test_bh_symmetry_and_cusp():
+    atoms, xyz = wl.h_chain(3, 1.8)
+    jas = wl.bh_jastrow(atoms, xyz, wl.bh_terms_c4(), np.random.default_rng(2), scale=0.3)
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(6, 3))
+    b = rng.normal(size=(6, 3))
+    assert np.allclose(jastrow.u_value(a, b, jas), jastrow.u_value(b, a, jas).T, rtol=1e-13)
+    # opposite-spin Kato: du/dr12 -> 1/2 as r12 -> 0 (no free term has o = 1)
+    p = np.array([[0.2, 0.1, 0.3]])
+    e = np.array([[0.0, 0.0, 1.0]])
+    # symmetric displacement keeps the e-n terms fixed to first order
+    r = 1e-6
+    slope = (jastrow.u_value(p + 0.5 * r * e, p - 0.5 * r * e, jas)
+             - jastrow.u_value(p, p, jas))[0, 0] / r
+    assert abs(slope - 0.5) < 1e-5
+
+
+def test_self_pair_masked():
+    jas = wl.radial_jastrow(np.zeros((1, 3)))
+    pts = np.random.default_rng(0).normal(size=(5, 3))
+    K = jastrow.kernels(pts, pts, jas, np.arange(5), np.arange(5))
+    assert np.all(K[:, np.arange(5), np.arange(5)] == 0.0)
+    assert np.all(np.isfinite(K))
+
+
+# ---------------------------------------------------------------- pivots
+
+def _dense_S(phi, dphi, w, grad):
+    t1 = phi.T @ phi
+    if grad:
+        t2 = sum(dphi[c].T @ dphi[c] for c in range(3))
+        return np.outer(w, w) * t1 * t2
+    return np.outer(w, w) * t1 * t1
+
+
+def test_first_pivot_is_argmax_of_closed_form(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 1, mode="scalar")
+    dens = np.sum(phi * phi, axis=0)
+    d0 = w.grid_w ** 2 * dens ** 2
+    assert res.piv_s[0] == int(np.argmax(d0))
+    res = pivots.select(phi, dphi, w.grid_w, 1, mode="gradient")
+    gd = np.sum(dphi * dphi, axis=(0, 1))
+    assert res.piv_v[0] == int(np.argmax(w.grid_w ** 2 * dens * gd))
+
+
+@pytest.mark.parametrize("grad", [False, True])
+def test_pivot_columns_match_dense_cholesky(tiny, grad):
+    """L = S[:, P] chol(S[P,P])^{-T} and d = diag(S) - rowsum(L^2), from a
+    dense S built with numpy."""
+    w, phi, dphi = tiny
+    k = 5
+    res = pivots.select(phi, dphi, w.grid_w, k, mode="gradient" if grad else "scalar")
+    P = res.piv_v if grad else res.piv_s
+    L = res.L_v if grad else res.L_s
+    S = _dense_S(phi, dphi, w.grid_w, grad)
+    R = np.linalg.cholesky(S[np.ix_(P, P)])
+    Lref = np.linalg.solve(R, S[P, :]).T                  # [n_g, k]
+    scale = np.max(np.abs(Lref))
+    assert np.max(np.abs(L.T - Lref)) < 1e-9 * scale
+    dref = np.diag(S) - np.sum(Lref ** 2, axis=1)
+    dref[P] = 0
+    assert np.max(np.abs((res.d_v if grad else res.d_s) - np.maximum(dref, 0))) < 1e-9 * np.max(np.diag(S))
+    # pivoted Cholesky picks non-increasing pivots
+    piv_vals = np.array([L[j, P[j]] for j in range(k)])
+    assert np.all(np.diff(piv_vals) <= 1e-12 * piv_vals[0])
+
+
+def test_scalar_rank_exhausts_at_pair_count(tiny):
+    """The scalar matrix has rank n_orb (n_orb + 1) / 2 (distinct pair
+    products); the pivot loop stops exactly there."""
+    w, phi, dphi = tiny
+    n = w.n_orb
+    res = pivots.select(phi, dphi, w.grid_w, 50, mode="scalar")
+    assert res.rank_exhausted
+    assert len(res.piv_s) == n * (n + 1) // 2
+
+
+def test_fusion_rule(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu, mode="fused")
+    assert len(res.pivots) == w.n_mu and not res.rank_exhausted
+    assert len(set(res.pivots.tolist())) == w.n_mu
+    # union in append order: alternate scalar / gradient, skip repeats
+    seq = []
+    for j in range(max(len(res.piv_s), len(res.piv_v))):
+        for lst in (res.piv_s, res.piv_v):
+            if j < len(lst) and lst[j] not in seq:
+                seq.append(int(lst[j]))
+    assert seq[:w.n_mu] == res.pivots.tolist()
+
+
+# ---------------------------------------------------------------- fit
+
+def test_nystrom_identity(h6):
+    """Pivot residual trace = weighted fit residual (scalar channel, same
+    pivots): sum_g d_g = sum_g w_g^2 r_g."""
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 40, mode="scalar")
+    xi, _, lams = fit.fit(phi, dphi, res.piv_s, channels=(0,))
+    assert lams[0] == 0.0
+    r = fit.fit_residual(phi, w.grid_w, res.piv_s, xi)
+    a, b = np.sum(res.d_s), np.sum(r)
+    assert abs(a - b) < 1e-8 * np.sum(w.grid_w ** 2 * np.sum(phi * phi, 0) ** 2)
+    assert abs(a - b) / abs(a) < 1e-5
+
+
+def test_interpolation_property(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu)
+    xi, xit, lams = fit.fit(phi, dphi, res.pivots)
+    assert np.all(lams == 0)
+    P = res.pivots
+    assert np.max(np.abs(xi[:, P] - np.eye(len(P)))) < 1e-7
+    for c in range(3):
+        assert np.max(np.abs(xit[c][:, P] - np.eye(len(P)))) < 1e-7
+
+
+def test_full_rank_reconstruction(tiny):
+    """At full scalar rank the ISDF reproduces every pair density."""
+    w, phi, dphi = tiny
+    n = w.n_orb
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    xi, _, _ = fit.fit(phi, dphi, res.piv_s, channels=(0,))
+    P = res.piv_s
+    for p in range(n):
+        for q in range(n):
+            rec = (phi[p, P] * phi[q, P]) @ xi
+            assert np.max(np.abs(rec - phi[p] * phi[q])) < 1e-8 * np.max(np.abs(phi[p] * phi[q]))
+
+
+# ---------------------------------------------------------------- W
+
+def test_w_staged_equals_brute_force():
+    w = wl.tiny_chain(n_atom=2, n_rad=6, n_ang=10, shells=(0, 1), n_mu=10, seed=4)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, 10)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    for jas in (w.jastrow, wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(9), 0.2)):
+        Wst, _ = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, jas, batch=7)
+        Wbf = wbuild.brute_force(w.grid_xyz, w.grid_w, xi, xit, jas)
+        assert np.max(np.abs(Wst - Wbf)) < 1e-11 * np.max(np.abs(Wbf))
+
+
+def test_zero_jastrow_gives_zero(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 24)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    jas = wl.radial_jastrow(w.xyz)
+    jas.cusp = False
+    W, calG = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, jas)
+    assert np.all(W == 0.0) and np.all(calG == 0.0)
+
+
+def test_radial_u3_symmetric_and_coulomb_like(tiny):
+    """Radial Jastrow: |grad u|^2 = u'(r)^2 is symmetric, so u3 is symmetric,
+    and at full scalar rank K3^{pq}_{rs} equals the direct double-grid
+    integral (pr|u'^2|qs)."""
+    w, phi, dphi = tiny
+    n = w.n_orb
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    P = res.piv_s
+    xi, _, _ = fit.fit(phi, dphi, P, channels=(0,))
+    calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, w.jastrow)
+    u3 = (xi * w.grid_w) @ calG[3].T
+    assert np.max(np.abs(u3 - u3.T)) < 1e-10 * np.max(np.abs(u3))
+    # direct: sum_{g,g'} w w phi_p phi_r (g) u'(r)^2 phi_q phi_s (g')
+    dv = w.grid_xyz[:, None, :] - w.grid_xyz[None, :, :]
+    r = np.sqrt(np.sum(dv * dv, axis=2))
+    k = 1.0 / (4.0 * (1.0 + r) ** 4)
+    np.fill_diagonal(k, 0.0)
+    C = phi[:, P]
+    for (p, rr, q, s) in [(0, 0, 1, 1), (0, 1, 2, 2), (1, 2, 0, 2), (2, 2, 2, 2)]:
+        direct = (w.grid_w * phi[p] * phi[rr]) @ k @ (w.grid_w * phi[q] * phi[s])
+        isdf = (C[p] * C[rr]) @ u3 @ (C[q] * C[s])
+        assert abs(isdf - direct) < 1e-8 * abs(direct)
+
+
+# ---------------------------------------------------------------- xTC
+
+def _pre_isdf_du(w, phi, n_occ, jas):
+    """Delta U of Eqs. deltaU-four / deltaU-fields / deltaU-preisdf, by
+    direct grid sums (no ISDF)."""
+    n, n_g = phi.shape
+    gw = w.grid_w
+    K = jastrow.kernels(w.grid_xyz, w.grid_xyz, jas, np.arange(n_g), np.arange(n_g))[:3]
+    gamma = np.zeros((n, n))
+    gamma[np.arange(n_occ), np.arange(n_occ)] = 1.0
+    rho = phi[:, None, :] * phi[None, :, :]                       # [a, b, g]
+    rho_g = np.einsum("tu,tug->g", gamma, rho)
+    beta = np.einsum("ut,tsg->usg", gamma, rho)
+    A = np.einsum("abh,cgh->abgc", rho * gw, K)                   # sum_g' w rho K(g,g')
+    Ag = np.einsum("h,cgh->gc", rho_g * gw, K)
+    B = np.einsum("ush,cgh->usgc", beta * gw, K)
+    T1 = 2 * np.einsum("g,prg,gc,qsgc->pqrs", gw, rho, Ag, A)
+    T2 = -np.einsum("g,prg,usgc,qugc->pqrs", gw, rho, B, A)
+    T3 = -np.einsum("g,prgc,usg,qugc->pqrs", gw, A, beta, A) \
+         - np.einsum("g,prgc,usgc,qug->pqrs", gw, A, B, rho)
+    T4 = np.einsum("g,g,prgc,qsgc->pqrs", gw, rho_g, A, A)
+    T = T1 + T2 + T3 + T4
+    return -(T + np.transpose(T, (1, 0, 3, 2)))
+
+
+def test_xtc_full_rank_equals_pre_isdf(tiny):
+    w, phi, dphi = tiny
+    n = w.n_orb
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    P = res.piv_s
+    xi, _, _ = fit.fit(phi, dphi, P, channels=(0,))
+    calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, w.jastrow)
+    phiP = xtc.pivot_factors(phi, P)
+    n_occ = 1
+    _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, n_occ))
+    X = xtc.x_projector(w.grid_w, xi, calG, phiP, n_occ)
+    idx = np.arange(n)
+    dU = energies.du_tensor(D, X, phiP, idx)
+    ref = _pre_isdf_du(w, phi, n_occ, w.jastrow)
+    assert np.max(np.abs(dU - ref)) < 1e-7 * np.max(np.abs(ref))
+
+
+def test_projector_equals_dense_and_symmetry(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 30)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, w.jastrow)
+    phiP = xtc.pivot_factors(phi, res.pivots)
+    phiP = phiP[:, :8]
+    X2, X3 = xtc.x_dense(w.grid_w, xi, calG, phiP, w.n_occ)
+    Xp = xtc.x_projector(w.grid_w, xi, calG, phiP, w.n_occ)
+    ref = X2 + X3
+    assert np.linalg.norm(Xp - ref) < 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(Xp - np.transpose(Xp, (1, 0, 2)))) < 1e-12 * np.max(np.abs(Xp))
+    D4, D1, _ = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, w.n_occ))
+    assert np.max(np.abs(D4 - D4.T)) < 1e-12 * np.max(np.abs(D4))
+
+
+def test_particle_exchange(h6):
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 30)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    W, calG = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, w.jastrow)
+    phiP = xtc.pivot_factors(phi, res.pivots)
+    dphiP = [dphi[c][:, res.pivots].T for c in range(3)]
+    idx = np.arange(5)
+    K = energies.k_tensor(W, phiP, dphiP, idx)
+    assert np.max(np.abs(K - np.transpose(K, (1, 0, 3, 2)))) < 1e-12 * np.max(np.abs(K))
+    # K is not Hermitian in the pair-block sense (Sec. IV.A)
+    assert np.max(np.abs(K - np.transpose(K, (2, 3, 0, 1)))) > 1e-6 * np.max(np.abs(K))
