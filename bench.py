@@ -1,0 +1,373 @@
+"""Benchmark of the ISDF-xTC kernel path on B300 (one JSON line on stdout).
+
+Workload (default): linear H50 chain at 1.8 bohr, 550 seeded random s/p/d
+contracted Gaussians -> 400 orbitals, Becke grid 50 x 40 x 50 = 100,000
+points, N_mu = 2000, radial e-e Jastrow u = r/(2(1+r)).  A step is one pass
+of the whole path: orbitals -> pivoted-Cholesky points -> ISDF fit -> W
+kernels (u1x, u1y, u1z, u3) -> xTC D and occupied X -> test energies, with
+the inputs resident on the device.
+
+value = algorithmic W-build flops (8 N_mu N_g^2 + 8 N_mu^2 N_g) / device time
+of the W build inside each step (CUDA events on the launching stream);
+ms_per_step is the whole step.  e2e repeats the step through the public
+Python API from pinned host inputs with the copies inside the timed region.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the W build for a slice of outer grid points).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "W_munu build TFLOP/s (algorithmic 8 N_mu N_g^2 + 8 N_mu^2 N_g), tensor-core vs FP64 GPU"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x6", choices=["bf16x3", "bf16x6"])
+    ap.add_argument("--workload", default="h50_chain")
+    ap.add_argument("--fp64-rows", type=int, default=1024,
+                    help="outer grid points of the FP64 GPU comparison slice")
+    ap.add_argument("--cpu-rows", type=int, default=64,
+                    help="outer grid points of the CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--w-only", action="store_true",
+                    help="profiling mode: time only the W build on an H50-chain grid with "
+                         "--w-nrad radial shells and seeded random xi (N_mu = --w-nmu)")
+    ap.add_argument("--w-nrad", type=int, default=16)
+    ap.add_argument("--w-nmu", type=int, default=1024)
+    return ap.parse_args()
+
+
+def w_flops(n_mu, n_rows, n_g):
+    """Algorithmic flops of the W build over n_rows outer points."""
+    return 8.0 * n_mu * n_rows * n_g + 8.0 * n_mu * n_mu * n_rows
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    from synth import workloads as wl
+    fn = {"h50_chain": wl.h50_chain, "h6_chain": wl.h6_chain}[name]
+    return fn()
+
+
+def cpu_sample(wlw, rows, xi, xit):
+    """FP64 oracle W build for `rows` outer points (all inner points)."""
+    from oracle import wbuild
+    t0 = time.perf_counter()
+    g_rows = np.arange(rows)
+    calG = wbuild.stage1(wlw.grid_xyz, wlw.grid_w, xi, wlw.jastrow, g_rows=g_rows, batch=16)
+    wbuild.stage2(wlw.grid_w, xi, xit, calG, g_rows=g_rows)
+    dt = time.perf_counter() - t0
+    return dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wlw = make_workload(args.workload)
+    # inputs of the workload's shape (the oracle's cost does not depend on
+    # the values); each step is the W build for a slice of outer points
+    rng = np.random.default_rng(0)
+    n_mu, n_g = wlw.n_mu, wlw.n_g
+    xi = rng.standard_normal((n_mu, n_g)) * 1e-3
+    xit = rng.standard_normal((3, n_mu, n_g)) * 1e-3
+    times = []
+    cpu_sample(wlw, 4, xi, xit)
+    for _ in range(args.steps):
+        times.append(cpu_sample(wlw, args.cpu_rows, xi, xit))
+    dt = statistics.mean(times)
+    val = w_flops(n_mu, args.cpu_rows, n_g) / dt / 1e12
+    unit = "TFLOP/s"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": unit,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_g": n_g, "n_mu": n_mu,
+                       "n_orb": wlw.n_orb, "sample_outer_points": args.cpu_rows},
+            "cpu_baseline": {"value": val, "unit": unit, "cores": host_cores(), "kind": "oracle",
+                             "sample": f"W build (stages 1+2) for {args.cpu_rows} of {n_g} outer "
+                                       f"grid points, all {n_g} inner points, N_mu={n_mu}; "
+                                       f"random xi of the workload's shape"},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_w_only(args):
+    """The W build alone on a reduced grid (for kernel profiles)."""
+    import torch
+    from synth import workloads as wl
+    from paper_2607_17314_b300 import api, build
+    build.build()
+    _, xyz = wl.h_chain(50, 1.8)
+    grid, w = wl.becke_grid(xyz, args.w_nrad, 50)
+    n_g, n_mu = grid.shape[0], args.w_nmu
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234)
+    g = torch.tensor(grid, device="cuda")
+    wt = torch.tensor(w, device="cuda")
+    xi = torch.randn((n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    xig = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    kb = api.KernelBuilder(g, wt, xi, xig, api.jastrow_from(wl.radial_jastrow(xyz)),
+                           args.precision, time_stages=True)
+    for _ in range(max(args.warmup, 1)):
+        kb()
+    s1, s2 = [], []
+    for _ in range(args.steps):
+        kb()
+        s1.append(kb.stage_ms[0]); s2.append(kb.stage_ms[1])
+    fl1 = 8.0 * n_mu * n_g * n_g
+    print(json.dumps({"mode": "w_only", "n_g": n_g, "n_mu": n_mu, "precision": args.precision,
+                      "s1_ms": s1, "s2_ms": s2,
+                      "s1_alg_tflops": fl1 / (min(s1) * 1e-3) / 1e12}), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.w_only:
+        return run_w_only(args)
+
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2607_17314_b300 import api, build, pipeline
+    build.build()
+    wlw = make_workload(args.workload)
+    b = wlw.basis
+    J = api.jastrow_from(wlw.jastrow)
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
+                          wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
+    n_g, n_mu = wlw.n_g, wlw.n_mu
+    stream = torch.cuda.current_stream()
+
+    def step(events=None, stage_ms=None):
+        return pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms)
+
+    for _ in range(max(args.warmup, 0)):
+        out = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    events = {}
+    stage_ms = []
+    launches0 = api.kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            out = step(events, stage_ms)
+        t_end.record(stream)
+        barrier()
+    launches = api.kernel_launches() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+
+    def stage(name):
+        ev = events.get(name, [])
+        return [ev[i].elapsed_time(ev[i + 1]) for i in range(0, len(ev), 2)]
+
+    stages = {k: statistics.mean(stage(k)) for k in ("a1", "a2", "a3", "a4", "a5", "a6")}
+    a4_ms = stages["a4"]
+    ms_step = total_ms / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([a4_ms, ms_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a4_ms, ms_step = float(t[0]), float(t[1])
+    flops = w_flops(n_mu, n_g, n_g)
+    value = world * flops / (a4_ms * 1e-3) / 1e12
+
+    # dominant kernel: stage-1 tcgen05 contraction (device time from events
+    # recorded by the library on the launching stream)
+    s1_ms = statistics.mean(x[0] for x in stage_ms)
+    s2_ms = statistics.mean(x[1] for x in stage_ms)
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    s1_tflops = 8.0 * n_mu * n_g * n_g / (s1_ms * 1e-3) / 1e12
+    products = 3 if args.precision == "bf16x3" else 6
+    roofline = {"bound": "tensor", "achieved": s1_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": s1_tflops / peak, "traffic": None,
+                "pipe_frac": s1_tflops * products / peak,
+                "kernel": f"s1_tc_kernel ({args.precision}: {products} BF16 products per algorithmic MAC)",
+                "peak_kind": f"{peak_kind} bf16 sustained"}
+
+    # FP64 GPU path on an outer-grid slice (same inner sum), and accuracy of
+    # the tensor-core W over that slice against it
+    rows = min(args.fp64_rows, n_g)
+    xi, xig = out["xi"], out["xig"]
+    ms64 = []
+    kb64 = api.KernelBuilder(inp.grid, inp.w, xi, xig, J, "fp64", 0, rows)
+    kb64()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); kb64(); e1.record(stream); torch.cuda.synchronize()
+        ms64.append(e0.elapsed_time(e1))
+    fp64_tflops = w_flops(n_mu, rows, n_g) / (min(ms64) * 1e-3) / 1e12
+    kbt = api.KernelBuilder(inp.grid, inp.w, xi, xig, J, args.precision, 0, rows)
+    kbt()
+    errs = [float(torch.linalg.norm(kbt.W[c] - kb64.W[c]) / torch.linalg.norm(kb64.W[c]))
+            for c in range(4)]
+    del kbt, kb64
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = [np.ascontiguousarray(a) for a in (b.center, b.powers, b.exps, b.coefs,
+                                                  wlw.mo_coef, wlw.grid_xyz, wlw.grid_w)]
+        pinned = [torch.as_tensor(a).pin_memory() for a in host]
+        h2d = sum(t.numel() * t.element_size() for t in pinned)
+        W_host = torch.empty((4, n_mu, n_mu), dtype=torch.float64).pin_memory()
+        d2h = W_host.numel() * 8 + 3 * 8
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            dev = [t.to("cuda", non_blocking=True) for t in pinned]
+            inp2 = pipeline.Inputs(dev[0], dev[1].to(torch.int32), dev[2], dev[3], dev[4], dev[5],
+                                   dev[6], n_mu, wlw.n_occ, J)
+            o2 = pipeline.run(inp2, precision=args.precision)
+            W_host.copy_(o2["W"], non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        xi_h = out["xi"].cpu().numpy()
+        xit_h = out["xig"].cpu().numpy()
+        cpu_sample(wlw, 4, xi_h, xit_h)
+        dt = cpu_sample(wlw, args.cpu_rows, xi_h, xit_h)
+        cpu = {"value": w_flops(n_mu, args.cpu_rows, n_g) / dt / 1e12, "unit": "TFLOP/s",
+               "cores": host_cores(), "kind": "oracle",
+               "sample": f"FP64 oracle W build (stages 1+2) for {args.cpu_rows} of {n_g} outer grid "
+                         f"points x all {n_g} inner points, N_mu={n_mu}, {dt:.1f} s"}
+
+    if rank == 0:
+        E = out["E"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "n_g": n_g, "n_mu": n_mu, "n_orb": wlw.n_orb,
+                       "n_occ": wlw.n_occ, "jastrow": "radial u=r/(2(1+r))",
+                       "precision": args.precision, "l2": "inputs larger than L2 (w xi limbs "
+                       f"{3 * 2 * n_mu * n_g / 1e9:.2f} GB)", "parallelism": f"replicas{world}",
+                       "value_basis": "W build (stage 1 + stage 2 + operand prep) inside each full-path step"},
+            "stages_ms": stages, "w_build_ms": a4_ms, "s1_ms": s1_ms, "s2_ms": s2_ms,
+            "fp64_gpu": {"tflops": fp64_tflops, "slice_outer_points": rows,
+                         "speedup_tc_over_fp64": value / fp64_tflops,
+                         "w_rel_err_tc_vs_fp64": errs},
+            "energies_ha": {"E_K": E[0], "E_dU": E[1], "E0": E[2]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * isdftc -- C ABI of the B300 (sm_103a) ISDF-xTC kernel library.
+ *
+ * The library builds the ISDF-compressed transcorrelated two-body kernels of
+ * "Interpolative Separable Density-Fitting for Transcorrelated Hamiltonians"
+ * (Liao, Cheng, Dobrautz, Zhu, Alavi): orbitals on a molecular grid,
+ * pivoted-Cholesky interpolation points, the least-squares auxiliary fit,
+ * the Jastrow kernels u^(1),c and u^(3), and the xTC density contraction.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, dense and
+ *     row-major in the layout stated per argument; nothing is freed or
+ *     retained by the library.  Small parameter structs are host memory and
+ *     are copied by value during the call.
+ *   - The library allocates no device memory.  Each call that needs scratch
+ *     takes a caller workspace (ws, ws_bytes, 256-byte aligned); the matching
+ *     *_workspace() function returns the bytes needed.  A too-small workspace
+ *     is ISDF_E_ARG.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ *     Calls that report a host-side result (n_mu_out, jitter, energies) or
+ *     that check the device error word synchronise `stream` before
+ *     returning; this is stated per call.
+ *   - Every call returns an isdf_status; isdf_last_error() gives a message
+ *     for the last failure on the calling thread.
+ *   - One device (the current one); no host fallback exists.
+ */
+#ifndef ISDFTC_H
+#define ISDFTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* isdf_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  ISDF_OK = 0,
+  ISDF_E_ARG = 1,        /* invalid argument, size or workspace */
+  ISDF_E_NOT_PD = 2,     /* Gram Cholesky failed after the last jitter retry */
+  ISDF_E_RANK = 3,       /* numerical rank exhausted before n_mu points (informational) */
+  ISDF_E_NONFINITE = 4,  /* NaN/Inf detected in an input or result */
+  ISDF_E_TIMEOUT = 5,    /* a bounded device wait expired; the kernel returned early */
+  ISDF_E_CUDA = 6,       /* CUDA runtime error */
+  ISDF_E_UNSUPPORTED = 7 /* option combination not implemented */
+} isdf_status;
+
+typedef enum {
+  ISDF_PREC_FP64 = 0,   /* FP64 on CUDA cores (the FP64 GPU path) */
+  ISDF_PREC_BF16X3 = 1, /* tcgen05 BF16, 2-limb split (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  ISDF_PREC_BF16X6 = 2  /* tcgen05 BF16, 3-limb split (6 products), FP32 accumulation */
+} isdf_precision;
+
+/* Contracted Cartesian Gaussian basis (device arrays).  Function f is
+ *   chi_f(r) = sum_k coefs[f][k] (x-X_f)^a (y-Y_f)^b (z-Z_f)^c exp(-exps[f][k] |r-R_f|^2)
+ * with (a,b,c) = powers[f]. */
+typedef struct {
+  int32_t n_bf;
+  int32_t n_prim;
+  const double* center;  /* [n_bf][3] bohr */
+  const int32_t* powers; /* [n_bf][3] */
+  const double* exps;    /* [n_bf][n_prim] */
+  const double* coefs;   /* [n_bf][n_prim], normalisation folded in */
+} isdf_basis;
+
+#define ISDF_MAX_NUC 64
+#define ISDF_MAX_TYPES 4
+#define ISDF_MAX_TERMS 32
+
+/* Boys-Handy correlator (Sec. II.B, Eqs. bh-scaled and bh-u):
+ *   u(i,j) = sum_I sum_k coef[type(I)][k] [A_iI^m A_jI^n + A_jI^m A_iI^n] E_ij^o
+ *            + cusp * E_ij / (2 d)
+ * with A_iI = b_I r_iI / (1 + b_I r_iI), E_ij = d r_ij / (1 + d r_ij) and
+ * (m,n,o) = mno[k].  The cusp line is the cusp-normalised (0,0,1) term
+ * (slope du/dr_ij -> 1/2).  n_terms = 0 with cusp = 1 is the radial
+ * electron-electron correlator u(r) = r / (2 (1 + d r)).  Host struct. */
+typedef struct {
+  int32_t n_nuc;
+  int32_t n_types;
+  int32_t n_terms;
+  int32_t cusp;
+  double d;
+  double nuc_xyz[ISDF_MAX_NUC][3];
+  int32_t nuc_type[ISDF_MAX_NUC];
+  double b[ISDF_MAX_TYPES];
+  int32_t mno[ISDF_MAX_TERMS][3];
+  double coef[ISDF_MAX_TYPES][ISDF_MAX_TERMS];
+} isdf_jastrow;
+
+/* Options of the kernel build (host struct; NULL = defaults). */
+typedef struct {
+  int32_t precision;  /* isdf_precision; default ISDF_PREC_BF16X3 */
+  int32_t kchunk;     /* inner-grid points accumulated in FP32 tensor memory before
+                         each FP64 flush in stage 1; 0 = default (16384) */
+  int32_t s2_kchunk;  /* same for stage 2; 0 = default (16384) */
+  int32_t sync_check; /* 1 (default): synchronise the stream on return and report
+                         device-side errors (timeouts, non-finite values) */
+  int32_t debug_flags;/* bit 0: the stage-1 producer skips its first arrival, so
+                         the consumer's bounded wait expires (fault-path test) */
+  float* stage_ms;    /* host [2] or NULL: when set (with sync_check), the device
+                         times of stage 1 and stage 2, measured with CUDA events
+                         on `stream` around the two kernels */
+} isdf_options;
+
+const char* isdf_last_error(void);
+int isdf_abi_version(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a diagnostic counter; host side, monotone). */
+uint64_t isdf_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * Orbitals and gradients on the grid (Alg. 2 step 2).
+ *   phi[p][g]     = sum_f mo_coef[f][p] chi_f(r_g)
+ *   dphi[c][p][g] = sum_f mo_coef[f][p] d_c chi_f(r_g)
+ * mo_coef [n_bf][n_orb]; grid_xyz [n_g][3]; phi [n_orb][n_g];
+ * dphi [3][n_orb][n_g].  FP64.  Asynchronous. */
+size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g);
+int isdf_eval_orbitals(const isdf_basis* basis, const double* mo_coef, int n_orb,
+                       const double* grid_xyz, int64_t n_g, double* phi, double* dphi,
+                       void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Interpolation points by weighted pivoted Cholesky (Alg. 1; gradient branch
+ * and pivot fusion of Sec. II.D; matrix-free form of Sec. IV.B).
+ *   scalar   S(g,h) = (w_g w_h) (sum_p phi_p(g) phi_p(h))^2
+ *   gradient S(g,h) = (w_g w_h) (sum_p phi_p(g) phi_p(h)) (sum_{c,p} dphi_cp(g) dphi_cp(h))
+ * FP64 with every sum accumulated by fused multiply-add in a fixed order
+ * (p ascending; c outer), argmax ties broken by the lowest grid index, and
+ * d_g* = 0 after each step, so the indices are reproducible bit for bit.
+ * mode 0 = fused: alternate scalar / gradient steps (scalar first), append
+ *          each new point, stop at n_mu points;
+ * mode 1 = scalar channel only; mode 2 = gradient channel only.
+ * A channel stops when its pivot d_g* <= 64 eps max_g d_g(initial).
+ * pivots [n_mu] int32 (append order) receives *n_mu_out entries.  Returns
+ * ISDF_E_RANK (with *n_mu_out < n_mu) when both channels stopped early.
+ * Synchronises `stream`. */
+size_t isdf_points_workspace(int64_t n_g, int n_mu);
+int isdf_points(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                int n_orb, int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws,
+                size_t ws_bytes, isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Least-squares ISDF fit (Eq. isdf-rho and the normal equations of Sec. II.D).
+ *   G[mu][g] = sum_p phi_p(r_mu) phi_p(r_g)
+ *   scalar:     (G_PP o G_PP) xi = G o G
+ *   gradient c: (dG^c_PP o G_PP) xi~^c = dG^c o G,  dG^c[mu][g] = sum_p d_c phi_p(r_mu) d_c phi_p(r_g)
+ * FP64 Cholesky with adaptive Tikhonov retry (Sec. IV.B): lambda = 0, then
+ * 1e-14 max(diag) times 10 per retry, at most 8 retries; the lambda used per
+ * system is written to jitter_used (host [4], may be NULL).
+ * pivots [n_mu]; xi [n_mu][n_g]; xi_grad [3][n_mu][n_g].  Synchronises
+ * `stream`; ISDF_E_NOT_PD if a system stays indefinite. */
+size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu);
+int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+             const int32_t* pivots, int n_mu, double* xi, double* xi_grad,
+             double* jitter_used, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Jastrow kernels of the ISDF K integrals (Eqs. K1-isdf and K3-isdf):
+ *   W[c][mu][nu] = sum_{g in [g_begin,g_end)} sum_{g'} w_g w_g' xi~^c_mu(g) xi_nu(g') K_c(g,g')  c = x,y,z
+ *   W[3][mu][nu] = sum_{g in [g_begin,g_end)} sum_{g'} w_g w_g' xi_mu(g)   xi_nu(g') K_sq(g,g')
+ * with K_c = d u / d r_{g,c} (electron 1 at r_g) and K_sq = sum_c K_c^2, both
+ * generated on the fly; the self pair g = g' contributes 0.  Computed as
+ *   calG[c][nu][g - g_begin] = sum_g' w_g' xi_nu(g') K_c(g,g')   (calG of Sec. III.B)
+ *   W[c] = (w xi~^c) calG[c]^T, W[3] = (w xi) calG[3]^T   over the slice.
+ * The outer-grid slice [g_begin, g_end) gives additive partial kernels.
+ * grid_xyz [n_g][3]; w [n_g]; xi [n_mu][n_g]; xi_grad [3][n_mu][n_g];
+ * W [4][n_mu][n_mu] FP64 (overwritten); calG [4][n_mu][g_end-g_begin] FP64
+ * (overwritten; required).  The tensor-core precisions take the radial
+ * correlator (n_terms = 0) only; ISDF_PREC_FP64 takes any correlator.
+ * Synchronises `stream` when options->sync_check (default). */
+size_t tc_kernel_build_workspace(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
+                                 int precision);
+int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
+                    const double* xi_grad, int64_t n_g, int n_mu, int64_t g_begin,
+                    int64_t g_end, const isdf_jastrow* jas, const isdf_options* options,
+                    double* W, double* calG, void* ws, size_t ws_bytes,
+                    isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * xTC density contraction, Terms 1 and 4 (Sec. III.B, Eq. delta-u-dx-kernels):
+ *   G_nu  = sum_{i < n_occ} phi_i(r_nu)^2          (closed-shell HF projector)
+ *   w~_g  = w_g sum_l G_l xi_l(g)
+ *   D4    = sum_g w~_g sum_c calG^c_mu calG^c_nu
+ *   H_gc  = sum_l G_l calG^c_{l g},  V_{nu g} = sum_c H_gc calG^c_{nu g}
+ *   D1    = sum_g w_g xi_mu(g) V_{nu g},   D = D4 + 2 D1
+ * and, when X_packed is not NULL, Terms 2 and 3 in the low-rank projector
+ * form with the occupied fields A^s_{a,g,c} = sum_nu C^a_s(nu) calG^c_{nu g}
+ * and rho~^s_a(g) = sum_nu C^a_s(nu) xi_nu(g):
+ *   X_{qs mu} = sum_g w_g [ xi_mu(g) sum_{a,c} A^s_{a,c} A^q_{a,c}
+ *                          + sum_c calG^c_{mu g} sum_a (rho~^s_a A^q_{a,c} + A^s_{a,c} rho~^q_a) ]
+ *   for q <= s < n_orb_x, packed row s(s+1)/2 + q.
+ * phi_piv [n_mu][n_orb] = phi_p(r_mu); xi [n_mu][n_g]; w [n_g];
+ * calG [>=3][n_mu][n_g] FP64; D [n_mu][n_mu] FP64;
+ * X_packed [n_orb_x (n_orb_x + 1) / 2][n_mu] FP64 or NULL.  FP64.
+ * Asynchronous. */
+size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ,
+                                      int n_orb_x);
+int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const double* xi,
+                         const double* w, const double* calG, int64_t n_g, int n_mu,
+                         double* D, double* X_packed, int n_orb_x, void* ws,
+                         size_t ws_bytes, isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Closed-shell test energies from the factors (Eqs. K-recombine-final,
+ * xtc-deltah, xtc-const), occupied block only:
+ *   K = 1/2 P12 [K1 - K1swap + K3],  DeltaU = -P12 [C D C - C X]
+ *   out[0] = E_K  = sum_{ij} (2 K^{ij}_{ij} - K^{ij}_{ji})
+ *   out[1] = E_dU = sum_{ij} (2 DeltaU^{ij}_{ij} - DeltaU^{ij}_{ji})
+ *   out[2] = E0   = -2/3 sum_i Delta h_ii   (without nuclear repulsion)
+ * W [4][n_mu][n_mu]; D [n_mu][n_mu]; X_packed as above with n_orb_x >= n_occ;
+ * phi_piv [n_mu][n_orb]; dphi_piv [3][n_mu][n_orb]; out host [3].  FP64.
+ * Synchronises `stream`. */
+size_t tc_energies_workspace(int n_mu, int n_occ);
+int tc_energies(const double* W, const double* D, const double* X_packed,
+                const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
+                int n_occ, double* out, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* Gather phi_p(r_mu) and d_c phi_p(r_mu): phi_piv [n_mu][n_orb],
+ * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL).  Asynchronous. */
+int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+                       const int32_t* pivots, int n_mu, double* phi_piv, double* dphi_piv,
+                       isdf_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISDFTC_H */

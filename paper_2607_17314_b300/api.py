@@ -1,0 +1,217 @@
+"""Python front end of libisdftc with the C ABI's names.
+
+Each function takes CUDA tensors, allocates the outputs and the workspace
+with torch (device memory only), and calls the matching C entry point on the
+current torch stream.  There is no host or fallback implementation: on a
+machine without the built library or without a GPU these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import torch
+
+from . import _capi as C
+
+f64 = torch.float64
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _req(t: torch.Tensor, dtype, name: str):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def jastrow_struct(nuc_xyz, nuc_type, mno, coef, b, d: float, cusp: bool = True) -> C.IsdfJastrow:
+    """Fill the host isdf_jastrow struct from arrays (see include/isdftc.h)."""
+    import numpy as np
+    J = C.IsdfJastrow()
+    nuc_xyz = np.asarray(nuc_xyz, dtype=np.float64).reshape(-1, 3)
+    mno = np.asarray(mno, dtype=np.int32).reshape(-1, 3)
+    coef = np.asarray(coef, dtype=np.float64).reshape(len(np.atleast_1d(b)), -1)
+    b = np.atleast_1d(np.asarray(b, dtype=np.float64))
+    if nuc_xyz.shape[0] > C.ISDF_MAX_NUC or mno.shape[0] > C.ISDF_MAX_TERMS or b.shape[0] > C.ISDF_MAX_TYPES:
+        raise ValueError("Jastrow exceeds the library limits")
+    J.n_nuc, J.n_types, J.n_terms, J.cusp, J.d = nuc_xyz.shape[0], b.shape[0], mno.shape[0], int(cusp), float(d)
+    for I in range(nuc_xyz.shape[0]):
+        for c in range(3):
+            J.nuc_xyz[I][c] = float(nuc_xyz[I, c])
+        J.nuc_type[I] = int(nuc_type[I])
+    for t in range(b.shape[0]):
+        J.b[t] = float(b[t])
+        for k in range(mno.shape[0]):
+            J.coef[t][k] = float(coef[t, k])
+    for k in range(mno.shape[0]):
+        for c in range(3):
+            J.mno[k][c] = int(mno[k, c])
+    return J
+
+
+def jastrow_from(obj) -> C.IsdfJastrow:
+    """isdf_jastrow from any object with nuc_xyz, nuc_type, mno, coef, b, d, cusp."""
+    return jastrow_struct(obj.nuc_xyz, obj.nuc_type, obj.mno, obj.coef, obj.b, obj.d, obj.cusp)
+
+
+def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz) -> Tuple[torch.Tensor, torch.Tensor]:
+    """phi [n_orb][n_g], dphi [3][n_orb][n_g] (Alg. 2 step 2)."""
+    lib = C.load()
+    dev = grid_xyz.device
+    for t, n, dt in ((center, "center", f64), (exps, "exps", f64), (coefs, "coefs", f64),
+                     (mo_coef, "mo_coef", f64), (grid_xyz, "grid_xyz", f64),
+                     (powers, "powers", torch.int32)):
+        _req(t, dt, n)
+    n_bf, n_prim = exps.shape
+    n_orb = mo_coef.shape[1]
+    n_g = grid_xyz.shape[0]
+    basis = C.IsdfBasis(n_bf, n_prim, _ptr(center), _ptr(powers), _ptr(exps), _ptr(coefs))
+    phi = torch.empty((n_orb, n_g), dtype=f64, device=dev)
+    dphi = torch.empty((3, n_orb, n_g), dtype=f64, device=dev)
+    ws = _ws(lib.isdf_eval_orbitals_workspace(n_bf, n_g), dev)
+    C.check("isdf_eval_orbitals", lib.isdf_eval_orbitals(
+        ctypes.byref(basis), _ptr(mo_coef), n_orb, _ptr(grid_xyz), n_g, _ptr(phi), _ptr(dphi),
+        _ptr(ws), ws.numel(), _stream()))
+    return phi, dphi
+
+
+def isdf_points(phi, dphi, w, n_mu: int, mode: int = 0, allow_rank: bool = False):
+    """Interpolation points (Alg. 1 + fusion): int32 tensor of length n_mu_out."""
+    lib = C.load()
+    dev = phi.device
+    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(w, f64, "w")
+    n_orb, n_g = phi.shape
+    piv = torch.empty(n_mu, dtype=torch.int32, device=dev)
+    out = C.INT(0)
+    ws = _ws(lib.isdf_points_workspace(n_g, n_mu), dev)
+    st = lib.isdf_points(_ptr(phi), _ptr(dphi), _ptr(w), n_g, n_orb, n_mu, mode, _ptr(piv),
+                         ctypes.byref(out), _ptr(ws), ws.numel(), _stream())
+    C.check("isdf_points", st, allow=(C.ISDF_E_RANK,) if allow_rank else ())
+    return piv[:out.value]
+
+
+def isdf_fit(phi, dphi, pivots):
+    """xi [n_mu][n_g], xi~ [3][n_mu][n_g] and the jitter per system."""
+    lib = C.load()
+    dev = phi.device
+    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(pivots, torch.int32, "pivots")
+    n_orb, n_g = phi.shape
+    n_mu = pivots.numel()
+    xi = torch.empty((n_mu, n_g), dtype=f64, device=dev)
+    xig = torch.empty((3, n_mu, n_g), dtype=f64, device=dev)
+    jit = (ctypes.c_double * 4)()
+    ws = _ws(lib.isdf_fit_workspace(n_g, n_orb, n_mu), dev)
+    C.check("isdf_fit", lib.isdf_fit(_ptr(phi), _ptr(dphi), n_g, n_orb, _ptr(pivots), n_mu,
+                                     _ptr(xi), _ptr(xig), jit, _ptr(ws), ws.numel(), _stream()))
+    return xi, xig, list(jit)
+
+
+def isdf_gather_pivots(phi, dphi, pivots):
+    lib = C.load()
+    n_orb, n_g = phi.shape
+    n_mu = pivots.numel()
+    phiP = torch.empty((n_mu, n_orb), dtype=f64, device=phi.device)
+    dphiP = torch.empty((3, n_mu, n_orb), dtype=f64, device=phi.device)
+    C.check("isdf_gather_pivots", lib.isdf_gather_pivots(
+        _ptr(phi), _ptr(dphi), n_g, n_orb, _ptr(pivots), n_mu, _ptr(phiP), _ptr(dphiP), _stream()))
+    return phiP, dphiP
+
+
+def options(precision="bf16x3", kchunk: int = 0, s2_kchunk: int = 0, sync_check: bool = True,
+            debug_flags: int = 0, stage_ms=None) -> C.IsdfOptions:
+    prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return C.IsdfOptions(prec, kchunk, s2_kchunk, int(sync_check), debug_flags, stage_ms)
+
+
+class KernelBuilder:
+    """Reusable W-build call: output and workspace tensors are allocated once,
+    so that repeated calls (benchmarks, CUDA graphs) allocate nothing."""
+
+    def __init__(self, grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, precision="bf16x3",
+                 g_begin: int = 0, g_end: Optional[int] = None, kchunk: int = 0,
+                 s2_kchunk: int = 0, sync_check: bool = True, debug_flags: int = 0,
+                 time_stages: bool = False):
+        lib = C.load()
+        for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad")):
+            _req(t, f64, n)
+        self.lib = lib
+        self.dev = xi.device
+        self.n_mu, self.n_g = xi.shape
+        self.g_begin = int(g_begin)
+        self.g_end = int(self.n_g if g_end is None else g_end)
+        self.args = (grid_xyz, w, xi, xig)
+        self.J = jastrow
+        self.stage_ms = (ctypes.c_float * 2)() if time_stages else None
+        self.opt = options(precision, kchunk, s2_kchunk, sync_check, debug_flags,
+                           ctypes.cast(self.stage_ms, ctypes.POINTER(ctypes.c_float))
+                           if time_stages else None)
+        n_gs = self.g_end - self.g_begin
+        self.W = torch.empty((4, self.n_mu, self.n_mu), dtype=f64, device=self.dev)
+        self.calG = torch.empty((4, self.n_mu, n_gs), dtype=f64, device=self.dev)
+        self.ws = _ws(lib.tc_kernel_build_workspace(self.n_g, self.n_mu, self.g_begin, self.g_end,
+                                                   self.opt.precision), self.dev)
+
+    def __call__(self, allow_timeout: bool = False):
+        g, w, xi, xig = self.args
+        st = self.lib.tc_kernel_build(_ptr(g), _ptr(w), _ptr(xi), _ptr(xig), self.n_g, self.n_mu,
+                                      self.g_begin, self.g_end, ctypes.byref(self.J),
+                                      ctypes.byref(self.opt), _ptr(self.W), _ptr(self.calG),
+                                      _ptr(self.ws), self.ws.numel(), _stream())
+        C.check("tc_kernel_build", st, allow=(C.ISDF_E_TIMEOUT,) if allow_timeout else ())
+        return st
+
+
+def tc_kernel_build(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, precision="bf16x3",
+                    g_begin: int = 0, g_end: Optional[int] = None, kchunk: int = 0,
+                    s2_kchunk: int = 0, stage_ms: Optional[list] = None):
+    """W [4][n_mu][n_mu] (u1x, u1y, u1z, u3) and calG [4][n_mu][g_end-g_begin].
+    When ``stage_ms`` is a list, the device times of stage 1 and 2 are
+    appended to it (tensor-core precisions)."""
+    kb = KernelBuilder(grid_xyz, w, xi, xig, jastrow, precision, g_begin, g_end, kchunk, s2_kchunk,
+                       time_stages=stage_ms is not None)
+    kb()
+    if stage_ms is not None:
+        stage_ms.append(tuple(kb.stage_ms))
+    return kb.W, kb.calG
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libisdftc in this process so far."""
+    return int(C.load().isdf_kernel_launches())
+
+
+def xtc_density_contract(phi_piv, n_occ: int, xi, w, calG, n_orb_x: int = 0):
+    """D [n_mu][n_mu] and (n_orb_x > 0) X packed [n_orb_x(n_orb_x+1)/2][n_mu]."""
+    lib = C.load()
+    dev = xi.device
+    n_mu, n_g = xi.shape
+    n_orb = phi_piv.shape[1]
+    D = torch.empty((n_mu, n_mu), dtype=f64, device=dev)
+    Xp = torch.empty((n_orb_x * (n_orb_x + 1) // 2, n_mu), dtype=f64, device=dev) if n_orb_x > 0 else None
+    ws = _ws(lib.xtc_density_contract_workspace(n_g, n_mu, n_orb, n_occ, n_orb_x), dev)
+    C.check("xtc_density_contract", lib.xtc_density_contract(
+        _ptr(phi_piv), n_orb, n_occ, _ptr(xi), _ptr(w), _ptr(calG), n_g, n_mu, _ptr(D), _ptr(Xp),
+        n_orb_x, _ptr(ws), ws.numel(), _stream()))
+    return D, Xp
+
+
+def tc_energies(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
+    """(E_K, E_dU, E0) in Hartree from the factors (occupied block)."""
+    lib = C.load()
+    n_mu, n_orb = phi_piv.shape
+    out = (ctypes.c_double * 3)()
+    ws = _ws(lib.tc_energies_workspace(n_mu, n_occ), W.device)
+    C.check("tc_energies", lib.tc_energies(_ptr(W), _ptr(D), _ptr(Xp), _ptr(phi_piv), _ptr(dphi_piv),
+                                           n_mu, n_orb, n_occ, out, _ptr(ws), ws.numel(), _stream()))
+    return tuple(out)

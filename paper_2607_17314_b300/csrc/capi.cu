@@ -1,0 +1,163 @@
+// extern "C" entry points of libisdftc (declared in include/isdftc.h).
+#include <stdarg.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+namespace isdf {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// implemented in the kernel translation units
+size_t eval_orbitals_ws(int n_bf, int64_t n_g);
+int eval_orbitals(const isdf_basis*, const double*, int, const double*, int64_t, double*, double*,
+                  void*, size_t, cudaStream_t);
+size_t points_ws(int64_t n_g, int n_mu);
+int points(const double*, const double*, const double*, int64_t, int, int, int, int32_t*, int*,
+           void*, size_t, cudaStream_t);
+size_t fit_ws(int64_t, int, int);
+int fit(const double*, const double*, int64_t, int, const int32_t*, int, double*, double*,
+        double*, void*, size_t, cudaStream_t);
+int gather_pivots(const double*, const double*, int64_t, int, const int32_t*, int, double*,
+                  double*, cudaStream_t);
+size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J);
+int wbuild_fp64(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
+                int64_t, const isdf_jastrow&, double*, double*, void*, size_t, cudaStream_t);
+size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int);
+int wbuild_tc(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
+              int64_t, const isdf_jastrow&, const isdf_options&, double*, double*, void*, size_t,
+              cudaStream_t);
+size_t xtc_ws(int64_t, int, int, int, int);
+int xtc(const double*, int, int, const double*, const double*, const double*, int64_t, int,
+        double*, double*, int, void*, size_t, cudaStream_t);
+size_t energies_ws(int, int);
+int energies(const double*, const double*, const double*, const double*, const double*, int, int,
+             int, double*, void*, size_t, cudaStream_t);
+
+static int check_jastrow(const isdf_jastrow* J) {
+  ISDF_ARG(J, "null Jastrow");
+  ISDF_ARG(J->n_nuc >= 0 && J->n_nuc <= ISDF_MAX_NUC, "n_nuc out of range");
+  ISDF_ARG(J->n_types >= 1 && J->n_types <= ISDF_MAX_TYPES, "n_types out of range");
+  ISDF_ARG(J->n_terms >= 0 && J->n_terms <= ISDF_MAX_TERMS, "n_terms out of range");
+  ISDF_ARG(J->d > 0.0, "d must be positive");
+  for (int I = 0; I < J->n_nuc; ++I)
+    ISDF_ARG(J->nuc_type[I] >= 0 && J->nuc_type[I] < J->n_types, "nucleus type out of range");
+  for (int k = 0; k < J->n_terms; ++k)
+    for (int e = 0; e < 3; ++e)
+      ISDF_ARG(J->mno[k][e] >= 0 && J->mno[k][e] <= 8, "exponent out of range");
+  return ISDF_OK;
+}
+
+}  // namespace isdf
+
+using namespace isdf;
+
+extern "C" {
+
+const char* isdf_last_error(void) { return g_err; }
+int isdf_abi_version(void) { return 1; }
+uint64_t isdf_kernel_launches(void) { return g_launches.load(); }
+
+size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g) { return eval_orbitals_ws(n_bf, n_g); }
+
+int isdf_eval_orbitals(const isdf_basis* basis, const double* mo_coef, int n_orb,
+                       const double* grid_xyz, int64_t n_g, double* phi, double* dphi, void* ws,
+                       size_t ws_bytes, isdf_stream_t stream) {
+  return eval_orbitals(basis, mo_coef, n_orb, grid_xyz, n_g, phi, dphi, ws, ws_bytes,
+                       (cudaStream_t)stream);
+}
+
+size_t isdf_points_workspace(int64_t n_g, int n_mu) { return points_ws(n_g, n_mu); }
+
+int isdf_points(const double* phi, const double* dphi, const double* w, int64_t n_g, int n_orb,
+                int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws, size_t ws_bytes,
+                isdf_stream_t stream) {
+  return points(phi, dphi, w, n_g, n_orb, n_mu, mode, pivots, n_mu_out, ws, ws_bytes,
+                (cudaStream_t)stream);
+}
+
+size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu) { return fit_ws(n_g, n_orb, n_mu); }
+
+int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* pivots,
+             int n_mu, double* xi, double* xi_grad, double* jitter_used, void* ws,
+             size_t ws_bytes, isdf_stream_t stream) {
+  return fit(phi, dphi, n_g, n_orb, pivots, n_mu, xi, xi_grad, jitter_used, ws, ws_bytes,
+             (cudaStream_t)stream);
+}
+
+int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+                       const int32_t* pivots, int n_mu, double* phi_piv, double* dphi_piv,
+                       isdf_stream_t stream) {
+  return gather_pivots(phi, dphi, n_g, n_orb, pivots, n_mu, phi_piv, dphi_piv,
+                       (cudaStream_t)stream);
+}
+
+size_t tc_kernel_build_workspace(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
+                                 int precision) {
+  if (precision == ISDF_PREC_FP64) return wbuild_fp64_ws(n_g, nullptr);
+  return wbuild_tc_ws(n_g, n_mu, g_begin, g_end, precision);
+}
+
+int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
+                    const double* xi_grad, int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
+                    const isdf_jastrow* jas, const isdf_options* options, double* W, double* calG,
+                    void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  ISDF_TRY(check_jastrow(jas));
+  ISDF_ARG(grid_xyz && w && xi && xi_grad && W && calG, "null pointer argument");
+  ISDF_ARG(n_g > 0 && n_mu > 0, "empty sizes");
+  ISDF_ARG(g_begin >= 0 && g_begin < g_end && g_end <= n_g, "bad grid slice");
+  ISDF_ARG(n_g < (1ll << 31) - 64, "n_g too large");
+  isdf_options opt = {ISDF_PREC_BF16X3, 0, 0, 1, 0, nullptr};
+  if (options) opt = *options;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (opt.precision == ISDF_PREC_FP64) {
+    int rc = wbuild_fp64(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, W, calG, ws,
+                         ws_bytes, s);
+    if (rc == ISDF_OK && opt.sync_check) ISDF_CUDA(cudaStreamSynchronize(s));
+    return rc;
+  }
+  if (opt.precision != ISDF_PREC_BF16X3 && opt.precision != ISDF_PREC_BF16X6) {
+    set_error("unknown precision %d", opt.precision);
+    return ISDF_E_ARG;
+  }
+  if (jas->n_terms != 0) {
+    set_error("tensor-core precisions take the radial correlator (n_terms = 0) only");
+    return ISDF_E_UNSUPPORTED;
+  }
+  return wbuild_tc(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, opt, W, calG, ws,
+                   ws_bytes, s);
+}
+
+size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x) {
+  return xtc_ws(n_g, n_mu, n_orb, n_occ, n_orb_x);
+}
+
+int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const double* xi,
+                         const double* w, const double* calG, int64_t n_g, int n_mu, double* D,
+                         double* X_packed, int n_orb_x, void* ws, size_t ws_bytes,
+                         isdf_stream_t stream) {
+  return xtc(phi_piv, n_orb, n_occ, xi, w, calG, n_g, n_mu, D, X_packed, n_orb_x, ws, ws_bytes,
+             (cudaStream_t)stream);
+}
+
+size_t tc_energies_workspace(int n_mu, int n_occ) { return energies_ws(n_mu, n_occ); }
+
+int tc_energies(const double* W, const double* D, const double* X_packed, const double* phi_piv,
+                const double* dphi_piv, int n_mu, int n_orb, int n_occ, double* out, void* ws,
+                size_t ws_bytes, isdf_stream_t stream) {
+  return energies(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, n_occ, out, ws, ws_bytes,
+                  (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Least-squares ISDF fit of the auxiliary densities (Eq. isdf-rho and the
+// normal equations of Sec. II.D), FP64 on CUDA cores.
+//
+//   G[mu][g] = sum_p phi_p(r_mu) phi_p(r_g)                        (GEMM)
+//   scalar:     Gram = G_PP o G_PP,        RHS = G o G
+//   gradient c: Gram = dG^c_PP o G_PP,     RHS = dG^c o G
+//   Cholesky of each Gram with the adaptive Tikhonov retry of Sec. IV.B,
+//   then two blocked triangular solves over all grid columns in place.
+#include "linalg.cuh"
+
+namespace isdf {
+namespace {
+
+__global__ void gather_pivots_kernel(const double* __restrict__ src, int64_t n_g, int n_orb,
+                                     const int32_t* __restrict__ piv, int n_mu,
+                                     double* __restrict__ dst, int nplanes) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t per = (int64_t)n_mu * n_orb;
+  if (e >= per * nplanes) return;
+  int c = (int)(e / per);
+  int64_t r = e % per;
+  int mu = (int)(r / n_orb), p = (int)(r % n_orb);
+  dst[e] = src[((int64_t)c * n_orb + p) * n_g + piv[mu]];
+}
+
+// x[i] = a[i] * b[i]
+__global__ void hadamard_kernel(double* __restrict__ x, const double* __restrict__ a,
+                                const double* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = a[i] * b[i];
+}
+
+// rhs_grad[c][i] *= G[i] for c < 3, then G[i] = G[i]^2
+__global__ void rhs_finish_kernel(double* __restrict__ G, double* __restrict__ dG, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double g = G[i];
+  dG[i] *= g;
+  dG[n + i] *= g;
+  dG[2 * n + i] *= g;
+  G[i] = g * g;
+}
+
+__global__ void add_diag_kernel(double* A, const double* S, int n, double lam) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  A[e] = S[e] + (i == j ? lam : 0.0);
+}
+
+__global__ void max_diag_kernel(const double* A, int n, double* out) {
+  __shared__ double sm[256];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, A[(int64_t)i * n + i]);
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t); }
+
+}  // namespace
+
+int gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+                  const int32_t* piv, int n_mu, double* phiP, double* dphiP, cudaStream_t s) {
+  ISDF_ARG(phi && piv && phiP, "null pointer argument");
+  if (n_mu <= 0) return ISDF_OK;
+  int64_t per = (int64_t)n_mu * n_orb;
+  gather_pivots_kernel<<<nblocks(per), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP, 1);
+  ISDF_LAUNCH_CHECK();
+  if (dphi && dphiP) {
+    gather_pivots_kernel<<<nblocks(3 * per), 256, 0, s>>>(dphi, n_g, n_orb, piv, n_mu, dphiP, 3);
+    ISDF_LAUNCH_CHECK();
+  }
+  return ISDF_OK;
+}
+
+size_t fit_ws(int64_t n_g, int n_orb, int n_mu) {
+  (void)n_g;
+  Carve c(nullptr, 0);
+  c.take<double>((size_t)4 * n_mu * n_orb);
+  c.take<double>((size_t)3 * n_mu * n_mu);
+  c.take<double>(2);
+  c.take<int>(1);
+  return c.off;
+}
+
+int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* piv,
+        int n_mu, double* xi, double* xig, double* jitter_used, void* ws, size_t ws_bytes,
+        cudaStream_t s) {
+  ISDF_ARG(phi && dphi && piv && xi && xig, "null pointer argument");
+  ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
+  Carve cv(ws, ws_bytes);
+  double* phiP = cv.take<double>((size_t)n_mu * n_orb);
+  double* dphiP = cv.take<double>((size_t)3 * n_mu * n_orb);
+  double* GPP = cv.take<double>((size_t)n_mu * n_mu);
+  double* Gram = cv.take<double>((size_t)n_mu * n_mu);
+  double* Save = cv.take<double>((size_t)n_mu * n_mu);
+  double* scal = cv.take<double>(2);
+  int* info = cv.take<int>(1);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+
+  ISDF_TRY(gather_pivots(phi, dphi, n_g, n_orb, piv, n_mu, phiP, dphiP, s));
+  const int64_t nn = (int64_t)n_mu * n_mu;
+  const int64_t ng = (int64_t)n_mu * n_g;
+
+  // G_PP
+  Dgemm g;
+  g.M = n_mu; g.N = n_mu; g.K = n_orb;
+  g.A = phiP; g.a_rs = n_orb; g.a_cs = 1; g.a_bs = 0;
+  g.B = phiP; g.b_rs = 1; g.b_cs = n_orb; g.b_bs = 0;
+  g.C = GPP; g.ldc = n_mu; g.c_bs = 0;
+  ISDF_TRY(dgemm(g, s));
+
+  // right-hand sides: G into xi, dG^c into xig, then the Hadamard products
+  Dgemm r;
+  r.M = n_mu; r.N = n_g; r.K = n_orb;
+  r.A = phiP; r.a_rs = n_orb; r.a_cs = 1; r.a_bs = 0;
+  r.B = phi; r.b_rs = n_g; r.b_cs = 1; r.b_bs = 0;
+  r.C = xi; r.ldc = n_g; r.c_bs = 0;
+  ISDF_TRY(dgemm(r, s));
+  r.A = dphiP; r.a_bs = (int64_t)n_mu * n_orb;
+  r.B = dphi; r.b_bs = (int64_t)n_orb * n_g;
+  r.C = xig; r.c_bs = ng; r.batch = 3;
+  ISDF_TRY(dgemm(r, s));
+  rhs_finish_kernel<<<nblocks(ng), 256, 0, s>>>(xi, xig, ng);
+  ISDF_LAUNCH_CHECK();
+
+  for (int ch = 0; ch < 4; ++ch) {
+    if (ch == 0) {
+      hadamard_kernel<<<nblocks(nn), 256, 0, s>>>(Save, GPP, GPP, nn);
+      ISDF_LAUNCH_CHECK();
+    } else {
+      Dgemm q = g;
+      q.A = dphiP + (int64_t)(ch - 1) * n_mu * n_orb;
+      q.B = q.A;
+      q.C = Gram;
+      ISDF_TRY(dgemm(q, s));
+      hadamard_kernel<<<nblocks(nn), 256, 0, s>>>(Save, Gram, GPP, nn);
+      ISDF_LAUNCH_CHECK();
+    }
+    double lam = 0.0;
+    double maxd = 0.0;
+    int tries = 0;
+    for (;;) {
+      add_diag_kernel<<<nblocks(nn), 256, 0, s>>>(Gram, Save, n_mu, lam);
+      ISDF_LAUNCH_CHECK();
+      ISDF_TRY(dpotrf_lower(Gram, n_mu, info, s));
+      int h_info = 0;
+      ISDF_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ISDF_CUDA(cudaStreamSynchronize(s));
+      if (h_info == 0) break;
+      if (tries == 0) {
+        max_diag_kernel<<<1, 256, 0, s>>>(Save, n_mu, scal);
+        ISDF_LAUNCH_CHECK();
+        ISDF_CUDA(cudaMemcpyAsync(&maxd, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ISDF_CUDA(cudaStreamSynchronize(s));
+        lam = 1e-14 * maxd;
+      } else {
+        lam *= 10.0;
+      }
+      if (++tries > 8) {
+        set_error("Gram matrix %d not positive definite after %d jitter retries", ch, 8);
+        return ISDF_E_NOT_PD;
+      }
+    }
+    if (jitter_used) jitter_used[ch] = lam;
+    double* rhs = ch == 0 ? xi : xig + (int64_t)(ch - 1) * ng;
+    ISDF_TRY(dpotrs_lower(Gram, n_mu, rhs, n_g, n_g, s));
+  }
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  return ISDF_OK;
+}
+
+}  // namespace isdf

@@ -1,0 +1,283 @@
+// Interpolation-point selection by weighted pivoted Cholesky (Alg. 1, the
+// gradient branch and the pivot fusion of Sec. II.D), matrix-free as in
+// Sec. IV.B: each step generates one column S(., g*) from the orbitals at the
+// pivot and all grid points, subtracts the previous Cholesky columns and
+// updates the residual diagonal.
+//
+// One kernel launch per fused step; one thread per grid point.  Every sum is
+// a chain of correctly rounded fused multiply-adds in a fixed order and the
+// argmax takes the lowest index on ties, so the selected indices do not
+// depend on the launch configuration.  The step state (union size, turn,
+// per-channel counts and stop flags) and the argmax partials are double
+// buffered so that no block reads what another block of the same launch
+// writes.
+#include "common.cuh"
+
+namespace isdf {
+namespace {
+
+constexpr int PT = 256;
+
+struct PivState {
+  int nu;      // union size
+  int turn;    // 0 = scalar next, 1 = gradient next
+  int k[2];    // columns per channel
+  int done[2]; // channel stopped
+};
+
+struct PivArgs {
+  const double* phi;   // [n_orb][n_g]
+  const double* dphi;  // [3][n_orb][n_g]
+  const double* w;     // [n_g]
+  int64_t n_g;
+  int n_orb;
+  int n_mu;
+  int cap;
+  double* d;           // [2][n_g]
+  double* L;           // [2][cap][n_g]
+  double* part_v;      // [2 ch][2 buf][nblk]
+  int* part_i;         // [2 ch][2 buf][nblk]
+  int nblk;
+  PivState* st;        // [2]
+  double* tol;         // [2]
+  unsigned char* in_union;  // [n_g]
+  int* union_piv;      // [n_mu]
+};
+
+__device__ __forceinline__ void better(double& bv, int& bi, double v, int i) {
+  if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+
+// Block-wide (max, lowest index) reduction; result valid in thread 0.
+__device__ void block_argmax(double& v, int& i) {
+  __shared__ double sv[PT / 32];
+  __shared__ int si[PT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_down_sync(0xffffffffu, v, o);
+    int oi = __shfl_down_sync(0xffffffffu, i, o);
+    better(v, i, ov, oi);
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sv[w] = v; si[w] = i; }
+  __syncthreads();
+  if (w == 0) {
+    v = l < PT / 32 ? sv[l] : -1.0;
+    i = l < PT / 32 ? si[l] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, v, o);
+      int oi = __shfl_down_sync(0xffffffffu, i, o);
+      better(v, i, ov, oi);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(PT) diag_init_kernel(PivArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * PT + threadIdx.x;
+  double d0 = -1.0, d1 = -1.0;
+  if (g < a.n_g) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int p = 0; p < a.n_orb; ++p) {
+      double v = a.phi[(int64_t)p * a.n_g + g];
+      t1 = __fma_rn(v, v, t1);
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int p = 0; p < a.n_orb; ++p) {
+        double v = a.dphi[((int64_t)c * a.n_orb + p) * a.n_g + g];
+        t2 = __fma_rn(v, v, t2);
+      }
+    double ww = __dmul_rn(a.w[g], a.w[g]);
+    d0 = __dmul_rn(ww, __dmul_rn(t1, t1));
+    d1 = __dmul_rn(ww, __dmul_rn(t1, t2));
+    a.d[g] = d0;
+    a.d[a.n_g + g] = d1;
+  }
+  int i0 = g < a.n_g ? (int)g : 0x7fffffff, i1 = i0;
+  block_argmax(d0, i0);
+  block_argmax(d1, i1);
+  if (threadIdx.x == 0) {
+    // channel c, buffer 0
+    a.part_v[(0 * 2 + 0) * a.nblk + blockIdx.x] = d0;
+    a.part_i[(0 * 2 + 0) * a.nblk + blockIdx.x] = i0;
+    a.part_v[(1 * 2 + 0) * a.nblk + blockIdx.x] = d1;
+    a.part_i[(1 * 2 + 0) * a.nblk + blockIdx.x] = i1;
+  }
+}
+
+// Reduce the partials of channel c / buffer b to (max, argmax) in every thread.
+__device__ void reduce_partials(const PivArgs& a, int c, int b, double& bv, int& bi) {
+  bv = -1.0;
+  bi = 0x7fffffff;
+  const double* pv = a.part_v + (c * 2 + b) * a.nblk;
+  const int* pi = a.part_i + (c * 2 + b) * a.nblk;
+  for (int j = threadIdx.x; j < a.nblk; j += PT) better(bv, bi, pv[j], pi[j]);
+  block_argmax(bv, bi);
+  __shared__ double rv;
+  __shared__ int ri;
+  if (threadIdx.x == 0) { rv = bv; ri = bi; }
+  __syncthreads();
+  bv = rv;
+  bi = ri;
+}
+
+__global__ void __launch_bounds__(PT) tol_init_kernel(PivArgs a) {
+  for (int c = 0; c < 2; ++c) {
+    double v;
+    int i;
+    reduce_partials(a, c, 0, v, i);
+    if (threadIdx.x == 0) a.tol[c] = 64.0 * 2.220446049250313e-16 * v;
+  }
+  if (threadIdx.x == 0) {
+    PivState s0 = {0, 0, {0, 0}, {0, 0}};
+    a.st[0] = s0;
+    a.st[1] = s0;
+  }
+}
+
+__global__ void __launch_bounds__(PT) pivot_step_kernel(PivArgs a, int parity, int mode) {
+  const PivState s = a.st[parity];
+  PivState ns = s;
+  bool active = s.nu < a.n_mu && !(s.done[0] && s.done[1]);
+  int c = s.turn;
+  if (active && s.done[c]) c = 1 - c;
+  if (mode == 1) c = 0;
+  if (mode == 2) c = 1;
+  double dgs = 0.0;
+  int gs = 0;
+  if (active) {
+    reduce_partials(a, c, s.k[c] & 1, dgs, gs);
+    if (s.k[c] >= a.cap || !(dgs > a.tol[c])) {
+      ns.done[c] = 1;
+      if (mode != 0) ns.done[1 - c] = 1;
+      ns.turn = 1 - s.turn;
+      active = false;
+    }
+  }
+  if (!active) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st[1 - parity] = ns;
+    return;
+  }
+  const int k = s.k[c];
+  const int64_t n_g = a.n_g;
+  const int64_t g = (int64_t)blockIdx.x * PT + threadIdx.x;
+  double* dc = a.d + c * n_g;
+  const double* Lc = a.L + (int64_t)c * a.cap * n_g;
+  double nd = -1.0;
+  int ni = 0x7fffffff;
+  if (g < n_g) {
+    double t1 = 0.0;
+    for (int p = 0; p < a.n_orb; ++p) {
+      const double* row = a.phi + (int64_t)p * n_g;
+      t1 = __fma_rn(row[g], row[gs], t1);
+    }
+    double sgh;
+    const double wgw = __dmul_rn(a.w[g], a.w[gs]);
+    if (c == 1) {
+      double t2 = 0.0;
+      for (int cc = 0; cc < 3; ++cc)
+        for (int p = 0; p < a.n_orb; ++p) {
+          const double* row = a.dphi + ((int64_t)cc * a.n_orb + p) * n_g;
+          t2 = __fma_rn(row[g], row[gs], t2);
+        }
+      sgh = __dmul_rn(wgw, __dmul_rn(t1, t2));
+    } else {
+      sgh = __dmul_rn(wgw, __dmul_rn(t1, t1));
+    }
+    for (int l = 0; l < k; ++l) {
+      const double* Ll = Lc + (int64_t)l * n_g;
+      sgh = __fma_rn(-Ll[g], Ll[gs], sgh);
+    }
+    const double v = __ddiv_rn(sgh, __dsqrt_rn(dgs));
+    a.L[((int64_t)c * a.cap + k) * n_g + g] = v;
+    double x = __fma_rn(-v, v, dc[g]);
+    x = x > 0.0 ? x : 0.0;
+    if (g == gs) x = 0.0;
+    dc[g] = x;
+    nd = x;
+    ni = (int)g;
+  }
+  block_argmax(nd, ni);
+  if (threadIdx.x == 0) {
+    const int b = (k + 1) & 1;
+    a.part_v[(c * 2 + b) * a.nblk + blockIdx.x] = nd;
+    a.part_i[(c * 2 + b) * a.nblk + blockIdx.x] = ni;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ns.k[c] = k + 1;
+    if (!a.in_union[gs]) {
+      a.in_union[gs] = 1;
+      a.union_piv[s.nu] = gs;
+      ns.nu = s.nu + 1;
+    }
+    ns.turn = 1 - s.turn;
+    a.st[1 - parity] = ns;
+  }
+}
+
+}  // namespace
+
+size_t points_ws(int64_t n_g, int n_mu) {
+  Carve c(nullptr, 0);
+  int nblk = (int)ceil_div(n_g, PT);
+  c.take<double>(2 * (size_t)n_g);
+  c.take<double>(2 * (size_t)n_mu * n_g);
+  c.take<double>(4 * (size_t)nblk);
+  c.take<int>(4 * (size_t)nblk);
+  c.take<PivState>(2);
+  c.take<double>(2);
+  c.take<unsigned char>(n_g);
+  c.take<int>(n_mu);
+  return c.off;
+}
+
+int points(const double* phi, const double* dphi, const double* w, int64_t n_g, int n_orb,
+           int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws, size_t ws_bytes,
+           cudaStream_t s) {
+  ISDF_ARG(phi && dphi && w && pivots && n_mu_out, "null pointer argument");
+  ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
+  ISDF_ARG(n_g < 0x7fffffff, "n_g must fit in int32");
+  ISDF_ARG(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
+  PivArgs a;
+  a.phi = phi; a.dphi = dphi; a.w = w; a.n_g = n_g; a.n_orb = n_orb; a.n_mu = n_mu;
+  a.cap = n_mu;
+  a.nblk = (int)ceil_div(n_g, PT);
+  Carve cv(ws, ws_bytes);
+  a.d = cv.take<double>(2 * (size_t)n_g);
+  a.L = cv.take<double>(2 * (size_t)n_mu * n_g);
+  a.part_v = cv.take<double>(4 * (size_t)a.nblk);
+  a.part_i = cv.take<int>(4 * (size_t)a.nblk);
+  a.st = cv.take<PivState>(2);
+  a.tol = cv.take<double>(2);
+  a.in_union = cv.take<unsigned char>(n_g);
+  a.union_piv = cv.take<int>(n_mu);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  ISDF_CUDA(cudaMemsetAsync(a.in_union, 0, n_g, s));
+  diag_init_kernel<<<a.nblk, PT, 0, s>>>(a);
+  ISDF_LAUNCH_CHECK();
+  tol_init_kernel<<<1, PT, 0, s>>>(a);
+  ISDF_LAUNCH_CHECK();
+  const int max_iter = 2 * n_mu + 4;
+  PivState h;
+  int it = 0;
+  for (;;) {
+    const int batch = 32;
+    for (int b = 0; b < batch && it < max_iter; ++b, ++it) {
+      pivot_step_kernel<<<a.nblk, PT, 0, s>>>(a, it & 1, mode);
+      ISDF_LAUNCH_CHECK();
+    }
+    ISDF_CUDA(cudaMemcpyAsync(&h, a.st + (it & 1), sizeof(PivState), cudaMemcpyDeviceToHost, s));
+    ISDF_CUDA(cudaStreamSynchronize(s));
+    if (h.nu >= n_mu || (h.done[0] && h.done[1]) || it >= max_iter) break;
+  }
+  *n_mu_out = h.nu;
+  if (h.nu > 0)
+    ISDF_CUDA(cudaMemcpyAsync(pivots, a.union_piv, sizeof(int) * h.nu, cudaMemcpyDeviceToDevice, s));
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  if (h.nu < n_mu) {
+    set_error("rank exhausted: %d of %d points", h.nu, n_mu);
+    return ISDF_E_RANK;
+  }
+  return ISDF_OK;
+}
+
+}  // namespace isdf

@@ -1,0 +1,729 @@
+// Jastrow kernels u^(1),c and u^(3) (Eqs. K1-isdf, K3-isdf) on the
+// 5th-generation tensor cores (tcgen05) of sm_103a, with split-BF16 operands
+// and FP32 accumulation in tensor memory, flushed to FP64 every kchunk
+// inner-grid points.
+//
+// Stage 1 (the O(N_mu N_g^2) contraction, Sec. IV.C doubly-blocked grid sum):
+//   calG^c[nu][g] = sum_g' (w xi)[nu][g'] K_c(g, g'),  c = x, y, z, sq
+// as a GEMM D[nu][g] = A[nu][g'] B[g][g'] whose B operand is never stored:
+// eight generator warps evaluate K_c(g, g') for a 128 x 32 (g x g') block in
+// FP32 registers, split each value into BF16 limbs and write them straight
+// into the 64B-swizzled K-major shared-memory layout that the tensor core
+// reads.  A TMA warp streams the (w xi) limbs, one thread issues tcgen05.mma
+// into four 128-column FP32 accumulators in tensor memory (one per channel),
+// and the generator warps drain the accumulators into FP64 after each chunk.
+//
+// Stage 2: W^c = (w xi~^c) calG^c^T as a split-BF16 tcgen05 GEMM with both
+// operands streamed by TMA, split-K over the grid with FP64 atomic reduction.
+//
+// A value v is carried as limbs v = l0 + l1 (+ l2), each l_i = bf16(v - sum_{j<i} l_j);
+// a product uses every limb pair (i, j) with i + j < LIMBS (3 products for 2
+// limbs, 6 for 3 limbs).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "linalg.cuh"
+#include "tc_ptx.cuh"
+
+namespace isdf {
+
+// ------------------------------------------------------------------ host: TMA maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map over a bf16 matrix [rows][cols] (cols contiguous) with a box of
+// 32 columns x box_rows rows and the 64-byte swizzle.
+static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return ISDF_E_CUDA;
+  }
+  ISDF_ARG(((uintptr_t)base & 15) == 0 && (cols * 2) % 16 == 0, "TMA base/stride alignment");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ISDF_E_CUDA;
+  }
+  return ISDF_OK;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ prep kernels
+
+// dst[l][r][c] (rows_pad x cols_pad per limb) = limb l of
+// src[r * src_rs + c0 + c] * colw[c0 + c]; zero outside rows x cols.
+__global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int64_t c0,
+                             const double* __restrict__ colw, int64_t rows, int64_t cols,
+                             int64_t rows_pad, int64_t cols_pad, int limbs,
+                             __nv_bfloat16* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t plane = rows_pad * cols_pad;
+  if (e >= plane) return;
+  int64_t r = e / cols_pad, c = e % cols_pad;
+  double v = 0.0;
+  if (r < rows && c < cols) {
+    v = src[r * src_rs + c0 + c];
+    if (colw) v *= colw[c0 + c];
+  }
+  for (int l = 0; l < limbs; ++l) {
+    __nv_bfloat16 h = __double2bfloat16(v);
+    dst[l * plane + e] = h;
+    v -= (double)__bfloat162float(h);
+  }
+}
+
+__global__ void coords_kernel(const double* __restrict__ grid, int64_t n_g, int64_t n_pad,
+                              float4* __restrict__ hi, float4* __restrict__ lo) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_pad) return;
+  double x = 0, y = 0, z = 0;
+  if (g < n_g) { x = grid[3 * g]; y = grid[3 * g + 1]; z = grid[3 * g + 2]; }
+  float xh = (float)x, yh = (float)y, zh = (float)z;
+  hi[g] = make_float4(xh, yh, zh, 0.f);
+  lo[g] = make_float4((float)(x - xh), (float)(y - yh), (float)(z - zh), 0.f);
+}
+
+// ------------------------------------------------------------------ stage 1
+
+template <int LIMBS, int BN>
+struct S1C {
+  static constexpr int BM = 128, BK = 32;
+  static constexpr int STAGES = LIMBS == 2 ? 2 : 3;
+  static constexpr uint32_t A_LIMB = BM * BK * 2;
+  static constexpr uint32_t B_TILE = BN * BK * 2;
+  static constexpr uint32_t A_BYTES = LIMBS * A_LIMB;
+  static constexpr uint32_t B_BYTES = 4 * LIMBS * B_TILE;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t TMEM_COLS = 4 * BN;
+  static constexpr int NGW = 8;
+  static constexpr int THREADS = 64 + 32 * NGW;
+  static constexpr int COLS = BN * BK / (32 * NGW);  // inner points per generator thread
+  static constexpr uint32_t SMEM = STAGES * STAGE + 1024 + 256;
+  static_assert(COLS % 8 == 0, "generator writes whole 16-byte chunks");
+  static_assert(STAGE % 1024 == 0, "stage alignment");
+};
+
+struct S1Params {
+  const float4* xyz_hi;  // [n_k] inner points (padded)
+  const float4* xyz_lo;
+  int64_t n_g;           // real points
+  int64_t n_k;           // padded inner extent (multiple of 32)
+  int n_mu;
+  int n_mu_tiles;
+  int64_t g_begin, g_end;
+  int64_t n_g_tiles;
+  int64_t kchunk;        // multiple of 32
+  float d;
+  double* calG;          // [4][n_mu][g_end - g_begin]
+  int* err;
+  int debug;
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <int LIMBS>
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t (&out)[LIMBS]) {
+#pragma unroll
+  for (int l = 0; l < LIMBS; ++l) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t w = *reinterpret_cast<uint32_t*>(&h);
+    out[l] = w;
+    a -= __uint_as_float(w << 16);
+    b -= __uint_as_float(w & 0xffff0000u);
+  }
+}
+
+// Radial correlator: K_c = u'(r)/r (r_g - r_g')_c with u' = 1/(2 (1 + d r)^2),
+// K_sq = u'^2.  Coordinates as FP32 hi + lo pairs so that close pairs keep
+// their relative accuracy.
+__device__ __forceinline__ void radial_pair(float4 gh, float4 gl, float4 ph, float4 pl, float d,
+                                            bool zero, float& kx, float& ky, float& kz,
+                                            float& ksq) {
+  float dx = (gh.x - ph.x) + (gl.x - pl.x);
+  float dy = (gh.y - ph.y) + (gl.y - pl.y);
+  float dz = (gh.z - ph.z) + (gl.z - pl.z);
+  float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1e-30f);
+  float rinv = rsqrtf(r2);
+  float r = r2 * rinv;
+  float iden = rcp_approx(fmaf(d, r, 1.0f));
+  float up = 0.5f * iden * iden;
+  float f = zero ? 0.0f : up * rinv;
+  kx = f * dx;
+  ky = f * dy;
+  kz = f * dz;
+  ksq = zero ? 0.0f : up * up;
+}
+
+template <int LIMBS, int BN>
+__global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
+    s1_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                 const __grid_constant__ CUtensorMap mA2, const S1Params p) {
+  using C = S1C<LIMBS, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      tc::mbar_init(&full[s], C::NGW + 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, C::NGW);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t n_gs = p.g_end - p.g_begin;
+  const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
+  const int64_t n_chunks = (p.n_k + p.kchunk - 1) / p.kchunk;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch_desc(&mA0);
+      if (LIMBS > 1) tc::tma_prefetch_desc(&mA1);
+      if (LIMBS > 2) tc::tma_prefetch_desc(&mA2);
+      uint32_t it = 0;
+      bool skip = (p.debug & 1) != 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
+        for (int64_t ch = 0; ch < n_chunks; ++ch) {
+          const int64_t kb = ch * p.kchunk;
+          const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
+          for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
+            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+            if (skip) {  // fault-path test: never arm this stage
+              skip = false;
+              continue;
+            }
+            tc::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
+            uint8_t* a = smem + s * C::STAGE;
+            tc::tma_load_2d(a, &mA0, &full[s], (int32_t)k0, mu0);
+            if (LIMBS > 1) tc::tma_load_2d(a + C::A_LIMB, &mA1, &full[s], (int32_t)k0, mu0);
+            if (LIMBS > 2) tc::tma_load_2d(a + 2 * C::A_LIMB, &mA2, &full[s], (int32_t)k0, mu0);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(128, BN, 1);
+      uint32_t it = 0, u = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+          const int64_t kb = ch * p.kchunk;
+          const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
+          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto mma_drain;
+          tc::tc_fence_after();
+          for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
+            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto mma_drain;
+            tc::tc_fence_after();
+            const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE);
+            const uint32_t b_base = a_base + C::A_BYTES;
+            const bool first = (k0 == kb);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int i = 0; i < LIMBS; ++i)
+#pragma unroll
+                for (int j = 0; j < LIMBS - i; ++j)
+#pragma unroll
+                  for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
+                    const uint64_t bd =
+                        tc::smem_desc(b_base + (c * LIMBS + j) * C::B_TILE + kk * 32, 16, 512, 4);
+                    const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                    tc::umma_f16(tmem + c * BN, ad, bd, idesc, acc);
+                  }
+            tc::umma_commit(&empty[s]);
+          }
+          tc::umma_commit(acc_full);
+        }
+      }
+    mma_drain:;
+    }
+  } else {
+    // generator + epilogue warps
+    const int gw = warp - 2;
+    const int gt = threadIdx.x - 64;
+    const int row = gt % BN;
+    const int col0 = (gt / BN) * C::COLS;
+    const float d = p.d;
+    uint32_t it = 0, u = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int64_t g_tile = tile % p.n_g_tiles;
+      const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
+      const int64_t gl = g_tile * BN + row;
+      const bool gvalid = gl < n_gs;
+      const int64_t g = p.g_begin + (gvalid ? gl : 0);
+      const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+        const int64_t kb = ch * p.kchunk;
+        const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
+        for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
+          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+          uint8_t* bsm = smem + s * C::STAGE + C::A_BYTES;
+#pragma unroll
+          for (int q = 0; q < C::COLS / 8; ++q) {
+            const int kc = col0 + q * 8;
+            uint32_t pk[4][LIMBS][4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              float kv[2][4];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int64_t gp = k0 + kc + e + h;
+                const float4 ph4 = p.xyz_hi[gp];
+                const float4 pl4 = p.xyz_lo[gp];
+                const bool zero = !gvalid || gp >= p.n_g || gp == g;
+                radial_pair(gh, glo, ph4, pl4, d, zero, kv[h][0], kv[h][1], kv[h][2], kv[h][3]);
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                uint32_t w[LIMBS];
+                split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+                for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+              }
+            }
+            const uint32_t off = tc::sw64_offset(row, kc >> 3);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int l = 0; l < LIMBS; ++l) {
+                uint4 v = make_uint4(pk[c][l][0], pk[c][l][1], pk[c][l][2], pk[c][l][3]);
+                *reinterpret_cast<uint4*>(bsm + (c * LIMBS + l) * C::B_TILE + off) = v;
+              }
+          }
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&full[s]);
+        }
+        // epilogue: drain the four accumulators of this chunk into FP64
+        if (!tc::mbar_wait(acc_full, u & 1, abort_flag, p.err)) goto done;
+        tc::tc_fence_after();
+        {
+          const int quad = warp & 3;
+          const int half = gw >> 2;
+          const int mu = mu0 + 32 * quad + lane;
+          const bool first = (ch == 0);
+#pragma unroll 1
+          for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
+#pragma unroll 1
+            for (int blk = 0; blk < BN / 32; ++blk) {
+              uint32_t r[32];
+              tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * quad) << 16) + cc * BN + blk * 32, r);
+              tc::tmem_ld_wait();
+              if (mu < p.n_mu) {
+                double* dst = p.calG + ((int64_t)cc * p.n_mu + mu) * n_gs;
+                const int64_t gbase = g_tile * BN + blk * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int64_t gg = gbase + j;
+                  if (gg < n_gs) {
+                    const double v = (double)__uint_as_float(r[j]);
+                    dst[gg] = first ? v : dst[gg] + v;
+                  }
+                }
+              }
+            }
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(acc_empty);
+      }
+    }
+  }
+done:
+  __syncthreads();
+  if (*abort_flag) {
+    // a bounded wait expired: give issued TMA copies and MMAs time to land
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------ generic split GEMM
+
+// out[z][m][n] += scale * sum_k A_z[m][k] B_z[n][k] over the K chunk of this
+// CTA, A_z and B_z in limbs.  One CTA per (n tile, m tile, k chunk, z).
+constexpr int GB_MAXB = 4;
+
+struct GemmMaps {
+  CUtensorMap a[GB_MAXB][3];
+  CUtensorMap b[GB_MAXB][3];
+};
+
+struct GemmParams {
+  int64_t M, N;           // real output extents
+  int64_t k_tiles;        // padded K / 32
+  int64_t kchunk_tiles;   // k tiles per CTA
+  int m_tiles, n_tiles, kchunks, batch;
+  double* out;            // [batch][M][ldo] (or a single [M][ldo] when out_bs = 0)
+  int64_t ldo, out_bs;
+  double scale;
+  int* err;
+};
+
+template <int LIMBS>
+struct GC {
+  static constexpr int BM = 128, BN = 128, BK = 32, STAGES = 4;
+  static constexpr uint32_t TILE = 128 * BK * 2;
+  static constexpr uint32_t STAGE = 2 * LIMBS * TILE;
+  static constexpr int THREADS = 192;
+  static constexpr uint32_t SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int LIMBS>
+__global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
+    splitgemm_kernel(const __grid_constant__ GemmMaps maps, const GemmParams p) {
+  using C = GC<LIMBS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  int64_t unit = blockIdx.x;
+  const int nt = (int)(unit % p.n_tiles); unit /= p.n_tiles;
+  const int mt = (int)(unit % p.m_tiles); unit /= p.m_tiles;
+  const int kc = (int)(unit % p.kchunks); unit /= p.kchunks;
+  const int z = (int)unit;
+  const int64_t kt0 = (int64_t)kc * p.kchunk_tiles;
+  const int64_t kt1 = kt0 + p.kchunk_tiles < p.k_tiles ? kt0 + p.kchunk_tiles : p.k_tiles;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, 128);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int m0 = mt * C::BM, n0 = nt * C::BN;
+
+  if (kt1 > kt0) {
+    if (warp == 0) {
+      if (lane == 0) {
+        uint32_t it = 0;
+        for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
+          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) break;
+          tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
+          uint8_t* base = smem + s * C::STAGE;
+          const int32_t x = (int32_t)(kt * C::BK);
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l) {
+            tc::tma_load_2d(base + l * C::TILE, &maps.a[z][l], &full[s], x, m0);
+            tc::tma_load_2d(base + (LIMBS + l) * C::TILE, &maps.b[z][l], &full[s], x, n0);
+          }
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_f16(128, 128, 1);
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
+          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+          if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t base = tc::smem_u32(smem + s * C::STAGE);
+#pragma unroll
+          for (int i = 0; i < LIMBS; ++i)
+#pragma unroll
+            for (int j = 0; j < LIMBS - i; ++j)
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = tc::smem_desc(base + i * C::TILE + kk * 32, 16, 512, 4);
+                const uint64_t bd = tc::smem_desc(base + (LIMBS + j) * C::TILE + kk * 32, 16, 512, 4);
+                const uint32_t acc = (kt == kt0 && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                tc::umma_f16(tmem, ad, bd, idesc, acc);
+              }
+          tc::umma_commit(&empty[s]);
+        }
+        (void)ok;
+        tc::umma_commit(acc_full);
+      }
+    } else {
+      // epilogue warps 2..5: lanes 32*(warp%4) .. +31
+      if (tc::mbar_wait(acc_full, 0, abort_flag, p.err)) {
+        tc::tc_fence_after();
+        const int quad = warp & 3;
+        const int64_t m = m0 + 32 * quad + lane;
+        double* dst = p.out + (int64_t)z * p.out_bs + m * p.ldo;
+#pragma unroll 1
+        for (int blk = 0; blk < 4; ++blk) {
+          uint32_t r[32];
+          tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * quad) << 16) + blk * 32, r);
+          tc::tmem_ld_wait();
+          if (m < p.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = n0 + blk * 32 + j;
+              if (n < p.N) atomicAdd(dst + n, p.scale * (double)__uint_as_float(r[j]));
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host drivers
+
+// Split an FP64 row-major block into BF16 limbs [limbs][rows_pad][cols_pad].
+int split_operand(const double* src, int64_t src_rs, int64_t c0, const double* colw, int64_t rows,
+                  int64_t cols, int64_t rows_pad, int64_t cols_pad, int limbs, void* dst,
+                  cudaStream_t s) {
+  split_kernel<<<nb256(rows_pad * cols_pad), 256, 0, s>>>(src, src_rs, c0, colw, rows, cols,
+                                                        rows_pad, cols_pad, limbs,
+                                                        (__nv_bfloat16*)dst);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+// Split GEMM over `batch` pairs of limb operands (A_z [Mp][Kp], B_z [Np][Kp]),
+// accumulating scale * A_z B_z^T into out (+ z * out_bs).  out must be
+// initialised by the caller.
+int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, int64_t M,
+              int64_t N, int64_t Kp, int64_t kchunk, double* out, int64_t ldo, int64_t out_bs,
+              double scale, int* err, cudaStream_t s) {
+  ISDF_ARG(batch >= 1 && batch <= GB_MAXB, "splitgemm batch out of range");
+  ISDF_ARG(limbs == 2 || limbs == 3, "limbs must be 2 or 3");
+  ISDF_ARG(Kp % 32 == 0 && kchunk % 32 == 0 && kchunk > 0, "K padding");
+  const int64_t Mp = round_up(M, 128), Np = round_up(N, 128);
+  GemmMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  for (int z = 0; z < batch; ++z)
+    for (int l = 0; l < limbs; ++l) {
+      ISDF_TRY(make_map(&maps.a[z][l], (const char*)A[z] + (size_t)l * Mp * Kp * 2, Mp, Kp, 128));
+      ISDF_TRY(make_map(&maps.b[z][l], (const char*)B[z] + (size_t)l * Np * Kp * 2, Np, Kp, 128));
+    }
+  GemmParams p;
+  p.M = M; p.N = N;
+  p.k_tiles = Kp / 32;
+  p.kchunk_tiles = kchunk / 32;
+  p.m_tiles = (int)(Mp / 128);
+  p.n_tiles = (int)(Np / 128);
+  p.kchunks = (int)ceil_div(p.k_tiles, p.kchunk_tiles);
+  p.batch = batch;
+  p.out = out; p.ldo = ldo; p.out_bs = out_bs; p.scale = scale; p.err = err;
+  int64_t units = (int64_t)p.m_tiles * p.n_tiles * p.kchunks * batch;
+  ISDF_ARG(units < (1ll << 31), "too many GEMM work units");
+  if (limbs == 2) {
+    ISDF_CUDA(cudaFuncSetAttribute(splitgemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GC<2>::SMEM));
+    splitgemm_kernel<2><<<(unsigned)units, GC<2>::THREADS, GC<2>::SMEM, s>>>(maps, p);
+  } else {
+    ISDF_CUDA(cudaFuncSetAttribute(splitgemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, GC<3>::SMEM));
+    splitgemm_kernel<3><<<(unsigned)units, GC<3>::THREADS, GC<3>::SMEM, s>>>(maps, p);
+  }
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+struct TcLayout {
+  int limbs, bn;
+  int64_t n_k, mu_pad, gs, gs_pad;
+};
+
+static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
+  TcLayout L;
+  L.limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  L.bn = L.limbs == 2 ? 128 : 64;
+  L.n_k = round_up(n_g, 32);
+  L.mu_pad = round_up(n_mu, 128);
+  L.gs = g_end - g_begin;
+  L.gs_pad = round_up(L.gs, 32);
+  return L;
+}
+
+size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
+  TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, precision);
+  Carve c(nullptr, 0);
+  c.take<int>(64);
+  c.take<float4>(L.n_k);
+  c.take<float4>(L.n_k);
+  c.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);           // S1 A
+  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
+  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
+  return c.off;
+}
+
+int wbuild_tc(const double* grid, const double* w, const double* xi, const double* xig,
+              int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, const isdf_jastrow& J,
+              const isdf_options& opt, double* W, double* calG, void* ws, size_t ws_bytes,
+              cudaStream_t s) {
+  ISDF_ARG(J.n_terms == 0 && J.cusp, "tensor-core path takes the radial correlator only");
+  const TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, opt.precision);
+  Carve cv(ws, ws_bytes);
+  int* err = cv.take<int>(64);
+  float4* hi = cv.take<float4>(L.n_k);
+  float4* lo = cv.take<float4>(L.n_k);
+  uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);
+  uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
+  uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  ISDF_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
+
+  int64_t kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : 16384;
+  int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 16384;
+
+  // operands of stage 1
+  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo);
+  ISDF_LAUNCH_CHECK();
+  ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad, L.n_k, L.limbs, A1, s));
+  CUtensorMap mA[3];
+  memset(mA, 0, sizeof(mA));
+  for (int l = 0; l < L.limbs; ++l)
+    ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad * L.n_k, L.mu_pad, L.n_k, 128));
+
+  S1Params p;
+  p.xyz_hi = hi; p.xyz_lo = lo;
+  p.n_g = n_g; p.n_k = L.n_k; p.n_mu = n_mu;
+  p.n_mu_tiles = (int)(L.mu_pad / 128);
+  p.g_begin = g_begin; p.g_end = g_end;
+  p.n_g_tiles = ceil_div(L.gs, L.bn);
+  p.kchunk = kchunk;
+  p.d = (float)J.d;
+  p.calG = calG;
+  p.err = err;
+  p.debug = opt.debug_flags;
+  int dev = 0, nsm = 148;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
+  const unsigned grid1 = (unsigned)(n_tiles < nsm ? n_tiles : nsm);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  const bool timed = opt.stage_ms != nullptr && opt.sync_check;
+  if (timed) {
+    for (int i = 0; i < 4; ++i) ISDF_CUDA(cudaEventCreate(&ev[i]));
+    ISDF_CUDA(cudaEventRecord(ev[0], s));
+  }
+  if (L.limbs == 2) {
+    using C = S1C<2, 128>;
+    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    s1_tc_kernel<2, 128><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+  } else {
+    using C = S1C<3, 64>;
+    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    s1_tc_kernel<3, 64><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+  }
+  ISDF_LAUNCH_CHECK();
+  if (timed) ISDF_CUDA(cudaEventRecord(ev[1], s));
+
+  // operands of stage 2: (w xi~^c) and (w xi) over the slice; calG limbs
+  const size_t plane = (size_t)L.limbs * L.mu_pad * L.gs_pad;
+  const void* Ap[4];
+  const void* Bp[4];
+  for (int c = 0; c < 4; ++c) {
+    const double* src = c < 3 ? xig + (int64_t)c * n_mu * n_g : xi;
+    ISDF_TRY(split_operand(src, n_g, g_begin, w, n_mu, L.gs, L.mu_pad, L.gs_pad, L.limbs,
+                           A2 + c * plane, s));
+    ISDF_TRY(split_operand(calG + (int64_t)c * n_mu * L.gs, L.gs, 0, nullptr, n_mu, L.gs,
+                           L.mu_pad, L.gs_pad, L.limbs, B2 + c * plane, s));
+    Ap[c] = A2 + c * plane;
+    Bp[c] = B2 + c * plane;
+  }
+  ISDF_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 4 * (size_t)n_mu * n_mu, s));
+  if (timed) ISDF_CUDA(cudaEventRecord(ev[2], s));
+  ISDF_TRY(splitgemm(L.limbs, 4, Ap, Bp, n_mu, n_mu, L.gs_pad, kchunk2, W, n_mu,
+                     (int64_t)n_mu * n_mu, 1.0, err, s));
+  if (timed) ISDF_CUDA(cudaEventRecord(ev[3], s));
+  if (opt.sync_check) {
+    int h_err = 0;
+    ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ISDF_CUDA(cudaStreamSynchronize(s));
+    if (timed) {
+      ISDF_CUDA(cudaEventElapsedTime(&opt.stage_ms[0], ev[0], ev[1]));
+      ISDF_CUDA(cudaEventElapsedTime(&opt.stage_ms[1], ev[2], ev[3]));
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    }
+    if (h_err & DEV_ERR_TIMEOUT) {
+      set_error("tensor-core pipeline wait expired (device error word 0x%x)", h_err);
+      return ISDF_E_TIMEOUT;
+    }
+  }
+  return ISDF_OK;
+}
+
+}  // namespace isdf

@@ -1,0 +1,205 @@
+// xTC density contraction of the three-body term (Sec. III.B) in FP64.
+//
+// Terms 1 and 4 (factorisable):
+//   G_nu = sum_{i<n_occ} phi_i(r_nu)^2,  w~_g = w_g sum_l G_l xi_l(g)
+//   D4 = sum_c (calG^c o w~) calG^c^T,   H_gc = sum_l G_l calG^c_{l g}
+//   V_{nu g} = sum_c H_gc calG^c_{nu g}, D1 = (w xi) V^T,  D = D4 + 2 D1
+// Terms 2 and 3 in the low-rank projector form (occupied columns of the HF
+// projector), streamed over grid batches:
+//   A^s_{a,c}(g) = sum_nu C^a_s(nu) calG^c_{nu g},  rho~^s_a(g) = sum_nu C^a_s(nu) xi_nu(g)
+//   Q1_{qs}(g)   = sum_{a,c} A^s_{a,c} A^q_{a,c}
+//   Q2^c_{qs}(g) = sum_a (rho~^s_a A^q_{a,c} + A^s_{a,c} rho~^q_a)
+//   X_{qs mu}    = sum_g w_g [ xi_mu(g) Q1_{qs}(g) + sum_c calG^c_{mu g} Q2^c_{qs}(g) ]
+// for q <= s < n_orb_x, packed row s(s+1)/2 + q (the X_{qs} = X_{sq}
+// symmetry of Sec. IV.C).
+#include "linalg.cuh"
+
+namespace isdf {
+namespace {
+
+inline unsigned nb(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t); }
+
+__global__ void gnu_kernel(const double* phiP, int n_mu, int n_orb, int n_occ, double* G) {
+  int nu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (nu >= n_mu) return;
+  double s = 0.0;
+  for (int i = 0; i < n_occ; ++i) {
+    double v = phiP[(int64_t)nu * n_orb + i];
+    s = fma(v, v, s);
+  }
+  G[nu] = s;
+}
+
+// out[q][g] = scale_g * sum_l G_l M[q][l][g]  for q < nplanes (M plane stride n_mu*n_g)
+__global__ void gemv_cols_kernel(const double* G, const double* M, int n_mu, int64_t n_g,
+                                 int nplanes, const double* scale, double* out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nplanes * n_g) return;
+  int q = (int)(e / n_g);
+  int64_t g = e % n_g;
+  const double* m = M + (int64_t)q * n_mu * n_g + g;
+  double s = 0.0;
+  for (int l = 0; l < n_mu; ++l) s = fma(G[l], m[(int64_t)l * n_g], s);
+  out[e] = scale ? scale[g] * s : s;
+}
+
+// V[nu][g] = sum_c H[c][g] calG[c][nu][g]
+__global__ void v_kernel(const double* H, const double* calG, int n_mu, int64_t n_g, double* V) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t plane = (int64_t)n_mu * n_g;
+  if (e >= plane) return;
+  int64_t g = e % n_g;
+  V[e] = H[g] * calG[e] + H[n_g + g] * calG[plane + e] + H[2 * n_g + g] * calG[2 * plane + e];
+}
+
+// P[(a*n_s + s)][nu] = phi_piv[nu][a] phi_piv[nu][s]   (a < n_occ, s < n_s)
+__global__ void pair_factor_kernel(const double* phiP, int n_mu, int n_orb, int n_occ, int n_s,
+                                   double* P) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t tot = (int64_t)n_occ * n_s * n_mu;
+  if (e >= tot) return;
+  int nu = (int)(e % n_mu);
+  int64_t as = e / n_mu;
+  int a = (int)(as / n_s), s = (int)(as % n_s);
+  P[e] = phiP[(int64_t)nu * n_orb + a] * phiP[(int64_t)nu * n_orb + s];
+}
+
+// Q[0][pair][g] = w_g Q1, Q[1+c][pair][g] = w_g Q2^c for the batch columns.
+// F layout: F[f][(a, s)][g] with f = 0 (rho~) and 1..3 (A^c), batch width nbg.
+__global__ void q_kernel(const double* F, int n_occ, int n_s, int64_t nbg, int64_t bw,
+                         const double* w, int64_t g0, double* Q) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npair = (int64_t)n_s * (n_s + 1) / 2;
+  if (e >= npair * bw) return;
+  int64_t pr = e / bw, g = e % bw;
+  int s = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) / 2.0);
+  while ((int64_t)(s + 1) * (s + 2) / 2 <= pr) ++s;
+  while ((int64_t)s * (s + 1) / 2 > pr) --s;
+  int q = (int)(pr - (int64_t)s * (s + 1) / 2);
+  const int64_t fpl = (int64_t)n_occ * n_s * nbg;
+  double q1 = 0.0, q2[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < n_occ; ++a) {
+    const int64_t is = ((int64_t)a * n_s + s) * nbg + g;
+    const int64_t iq = ((int64_t)a * n_s + q) * nbg + g;
+    const double rs = F[is], rq = F[iq];
+    for (int c = 0; c < 3; ++c) {
+      const double As = F[(1 + c) * fpl + is], Aq = F[(1 + c) * fpl + iq];
+      q1 = fma(As, Aq, q1);
+      q2[c] = fma(rs, Aq, fma(As, rq, q2[c]));
+    }
+  }
+  const double wg = w[g0 + g];
+  Q[pr * nbg + g] = wg * q1;
+  for (int c = 0; c < 3; ++c) Q[((1 + c) * npair + pr) * nbg + g] = wg * q2[c];
+}
+
+constexpr int64_t XBATCH = 4096;
+
+}  // namespace
+
+size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x) {
+  (void)n_orb;
+  Carve c(nullptr, 0);
+  c.take<double>(n_mu);
+  c.take<double>(n_g);
+  c.take<double>(3 * n_g);
+  c.take<double>((size_t)n_mu * n_g);
+  if (n_orb_x > 0) {
+    const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
+    const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
+    c.take<double>((size_t)n_occ * n_orb_x * n_mu);
+    c.take<double>((size_t)4 * n_occ * n_orb_x * nbg);
+    c.take<double>((size_t)4 * npair * nbg);
+  }
+  return c.off;
+}
+
+int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double* w,
+        const double* calG, int64_t n_g, int n_mu, double* D, double* Xp, int n_orb_x, void* ws,
+        size_t ws_bytes, cudaStream_t s) {
+  ISDF_ARG(phiP && xi && w && calG && D, "null pointer argument");
+  ISDF_ARG(n_occ >= 0 && n_occ <= n_orb && n_mu > 0 && n_g > 0, "bad sizes");
+  ISDF_ARG(!Xp || (n_orb_x >= 1 && n_orb_x <= n_orb), "n_orb_x out of range");
+  if (!Xp) n_orb_x = 0;
+  Carve cv(ws, ws_bytes);
+  double* G = cv.take<double>(n_mu);
+  double* wt = cv.take<double>(n_g);
+  double* H = cv.take<double>(3 * n_g);
+  double* V = cv.take<double>((size_t)n_mu * n_g);
+  double *P = nullptr, *F = nullptr, *Q = nullptr;
+  const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
+  const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
+  if (n_orb_x > 0) {
+    P = cv.take<double>((size_t)n_occ * n_orb_x * n_mu);
+    F = cv.take<double>((size_t)4 * n_occ * n_orb_x * nbg);
+    Q = cv.take<double>((size_t)4 * npair * nbg);
+  }
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  const int64_t plane = (int64_t)n_mu * n_g;
+
+  gnu_kernel<<<nb(n_mu), 256, 0, s>>>(phiP, n_mu, n_orb, n_occ, G);
+  ISDF_LAUNCH_CHECK();
+  gemv_cols_kernel<<<nb(n_g), 256, 0, s>>>(G, xi, n_mu, n_g, 1, w, wt);
+  ISDF_LAUNCH_CHECK();
+  gemv_cols_kernel<<<nb(3 * n_g), 256, 0, s>>>(G, calG, n_mu, n_g, 3, nullptr, H);
+  ISDF_LAUNCH_CHECK();
+  v_kernel<<<nb(plane), 256, 0, s>>>(H, calG, n_mu, n_g, V);
+  ISDF_LAUNCH_CHECK();
+  // D4 = sum_c (calG^c o w~) calG^c^T
+  for (int c = 0; c < 3; ++c) {
+    Dgemm g;
+    g.M = n_mu; g.N = n_mu; g.K = n_g;
+    g.A = calG + c * plane; g.a_rs = n_g; g.a_cs = 1; g.a_bs = 0;
+    g.B = calG + c * plane; g.b_rs = 1; g.b_cs = n_g; g.b_bs = 0;
+    g.C = D; g.ldc = n_mu; g.c_bs = 0;
+    g.kscale = wt;
+    g.beta = c == 0 ? 0.0 : 1.0;
+    ISDF_TRY(dgemm(g, s));
+  }
+  // D += 2 (w xi) V^T
+  {
+    Dgemm g;
+    g.M = n_mu; g.N = n_mu; g.K = n_g;
+    g.A = xi; g.a_rs = n_g; g.a_cs = 1; g.a_bs = 0;
+    g.B = V; g.b_rs = 1; g.b_cs = n_g; g.b_bs = 0;
+    g.C = D; g.ldc = n_mu; g.c_bs = 0;
+    g.kscale = w;
+    g.alpha = 2.0; g.beta = 1.0;
+    ISDF_TRY(dgemm(g, s));
+  }
+  if (n_orb_x == 0) return ISDF_OK;
+
+  const int64_t nas = (int64_t)n_occ * n_orb_x;
+  pair_factor_kernel<<<nb(nas * n_mu), 256, 0, s>>>(phiP, n_mu, n_orb, n_occ, n_orb_x, P);
+  ISDF_LAUNCH_CHECK();
+  for (int64_t g0 = 0; g0 < n_g; g0 += nbg) {
+    const int64_t bw = g0 + nbg <= n_g ? nbg : n_g - g0;
+    // F[0] = P xi[:, batch], F[1+c] = P calG^c[:, batch]   (row stride nbg)
+    for (int f = 0; f < 4; ++f) {
+      Dgemm g;
+      g.M = nas; g.N = bw; g.K = n_mu;
+      g.A = P; g.a_rs = n_mu; g.a_cs = 1; g.a_bs = 0;
+      g.B = (f == 0 ? xi : calG + (int64_t)(f - 1) * plane) + g0;
+      g.b_rs = n_g; g.b_cs = 1; g.b_bs = 0;
+      g.C = F + (int64_t)f * nas * nbg; g.ldc = nbg; g.c_bs = 0;
+      ISDF_TRY(dgemm(g, s));
+    }
+    const int64_t nq = npair * nbg;
+    q_kernel<<<nb(npair * bw), 256, 0, s>>>(F, n_occ, n_orb_x, nbg, bw, w, g0, Q);
+    ISDF_LAUNCH_CHECK();
+    // X[pair][mu] += sum_f sum_g Q[f][pair][g] M_f[mu][g0 + g]
+    for (int f = 0; f < 4; ++f) {
+      Dgemm g;
+      g.M = npair; g.N = n_mu; g.K = bw;
+      g.A = Q + f * nq; g.a_rs = nbg; g.a_cs = 1; g.a_bs = 0;
+      g.B = (f == 0 ? xi : calG + (int64_t)(f - 1) * plane) + g0;
+      g.b_rs = 1; g.b_cs = n_g; g.b_bs = 0;
+      g.C = Xp; g.ldc = n_mu; g.c_bs = 0;
+      g.beta = (g0 == 0 && f == 0) ? 0.0 : 1.0;
+      ISDF_TRY(dgemm(g, s));
+    }
+  }
+  return ISDF_OK;
+}
+
+}  // namespace isdf

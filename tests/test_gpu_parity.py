@@ -1,0 +1,214 @@
+"""GPU parity of every step of the path against the FP64 oracle, through the
+C ABI, on seeded inputs (H6 chain: 4800 points = 37.5 tiles of 128, N_mu = 96
+< one 128 tile, and smaller ragged systems).
+
+Tolerances: bit-exact pivot indices given identical inputs; 1e-10 relative
+for FP64 paths (loosened only where the fit's conditioning amplifies FP64
+rounding, stated per test); 1e-5 relative Frobenius per W channel and 1e-6 Ha
+in the energies for the split-BF16 tensor-core path.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import workloads as wl
+from oracle import orbitals, pivots, fit, wbuild, xtc, energies
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cu(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dt).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_17314_b300 import build
+    build.build()
+    import paper_2607_17314_b300 as P
+    P._capi.load()
+    return P
+
+
+def oracle_case(w):
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu)
+    xi, xit, lams = fit.fit(phi, dphi, res.pivots)
+    W, calG = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, w.jastrow)
+    phiP = xtc.pivot_factors(phi, res.pivots)
+    dphiP = [dphi[c][:, res.pivots].T for c in range(3)]
+    _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, w.n_occ))
+    X = xtc.x_projector(w.grid_w, xi, calG, phiP, w.n_occ)
+    E = energies.energies(W, D, X, phiP, dphiP, w.n_occ)
+    return dict(phi=phi, dphi=dphi, res=res, xi=xi, xit=xit, lams=lams, W=W, calG=calG,
+                phiP=phiP, dphiP=np.stack(dphiP), D=D, X=X, E=E)
+
+
+@pytest.fixture(scope="module")
+def h6():
+    w = wl.h6_chain()
+    return w, oracle_case(w)
+
+
+def test_orbitals(P, h6):
+    w, o = h6
+    b = w.basis
+    phi, dphi = P.isdf_eval_orbitals(cu(b.center), cu(b.powers, torch.int32), cu(b.exps),
+                                     cu(b.coefs), cu(w.mo_coef), cu(w.grid_xyz))
+    assert rel(host(phi), o["phi"]) < 1e-12
+    assert rel(host(dphi), o["dphi"]) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_pivots_bit_exact(P, h6, mode):
+    w, o = h6
+    ref = pivots.select(o["phi"], o["dphi"], w.grid_w, w.n_mu,
+                        mode={0: "fused", 1: "scalar", 2: "gradient"}[mode])
+    piv = P.isdf_points(cu(o["phi"]), cu(o["dphi"]), cu(w.grid_w), w.n_mu, mode)
+    want = {0: ref.pivots, 1: ref.piv_s, 2: ref.piv_v}[mode]
+    assert np.array_equal(host(piv), want)
+
+
+def test_pivots_rank_exhaustion(P):
+    """3 s orbitals: the scalar channel has rank 6; asking for 50 stops at 6
+    with ISDF_E_RANK, identically to the oracle."""
+    w = wl.tiny_chain(n_atom=3, n_rad=16, n_ang=26, shells=(0,), seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    ref = pivots.select(phi, dphi, w.grid_w, 50, mode="scalar")
+    piv = P.isdf_points(cu(phi), cu(dphi), cu(w.grid_w), 50, 1, allow_rank=True)
+    assert ref.rank_exhausted and np.array_equal(host(piv), ref.piv_s)
+
+
+def test_fit(P, h6):
+    w, o = h6
+    xi, xig, jit = P.isdf_fit(cu(o["phi"]), cu(o["dphi"]), cu(o["res"].pivots, torch.int32))
+    assert np.allclose(jit, o["lams"])
+    # FP64 solve of a Hadamard-squared Gram: agreement is limited by its
+    # conditioning times the FP64 unit roundoff
+    assert rel(host(xi), o["xi"]) < 1e-9
+    assert rel(host(xig), o["xit"]) < 1e-9
+
+
+def _jas(P, w):
+    return P.jastrow_from(w.jastrow)
+
+
+def test_w_fp64(P, h6):
+    w, o = h6
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
+                                _jas(P, w), "fp64")
+    for c in range(4):
+        assert rel(host(W[c]), o["W"][c]) < 1e-10, c
+        assert rel(host(calG[c]), o["calG"][c]) < 1e-10, c
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_w_tensor_core(P, h6, prec):
+    w, o = h6
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
+                                _jas(P, w), prec)
+    errs = [rel(host(W[c]), o["W"][c]) for c in range(4)]
+    gerrs = [rel(host(calG[c]), o["calG"][c]) for c in range(4)]
+    print(prec, "W rel", errs, "calG rel", gerrs)
+    # 3 BF16 limbs (6 products) carry ~24 bits and meet the 1e-5 bar; 2 limbs
+    # (3 products) carry ~16 bits and are the fast, looser mode
+    assert max(errs) < (1e-5 if prec == "bf16x6" else 1e-4), errs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_w_slices_additive(P, h6, prec):
+    w, o = h6
+    args = (cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w), prec)
+    Wf, Gf = P.tc_kernel_build(*args)
+    cut = 1717
+    Wa, Ga = P.tc_kernel_build(*args, g_begin=0, g_end=cut)
+    Wb, Gb = P.tc_kernel_build(*args, g_begin=cut, g_end=w.n_g)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert rel(host(Wa + Wb), host(Wf)) < tol
+    assert rel(host(torch.cat([Ga, Gb], dim=2)), host(Gf)) < tol
+
+
+def test_xtc(P, h6):
+    w, o = h6
+    n_orb = w.n_orb
+    D, Xp = P.xtc_density_contract(cu(o["phiP"]), w.n_occ, cu(o["xi"]), cu(w.grid_w),
+                                   cu(o["calG"]), n_orb_x=n_orb)
+    _, _, Dref = xtc.d_kernels(w.grid_w, o["xi"], o["calG"], xtc.g_nu(o["phiP"], w.n_occ))
+    assert rel(host(D), Dref) < 1e-10
+    Xfull = xtc.x_projector(w.grid_w, o["xi"], o["calG"], o["phiP"], w.n_occ)
+    assert rel(host(Xp), xtc.pack_upper(Xfull)) < 1e-10
+
+
+def test_energies_fp64(P, h6):
+    w, o = h6
+    Xp = xtc.pack_upper(o["X"])
+    E = P.tc_energies(cu(o["W"]), cu(o["D"]), cu(Xp), cu(o["phiP"]), cu(o["dphiP"]), w.n_occ)
+    ref = o["E"]
+    for got, key in zip(E, ("E_K", "E_dU", "E0")):
+        assert abs(got - ref[key]) <= 1e-10 * abs(ref[key]) + 1e-14, (key, got, ref[key])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x3"])
+def test_end_to_end(P, h6, prec):
+    """Full path on the GPU (a1 -> a6) against the oracle's energies."""
+    from paper_2607_17314_b300 import pipeline
+    w, o = h6
+    b = w.basis
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, w.mo_coef, w.grid_xyz, w.grid_w,
+                          w.n_mu, w.n_occ, _jas(P, w))
+    out = pipeline.run(inp, precision=prec)
+    piv = host(out["pivots"])
+    same = np.array_equal(piv, o["res"].pivots)
+    print("pivots identical end to end:", same)
+    if not same:
+        # GPU-evaluated orbitals differ in the last bits; a different index
+        # must come from a near tie, which leaves the fitted span (and hence
+        # the energies) essentially unchanged
+        assert len(set(piv) & set(o["res"].pivots)) >= 0.9 * len(piv)
+    for got, key in zip(out["E"], ("E_K", "E_dU", "E0")):
+        tol = 1e-6 if prec != "fp64" else max(1e-9 * abs(o["E"][key]), 1e-12)
+        if not same:
+            tol = max(tol, 1e-6)
+        assert abs(got - o["E"][key]) <= tol, (key, got, o["E"][key])
+
+
+def test_ragged_small_system(P):
+    """n_g = 2 x 9 x 14 = 252 (ragged against 128 and 32), n_mu = 13."""
+    w = wl.tiny_chain(n_atom=2, n_rad=9, n_ang=14, shells=(0, 1), n_mu=13, seed=21)
+    o = oracle_case(w)
+    args = (cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w))
+    W64, G64 = P.tc_kernel_build(*args, "fp64")
+    assert max(rel(host(W64[c]), o["W"][c]) for c in range(4)) < 1e-10
+    W16, _ = P.tc_kernel_build(*args, "bf16x6")
+    assert max(rel(host(W16[c]), o["W"][c]) for c in range(4)) < 1e-5
+
+
+def test_bh_jastrow_fp64(P):
+    """Multi-centre Boys-Handy correlator (e-e, e-n, e-e-n terms) on the FP64 path."""
+    w = wl.tiny_chain(n_atom=3, n_rad=8, n_ang=14, shells=(0, 1), n_mu=20, seed=5,
+                      jkind="bh", jterms=wl.bh_terms_c4())
+    o = oracle_case(w)
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
+                                _jas(P, w), "fp64")
+    for c in range(4):
+        assert rel(host(W[c]), o["W"][c]) < 1e-10, c
+
+
+def test_zero_jastrow_fp64(P, h6):
+    w, o = h6
+    J = _jas(P, w)
+    J.cusp = 0
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), J, "fp64")
+    assert float(W.abs().max()) == 0.0 and float(calG.abs().max()) == 0.0
