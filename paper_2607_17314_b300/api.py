@@ -156,7 +156,7 @@ class KernelBuilder:
         self.opt = options(precision, kchunk, s2_kchunk, sync_check, debug_flags,
                            ctypes.cast(self.stage_ms, ctypes.POINTER(ctypes.c_float))
                            if time_stages else None)
-        n_gs = self.g_end - self.g_begin
+        n_gs = max(self.g_end - self.g_begin, 0)  # an empty slice is rejected by the library
         self.W = torch.empty((4, self.n_mu, self.n_mu), dtype=f64, device=self.dev)
         self.calG = torch.empty((4, self.n_mu, n_gs), dtype=f64, device=self.dev)
         self.ws = _ws(lib.tc_kernel_build_workspace(self.n_g, self.n_mu, self.g_begin, self.g_end,

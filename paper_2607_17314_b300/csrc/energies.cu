@@ -86,7 +86,7 @@ size_t energies_ws(int n_mu, int n_occ) {
   c.take<double>(3 * n_mu * n2);  // Ct
   c.take<double>(n_mu * n2);      // Y
   c.take<double>(n2 * n_mu);      // Xo
-  c.take<double>(4 * n2 * n2);    // K1, K3, DCD, XC
+  for (int i = 0; i < 4; ++i) c.take<double>(n2 * n2);  // K1, K3, DCD, XC
   c.take<double>(4);
   return c.off;
 }

@@ -131,6 +131,42 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 registers per thread -> 32 lanes x 32 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Fold one 32-column block of a chunk accumulator into a running FP32 sum
+// held in tensor memory (IEEE round-to-nearest adds on the CUDA cores).
+// first: the running sum starts as the chunk; out receives the new sum.
+__device__ __forceinline__ void tmem_fold_block(uint32_t t_chunk, uint32_t t_run, bool first,
+                                                uint32_t (&out)[32]) {
+  uint32_t a[32];
+  tmem_ld_32x32b_x32(t_chunk, a);
+  if (!first) tmem_ld_32x32b_x32(t_run, out);
+  tmem_ld_wait();
+  if (first) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) out[j] = a[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      out[j] = __float_as_uint(__fadd_rn(__uint_as_float(out[j]), __uint_as_float(a[j])));
+  }
+}
+
 // ------------------------------------------------------------------ UMMA
 
 // Shared-memory matrix descriptor (tcgen05 format, version 1).
@@ -168,6 +204,20 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ float4 lds_f4(uint32_t saddr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ void sts_u4(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c,
+                                       uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
 }
 
 // Byte offset of element (row, k) in a K-major tile with 64-byte rows

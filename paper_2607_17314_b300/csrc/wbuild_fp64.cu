@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(256) s1_fp64_kernel(S1F64 a, const __grid_cons
       if (gl < n_gs && gp < a.n_g) {
         int64_t g = a.g_begin + gl;
         if (g != gp) {
-          if (RADIAL) radial_grad(J.d, a.grid + 3 * g, a.grid + 3 * gp, K);
+          if (RADIAL) {
+            if (J.cusp) radial_grad(J.d, a.grid + 3 * g, a.grid + 3 * gp, K);
+          }
           else bh_grad(J, a.tab, g, gp, a.grid + 3 * g, a.grid + 3 * gp, K);
         }
       }

@@ -96,47 +96,75 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int
   }
 }
 
+// hi/lo: FP32 pair of every point; loc: point minus the first point of its
+// 32-point block (FP32 of the FP64 difference); org[2b], org[2b+1]: hi/lo
+// pair of the first point of block b.  Padding points sit at the origin.
 __global__ void coords_kernel(const double* __restrict__ grid, int64_t n_g, int64_t n_pad,
-                              float4* __restrict__ hi, float4* __restrict__ lo) {
+                              float4* __restrict__ hi, float4* __restrict__ lo,
+                              float4* __restrict__ loc, float4* __restrict__ org) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_pad) return;
   double x = 0, y = 0, z = 0;
   if (g < n_g) { x = grid[3 * g]; y = grid[3 * g + 1]; z = grid[3 * g + 2]; }
+  const int64_t b0 = g & ~(int64_t)31;
+  double ox = 0, oy = 0, oz = 0;
+  if (b0 < n_g) { ox = grid[3 * b0]; oy = grid[3 * b0 + 1]; oz = grid[3 * b0 + 2]; }
   float xh = (float)x, yh = (float)y, zh = (float)z;
   hi[g] = make_float4(xh, yh, zh, 0.f);
   lo[g] = make_float4((float)(x - xh), (float)(y - yh), (float)(z - zh), 0.f);
+  loc[g] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
+  if (g == b0) {
+    float ohx = (float)ox, ohy = (float)oy, ohz = (float)oz;
+    org[2 * (g >> 5)] = make_float4(ohx, ohy, ohz, 0.f);
+    org[2 * (g >> 5) + 1] = make_float4((float)(ox - ohx), (float)(oy - ohy), (float)(oz - ohz), 0.f);
+  }
 }
 
 // ------------------------------------------------------------------ stage 1
 
-template <int LIMBS, int BN>
+// Tile: 128 nu (M) x 64 g (N) per CTA, 32 inner points g' per stage.  Tensor
+// memory holds one FP32 chunk accumulator (4 channels x 64 columns) that the
+// MMAs fill over kchunk inner points, and an FP32 running sum of the same
+// shape into which the epilogue warps fold each chunk with IEEE-rounded adds.
+// Short tensor-core accumulation runs keep the accumulation error small;
+// the tile is written to FP64 calG once, after its last chunk.
+template <int LIMBS>
 struct S1C {
-  static constexpr int BM = 128, BK = 32;
-  static constexpr int STAGES = LIMBS == 2 ? 2 : 3;
+  static constexpr int BM = 128, BN = 64, BK = 32;
+  static constexpr int STAGES = LIMBS == 2 ? 4 : 3;
+  static constexpr int CSTAGES = 8;  // coordinate ring
   static constexpr uint32_t A_LIMB = BM * BK * 2;
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t A_BYTES = LIMBS * A_LIMB;
   static constexpr uint32_t B_BYTES = 4 * LIMBS * B_TILE;
+  static constexpr uint32_t C_BYTES = BK * 16 + 32;  // block-local coordinates + block origin
   static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
-  static constexpr uint32_t TMEM_COLS = 4 * BN;
-  static constexpr int NGW = 8;
-  static constexpr int THREADS = 64 + 32 * NGW;
+  static constexpr uint32_t ACC_COLS = 4 * BN;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static constexpr int NGW = 8;  // generator warps: 2 .. 9
+  static constexpr int NEW = 4;  // epilogue warps: 10 .. 13
+  static constexpr int CW = 2 + NGW + NEW;  // coordinate producer warp
+  static constexpr int THREADS = 32 * (CW + 1);
   static constexpr int COLS = BN * BK / (32 * NGW);  // inner points per generator thread
-  static constexpr uint32_t SMEM = STAGES * STAGE + 1024 + 256;
-  static_assert(COLS % 8 == 0, "generator writes whole 16-byte chunks");
-  static_assert(STAGE % 1024 == 0, "stage alignment");
+  static constexpr uint32_t SMEM = STAGES * STAGE + CSTAGES * C_BYTES + 1024 + 512;
+  static_assert(COLS == 8, "one 16-byte chunk per generator thread and operand");
+  static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0 && B_TILE % 1024 == 0, "alignment");
+  static_assert(TMEM_COLS == 512, "tensor memory budget");
+  static_assert(SMEM <= 232448, "shared memory budget");
 };
 
 struct S1Params {
-  const float4* xyz_hi;  // [n_k] inner points (padded)
+  const float4* xyz_hi;  // [n_k] points as FP32 hi/lo pairs (padded)
   const float4* xyz_lo;
+  const float4* loc;     // [n_k] point minus its 32-block origin
+  const float4* org;     // [n_k / 32][2] block origins, hi/lo
   int64_t n_g;           // real points
   int64_t n_k;           // padded inner extent (multiple of 32)
   int n_mu;
   int n_mu_tiles;
   int64_t g_begin, g_end;
   int64_t n_g_tiles;
-  int64_t kchunk;        // multiple of 32
+  int64_t kchunk;        // fold interval, multiple of 32
   float d;
   double* calG;          // [4][n_mu][g_end - g_begin]
   int* err;
@@ -149,6 +177,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+// Limbs of two values packed as bf16x2 words; each limb is the
+// round-to-nearest bf16 of the remainder left by the previous ones.
 template <int LIMBS>
 __device__ __forceinline__ void split_pack(float a, float b, uint32_t (&out)[LIMBS]) {
 #pragma unroll
@@ -156,42 +195,48 @@ __device__ __forceinline__ void split_pack(float a, float b, uint32_t (&out)[LIM
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     uint32_t w = *reinterpret_cast<uint32_t*>(&h);
     out[l] = w;
-    a -= __uint_as_float(w << 16);
-    b -= __uint_as_float(w & 0xffff0000u);
+    if (l + 1 < LIMBS) {
+      a -= __uint_as_float(w << 16);
+      b -= __uint_as_float(w & 0xffff0000u);
+    }
   }
 }
 
-// Radial correlator: K_c = u'(r)/r (r_g - r_g')_c with u' = 1/(2 (1 + d r)^2),
-// K_sq = u'^2.  Coordinates as FP32 hi + lo pairs so that close pairs keep
-// their relative accuracy.
-__device__ __forceinline__ void radial_pair(float4 gh, float4 gl, float4 ph, float4 pl, float d,
-                                            bool zero, float& kx, float& ky, float& kz,
-                                            float& ksq) {
-  float dx = (gh.x - ph.x) + (gl.x - pl.x);
-  float dy = (gh.y - ph.y) + (gl.y - pl.y);
-  float dz = (gh.z - ph.z) + (gl.z - pl.z);
-  float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1e-30f);
-  float rinv = rsqrtf(r2);
-  float r = r2 * rinv;
-  float iden = rcp_approx(fmaf(d, r, 1.0f));
-  float up = 0.5f * iden * iden;
-  float f = zero ? 0.0f : up * rinv;
+// Radial correlator u = r / (2 (1 + d r)):  K_c = u'(r)/r (r_g - r_g')_c with
+// u' = 1/(2 (1 + d r)^2), and K_sq = u'^2.  The difference vector is formed
+// as m - l with m = r_g - o (o = origin of the inner point's 32-point block,
+// from FP32 hi/lo pairs) and l = r_g' - o, so that close pairs keep their
+// relative accuracy.  The self pair (flagged by the caller) gives zero.
+__device__ __forceinline__ void radial_pair(float4 m, float4 l, float d, bool self, float& kx,
+                                            float& ky, float& kz, float& ksq) {
+  const float dx = m.x - l.x;
+  const float dy = m.y - l.y;
+  const float dz = m.z - l.z;
+  const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1e-30f);
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
+  const float iden = rcp_approx(fmaf(d, r, 1.0f));
+  const float up = 0.5f * iden * iden;
+  const float f = self ? 0.0f : up * rinv;
   kx = f * dx;
   ky = f * dy;
   kz = f * dz;
-  ksq = zero ? 0.0f : up * up;
+  ksq = self ? 0.0f : up * up;
 }
 
-template <int LIMBS, int BN>
-__global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
+template <int LIMBS>
+__global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
     s1_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                  const __grid_constant__ CUtensorMap mA2, const S1Params p) {
-  using C = S1C<LIMBS, BN>;
+  using C = S1C<LIMBS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint8_t* csm = smem + C::STAGES * C::STAGE;  // coordinate ring
+  uint64_t* full = (uint64_t*)(csm + C::CSTAGES * C::C_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* acc_full = empty + C::STAGES;
+  uint64_t* cfull = empty + C::STAGES;
+  uint64_t* cempty = cfull + C::CSTAGES;
+  uint64_t* acc_full = cempty + C::CSTAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -202,8 +247,12 @@ __global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
       tc::mbar_init(&full[s], C::NGW + 1);
       tc::mbar_init(&empty[s], 1);
     }
+    for (int s = 0; s < C::CSTAGES; ++s) {
+      tc::mbar_init(&cfull[s], 1);
+      tc::mbar_init(&cempty[s], C::NGW);
+    }
     tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, C::NGW);
+    tc::mbar_init(acc_empty, C::NEW);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -221,6 +270,7 @@ __global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
   const int64_t n_chunks = (p.n_k + p.kchunk - 1) / p.kchunk;
 
   if (warp == 0) {
+    // producer of the (w xi) limbs (TMA)
     if (lane == 0) {
       tc::tma_prefetch_desc(&mA0);
       if (LIMBS > 1) tc::tma_prefetch_desc(&mA1);
@@ -229,38 +279,50 @@ __global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
       bool skip = (p.debug & 1) != 0;
       for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
-        for (int64_t ch = 0; ch < n_chunks; ++ch) {
-          const int64_t kb = ch * p.kchunk;
-          const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-          for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
-            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-            if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
-            if (skip) {  // fault-path test: never arm this stage
-              skip = false;
-              continue;
-            }
-            tc::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
-            uint8_t* a = smem + s * C::STAGE;
-            tc::tma_load_2d(a, &mA0, &full[s], (int32_t)k0, mu0);
-            if (LIMBS > 1) tc::tma_load_2d(a + C::A_LIMB, &mA1, &full[s], (int32_t)k0, mu0);
-            if (LIMBS > 2) tc::tma_load_2d(a + 2 * C::A_LIMB, &mA2, &full[s], (int32_t)k0, mu0);
+        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+          if (skip) {  // fault-path test: this stage's operand never arrives
+            skip = false;
+            continue;
           }
+          uint8_t* st = smem + s * C::STAGE;
+          tc::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
+          tc::tma_load_2d(st, &mA0, &full[s], (int32_t)k0, mu0);
+          if (LIMBS > 1) tc::tma_load_2d(st + C::A_LIMB, &mA1, &full[s], (int32_t)k0, mu0);
+          if (LIMBS > 2) tc::tma_load_2d(st + 2 * C::A_LIMB, &mA2, &full[s], (int32_t)k0, mu0);
+        }
+      }
+    }
+  } else if (warp == C::CW) {
+    // producer of the inner-point coordinates (bulk copies, runs ahead)
+    if (lane == 0) {
+      uint32_t cit = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
+          const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
+          if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err)) goto done;
+          uint8_t* dst = csm + cs * C::C_BYTES;
+          tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
+          bulk_copy_g2s(dst, p.loc + k0, C::BK * 16, &cfull[cs]);
+          bulk_copy_g2s(dst + C::BK * 16, p.org + 2 * (k0 / C::BK), 32, &cfull[cs]);
         }
       }
     }
   } else if (warp == 1) {
+    // MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16(128, BN, 1);
+      constexpr uint32_t idesc = tc::idesc_f16(128, C::BN, 1);
       uint32_t it = 0, u = 0;
       for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
           const int64_t kb = ch * p.kchunk;
           const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto mma_drain;
+          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto mma_out;
           tc::tc_fence_after();
           for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
             const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto mma_drain;
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto mma_out;
             tc::tc_fence_after();
             const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE);
             const uint32_t b_base = a_base + C::A_BYTES;
@@ -277,104 +339,107 @@ __global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
                     const uint64_t bd =
                         tc::smem_desc(b_base + (c * LIMBS + j) * C::B_TILE + kk * 32, 16, 512, 4);
                     const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                    tc::umma_f16(tmem + c * BN, ad, bd, idesc, acc);
+                    tc::umma_f16(tmem + c * C::BN, ad, bd, idesc, acc);
                   }
             tc::umma_commit(&empty[s]);
           }
           tc::umma_commit(acc_full);
         }
       }
-    mma_drain:;
+    mma_out:;
     }
-  } else {
-    // generator + epilogue warps
-    const int gw = warp - 2;
+  } else if (warp < 2 + C::NGW) {
+    // generators: K_c(g, g') for a 64 x 32 block, split into BF16 limbs,
+    // stored into the 64B-swizzled K-major B tiles
     const int gt = threadIdx.x - 64;
-    const int row = gt % BN;
-    const int col0 = (gt / BN) * C::COLS;
+    const int row = gt % C::BN;
+    const int kc = (gt / C::BN) * C::COLS;
     const float d = p.d;
-    uint32_t it = 0, u = 0;
+    uint32_t it = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int64_t g_tile = tile % p.n_g_tiles;
-      const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
-      const int64_t gl = g_tile * BN + row;
+      const int64_t gl = g_tile * C::BN + row;
       const bool gvalid = gl < n_gs;
       const int64_t g = p.g_begin + (gvalid ? gl : 0);
       const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
-        const int64_t kb = ch * p.kchunk;
-        const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-        for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
-          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
-          uint8_t* bsm = smem + s * C::STAGE + C::A_BYTES;
+      const int64_t gself = gvalid ? g : -1;
+      for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+        const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
+        if (!tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err)) goto done;
+        const uint32_t cbase = tc::smem_u32(csm + cs * C::C_BYTES);
+        float4 l4[8];
 #pragma unroll
-          for (int q = 0; q < C::COLS / 8; ++q) {
-            const int kc = col0 + q * 8;
-            uint32_t pk[4][LIMBS][4];
+        for (int e = 0; e < 8; ++e) l4[e] = tc::lds_f4(cbase + (kc + e) * 16);
+        const float4 oh = tc::lds_f4(cbase + C::BK * 16);
+        const float4 ol = tc::lds_f4(cbase + C::BK * 16 + 16);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&cempty[cs]);
+        // row point relative to the block origin
+        const float4 m = make_float4((gh.x - oh.x) + (glo.x - ol.x), (gh.y - oh.y) + (glo.y - ol.y),
+                                     (gh.z - oh.z) + (glo.z - ol.z), 0.f);
+        // the self pair can only fall in this block when the index ranges meet
+        const bool may_self = gself >= k0 && gself < k0 + C::BK;
+        uint32_t pk[4][LIMBS][4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-              float kv[2][4];
+        for (int e = 0; e < 8; e += 2) {
+          float kv[2][4];
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int64_t gp = k0 + kc + e + h;
-                const float4 ph4 = p.xyz_hi[gp];
-                const float4 pl4 = p.xyz_lo[gp];
-                const bool zero = !gvalid || gp >= p.n_g || gp == g;
-                radial_pair(gh, glo, ph4, pl4, d, zero, kv[h][0], kv[h][1], kv[h][2], kv[h][3]);
-              }
+          for (int h = 0; h < 2; ++h)
+            radial_pair(m, l4[e + h], d, may_self && (k0 + kc + e + h) == gself, kv[h][0],
+                        kv[h][1], kv[h][2], kv[h][3]);
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                uint32_t w[LIMBS];
-                split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+          for (int c = 0; c < 4; ++c) {
+            uint32_t w[LIMBS];
+            split_pack<LIMBS>(kv[0][c], kv[1][c], w);
 #pragma unroll
-                for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
-              }
-            }
-            const uint32_t off = tc::sw64_offset(row, kc >> 3);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int l = 0; l < LIMBS; ++l) {
-                uint4 v = make_uint4(pk[c][l][0], pk[c][l][1], pk[c][l][2], pk[c][l][3]);
-                *reinterpret_cast<uint4*>(bsm + (c * LIMBS + l) * C::B_TILE + off) = v;
-              }
+            for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
           }
-          tc::fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&full[s]);
         }
-        // epilogue: drain the four accumulators of this chunk into FP64
+        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+        const uint32_t bsm = tc::smem_u32(smem + s * C::STAGE + C::A_BYTES) +
+                             tc::sw64_offset(row, kc >> 3);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l)
+            tc::sts_u4(bsm + (c * LIMBS + l) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
+                       pk[c][l][3]);
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full[s]);
+      }
+    }
+  } else {
+    // epilogue: fold each chunk into the running sum; write the tile at the end
+    const int quad = warp & 3;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    uint32_t u = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int64_t g_tile = tile % p.n_g_tiles;
+      const int mu = (int)(tile / p.n_g_tiles) * C::BM + 32 * quad + lane;
+      for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
         if (!tc::mbar_wait(acc_full, u & 1, abort_flag, p.err)) goto done;
         tc::tc_fence_after();
-        {
-          const int quad = warp & 3;
-          const int half = gw >> 2;
-          const int mu = mu0 + 32 * quad + lane;
-          const bool first = (ch == 0);
+        const bool first = (ch == 0), last = (ch + 1 == n_chunks);
 #pragma unroll 1
-          for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-#pragma unroll 1
-            for (int blk = 0; blk < BN / 32; ++blk) {
-              uint32_t r[32];
-              tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * quad) << 16) + cc * BN + blk * 32, r);
-              tc::tmem_ld_wait();
-              if (mu < p.n_mu) {
-                double* dst = p.calG + ((int64_t)cc * p.n_mu + mu) * n_gs;
-                const int64_t gbase = g_tile * BN + blk * 32;
+        for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
+          uint32_t r[32];
+          tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
+                              first, r);
+          if (!last) {
+            tc::tmem_st_32x32b_x32(tmem + lane_base + C::ACC_COLS + blk * 32, r);
+          } else if (mu < p.n_mu) {
+            const int c = blk / (C::BN / 32);
+            double* dst = p.calG + ((int64_t)c * p.n_mu + mu) * n_gs;
+            const int64_t gbase = g_tile * C::BN + (blk % (C::BN / 32)) * 32;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int64_t gg = gbase + j;
-                  if (gg < n_gs) {
-                    const double v = (double)__uint_as_float(r[j]);
-                    dst[gg] = first ? v : dst[gg] + v;
-                  }
-                }
-              }
-            }
+            for (int j = 0; j < 32; ++j)
+              if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
           }
         }
+        if (!last) tc::tmem_st_wait();
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(acc_empty);
@@ -384,7 +449,7 @@ __global__ void __launch_bounds__(S1C<LIMBS, BN>::THREADS, 1)
 done:
   __syncthreads();
   if (*abort_flag) {
-    // a bounded wait expired: give issued TMA copies and MMAs time to land
+    // a bounded wait expired: give issued copies and MMAs time to land
     const uint64_t t0 = globaltimer_ns();
     while (globaltimer_ns() - t0 < 200000ull) {
     }
@@ -397,8 +462,11 @@ done:
 
 // ------------------------------------------------------------------ generic split GEMM
 
-// out[z][m][n] += scale * sum_k A_z[m][k] B_z[n][k] over the K chunk of this
-// CTA, A_z and B_z in limbs.  One CTA per (n tile, m tile, k chunk, z).
+// out[z][m][n] += scale * sum_k A_z[m][k] B_z[n][k] over the K range of this
+// CTA, A_z and B_z in BF16 limbs.  One CTA per (n tile, m tile, K range, z).
+// The tensor core accumulates fold_tiles x 32 points at a time; the epilogue
+// folds each chunk into an FP32 running sum in tensor memory and finally
+// adds the tile into the FP64 output with atomics.
 constexpr int GB_MAXB = 4;
 
 struct GemmMaps {
@@ -410,6 +478,7 @@ struct GemmParams {
   int64_t M, N;           // real output extents
   int64_t k_tiles;        // padded K / 32
   int64_t kchunk_tiles;   // k tiles per CTA
+  int64_t fold_tiles;     // k tiles per tensor-core accumulation run
   int m_tiles, n_tiles, kchunks, batch;
   double* out;            // [batch][M][ldo] (or a single [M][ldo] when out_bs = 0)
   int64_t ldo, out_bs;
@@ -435,7 +504,8 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   int64_t unit = blockIdx.x;
@@ -445,6 +515,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
   const int z = (int)unit;
   const int64_t kt0 = (int64_t)kc * p.kchunk_tiles;
   const int64_t kt1 = kt0 + p.kchunk_tiles < p.k_tiles ? kt0 + p.kchunk_tiles : p.k_tiles;
+  const int64_t n_folds = (kt1 - kt0 + p.fold_tiles - 1) / p.fold_tiles;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -453,11 +524,12 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
       tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, 4);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, 128);
+    tc::tmem_alloc(tmem_slot, 256);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -487,41 +559,51 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
       if (lane == 0) {
         constexpr uint32_t idesc = tc::idesc_f16(128, 128, 1);
         uint32_t it = 0;
-        bool ok = true;
-        for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
-          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-          if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+        for (int64_t f = 0; f < n_folds; ++f) {
+          const int64_t fb = kt0 + f * p.fold_tiles;
+          const int64_t fe = fb + p.fold_tiles < kt1 ? fb + p.fold_tiles : kt1;
+          if (!tc::mbar_wait(acc_empty, (f & 1) ^ 1, abort_flag, p.err)) break;
           tc::tc_fence_after();
-          const uint32_t base = tc::smem_u32(smem + s * C::STAGE);
+          bool ok = true;
+          for (int64_t kt = fb; kt < fe; ++kt, ++it) {
+            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+            tc::tc_fence_after();
+            const uint32_t base = tc::smem_u32(smem + s * C::STAGE);
 #pragma unroll
-          for (int i = 0; i < LIMBS; ++i)
+            for (int i = 0; i < LIMBS; ++i)
 #pragma unroll
-            for (int j = 0; j < LIMBS - i; ++j)
+              for (int j = 0; j < LIMBS - i; ++j)
 #pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t ad = tc::smem_desc(base + i * C::TILE + kk * 32, 16, 512, 4);
-                const uint64_t bd = tc::smem_desc(base + (LIMBS + j) * C::TILE + kk * 32, 16, 512, 4);
-                const uint32_t acc = (kt == kt0 && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                tc::umma_f16(tmem, ad, bd, idesc, acc);
-              }
-          tc::umma_commit(&empty[s]);
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t ad = tc::smem_desc(base + i * C::TILE + kk * 32, 16, 512, 4);
+                  const uint64_t bd = tc::smem_desc(base + (LIMBS + j) * C::TILE + kk * 32, 16, 512, 4);
+                  const uint32_t acc = (kt == fb && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                  tc::umma_f16(tmem, ad, bd, idesc, acc);
+                }
+            tc::umma_commit(&empty[s]);
+          }
+          if (!ok) break;
+          tc::umma_commit(acc_full);
         }
-        (void)ok;
-        tc::umma_commit(acc_full);
       }
     } else {
       // epilogue warps 2..5: lanes 32*(warp%4) .. +31
-      if (tc::mbar_wait(acc_full, 0, abort_flag, p.err)) {
+      const int quad = warp & 3;
+      const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+      const int64_t m = m0 + 32 * quad + lane;
+      double* dst = p.out + (int64_t)z * p.out_bs + m * p.ldo;
+      for (int64_t f = 0; f < n_folds; ++f) {
+        if (!tc::mbar_wait(acc_full, f & 1, abort_flag, p.err)) break;
         tc::tc_fence_after();
-        const int quad = warp & 3;
-        const int64_t m = m0 + 32 * quad + lane;
-        double* dst = p.out + (int64_t)z * p.out_bs + m * p.ldo;
+        const bool first = (f == 0), last = (f + 1 == n_folds);
 #pragma unroll 1
         for (int blk = 0; blk < 4; ++blk) {
           uint32_t r[32];
-          tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * quad) << 16) + blk * 32, r);
-          tc::tmem_ld_wait();
-          if (m < p.M) {
+          tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + 128 + blk * 32, first, r);
+          if (!last) {
+            tc::tmem_st_32x32b_x32(tmem + lane_base + 128 + blk * 32, r);
+          } else if (m < p.M) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int64_t n = n0 + blk * 32 + j;
@@ -529,6 +611,10 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
             }
           }
         }
+        if (!last) tc::tmem_st_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(acc_empty);
       }
     }
   }
@@ -541,11 +627,16 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
   }
   if (warp == 0) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 128);
+    tc::tmem_dealloc(tmem, 256);
   }
 }
 
 inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
+
+// Inner points per tensor-core accumulation run before each fold into the
+// running sum (both stages), and grid points per stage-2 CTA.
+constexpr int64_t kDefaultChunk = 512;
+constexpr int64_t kS2Range = 8192;
 
 }  // namespace
 
@@ -566,11 +657,12 @@ int split_operand(const double* src, int64_t src_rs, int64_t c0, const double* c
 // accumulating scale * A_z B_z^T into out (+ z * out_bs).  out must be
 // initialised by the caller.
 int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, int64_t M,
-              int64_t N, int64_t Kp, int64_t kchunk, double* out, int64_t ldo, int64_t out_bs,
-              double scale, int* err, cudaStream_t s) {
+              int64_t N, int64_t Kp, int64_t kchunk, int64_t fold, double* out, int64_t ldo,
+              int64_t out_bs, double scale, int* err, cudaStream_t s) {
   ISDF_ARG(batch >= 1 && batch <= GB_MAXB, "splitgemm batch out of range");
   ISDF_ARG(limbs == 2 || limbs == 3, "limbs must be 2 or 3");
-  ISDF_ARG(Kp % 32 == 0 && kchunk % 32 == 0 && kchunk > 0, "K padding");
+  ISDF_ARG(Kp % 32 == 0 && kchunk % 32 == 0 && kchunk > 0 && fold % 32 == 0 && fold > 0,
+           "K padding");
   const int64_t Mp = round_up(M, 128), Np = round_up(N, 128);
   GemmMaps maps;
   memset(&maps, 0, sizeof(maps));
@@ -583,6 +675,7 @@ int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, 
   p.M = M; p.N = N;
   p.k_tiles = Kp / 32;
   p.kchunk_tiles = kchunk / 32;
+  p.fold_tiles = fold / 32;
   p.m_tiles = (int)(Mp / 128);
   p.n_tiles = (int)(Np / 128);
   p.kchunks = (int)ceil_div(p.k_tiles, p.kchunk_tiles);
@@ -609,7 +702,7 @@ struct TcLayout {
 static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
   TcLayout L;
   L.limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
-  L.bn = L.limbs == 2 ? 128 : 64;
+  L.bn = 64;
   L.n_k = round_up(n_g, 32);
   L.mu_pad = round_up(n_mu, 128);
   L.gs = g_end - g_begin;
@@ -623,6 +716,8 @@ size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int p
   c.take<int>(64);
   c.take<float4>(L.n_k);
   c.take<float4>(L.n_k);
+  c.take<float4>(L.n_k);
+  c.take<float4>(L.n_k / 16);
   c.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);           // S1 A
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
@@ -639,17 +734,19 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   int* err = cv.take<int>(64);
   float4* hi = cv.take<float4>(L.n_k);
   float4* lo = cv.take<float4>(L.n_k);
+  float4* loc = cv.take<float4>(L.n_k);
+  float4* org = cv.take<float4>(L.n_k / 16);
   uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);
   uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   ISDF_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
 
-  int64_t kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : 16384;
-  int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 16384;
+  int64_t kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : kDefaultChunk;
+  int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 256;
 
   // operands of stage 1
-  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo);
+  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo, loc, org);
   ISDF_LAUNCH_CHECK();
   ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad, L.n_k, L.limbs, A1, s));
   CUtensorMap mA[3];
@@ -658,7 +755,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad * L.n_k, L.mu_pad, L.n_k, 128));
 
   S1Params p;
-  p.xyz_hi = hi; p.xyz_lo = lo;
+  p.xyz_hi = hi; p.xyz_lo = lo; p.loc = loc; p.org = org;
   p.n_g = n_g; p.n_k = L.n_k; p.n_mu = n_mu;
   p.n_mu_tiles = (int)(L.mu_pad / 128);
   p.g_begin = g_begin; p.g_end = g_end;
@@ -680,13 +777,13 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     ISDF_CUDA(cudaEventRecord(ev[0], s));
   }
   if (L.limbs == 2) {
-    using C = S1C<2, 128>;
-    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    s1_tc_kernel<2, 128><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+    using C = S1C<2>;
+    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    s1_tc_kernel<2><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
   } else {
-    using C = S1C<3, 64>;
-    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    s1_tc_kernel<3, 64><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+    using C = S1C<3>;
+    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    s1_tc_kernel<3><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
   }
   ISDF_LAUNCH_CHECK();
   if (timed) ISDF_CUDA(cudaEventRecord(ev[1], s));
@@ -706,7 +803,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   }
   ISDF_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 4 * (size_t)n_mu * n_mu, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[2], s));
-  ISDF_TRY(splitgemm(L.limbs, 4, Ap, Bp, n_mu, n_mu, L.gs_pad, kchunk2, W, n_mu,
+  ISDF_TRY(splitgemm(L.limbs, 4, Ap, Bp, n_mu, n_mu, L.gs_pad, kS2Range, kchunk2, W, n_mu,
                      (int64_t)n_mu * n_mu, 1.0, err, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[3], s));
   if (opt.sync_check) {
