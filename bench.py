@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6"])
     ap.add_argument("--workload", default="h50_chain")
     ap.add_argument("--fp64-rows", type=int, default=1024,
                     help="outer grid points of the FP64 GPU comparison slice")

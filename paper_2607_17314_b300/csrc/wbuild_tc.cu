@@ -244,15 +244,18 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
-      tc::mbar_init(&full[s], C::NGW + 1);
+      // every generator thread arrives: its own shared-memory writes must be
+      // ordered before the tensor core reads them (a warp-level sync followed
+      // by one lane's arrive does not give that ordering)
+      tc::mbar_init(&full[s], C::NGW * 32 + 1);
       tc::mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < C::CSTAGES; ++s) {
       tc::mbar_init(&cfull[s], 1);
-      tc::mbar_init(&cempty[s], C::NGW);
+      tc::mbar_init(&cempty[s], C::NGW * 32);
     }
     tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, C::NEW);
+    tc::mbar_init(acc_empty, C::NEW * 32);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -374,8 +377,7 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
         for (int e = 0; e < 8; ++e) l4[e] = tc::lds_f4(cbase + (kc + e) * 16);
         const float4 oh = tc::lds_f4(cbase + C::BK * 16);
         const float4 ol = tc::lds_f4(cbase + C::BK * 16 + 16);
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&cempty[cs]);
+        tc::mbar_arrive(&cempty[cs]);  // this thread's reads precede the next bulk copy
         // row point relative to the block origin
         const float4 m = make_float4((gh.x - oh.x) + (glo.x - ol.x), (gh.y - oh.y) + (glo.y - ol.y),
                                      (gh.z - oh.z) + (glo.z - ol.z), 0.f);
@@ -407,8 +409,7 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
             tc::sts_u4(bsm + (c * LIMBS + l) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
                        pk[c][l][3]);
         tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&full[s]);
+        tc::mbar_arrive(&full[s]);
       }
     }
   } else {
@@ -441,8 +442,7 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
         }
         if (!last) tc::tmem_st_wait();
         tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(acc_empty);
+        tc::mbar_arrive(acc_empty);
       }
     }
   }
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
       tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, 4);
+    tc::mbar_init(acc_empty, 4 * 32);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -613,8 +613,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
         }
         if (!last) tc::tmem_st_wait();
         tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(acc_empty);
+        tc::mbar_arrive(acc_empty);
       }
     }
   }

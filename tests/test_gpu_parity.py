@@ -122,12 +122,13 @@ def test_w_tensor_core(P, h6, prec):
     errs = [rel(host(W[c]), o["W"][c]) for c in range(4)]
     gerrs = [rel(host(calG[c]), o["calG"][c]) for c in range(4)]
     print(prec, "W rel", errs, "calG rel", gerrs)
-    # 3 BF16 limbs (6 products) carry ~24 bits and meet the 1e-5 bar; 2 limbs
-    # (3 products) carry ~16 bits and are the fast, looser mode
-    assert max(errs) < (1e-5 if prec == "bf16x6" else 1e-4), errs
+    # the error is dominated by the tensor core's FP32 accumulation, kept
+    # short by folding every 512 inner points into an FP32 running sum;
+    # both limb counts meet the 1e-5 bar
+    assert max(errs) < 1e-5, errs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_w_slices_additive(P, h6, prec):
     w, o = h6
     args = (cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w), prec)
@@ -135,7 +136,8 @@ def test_w_slices_additive(P, h6, prec):
     cut = 1717
     Wa, Ga = P.tc_kernel_build(*args, g_begin=0, g_end=cut)
     Wb, Gb = P.tc_kernel_build(*args, g_begin=cut, g_end=w.n_g)
-    tol = 1e-12 if prec == "fp64" else 1e-6
+    # tensor-core partials each carry their own accumulation rounding
+    tol = 1e-12 if prec == "fp64" else 1e-5
     assert rel(host(Wa + Wb), host(Wf)) < tol
     assert rel(host(torch.cat([Ga, Gb], dim=2)), host(Gf)) < tol
 
