@@ -284,8 +284,11 @@ def main():
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     s1_tflops = 8.0 * n_mu * n_g * n_g / (s1_ms * 1e-3) / 1e12
     products = 3 if args.precision == "bf16x3" else 6
+    # DRAM bytes per (mu, g) output element of stage 1 from the ncu capture in
+    # profiles/s1_tc_kernel_bf16x3.md (input and output both scale with N_mu n_g)
+    traffic = 36.9 * n_mu * n_g if args.precision == "bf16x3" else None
     roofline = {"bound": "tensor", "achieved": s1_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": s1_tflops / peak, "traffic": None,
+                "frac": s1_tflops / peak, "traffic": traffic,
                 "pipe_frac": s1_tflops * products / peak,
                 "kernel": f"s1_tc_kernel ({args.precision}: {products} BF16 products per algorithmic MAC)",
                 "peak_kind": f"{peak_kind} bf16 sustained"}

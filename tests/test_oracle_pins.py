@@ -354,3 +354,64 @@ def test_particle_exchange(h6):
     assert np.max(np.abs(K - np.transpose(K, (1, 0, 3, 2)))) < 1e-12 * np.max(np.abs(K))
     # K is not Hermitian in the pair-block sense (Sec. IV.A)
     assert np.max(np.abs(K - np.transpose(K, (2, 3, 0, 1)))) > 1e-6 * np.max(np.abs(K))
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_dgrad_dtheta_matches_fd():
+    from oracle import adjoint
+    atoms, xyz = wl.h_chain(3, 1.8)
+    jas = wl.bh_jastrow(atoms, xyz, wl.bh_terms_c4(), np.random.default_rng(4), scale=0.3)
+    jas.b = np.array([1.2])
+    jas.d = 0.9
+    rng = np.random.default_rng(8)
+    ri = rng.normal(size=(5, 3)) * 2
+    rj = rng.normal(size=(4, 3)) * 2
+    an = adjoint.dgrad_dtheta(ri, rj, jas)
+    th = adjoint.get_theta(jas)
+    h = 1e-6
+    for p in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (jastrow.grad1_u(ri, rj, adjoint.set_theta(jas, tp))
+              - jastrow.grad1_u(ri, rj, adjoint.set_theta(jas, tm))) / (2 * h)
+        assert np.max(np.abs(fd - an[p])) < 1e-7 * max(1.0, np.max(np.abs(an[p]))), p
+
+
+def test_adjoint_gradient_matches_fd_of_loss():
+    """dL/dtheta of L = sum_c <Wbar^c, W^c> against central differences."""
+    from oracle import adjoint
+    w = wl.tiny_chain(n_atom=2, n_rad=6, n_ang=10, shells=(0, 1), n_mu=8, seed=6,
+                      jkind="bh", jterms=wl.bh_terms_c4()[:9])
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    Wbar = wl.seeded_matrix((4, w.n_mu, w.n_mu), 99)
+    jas = w.jastrow
+    jas.coef = jas.coef * 4.0
+    g = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, jas, Wbar, batch=37)
+    th = adjoint.get_theta(jas)
+    h = 1e-5
+    for p in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (adjoint.loss(w.grid_xyz, w.grid_w, xi, xit, adjoint.set_theta(jas, tp), Wbar)
+              - adjoint.loss(w.grid_xyz, w.grid_w, xi, xit, adjoint.set_theta(jas, tm), Wbar)) / (2 * h)
+        assert abs(fd - g[p]) < 1e-6 * max(1.0, abs(g[p])), (p, fd, g[p])
+
+
+def test_adjoint_linear_in_seed():
+    from oracle import adjoint
+    w = wl.tiny_chain(n_atom=2, n_rad=5, n_ang=8, shells=(0,), n_mu=3, seed=2,
+                      jkind="bh", jterms=wl.BH_TERMS_C3[:4])
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    A = wl.seeded_matrix((4, 3, 3), 1)
+    B = wl.seeded_matrix((4, 3, 3), 2)
+    gA = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, A)
+    gB = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, B)
+    gAB = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, 2.0 * A - 3.0 * B)
+    assert np.allclose(gAB, 2.0 * gA - 3.0 * gB, rtol=1e-10, atol=1e-12)
