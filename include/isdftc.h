@@ -50,7 +50,8 @@ typedef enum {
 typedef enum {
   ISDF_PREC_FP64 = 0,   /* FP64 on CUDA cores (the FP64 GPU path) */
   ISDF_PREC_BF16X3 = 1, /* tcgen05 BF16, 2-limb split (hi*hi + hi*lo + lo*hi), FP32 accumulation */
-  ISDF_PREC_BF16X6 = 2  /* tcgen05 BF16, 3-limb split (6 products), FP32 accumulation */
+  ISDF_PREC_BF16X6 = 2, /* tcgen05 BF16, 3-limb split (6 products), FP32 accumulation */
+  ISDF_PREC_FP32 = 3    /* FP32 on CUDA cores (adjoint) */
 } isdf_precision;
 
 /* Contracted Cartesian Gaussian basis (device arrays).  Function f is
@@ -177,6 +178,24 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
                     int64_t g_end, const isdf_jastrow* jas, const isdf_options* options,
                     double* W, double* calG, void* ws, size_t ws_bytes,
                     isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of the Jastrow kernels with respect to the correlator parameters
+ * (not in the paper).  For the seed Wbar [4][n_mu][n_mu] and
+ *   L(theta) = sum_c <Wbar^c, W^c(theta)>      (W of tc_kernel_build, full grid)
+ * writes dtheta[j] = dL/dtheta_j for theta = (d, b_0, c_0 .. c_{K-1}):
+ *   dL/dtheta_j = sum_{g != g'} sum_{c<3} (M^c + 2 M^sq K_c)(g,g') dK_c(g,g')/dtheta_j
+ *   M^c(g,g') = [(w xi~^c)^T Wbar^c (w xi)]_{g g'},  M^sq with w xi and Wbar^sq,
+ * recomputing the M tiles from the factors (nothing of size n_g^2 is stored).
+ * One nucleus type and at most 30 free terms (else ISDF_E_UNSUPPORTED);
+ * precision ISDF_PREC_FP64 or ISDF_PREC_FP32 (pair arithmetic; the
+ * reduction is FP64).  dtheta: device [2 + n_terms] FP64 (overwritten).
+ * Asynchronous. */
+size_t tc_kernel_adjoint_workspace(int64_t n_g, int n_mu, int n_nuc, int precision);
+int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
+                      const double* xi_grad, int64_t n_g, int n_mu, const isdf_jastrow* jas,
+                      const double* Wbar, int precision, double* dtheta, void* ws,
+                      size_t ws_bytes, isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * xTC density contraction, Terms 1 and 4 (Sec. III.B, Eq. delta-u-dx-kernels):

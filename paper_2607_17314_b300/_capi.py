@@ -17,8 +17,9 @@ ISDF_OK, ISDF_E_ARG, ISDF_E_NOT_PD, ISDF_E_RANK, ISDF_E_NONFINITE, ISDF_E_TIMEOU
 STATUS_NAMES = ["ISDF_OK", "ISDF_E_ARG", "ISDF_E_NOT_PD", "ISDF_E_RANK", "ISDF_E_NONFINITE",
                 "ISDF_E_TIMEOUT", "ISDF_E_CUDA", "ISDF_E_UNSUPPORTED"]
 
-ISDF_PREC_FP64, ISDF_PREC_BF16X3, ISDF_PREC_BF16X6 = 0, 1, 2
-PRECISIONS = {"fp64": ISDF_PREC_FP64, "bf16x3": ISDF_PREC_BF16X3, "bf16x6": ISDF_PREC_BF16X6}
+ISDF_PREC_FP64, ISDF_PREC_BF16X3, ISDF_PREC_BF16X6, ISDF_PREC_FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": ISDF_PREC_FP64, "bf16x3": ISDF_PREC_BF16X3, "bf16x6": ISDF_PREC_BF16X6,
+              "fp32": ISDF_PREC_FP32}
 
 ISDF_MAX_NUC, ISDF_MAX_TYPES, ISDF_MAX_TERMS = 64, 4, 32
 
@@ -64,6 +65,9 @@ SIGNATURES = {
     "tc_kernel_build_workspace": (SZ, [I64, INT, I64, I64, INT]),
     "tc_kernel_build": (INT, [P, P, P, P, I64, INT, I64, I64, ctypes.POINTER(IsdfJastrow),
                               ctypes.POINTER(IsdfOptions), P, P, P, SZ, P]),
+    "tc_kernel_adjoint_workspace": (SZ, [I64, INT, INT, INT]),
+    "tc_kernel_adjoint": (INT, [P, P, P, P, I64, INT, ctypes.POINTER(IsdfJastrow), P, INT, P, P,
+                                SZ, P]),
     "xtc_density_contract_workspace": (SZ, [I64, INT, INT, INT, INT]),
     "xtc_density_contract": (INT, [P, INT, INT, P, P, P, I64, INT, P, P, INT, P, SZ, P]),
     "tc_energies_workspace": (SZ, [INT, INT]),

@@ -215,3 +215,53 @@ def tc_energies(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
     C.check("tc_energies", lib.tc_energies(_ptr(W), _ptr(D), _ptr(Xp), _ptr(phi_piv), _ptr(dphi_piv),
                                            n_mu, n_orb, n_occ, out, _ptr(ws), ws.numel(), _stream()))
     return tuple(out)
+
+
+def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precision="fp32"):
+    """dL/dtheta for L = sum_c <Wbar^c, W^c>, theta = (d, b, c_0 .. c_{K-1})."""
+    lib = C.load()
+    for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad"), (Wbar, "Wbar")):
+        _req(t, f64, n)
+    n_mu, n_g = xi.shape
+    prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dtheta = torch.empty(2 + jastrow.n_terms, dtype=f64, device=xi.device)
+    ws = _ws(lib.tc_kernel_adjoint_workspace(n_g, n_mu, jastrow.n_nuc, prec), xi.device)
+    C.check("tc_kernel_adjoint", lib.tc_kernel_adjoint(
+        _ptr(grid_xyz), _ptr(w), _ptr(xi), _ptr(xig), n_g, n_mu, ctypes.byref(jastrow), _ptr(Wbar),
+        prec, _ptr(dtheta), _ptr(ws), ws.numel(), _stream()))
+    return dtheta
+
+
+def jastrow_with_theta(template: C.IsdfJastrow, theta) -> C.IsdfJastrow:
+    """Copy of a one-type correlator with theta = (d, b, c_0 .. c_{K-1})."""
+    J = C.IsdfJastrow()
+    ctypes.pointer(J)[0] = template
+    th = [float(x) for x in theta]
+    J.d = th[0]
+    J.b[0] = th[1]
+    for k in range(template.n_terms):
+        J.coef[0][k] = th[2 + k]
+    return J
+
+
+class TCKernel(torch.autograd.Function):
+    """W = {u1x, u1y, u1z, u3} as a differentiable function of the correlator
+    parameters theta.  Forward: FP64 kernel build; backward: the adjoint
+    kernel (dW/dtheta contracted with the incoming gradient), with the M
+    tiles recomputed instead of stored."""
+
+    @staticmethod
+    def forward(ctx, theta, grid_xyz, w, xi, xig, template, adjoint_precision="fp32"):
+        J = jastrow_with_theta(template, theta.detach().cpu().tolist())
+        W, _ = tc_kernel_build(grid_xyz, w, xi, xig, J, "fp64")
+        ctx.save_for_backward(grid_xyz, w, xi, xig)
+        ctx.J = J
+        ctx.prec = adjoint_precision
+        ctx.theta_device = theta.device
+        return W
+
+    @staticmethod
+    def backward(ctx, Wbar):
+        grid_xyz, w, xi, xig = ctx.saved_tensors
+        g = tc_kernel_adjoint(grid_xyz, w, xi, xig, ctx.J, Wbar.contiguous(), ctx.prec)
+        return g.to(ctx.theta_device), None, None, None, None, None, None

@@ -44,6 +44,9 @@ int xtc(const double*, int, int, const double*, const double*, const double*, in
 size_t energies_ws(int, int);
 int energies(const double*, const double*, const double*, const double*, const double*, int, int,
              int, double*, void*, size_t, cudaStream_t);
+size_t adjoint_ws(int64_t, int, int, int);
+int adjoint(const double*, const double*, const double*, const double*, int64_t, int,
+            const isdf_jastrow&, const double*, int, double*, void*, size_t, cudaStream_t);
 
 static int check_jastrow(const isdf_jastrow* J) {
   ISDF_ARG(J, "null Jastrow");
@@ -149,6 +152,21 @@ int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const doub
                          isdf_stream_t stream) {
   return xtc(phi_piv, n_orb, n_occ, xi, w, calG, n_g, n_mu, D, X_packed, n_orb_x, ws, ws_bytes,
              (cudaStream_t)stream);
+}
+
+size_t tc_kernel_adjoint_workspace(int64_t n_g, int n_mu, int n_nuc, int precision) {
+  return adjoint_ws(n_g, n_mu, n_nuc, precision);
+}
+
+int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
+                      const double* xi_grad, int64_t n_g, int n_mu, const isdf_jastrow* jas,
+                      const double* Wbar, int precision, double* dtheta, void* ws,
+                      size_t ws_bytes, isdf_stream_t stream) {
+  ISDF_TRY(check_jastrow(jas));
+  ISDF_ARG(precision == ISDF_PREC_FP64 || precision == ISDF_PREC_FP32,
+           "adjoint precision must be ISDF_PREC_FP64 or ISDF_PREC_FP32");
+  return adjoint(grid_xyz, w, xi, xi_grad, n_g, n_mu, *jas, Wbar, precision, dtheta, ws, ws_bytes,
+                 (cudaStream_t)stream);
 }
 
 size_t tc_energies_workspace(int n_mu, int n_occ) { return energies_ws(n_mu, n_occ); }
