@@ -236,6 +236,23 @@ int tc_energies(const double* W, const double* D, const double* X_packed,
                 const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
                 int n_occ, double* out, void* ws, size_t ws_bytes, isdf_stream_t stream);
 
+/* The energies call above without a workspace argument, for callers that
+ * cannot allocate device memory: code running inside another framework's
+ * memory pool (cudaMalloc may synchronise the device and fragments a pool it
+ * does not own) and latency-critical loops that must not block on an
+ * allocator.  The paper has no counterpart; this is an interface convenience.
+ * Arguments, layouts and results are those of tc_energies.  Its scratch is a
+ * fixed 16 MiB device array inside the library (held by every GPU that loads
+ * the library until exit); sizes needing more (6 n_mu n_occ^2 + 4 n_occ^4
+ * doubles plus alignment) return ISDF_E_ARG.  The first call on a device looks
+ * up the array's device address with that device current; make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams or host threads) race.  No device memory is allocated.
+ * Synchronises `stream`. */
+int tc_energies_noalloc(const double* W, const double* D, const double* X_packed,
+                        const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
+                        int n_occ, double* out, isdf_stream_t stream);
+
 /* Gather phi_p(r_mu) and d_c phi_p(r_mu): phi_piv [n_mu][n_orb],
  * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL).  Asynchronous. */
 int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,

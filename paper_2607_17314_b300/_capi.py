@@ -72,6 +72,7 @@ SIGNATURES = {
     "xtc_density_contract": (INT, [P, INT, INT, P, P, P, I64, INT, P, P, INT, P, SZ, P]),
     "tc_energies_workspace": (SZ, [INT, INT]),
     "tc_energies": (INT, [P, P, P, P, P, INT, INT, INT, P, P, SZ, P]),
+    "tc_energies_noalloc": (INT, [P, P, P, P, P, INT, INT, INT, P, P]),
 }
 
 _lib = None

@@ -47,6 +47,8 @@ int energies(const double*, const double*, const double*, const double*, const d
 size_t adjoint_ws(int64_t, int, int, int);
 int adjoint(const double*, const double*, const double*, const double*, int64_t, int,
             const isdf_jastrow&, const double*, int, double*, void*, size_t, cudaStream_t);
+int energies_noalloc(const double*, const double*, const double*, const double*, const double*,
+                     int, int, int, double*, cudaStream_t);
 
 static int check_jastrow(const isdf_jastrow* J) {
   ISDF_ARG(J, "null Jastrow");
@@ -176,6 +178,13 @@ int tc_energies(const double* W, const double* D, const double* X_packed, const 
                 size_t ws_bytes, isdf_stream_t stream) {
   return energies(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, n_occ, out, ws, ws_bytes,
                   (cudaStream_t)stream);
+}
+
+int tc_energies_noalloc(const double* W, const double* D, const double* X_packed,
+                        const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
+                        int n_occ, double* out, isdf_stream_t stream) {
+  return energies_noalloc(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, n_occ, out,
+                          (cudaStream_t)stream);
 }
 
 }  // extern "C"

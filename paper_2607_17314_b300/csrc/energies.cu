@@ -6,6 +6,8 @@
 //   K1[(p,r),(q,s)] = sum_c Ct^c^T W^c Cs,  K3 = Cs^T W^3 Cs
 //   T = K1 - K1swap + K3,  K^{pq}_{rs} = (T^{pq}_{rs} + T^{qp}_{sr}) / 2
 //   DeltaU^{pq}_{rs} = -(U^{pq}_{rs} + U^{qp}_{sr}),  U = Cs^T D Cs - Cs^T X
+#include <mutex>
+
 #include "linalg.cuh"
 
 namespace isdf {
@@ -153,6 +155,67 @@ int energies(const double* W, const double* D, const double* Xp, const double* p
   ISDF_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ISDF_CUDA(cudaStreamSynchronize(s));
   return ISDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the energies call.
+//
+// Some callers cannot allocate device memory: code that runs inside another
+// framework's memory pool (cudaMalloc may synchronise the device and
+// fragments a pool it does not own) and latency-critical loops that must not
+// block on an allocator.  For them the scratch of the energies call lives in
+// one fixed device array of this library instead of a caller workspace.  The
+// array is kEnergiesScratchBytes large and every GPU that loads the library
+// holds it until the process exits.  Its device address is looked up once per
+// device, with that device current, on the first call made on that device;
+// make that first call before any stream capture.  All calls share the array
+// and it keeps the last call's contents: every region the energies path reads
+// is written earlier in the same call, so nothing needs clearing, but calls
+// that overlap on the GPU (other streams, other host threads) race on it.
+
+namespace {
+
+constexpr size_t kEnergiesScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_energies_scratch[kEnergiesScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+int scratch_address(void** out) {
+  int dev = 0;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_ARG(dev >= 0 && dev < kMaxDevices, "device ordinal %d beyond the scratch table", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_energies_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("cudaGetSymbolAddress of the energies scratch failed on device %d: %s", dev,
+                cudaGetErrorString(e));
+      return ISDF_E_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return ISDF_OK;
+}
+
+}  // namespace
+
+int energies_noalloc(const double* W, const double* D, const double* Xp, const double* phiP,
+                     const double* dphiP, int n_mu, int n_orb, int n, double* out_host,
+                     cudaStream_t s) {
+  ISDF_ARG(n > 0 && n <= n_orb && n_mu > 0, "bad sizes");
+  const size_t need = energies_ws(n_mu, n);
+  ISDF_ARG(need <= kEnergiesScratchBytes,
+           "n_mu = %d with n_occ = %d needs %zu bytes of scratch; the allocation-free call "
+           "holds %zu bytes (use tc_energies with a workspace)",
+           n_mu, n, need, kEnergiesScratchBytes);
+  void* scratch = nullptr;
+  ISDF_TRY(scratch_address(&scratch));
+  return energies(W, D, Xp, phiP, dphiP, n_mu, n_orb, n, out_host, scratch,
+                  kEnergiesScratchBytes, s);
 }
 
 }  // namespace isdf
