@@ -198,6 +198,63 @@ int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
                       size_t ws_bytes, isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned interpolation-point proposer (not in the paper).  A network
+ * s = W3 relu(W2 relu(W1 x + b1) + b2) + b3 (8 -> 128 -> 128 -> 1) scores grid
+ * points; the highest-scoring kappa N_mu points form a candidate set on which
+ * the plain pivoted Cholesky (isdf_points) runs; the scalar-channel fit error
+ * judges the result against the plain selection, which stays the fallback.
+ * params: device FP32 [isdf_mlp_n_params()] laid out W1 [128][8], b1 [128],
+ * W2 [128][128], b2 [128], W3 [128], b3; the forward uses their BF16
+ * roundings with FP32 arithmetic. */
+int isdf_mlp_n_params(void);
+
+/* Per-point features feat [n_g][8] (FP32): log10 of the scalar and gradient
+ * pivot diagonals w^2 rho^2 and w^2 rho tau (Alg. 1, Sec. II.D), of w, rho =
+ * sum_p phi_p^2 and tau = sum_{c,p} (d_c phi_p)^2 (each / 10), the distances to
+ * the two nearest nuclei / 5, and log10(r_1 + 1e-3).  nuc_xyz: HOST
+ * [n_nuc][3] (n_nuc <= ISDF_MAX_NUC).  Asynchronous. */
+int isdf_mlp_features(const double* phi, const double* dphi, const double* w,
+                      const double* grid_xyz, int64_t n_g, int n_orb, const double* nuc_xyz,
+                      int n_nuc, float* feat, isdf_stream_t stream);
+
+/* scores[n] = network(feat[n][8]).  Asynchronous. */
+int isdf_mlp_forward(const float* params, const float* feat, int64_t n, float* scores,
+                     isdf_stream_t stream);
+
+/* Adds to grad [n_params] the gradient of (1/n_total) sum over these n points of
+ * the weighted binary cross-entropy pos_w y softplus(-s) + (1 - y) softplus(s)
+ * (labels y in {0, 1}), and adds the unnormalised loss sum to *loss (device
+ * FP64).  Gradients pass through the BF16 rounding unchanged.  Asynchronous. */
+int isdf_mlp_backward(const float* params, const float* feat, const float* labels, int64_t n,
+                      float pos_w, int64_t n_total, float* grad, double* loss,
+                      isdf_stream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with the
+ * 1-based step count) on params with moments m, v [n_params].  Asynchronous. */
+int isdf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
+                  isdf_stream_t stream);
+
+/* out[k] = indices of the k highest scores (ties by lowest index), ascending.
+ * Asynchronous. */
+int isdf_mlp_topk(const float* scores, int64_t n, int k, int32_t* out, isdf_stream_t stream);
+
+/* isdf_points (fused mode) on the candidate points cand[n_cand] only; pivots
+ * receive grid indices.  Synchronises `stream`; ISDF_E_RANK as isdf_points. */
+size_t isdf_points_restricted_workspace(int n_cand, int n_orb, int n_mu);
+int isdf_points_restricted(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                           int n_orb, const int32_t* cand, int n_cand, int n_mu, int32_t* pivots,
+                           int* n_mu_out, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* Scalar-channel ISDF fit error of a pivot set over the whole grid:
+ *   *eps = sum_g w_g^2 [(sum_p phi_p^2)^2 - sum_mu xi_mu(g) G_{mu g}^2] / sum_g w_g^2 (sum_p phi_p^2)^2
+ * with xi from the FP64 normal equations of Eq. isdf-rho (the weighted
+ * Frobenius residual).  eps host.  Synchronises `stream`. */
+size_t isdf_fit_error_workspace(int64_t n_g, int n_orb, int n_mu);
+int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
+                   const int32_t* pivots, int n_mu, double* eps, void* ws, size_t ws_bytes,
+                   isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * xTC density contraction, Terms 1 and 4 (Sec. III.B, Eq. delta-u-dx-kernels):
  *   G_nu  = sum_{i < n_occ} phi_i(r_nu)^2          (closed-shell HF projector)
  *   w~_g  = w_g sum_l G_l xi_l(g)

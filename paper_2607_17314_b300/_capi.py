@@ -68,6 +68,17 @@ SIGNATURES = {
     "tc_kernel_adjoint_workspace": (SZ, [I64, INT, INT, INT]),
     "tc_kernel_adjoint": (INT, [P, P, P, P, I64, INT, ctypes.POINTER(IsdfJastrow), P, INT, P, P,
                                 SZ, P]),
+    "isdf_mlp_n_params": (INT, []),
+    "isdf_mlp_features": (INT, [P, P, P, P, I64, INT, P, INT, P, P]),
+    "isdf_mlp_forward": (INT, [P, P, I64, P, P]),
+    "isdf_mlp_backward": (INT, [P, P, P, I64, ctypes.c_float, I64, P, P, P]),
+    "isdf_mlp_adam": (INT, [P, P, P, P, INT, ctypes.c_float, P]),
+    "isdf_mlp_topk": (INT, [P, I64, INT, P, P]),
+    "isdf_points_restricted_workspace": (SZ, [INT, INT, INT]),
+    "isdf_points_restricted": (INT, [P, P, P, I64, INT, P, INT, INT, P, ctypes.POINTER(INT), P,
+                                     SZ, P]),
+    "isdf_fit_error_workspace": (SZ, [I64, INT, INT]),
+    "isdf_fit_error": (INT, [P, P, I64, INT, P, INT, ctypes.POINTER(ctypes.c_double), P, SZ, P]),
     "xtc_density_contract_workspace": (SZ, [I64, INT, INT, INT, INT]),
     "xtc_density_contract": (INT, [P, INT, INT, P, P, P, I64, INT, P, P, INT, P, SZ, P]),
     "tc_energies_workspace": (SZ, [INT, INT]),

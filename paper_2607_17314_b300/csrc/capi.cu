@@ -47,6 +47,20 @@ int energies(const double*, const double*, const double*, const double*, const d
 size_t adjoint_ws(int64_t, int, int, int);
 int adjoint(const double*, const double*, const double*, const double*, int64_t, int,
             const isdf_jastrow&, const double*, int, double*, void*, size_t, cudaStream_t);
+int mlp_n_params();
+int mlp_features(const double*, const double*, const double*, const double*, int64_t, int,
+                 const double*, int, float*, cudaStream_t);
+int mlp_forward(const float*, const float*, int64_t, float*, cudaStream_t);
+int mlp_backward(const float*, const float*, const float*, int64_t, float, int64_t, float*, double*,
+                 cudaStream_t);
+int mlp_adam(float*, const float*, float*, float*, int, float, cudaStream_t);
+int mlp_topk(const float*, int64_t, int, int32_t*, cudaStream_t);
+size_t points_restricted_ws(int, int, int);
+int points_restricted(const double*, const double*, const double*, int64_t, int, const int32_t*,
+                      int, int, int32_t*, int*, void*, size_t, cudaStream_t);
+size_t fit_error_ws(int64_t, int, int);
+int fit_error(const double*, const double*, int64_t, int, const int32_t*, int, double*, void*,
+              size_t, cudaStream_t);
 int energies_noalloc(const double*, const double*, const double*, const double*, const double*,
                      int, int, int, double*, cudaStream_t);
 
@@ -169,6 +183,56 @@ int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
            "adjoint precision must be ISDF_PREC_FP64 or ISDF_PREC_FP32");
   return adjoint(grid_xyz, w, xi, xi_grad, n_g, n_mu, *jas, Wbar, precision, dtheta, ws, ws_bytes,
                  (cudaStream_t)stream);
+}
+
+int isdf_mlp_n_params(void) { return mlp_n_params(); }
+
+int isdf_mlp_features(const double* phi, const double* dphi, const double* w,
+                      const double* grid_xyz, int64_t n_g, int n_orb, const double* nuc_xyz,
+                      int n_nuc, float* feat, isdf_stream_t stream) {
+  return mlp_features(phi, dphi, w, grid_xyz, n_g, n_orb, nuc_xyz, n_nuc, feat,
+                      (cudaStream_t)stream);
+}
+
+int isdf_mlp_forward(const float* params, const float* feat, int64_t n, float* scores,
+                     isdf_stream_t stream) {
+  return mlp_forward(params, feat, n, scores, (cudaStream_t)stream);
+}
+
+int isdf_mlp_backward(const float* params, const float* feat, const float* labels, int64_t n,
+                      float pos_w, int64_t n_total, float* grad, double* loss,
+                      isdf_stream_t stream) {
+  return mlp_backward(params, feat, labels, n, pos_w, n_total, grad, loss, (cudaStream_t)stream);
+}
+
+int isdf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
+                  isdf_stream_t stream) {
+  return mlp_adam(params, grad, m, v, step, lr, (cudaStream_t)stream);
+}
+
+int isdf_mlp_topk(const float* scores, int64_t n, int k, int32_t* out, isdf_stream_t stream) {
+  return mlp_topk(scores, n, k, out, (cudaStream_t)stream);
+}
+
+size_t isdf_points_restricted_workspace(int n_cand, int n_orb, int n_mu) {
+  return points_restricted_ws(n_cand, n_orb, n_mu);
+}
+
+int isdf_points_restricted(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                           int n_orb, const int32_t* cand, int n_cand, int n_mu, int32_t* pivots,
+                           int* n_mu_out, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  return points_restricted(phi, dphi, w, n_g, n_orb, cand, n_cand, n_mu, pivots, n_mu_out, ws,
+                           ws_bytes, (cudaStream_t)stream);
+}
+
+size_t isdf_fit_error_workspace(int64_t n_g, int n_orb, int n_mu) {
+  return fit_error_ws(n_g, n_orb, n_mu);
+}
+
+int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
+                   const int32_t* pivots, int n_mu, double* eps, void* ws, size_t ws_bytes,
+                   isdf_stream_t stream) {
+  return fit_error(phi, w, n_g, n_orb, pivots, n_mu, eps, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 size_t tc_energies_workspace(int n_mu, int n_occ) { return energies_ws(n_mu, n_occ); }

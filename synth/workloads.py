@@ -463,6 +463,20 @@ def h30_chain_perturbed(k: int, n_rad: int = 40, n_ang: int = 50) -> Workload:
                      240, 15, 1200, "radial", seed + 1)
 
 
+def perturbed_chain(k: int, n_atom: int = 30, n_rad: int = 40, n_ang: int = 50,
+                    n_mu: int = 1200, shells=(0, 0, 1, 1), base_seed: int = 5001) -> Workload:
+    """Geometry k of a perturbed H_n family: spacing s ~ U(1.6, 2.2) bohr plus
+    0.05 bohr per-atom jitter along z; cusp-only Jastrow."""
+    seed = base_seed + 7 * k
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(1.6, 2.2)
+    z = np.arange(n_atom) * s + rng.uniform(-0.05, 0.05, size=n_atom)
+    atoms, xyz = h_chain_positions(z)
+    n_orb = n_atom * sum(len(cart_tuples(l)) for l in shells)
+    return _assemble(f"h{n_atom}_{k}", atoms, xyz, n_rad, n_ang, {"H": list(shells)}, n_orb,
+                     n_orb // 16 or 1, n_mu, "radial", seed + 1)
+
+
 def tiny_chain(n_atom: int = 2, n_rad: int = 10, n_ang: int = 16,
                shells=(0,), n_orb: Optional[int] = None, n_mu: int = 8,
                spacing: float = 1.6, seed: int = 7, jkind: str = "radial",

@@ -415,3 +415,63 @@ def test_adjoint_linear_in_seed():
     gB = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, B)
     gAB = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, 2.0 * A - 3.0 * B)
     assert np.allclose(gAB, 2.0 * gA - 3.0 * gB, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- learned proposer
+
+def test_mlp_gradient_matches_fd():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((40, mlp.F))
+    y = (rng.random(40) < 0.2).astype(float)
+    th = mlp.init_params(1) + 0.01 * rng.standard_normal(mlp.N_PARAMS)
+    l, g = mlp.loss_and_grad(th, x, y, 4.0, rounding=False)
+    h = 1e-6
+    for p in rng.choice(mlp.N_PARAMS, 25, replace=False).tolist() + [mlp.N_PARAMS - 1]:
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (mlp.loss_and_grad(tp, x, y, 4.0, False)[0] - mlp.loss_and_grad(tm, x, y, 4.0, False)[0]) / (2 * h)
+        assert abs(fd - g[p]) < 1e-7 * max(1.0, abs(g[p])), (p, fd, g[p])
+
+
+def test_mlp_bce_at_zero_logit_and_bf16_rounding():
+    from oracle import mlp
+    th = np.zeros(mlp.N_PARAMS)
+    x = np.ones((10, mlp.F))
+    y = np.array([1.0, 0, 0, 1, 0, 0, 0, 0, 0, 0])
+    l, _ = mlp.loss_and_grad(th, x, y, 3.0)
+    # softplus(0) = log 2 for every point, weighted by 3 for the two positives
+    assert abs(l - math.log(2.0) * (3.0 * 2 + 8) / 10) < 1e-15
+    # bf16 rounding: exactly representable values are fixed points, ties go to even
+    vals = np.array([1.0, 1.0 + 2 ** -7, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 3.0e-30])
+    r = mlp.bf16_round(vals)
+    assert r[0] == 1.0 and r[1] == 1.0 + 2 ** -7
+    assert r[2] == 1.0                    # halfway, rounds to the even neighbour 1.0
+    assert r[3] == 1.0 + 2 ** -6          # halfway, rounds to the even neighbour
+    assert r[4] == -2.5
+    assert abs(r[5] - 3.0e-30) < 3.0e-30 * 2 ** -8
+
+
+def test_adam_first_step_is_sign_step():
+    from oracle import mlp
+    th = np.array([0.5, -1.0, 2.0])
+    g = np.array([3.0, -0.2, 1e-3])
+    new, m, v = mlp.adam(th, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    # bias-corrected first moments equal g and g^2: the step is lr * g / (|g| + eps)
+    assert np.allclose(new, th - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_candidates_and_fit_error():
+    from oracle import mlp
+    s = np.array([0.5, 2.0, 2.0, -1.0, 0.7, 2.0, 0.1])
+    assert mlp.candidates(s, 2).tolist() == [1, 2]      # ties by lowest index
+    assert mlp.candidates(s, 4).tolist() == [1, 2, 4, 5]
+    # at full scalar rank the fit error vanishes
+    w = wl.tiny_chain(n_atom=3, n_rad=16, n_ang=26, shells=(0,), seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, 6, mode="scalar")
+    assert mlp.fit_error(phi, w.grid_w, res.piv_s) < 1e-12
+    res3 = pivots.select(phi, dphi, w.grid_w, 3, mode="scalar")
+    e3 = mlp.fit_error(phi, w.grid_w, res3.piv_s)
+    assert 0 < e3 < 1
