@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--w-only", action="store_true",
                     help="profiling mode: time only the W build on an H50-chain grid with "
                          "--w-nrad radial shells and seeded random xi (N_mu = --w-nmu)")
+    ap.add_argument("--proposer", action="store_true",
+                    help="learned proposer on perturbed H30 chains (60,000 points, 240 orbitals, "
+                         "N_mu = 1200): train on --n-train, report on --n-test held-out chains")
+    ap.add_argument("--n-train", type=int, default=24)
+    ap.add_argument("--n-test", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--kappa", type=float, default=3.0)
     ap.add_argument("--w-nrad", type=int, default=16)
     ap.add_argument("--w-nmu", type=int, default=1024)
     return ap.parse_args()
@@ -210,6 +217,73 @@ def run_w_only(args):
                       "s1_alg_tflops": fl1 / (min(s1) * 1e-3) / 1e12}), flush=True)
 
 
+def _chain(k):
+    from synth import workloads as wl
+    return wl.perturbed_chain(k)
+
+
+def run_proposer(args):
+    """Learned interpolation-point proposer at the perturbed-H30 scale."""
+    import multiprocessing as mp
+    ks = list(range(args.n_train)) + list(range(1000, 1000 + args.n_test))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        chains = pool.map(_chain, ks)
+    import torch
+    from paper_2607_17314_b300 import api, build, proposer as PR
+    build.build()
+
+    def cu(a, dt=torch.float64):
+        return torch.as_tensor(np.ascontiguousarray(a)).to(dt).cuda()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    samples, plain_ms = [], []
+    for w in chains:
+        b = w.basis
+        phi, dphi = api.isdf_eval_orbitals(cu(b.center), cu(b.powers, torch.int32), cu(b.exps),
+                                           cu(b.coefs), cu(w.mo_coef), cu(w.grid_xyz))
+        wt = cu(w.grid_w)
+        e0 = ev()
+        plain = api.isdf_points(phi, dphi, wt, w.n_mu)
+        e1 = ev()
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+        labels = torch.zeros(w.n_g, dtype=torch.float32, device="cuda")
+        labels[plain.long()] = 1.0
+        feat = PR.features(phi, dphi, wt, cu(w.grid_xyz), w.xyz)
+        samples.append(PR.Sample(feat=feat, labels=labels, phi=phi, dphi=dphi, w=wt, plain=plain,
+                                 n_mu=w.n_mu))
+    train, test = samples[:args.n_train], samples[args.n_train:]
+    prop = PR.Proposer(seed=0, lr=3e-3)
+    e0 = ev()
+    losses = [prop.train_epoch(train) for _ in range(args.epochs)]
+    e1 = ev()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    rows = []
+    for smp, pm in zip(test, plain_ms[args.n_train:]):
+        e0 = ev()
+        piv = prop.propose(smp, args.kappa)
+        e1 = ev()
+        torch.cuda.synchronize()
+        ep = PR.fit_error(smp.phi, smp.w, piv)
+        el = PR.fit_error(smp.phi, smp.w, smp.plain)
+        overlap = len(set(piv.cpu().tolist()) & set(smp.plain.cpu().tolist())) / smp.n_mu
+        rows.append({"plain_ms": pm, "proposal_ms": e0.elapsed_time(e1), "eps_plain": el,
+                     "eps_proposal": ep, "ratio": ep / el, "overlap": overlap})
+    line = {"mode": "proposer", "workload": "perturbed H30 chains", "n_g": int(test[0].feat.shape[0]),
+            "n_mu": test[0].n_mu, "n_train": args.n_train, "n_test": args.n_test,
+            "epochs": args.epochs, "kappa": args.kappa, "train_ms": train_ms,
+            "loss_first": losses[0], "loss_last": losses[-1],
+            "median_selection_speedup": float(np.median([r["plain_ms"] / r["proposal_ms"] for r in rows])),
+            "median_fit_error_ratio": float(np.median([r["ratio"] for r in rows])),
+            "per_chain": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -218,6 +292,8 @@ def main():
         return run_reference(args, rank, world)
     if args.w_only:
         return run_w_only(args)
+    if args.proposer:
+        return run_proposer(args)
 
     import torch
     import torch.distributed as dist

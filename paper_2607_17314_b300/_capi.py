@@ -79,8 +79,8 @@ SIGNATURES = {
                                      SZ, P]),
     "isdf_fit_error_workspace": (SZ, [I64, INT, INT]),
     "isdf_fit_error": (INT, [P, P, I64, INT, P, INT, ctypes.POINTER(ctypes.c_double), P, SZ, P]),
-    "xtc_density_contract_workspace": (SZ, [I64, INT, INT, INT, INT]),
-    "xtc_density_contract": (INT, [P, INT, INT, P, P, P, I64, INT, P, P, INT, P, SZ, P]),
+    "xtc_density_contract_workspace": (SZ, [I64, INT, INT, INT, INT, INT]),
+    "xtc_density_contract": (INT, [P, INT, INT, P, P, P, I64, INT, P, P, INT, INT, P, SZ, P]),
     "tc_energies_workspace": (SZ, [INT, INT]),
     "tc_energies": (INT, [P, P, P, P, P, INT, INT, INT, P, P, SZ, P]),
     "tc_energies_noalloc": (INT, [P, P, P, P, P, INT, INT, INT, P, P]),

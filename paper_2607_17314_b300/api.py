@@ -191,18 +191,20 @@ def kernel_launches() -> int:
     return int(C.load().isdf_kernel_launches())
 
 
-def xtc_density_contract(phi_piv, n_occ: int, xi, w, calG, n_orb_x: int = 0):
+def xtc_density_contract(phi_piv, n_occ: int, xi, w, calG, n_orb_x: int = 0,
+                         precision="fp64"):
     """D [n_mu][n_mu] and (n_orb_x > 0) X packed [n_orb_x(n_orb_x+1)/2][n_mu]."""
     lib = C.load()
     dev = xi.device
     n_mu, n_g = xi.shape
     n_orb = phi_piv.shape[1]
+    prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     D = torch.empty((n_mu, n_mu), dtype=f64, device=dev)
     Xp = torch.empty((n_orb_x * (n_orb_x + 1) // 2, n_mu), dtype=f64, device=dev) if n_orb_x > 0 else None
-    ws = _ws(lib.xtc_density_contract_workspace(n_g, n_mu, n_orb, n_occ, n_orb_x), dev)
+    ws = _ws(lib.xtc_density_contract_workspace(n_g, n_mu, n_orb, n_occ, n_orb_x, prec), dev)
     C.check("xtc_density_contract", lib.xtc_density_contract(
         _ptr(phi_piv), n_orb, n_occ, _ptr(xi), _ptr(w), _ptr(calG), n_g, n_mu, _ptr(D), _ptr(Xp),
-        n_orb_x, _ptr(ws), ws.numel(), _stream()))
+        n_orb_x, prec, _ptr(ws), ws.numel(), _stream()))
     return D, Xp
 
 

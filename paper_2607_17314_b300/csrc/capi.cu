@@ -38,9 +38,9 @@ size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int);
 int wbuild_tc(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
               int64_t, const isdf_jastrow&, const isdf_options&, double*, double*, void*, size_t,
               cudaStream_t);
-size_t xtc_ws(int64_t, int, int, int, int);
+size_t xtc_ws(int64_t, int, int, int, int, int);
 int xtc(const double*, int, int, const double*, const double*, const double*, int64_t, int,
-        double*, double*, int, void*, size_t, cudaStream_t);
+        double*, double*, int, int, void*, size_t, cudaStream_t);
 size_t energies_ws(int, int);
 int energies(const double*, const double*, const double*, const double*, const double*, int, int,
              int, double*, void*, size_t, cudaStream_t);
@@ -158,16 +158,17 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
                    ws_bytes, s);
 }
 
-size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x) {
-  return xtc_ws(n_g, n_mu, n_orb, n_occ, n_orb_x);
+size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x,
+                                      int precision) {
+  return xtc_ws(n_g, n_mu, n_orb, n_occ, n_orb_x, precision);
 }
 
 int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const double* xi,
                          const double* w, const double* calG, int64_t n_g, int n_mu, double* D,
-                         double* X_packed, int n_orb_x, void* ws, size_t ws_bytes,
+                         double* X_packed, int n_orb_x, int precision, void* ws, size_t ws_bytes,
                          isdf_stream_t stream) {
-  return xtc(phi_piv, n_orb, n_occ, xi, w, calG, n_g, n_mu, D, X_packed, n_orb_x, ws, ws_bytes,
-             (cudaStream_t)stream);
+  return xtc(phi_piv, n_orb, n_occ, xi, w, calG, n_g, n_mu, D, X_packed, n_orb_x, precision, ws,
+             ws_bytes, (cudaStream_t)stream);
 }
 
 size_t tc_kernel_adjoint_workspace(int64_t n_g, int n_mu, int n_nuc, int precision) {

@@ -257,17 +257,53 @@ int points(const double* phi, const double* dphi, const double* w, int64_t n_g, 
   tol_init_kernel<<<1, PT, 0, s>>>(a);
   ISDF_LAUNCH_CHECK();
   const int max_iter = 2 * n_mu + 4;
+  // Steps run in batches of 32 launches replayed from a CUDA graph on a private
+  // stream (the launch cost dominates the short steps of small grids); the host
+  // reads the step state between batches to stop.  Steps past the end are no-ops.
+  constexpr int kBatch = 32;
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  cudaStream_t ps = nullptr;
+  ISDF_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = false;
+  if (cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    for (int b = 0; b < kBatch; ++b) pivot_step_kernel<<<a.nblk, PT, 0, ps>>>(a, b & 1, mode);
+    if (cudaStreamEndCapture(ps, &graph) == cudaSuccess &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+      use_graph = true;
+  }
+  (void)cudaGetLastError();
   PivState h;
   int it = 0;
+  int rc = ISDF_OK;
   for (;;) {
-    const int batch = 32;
-    for (int b = 0; b < batch && it < max_iter; ++b, ++it) {
-      pivot_step_kernel<<<a.nblk, PT, 0, s>>>(a, it & 1, mode);
-      ISDF_LAUNCH_CHECK();
+    if (use_graph) {
+      if (cudaGraphLaunch(exec, ps) != cudaSuccess) { rc = ISDF_E_CUDA; break; }
+      for (int b = 0; b < kBatch; ++b) count_launch();
+      it += kBatch;
+    } else {
+      for (int b = 0; b < kBatch && it < max_iter; ++b, ++it) {
+        pivot_step_kernel<<<a.nblk, PT, 0, ps>>>(a, it & 1, mode);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) { rc = ISDF_E_CUDA; break; }
+      }
+      if (rc != ISDF_OK) break;
     }
-    ISDF_CUDA(cudaMemcpyAsync(&h, a.st + (it & 1), sizeof(PivState), cudaMemcpyDeviceToHost, s));
-    ISDF_CUDA(cudaStreamSynchronize(s));
+    if (cudaMemcpyAsync(&h, a.st + (it & 1), sizeof(PivState), cudaMemcpyDeviceToHost, ps) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ps) != cudaSuccess) {
+      rc = ISDF_E_CUDA;
+      break;
+    }
     if (h.nu >= n_mu || (h.done[0] && h.done[1]) || it >= max_iter) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(ps);
+  if (rc != ISDF_OK) {
+    set_error("pivot step launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
   }
   *n_mu_out = h.nu;
   if (h.nu > 0)

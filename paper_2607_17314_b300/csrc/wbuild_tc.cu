@@ -122,7 +122,9 @@ __global__ void coords_kernel(const double* __restrict__ grid, int64_t n_g, int6
 
 // ------------------------------------------------------------------ stage 1
 
-// Tile: 128 nu (M) x 64 g (N) per CTA, 32 inner points g' per stage.  Tensor
+// Tile: 128 nu (M) x 64 g (N) per CTA, 32 inner points g' per stage; the B
+// tiles of one limb for the four channels are stored back to back (limb-major)
+// and consumed by one N = 256 MMA per limb product.  Tensor
 // memory holds one FP32 chunk accumulator (4 channels x 64 columns) that the
 // MMAs fill over kchunk inner points, and an FP32 running sum of the same
 // shape into which the epilogue warps fold each chunk with IEEE-rounded adds.
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
   } else if (warp == 1) {
     // MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16(128, C::BN, 1);
+      constexpr uint32_t idesc = tc::idesc_f16(128, 4 * C::BN, 1);
       uint32_t it = 0, u = 0;
       for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
@@ -330,20 +332,20 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
             const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE);
             const uint32_t b_base = a_base + C::A_BYTES;
             const bool first = (k0 == kb);
+            // one N = 256 MMA covers the four channels: the limb-j tiles of
+            // channels 0..3 are contiguous, so A is read once per product
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+            for (int i = 0; i < LIMBS; ++i)
 #pragma unroll
-              for (int i = 0; i < LIMBS; ++i)
+              for (int j = 0; j < LIMBS - i; ++j)
 #pragma unroll
-                for (int j = 0; j < LIMBS - i; ++j)
-#pragma unroll
-                  for (int kk = 0; kk < 2; ++kk) {
-                    const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
-                    const uint64_t bd =
-                        tc::smem_desc(b_base + (c * LIMBS + j) * C::B_TILE + kk * 32, 16, 512, 4);
-                    const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                    tc::umma_f16(tmem + c * C::BN, ad, bd, idesc, acc);
-                  }
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
+                  const uint64_t bd =
+                      tc::smem_desc(b_base + j * 4 * C::B_TILE + kk * 32, 16, 512, 4);
+                  const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                  tc::umma_f16(tmem, ad, bd, idesc, acc);
+                }
             tc::umma_commit(&empty[s]);
           }
           tc::umma_commit(acc_full);
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
         for (int c = 0; c < 4; ++c)
 #pragma unroll
           for (int l = 0; l < LIMBS; ++l)
-            tc::sts_u4(bsm + (c * LIMBS + l) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
+            tc::sts_u4(bsm + (l * 4 + c) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
                        pk[c][l][3]);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&full[s]);

@@ -15,7 +15,18 @@
 #include "linalg.cuh"
 
 namespace isdf {
+
+int split_operand(const double* src, int64_t src_rs, int64_t c0, const double* colw, int64_t rows,
+                  int64_t cols, int64_t rows_pad, int64_t cols_pad, int limbs, void* dst,
+                  cudaStream_t s);
+int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, int64_t M,
+              int64_t N, int64_t Kp, int64_t kchunk, int64_t fold, double* out, int64_t ldo,
+              int64_t out_bs, double scale, int* err, cudaStream_t s);
+
 namespace {
+
+// grid points per tensor-core chunk of the D contraction
+constexpr int64_t DCHUNK = 32768;
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t); }
 
@@ -97,13 +108,19 @@ constexpr int64_t XBATCH = 4096;
 
 }  // namespace
 
-size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x) {
+size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x, int precision) {
   (void)n_orb;
   Carve c(nullptr, 0);
   c.take<double>(n_mu);
   c.take<double>(n_g);
   c.take<double>(3 * n_g);
   c.take<double>((size_t)n_mu * n_g);
+  if (precision != ISDF_PREC_FP64) {
+    const int limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+    const int64_t mp = round_up(n_mu, 128), kc = DCHUNK < round_up(n_g, 32) ? DCHUNK : round_up(n_g, 32);
+    c.take<uint16_t>((size_t)8 * limbs * mp * kc);
+    c.take<int>(64);
+  }
   if (n_orb_x > 0) {
     const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
     const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
@@ -115,8 +132,11 @@ size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x) {
 }
 
 int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double* w,
-        const double* calG, int64_t n_g, int n_mu, double* D, double* Xp, int n_orb_x, void* ws,
-        size_t ws_bytes, cudaStream_t s) {
+        const double* calG, int64_t n_g, int n_mu, double* D, double* Xp, int n_orb_x,
+        int precision, void* ws, size_t ws_bytes, cudaStream_t s) {
+  ISDF_ARG(precision == ISDF_PREC_FP64 || precision == ISDF_PREC_BF16X3 ||
+               precision == ISDF_PREC_BF16X6,
+           "xtc precision must be FP64, BF16X3 or BF16X6");
   ISDF_ARG(phiP && xi && w && calG && D, "null pointer argument");
   ISDF_ARG(n_occ >= 0 && n_occ <= n_orb && n_mu > 0 && n_g > 0, "bad sizes");
   ISDF_ARG(!Xp || (n_orb_x >= 1 && n_orb_x <= n_orb), "n_orb_x out of range");
@@ -126,6 +146,15 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
   double* wt = cv.take<double>(n_g);
   double* H = cv.take<double>(3 * n_g);
   double* V = cv.take<double>((size_t)n_mu * n_g);
+  const int limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  const int64_t mp = round_up(n_mu, 128);
+  const int64_t kc = DCHUNK < round_up(n_g, 32) ? DCHUNK : round_up(n_g, 32);
+  uint16_t* ops = nullptr;
+  int* err = nullptr;
+  if (precision != ISDF_PREC_FP64) {
+    ops = cv.take<uint16_t>((size_t)8 * limbs * mp * kc);
+    err = cv.take<int>(64);
+  }
   double *P = nullptr, *F = nullptr, *Q = nullptr;
   const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
   const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
@@ -145,19 +174,19 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
   ISDF_LAUNCH_CHECK();
   v_kernel<<<nb(plane), 256, 0, s>>>(H, calG, n_mu, n_g, V);
   ISDF_LAUNCH_CHECK();
-  // D4 = sum_c (calG^c o w~) calG^c^T
-  for (int c = 0; c < 3; ++c) {
-    Dgemm g;
-    g.M = n_mu; g.N = n_mu; g.K = n_g;
-    g.A = calG + c * plane; g.a_rs = n_g; g.a_cs = 1; g.a_bs = 0;
-    g.B = calG + c * plane; g.b_rs = 1; g.b_cs = n_g; g.b_bs = 0;
-    g.C = D; g.ldc = n_mu; g.c_bs = 0;
-    g.kscale = wt;
-    g.beta = c == 0 ? 0.0 : 1.0;
-    ISDF_TRY(dgemm(g, s));
-  }
-  // D += 2 (w xi) V^T
-  {
+  if (precision == ISDF_PREC_FP64) {
+    // D4 = sum_c (calG^c o w~) calG^c^T
+    for (int c = 0; c < 3; ++c) {
+      Dgemm g;
+      g.M = n_mu; g.N = n_mu; g.K = n_g;
+      g.A = calG + c * plane; g.a_rs = n_g; g.a_cs = 1; g.a_bs = 0;
+      g.B = calG + c * plane; g.b_rs = 1; g.b_cs = n_g; g.b_bs = 0;
+      g.C = D; g.ldc = n_mu; g.c_bs = 0;
+      g.kscale = wt;
+      g.beta = c == 0 ? 0.0 : 1.0;
+      ISDF_TRY(dgemm(g, s));
+    }
+    // D += 2 (w xi) V^T
     Dgemm g;
     g.M = n_mu; g.N = n_mu; g.K = n_g;
     g.A = xi; g.a_rs = n_g; g.a_cs = 1; g.a_bs = 0;
@@ -166,6 +195,41 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
     g.kscale = w;
     g.alpha = 2.0; g.beta = 1.0;
     ISDF_TRY(dgemm(g, s));
+  } else {
+    // the same contractions as split-BF16 tcgen05 GEMMs over grid chunks
+    ISDF_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n_mu * n_mu, s));
+    ISDF_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
+    const size_t opl = (size_t)limbs * mp * kc;
+    for (int64_t g0 = 0; g0 < n_g; g0 += kc) {
+      const int64_t cols = g0 + kc <= n_g ? kc : n_g - g0;
+      const int64_t kp = round_up(cols, 32);
+      const void* A[4];
+      const void* B[4];
+      for (int c = 0; c < 3; ++c) {
+        uint16_t* a = ops + (2 * c) * opl;
+        uint16_t* b = ops + (2 * c + 1) * opl;
+        ISDF_TRY(split_operand(calG + c * plane, n_g, g0, wt, n_mu, cols, mp, kp, limbs, a, s));
+        ISDF_TRY(split_operand(calG + c * plane, n_g, g0, nullptr, n_mu, cols, mp, kp, limbs, b, s));
+        A[c] = a;
+        B[c] = b;
+      }
+      ISDF_TRY(splitgemm(limbs, 3, A, B, n_mu, n_mu, kp, kp, 256, D, n_mu, 0, 1.0, err, s));
+      uint16_t* a = ops + 6 * opl;
+      uint16_t* b = ops + 7 * opl;
+      ISDF_TRY(split_operand(xi, n_g, g0, w, n_mu, cols, mp, kp, limbs, a, s));
+      ISDF_TRY(split_operand(V, n_g, g0, nullptr, n_mu, cols, mp, kp, limbs, b, s));
+      const void* A1[1] = {a};
+      const void* B1[1] = {b};
+      ISDF_TRY(splitgemm(limbs, 1, A1, B1, n_mu, n_mu, kp, kp, 256, D, n_mu, 0, 2.0, err, s));
+    }
+    int h_err = 0;
+    ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ISDF_CUDA(cudaStreamSynchronize(s));
+    if (h_err) {
+      set_error("tensor-core pipeline wait expired in the D contraction (device error word 0x%x)",
+                h_err);
+      return ISDF_E_TIMEOUT;
+    }
   }
   if (n_orb_x == 0) return ISDF_OK;
 

@@ -80,7 +80,7 @@ def run(inp: Inputs, precision: str = "bf16x3", n_orb_x: Optional[int] = None,
     mark("a5")
     phiP, dphiP = api.isdf_gather_pivots(phi, dphi, piv)
     nx = inp.n_occ if n_orb_x is None else n_orb_x
-    D, Xp = api.xtc_density_contract(phiP, inp.n_occ, xi, inp.w, calG, nx)
+    D, Xp = api.xtc_density_contract(phiP, inp.n_occ, xi, inp.w, calG, nx, precision=precision)
     mark("a5")
     mark("a6")
     E = api.tc_energies(W, D, Xp, phiP, dphiP, inp.n_occ)

@@ -153,6 +153,32 @@ def test_xtc(P, h6):
     assert rel(host(Xp), xtc.pack_upper(Xfull)) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_xtc_tensor_core(P, h6, prec):
+    """D on the split-BF16 tensor-core GEMMs; X stays FP64."""
+    w, o = h6
+    n_orb = w.n_orb
+    D, Xp = P.xtc_density_contract(cu(o["phiP"]), w.n_occ, cu(o["xi"]), cu(w.grid_w),
+                                   cu(o["calG"]), n_orb_x=n_orb, precision=prec)
+    _, _, Dref = xtc.d_kernels(w.grid_w, o["xi"], o["calG"], xtc.g_nu(o["phiP"], w.n_occ))
+    assert rel(host(D), Dref) < 1e-5
+    Xfull = xtc.x_projector(w.grid_w, o["xi"], o["calG"], o["phiP"], w.n_occ)
+    assert rel(host(Xp), xtc.pack_upper(Xfull)) < 1e-10
+
+
+def test_xtc_tensor_core_chunks(P):
+    """Several 32768-point grid chunks with a ragged tail (n_g = 70001) and
+    n_mu = 200 (two M tiles, ragged): seeded standard-normal factors."""
+    n_mu, n_g, n_orb, n_occ = 200, 70001, 12, 5
+    phiP = wl.seeded_matrix((n_mu, n_orb), 11)
+    xi = wl.seeded_matrix((n_mu, n_g), 12)
+    calG = wl.seeded_matrix((3, n_mu, n_g), 13)
+    wg = np.abs(wl.seeded_matrix((n_g,), 14)) + 0.1
+    D, _ = P.xtc_density_contract(cu(phiP), n_occ, cu(xi), cu(wg), cu(calG), precision="bf16x6")
+    _, _, Dref = xtc.d_kernels(wg, xi, calG, xtc.g_nu(phiP, n_occ))
+    assert rel(host(D), Dref) < 1e-5
+
+
 def test_energies_fp64(P, h6):
     w, o = h6
     Xp = xtc.pack_upper(o["X"])
