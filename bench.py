@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--kappa", type=float, default=3.0)
     ap.add_argument("--w-nrad", type=int, default=16)
     ap.add_argument("--w-nmu", type=int, default=1024)
+    ap.add_argument("--w-nang", type=int, default=50)
+    ap.add_argument("--w-geom", default="h50_chain", choices=["h50_chain", "benzene"])
+    ap.add_argument("--w-fp64-rows", type=int, default=0,
+                    help="--w-only: also time the FP64 GPU path on this many outer points")
+    ap.add_argument("--w-slice", type=int, default=0,
+                    help="--w-only: outer grid points of the W build (0: all)")
     return ap.parse_args()
 
 
@@ -189,13 +195,22 @@ def run_reference(args, rank, world):
 
 
 def run_w_only(args):
-    """The W build alone on a reduced grid (for kernel profiles)."""
+    """The W build alone (kernel profiles; the benzene-geometry timing): the
+    H50-chain geometry with the radial correlator, or the benzene geometry
+    with its two-type multi-centre correlator; seeded random xi."""
+    import numpy as np
     import torch
     from synth import workloads as wl
     from paper_2607_17314_b300 import api, build
     build.build()
-    _, xyz = wl.h_chain(50, 1.8)
-    grid, w = wl.becke_grid(xyz, args.w_nrad, 50)
+    if args.w_geom == "benzene":
+        atoms, xyz = wl.benzene()
+        grid, w = wl.becke_grid(xyz, args.w_nrad, args.w_nang)
+        jas = wl.bh_jastrow(atoms, xyz, wl.BH_TERMS_C3, np.random.default_rng(3001))
+    else:
+        _, xyz = wl.h_chain(50, 1.8)
+        grid, w = wl.becke_grid(xyz, args.w_nrad, args.w_nang)
+        jas = wl.radial_jastrow(xyz)
     n_g, n_mu = grid.shape[0], args.w_nmu
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1234)
@@ -203,18 +218,41 @@ def run_w_only(args):
     wt = torch.tensor(w, device="cuda")
     xi = torch.randn((n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
     xig = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
-    kb = api.KernelBuilder(g, wt, xi, xig, api.jastrow_from(wl.radial_jastrow(xyz)),
-                           args.precision, time_stages=True)
+    g1 = n_g if args.w_slice <= 0 else min(n_g, args.w_slice)
+    kb = api.KernelBuilder(g, wt, xi, xig, api.jastrow_from(jas), args.precision, g_end=g1,
+                           time_stages=True)
     for _ in range(max(args.warmup, 1)):
         kb()
     s1, s2 = [], []
     for _ in range(args.steps):
         kb()
         s1.append(kb.stage_ms[0]); s2.append(kb.stage_ms[1])
-    fl1 = 8.0 * n_mu * n_g * n_g
-    print(json.dumps({"mode": "w_only", "n_g": n_g, "n_mu": n_mu, "precision": args.precision,
-                      "s1_ms": s1, "s2_ms": s2,
-                      "s1_alg_tflops": fl1 / (min(s1) * 1e-3) / 1e12}), flush=True)
+    fl1 = 8.0 * n_mu * n_g * g1
+    out = {"mode": "w_only", "geometry": args.w_geom, "n_g": n_g, "outer_points": g1,
+           "n_mu": n_mu, "precision": args.precision, "s1_ms": s1, "s2_ms": s2,
+           "s1_alg_tflops": fl1 / (min(s1) * 1e-3) / 1e12}
+    if args.w_fp64_rows > 0:
+        # the FP64 GPU path and the tensor-core path on the same outer slice
+        rows = min(args.w_fp64_rows, g1)
+        J = api.jastrow_from(jas)
+        k64 = api.KernelBuilder(g, wt, xi, xig, J, "fp64", g_end=rows)
+        k16 = api.KernelBuilder(g, wt, xi, xig, J, args.precision, g_end=rows)
+        k64()
+        k16()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        k64()
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        fl64 = 8.0 * n_mu * n_g * rows + 8.0 * n_mu * n_mu * rows
+        err = [float(torch.linalg.norm(k16.W[c] - k64.W[c]) / torch.linalg.norm(k64.W[c]))
+               for c in range(4)]
+        out["fp64_gpu"] = {"outer_points": rows, "ms": t64, "tflops": fl64 / (t64 * 1e-3) / 1e12,
+                           "w_rel_err_tc_vs_fp64": err}
+        out["speedup_tc_over_fp64"] = out["s1_alg_tflops"] / out["fp64_gpu"]["tflops"]
+    print(json.dumps(out), flush=True)
 
 
 def _chain(k):
@@ -362,7 +400,7 @@ def main():
     products = 3 if args.precision == "bf16x3" else 6
     # DRAM bytes per (mu, g) output element of stage 1 from the ncu capture in
     # profiles/s1_tc_kernel_bf16x3.md (input and output both scale with N_mu n_g)
-    traffic = 36.9 * n_mu * n_g if args.precision == "bf16x3" else None
+    traffic = 36.6 * n_mu * n_g if args.precision == "bf16x3" else None
     roofline = {"bound": "tensor", "achieved": s1_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": s1_tflops / peak, "traffic": traffic,
                 "pipe_frac": s1_tflops * products / peak,

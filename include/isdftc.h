@@ -168,11 +168,17 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * The outer-grid slice [g_begin, g_end) gives additive partial kernels.
  * grid_xyz [n_g][3]; w [n_g]; xi [n_mu][n_g]; xi_grad [3][n_mu][n_g];
  * W [4][n_mu][n_mu] FP64 (overwritten); calG [4][n_mu][g_end-g_begin] FP64
- * (overwritten; required).  The tensor-core precisions take the radial
- * correlator (n_terms = 0) only; ISDF_PREC_FP64 takes any correlator.
- * Synchronises `stream` when options->sync_check (default). */
+ * (overwritten; required).  ISDF_PREC_FP64 takes any correlator.  The
+ * tensor-core precisions take the radial correlator (n_terms = 0, cusp = 1)
+ * and multi-centre correlators whose terms have m, n <= 3, o <= 4 and at most
+ * two distinct E exponents o among the terms with (m, n) != (0, 0), with the
+ * nucleus count limited by shared memory (ISDF_E_ARG beyond it; 12 centres
+ * with three E-exponent-2 electron-electron-nucleus terms use 198 KB).
+ * Synchronises `stream` when options->sync_check (default).
+ * The workspace query takes the correlator (NULL: the largest layout the
+ * call accepts). */
 size_t tc_kernel_build_workspace(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
-                                 int precision);
+                                 int precision, const isdf_jastrow* jas);
 int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
                     const double* xi_grad, int64_t n_g, int n_mu, int64_t g_begin,
                     int64_t g_end, const isdf_jastrow* jas, const isdf_options* options,

@@ -62,7 +62,7 @@ SIGNATURES = {
     "isdf_fit_workspace": (SZ, [I64, INT, INT]),
     "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, SZ, P]),
     "isdf_gather_pivots": (INT, [P, P, I64, INT, P, INT, P, P, P]),
-    "tc_kernel_build_workspace": (SZ, [I64, INT, I64, I64, INT]),
+    "tc_kernel_build_workspace": (SZ, [I64, INT, I64, I64, INT, ctypes.POINTER(IsdfJastrow)]),
     "tc_kernel_build": (INT, [P, P, P, P, I64, INT, I64, I64, ctypes.POINTER(IsdfJastrow),
                               ctypes.POINTER(IsdfOptions), P, P, P, SZ, P]),
     "tc_kernel_adjoint_workspace": (SZ, [I64, INT, INT, INT]),

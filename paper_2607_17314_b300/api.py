@@ -160,7 +160,8 @@ class KernelBuilder:
         self.W = torch.empty((4, self.n_mu, self.n_mu), dtype=f64, device=self.dev)
         self.calG = torch.empty((4, self.n_mu, n_gs), dtype=f64, device=self.dev)
         self.ws = _ws(lib.tc_kernel_build_workspace(self.n_g, self.n_mu, self.g_begin, self.g_end,
-                                                   self.opt.precision), self.dev)
+                                                   self.opt.precision, ctypes.byref(self.J)),
+                      self.dev)
 
     def __call__(self, allow_timeout: bool = False):
         g, w, xi, xig = self.args

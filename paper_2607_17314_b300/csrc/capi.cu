@@ -34,7 +34,7 @@ int gather_pivots(const double*, const double*, int64_t, int, const int32_t*, in
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J);
 int wbuild_fp64(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
                 int64_t, const isdf_jastrow&, double*, double*, void*, size_t, cudaStream_t);
-size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int);
+size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int, const isdf_jastrow*);
 int wbuild_tc(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
               int64_t, const isdf_jastrow&, const isdf_options&, double*, double*, void*, size_t,
               cudaStream_t);
@@ -123,9 +123,9 @@ int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n
 }
 
 size_t tc_kernel_build_workspace(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
-                                 int precision) {
-  if (precision == ISDF_PREC_FP64) return wbuild_fp64_ws(n_g, nullptr);
-  return wbuild_tc_ws(n_g, n_mu, g_begin, g_end, precision);
+                                 int precision, const isdf_jastrow* jas) {
+  if (precision == ISDF_PREC_FP64) return wbuild_fp64_ws(n_g, jas);
+  return wbuild_tc_ws(n_g, n_mu, g_begin, g_end, precision, jas);
 }
 
 int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
@@ -149,10 +149,6 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
   if (opt.precision != ISDF_PREC_BF16X3 && opt.precision != ISDF_PREC_BF16X6) {
     set_error("unknown precision %d", opt.precision);
     return ISDF_E_ARG;
-  }
-  if (jas->n_terms != 0) {
-    set_error("tensor-core precisions take the radial correlator (n_terms = 0) only");
-    return ISDF_E_UNSUPPORTED;
   }
   return wbuild_tc(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, opt, W, calG, ws,
                    ws_bytes, s);

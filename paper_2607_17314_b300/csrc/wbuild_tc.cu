@@ -96,28 +96,17 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int
   }
 }
 
-// hi/lo: FP32 pair of every point; loc: point minus the first point of its
-// 32-point block (FP32 of the FP64 difference); org[2b], org[2b+1]: hi/lo
-// pair of the first point of block b.  Padding points sit at the origin.
+// hi/lo: FP32 pair of every point (hi = FP32 rounding, lo = FP32 of the
+// remainder).  Padding points sit at the origin.
 __global__ void coords_kernel(const double* __restrict__ grid, int64_t n_g, int64_t n_pad,
-                              float4* __restrict__ hi, float4* __restrict__ lo,
-                              float4* __restrict__ loc, float4* __restrict__ org) {
+                              float4* __restrict__ hi, float4* __restrict__ lo) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_pad) return;
   double x = 0, y = 0, z = 0;
   if (g < n_g) { x = grid[3 * g]; y = grid[3 * g + 1]; z = grid[3 * g + 2]; }
-  const int64_t b0 = g & ~(int64_t)31;
-  double ox = 0, oy = 0, oz = 0;
-  if (b0 < n_g) { ox = grid[3 * b0]; oy = grid[3 * b0 + 1]; oz = grid[3 * b0 + 2]; }
   float xh = (float)x, yh = (float)y, zh = (float)z;
   hi[g] = make_float4(xh, yh, zh, 0.f);
   lo[g] = make_float4((float)(x - xh), (float)(y - yh), (float)(z - zh), 0.f);
-  loc[g] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
-  if (g == b0) {
-    float ohx = (float)ox, ohy = (float)oy, ohz = (float)oz;
-    org[2 * (g >> 5)] = make_float4(ohx, ohy, ohz, 0.f);
-    org[2 * (g >> 5) + 1] = make_float4((float)(ox - ohx), (float)(oy - ohy), (float)(oz - ohz), 0.f);
-  }
 }
 
 // ------------------------------------------------------------------ stage 1
@@ -130,16 +119,19 @@ __global__ void coords_kernel(const double* __restrict__ grid, int64_t n_g, int6
 // shape into which the epilogue warps fold each chunk with IEEE-rounded adds.
 // Short tensor-core accumulation runs keep the accumulation error small;
 // the tile is written to FP64 calG once, after its last chunk.
-template <int LIMBS>
+//
+// BH selects the multi-centre generator, which needs shared memory for a
+// per-row nucleus table (sized at launch) and so keeps one operand stage less.
+template <int LIMBS, bool BH>
 struct S1C {
   static constexpr int BM = 128, BN = 64, BK = 32;
-  static constexpr int STAGES = LIMBS == 2 ? 4 : 3;
+  static constexpr int STAGES = BH ? (LIMBS == 2 ? 3 : 2) : (LIMBS == 2 ? 4 : 3);
   static constexpr int CSTAGES = 8;  // coordinate ring
   static constexpr uint32_t A_LIMB = BM * BK * 2;
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t A_BYTES = LIMBS * A_LIMB;
   static constexpr uint32_t B_BYTES = 4 * LIMBS * B_TILE;
-  static constexpr uint32_t C_BYTES = BK * 16 + 32;  // block-local coordinates + block origin
+  static constexpr uint32_t C_BASE = BK * 32;  // inner-point coordinates, FP32 hi then lo
   static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
   static constexpr uint32_t ACC_COLS = 4 * BN;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
@@ -148,18 +140,20 @@ struct S1C {
   static constexpr int CW = 2 + NGW + NEW;  // coordinate producer warp
   static constexpr int THREADS = 32 * (CW + 1);
   static constexpr int COLS = BN * BK / (32 * NGW);  // inner points per generator thread
-  static constexpr uint32_t SMEM = STAGES * STAGE + CSTAGES * C_BYTES + 1024 + 512;
+  // operand stages + alignment slack + barriers; the coordinate ring and the
+  // nucleus table are added at launch
+  static constexpr uint32_t FIXED = STAGES * STAGE + 1024 + 512;
   static_assert(COLS == 8, "one 16-byte chunk per generator thread and operand");
   static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0 && B_TILE % 1024 == 0, "alignment");
   static_assert(TMEM_COLS == 512, "tensor memory budget");
-  static_assert(SMEM <= 232448, "shared memory budget");
+  static_assert(FIXED + CSTAGES * C_BASE <= 232448, "shared memory budget");
 };
+
+constexpr uint32_t kSmemLimit = 232448;
 
 struct S1Params {
   const float4* xyz_hi;  // [n_k] points as FP32 hi/lo pairs (padded)
   const float4* xyz_lo;
-  const float4* loc;     // [n_k] point minus its 32-block origin
-  const float4* org;     // [n_k / 32][2] block origins, hi/lo
   int64_t n_g;           // real points
   int64_t n_k;           // padded inner extent (multiple of 32)
   int n_mu;
@@ -168,9 +162,18 @@ struct S1Params {
   int64_t n_g_tiles;
   int64_t kchunk;        // fold interval, multiple of 32
   float d;
+  uint32_t cbytes;       // bytes per coordinate-ring stage
+  uint32_t tab_bytes;    // bytes of the per-row nucleus table
   double* calG;          // [4][n_mu][g_end - g_begin]
   int* err;
   int debug;
+  // multi-centre correlator (BH kernels only)
+  int n_nuc;
+  int oexp[2];           // E exponents o of the pair-term groups
+  float rho[4];          // radial factor sum_e rho_e E^e of the E-gradient
+  const float4* rowslots;  // [n_k][n_nuc][ns4] per (point, nucleus) slots
+  const float4* fvec;      // [n_k] gradient part independent of the inner point
+  const float* ajtab;      // [n_k / 32][n_nuc][32] A_{g'I}
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -204,16 +207,21 @@ __device__ __forceinline__ void split_pack(float a, float b, uint32_t (&out)[LIM
   }
 }
 
+// Difference vector r_g - r_g' from FP32 hi/lo pairs: the hi parts of close
+// points cancel exactly, so every pair keeps relative accuracy ~1e-7 whatever
+// the order of the grid points.
+__device__ __forceinline__ void pair_diff(const float4& gh, const float4& gl, const float4& h,
+                                          const float4& l, float& dx, float& dy, float& dz) {
+  dx = (gh.x - h.x) + (gl.x - l.x);
+  dy = (gh.y - h.y) + (gl.y - l.y);
+  dz = (gh.z - h.z) + (gl.z - l.z);
+}
+
 // Radial correlator u = r / (2 (1 + d r)):  K_c = u'(r)/r (r_g - r_g')_c with
-// u' = 1/(2 (1 + d r)^2), and K_sq = u'^2.  The difference vector is formed
-// as m - l with m = r_g - o (o = origin of the inner point's 32-point block,
-// from FP32 hi/lo pairs) and l = r_g' - o, so that close pairs keep their
-// relative accuracy.  The self pair (flagged by the caller) gives zero.
-__device__ __forceinline__ void radial_pair(float4 m, float4 l, float d, bool self, float& kx,
-                                            float& ky, float& kz, float& ksq) {
-  const float dx = m.x - l.x;
-  const float dy = m.y - l.y;
-  const float dz = m.z - l.z;
+// u' = 1/(2 (1 + d r)^2), and K_sq = u'^2.  The self pair (flagged by the
+// caller) gives zero.
+__device__ __forceinline__ void radial_pair(float dx, float dy, float dz, float d, bool self,
+                                            float& kx, float& ky, float& kz, float& ksq) {
   const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1e-30f);
   const float rinv = rsqrtf(r2);
   const float r = r2 * rinv;
@@ -226,22 +234,385 @@ __device__ __forceinline__ void radial_pair(float4 m, float4 l, float d, bool se
   ksq = self ? 0.0f : up * up;
 }
 
-template <int LIMBS>
-__global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
+// Shared-memory carve-up and barriers common to the stage-1 roles.
+struct S1Smem {
+  uint8_t* stages;
+  uint8_t* ring;
+  uint8_t* tab;
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* cfull;
+  uint64_t* cempty;
+  uint64_t* acc_full;
+  uint64_t* acc_empty;
+  volatile int* abort_flag;
+};
+
+// (w xi) limbs by TMA, one 128 x 32 box per limb and stage.
+template <class C, int LIMBS>
+__device__ __forceinline__ void s1_load_a(const CUtensorMap* mA0, const CUtensorMap* mA1,
+                                          const CUtensorMap* mA2, const S1Params& p,
+                                          const S1Smem& sm, int64_t n_tiles) {
+  tc::tma_prefetch_desc(mA0);
+  if (LIMBS > 1) tc::tma_prefetch_desc(mA1);
+  if (LIMBS > 2) tc::tma_prefetch_desc(mA2);
+  uint32_t it = 0;
+  bool skip = (p.debug & 1) != 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
+    for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+      const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err)) return;
+      if (skip) {  // fault-path test: this stage's operand never arrives
+        skip = false;
+        continue;
+      }
+      uint8_t* st = sm.stages + s * C::STAGE;
+      tc::mbar_arrive_expect_tx(&sm.full[s], C::A_BYTES);
+      tc::tma_load_2d(st, mA0, &sm.full[s], (int32_t)k0, mu0);
+      if (LIMBS > 1) tc::tma_load_2d(st + C::A_LIMB, mA1, &sm.full[s], (int32_t)k0, mu0);
+      if (LIMBS > 2) tc::tma_load_2d(st + 2 * C::A_LIMB, mA2, &sm.full[s], (int32_t)k0, mu0);
+    }
+  }
+}
+
+// Inner-point data by bulk copy, running ahead of the generators: FP32 hi and
+// lo coordinates, plus A_{g'I} for the multi-centre generator.
+template <class C, bool BH>
+__device__ __forceinline__ void s1_load_coords(const S1Params& p, const S1Smem& sm,
+                                               int64_t n_tiles) {
+  uint32_t cit = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
+      const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
+      if (!tc::mbar_wait(&sm.cempty[cs], ph ^ 1, sm.abort_flag, p.err)) return;
+      uint8_t* dst = sm.ring + cs * p.cbytes;
+      tc::mbar_arrive_expect_tx(&sm.cfull[cs], p.cbytes);
+      bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &sm.cfull[cs]);
+      bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + k0, C::BK * 16, &sm.cfull[cs]);
+      if (BH && p.n_nuc > 0)
+        bulk_copy_g2s(dst + C::C_BASE, p.ajtab + (k0 / C::BK) * p.n_nuc * C::BK,
+                      (uint32_t)p.n_nuc * C::BK * 4, &sm.cfull[cs]);
+    }
+  }
+}
+
+// MMA issuer (one thread): one N = 256 MMA per limb product and k-step covers
+// the four channels, since the limb-j tiles of channels 0..3 are contiguous.
+template <class C, int LIMBS>
+__device__ __forceinline__ void s1_issue_mma(const S1Params& p, const S1Smem& sm, uint32_t tmem,
+                                             int64_t n_tiles, int64_t n_chunks) {
+  constexpr uint32_t idesc = tc::idesc_f16(128, 4 * C::BN, 1);
+  uint32_t it = 0, u = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+      const int64_t kb = ch * p.kchunk;
+      const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
+      if (!tc::mbar_wait(sm.acc_empty, (u & 1) ^ 1, sm.abort_flag, p.err)) return;
+      tc::tc_fence_after();
+      for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
+        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+        if (!tc::mbar_wait(&sm.full[s], ph, sm.abort_flag, p.err)) return;
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_u32(sm.stages + s * C::STAGE);
+        const uint32_t b_base = a_base + C::A_BYTES;
+        const bool first = (k0 == kb);
+#pragma unroll
+        for (int i = 0; i < LIMBS; ++i)
+#pragma unroll
+          for (int j = 0; j < LIMBS - i; ++j)
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
+              const uint64_t bd = tc::smem_desc(b_base + j * 4 * C::B_TILE + kk * 32, 16, 512, 4);
+              const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+              tc::umma_f16(tmem, ad, bd, idesc, acc);
+            }
+        tc::umma_commit(&sm.empty[s]);
+      }
+      tc::umma_commit(sm.acc_full);
+    }
+  }
+}
+
+// Store one thread's 8 generated pairs (4 channels, LIMBS limbs) into the
+// 64B-swizzled K-major B tiles of stage s and signal the MMA issuer.
+template <class C, int LIMBS>
+__device__ __forceinline__ void s1_store_b(const S1Smem& sm, uint32_t s, int row, int kc,
+                                           const uint32_t (&pk)[4][LIMBS][4]) {
+  const uint32_t bsm =
+      tc::smem_u32(sm.stages + s * C::STAGE + C::A_BYTES) + tc::sw64_offset(row, kc >> 3);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l)
+      tc::sts_u4(bsm + (l * 4 + c) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
+                 pk[c][l][3]);
+  tc::fence_proxy_async_smem();
+  tc::mbar_arrive(&sm.full[s]);
+}
+
+// Radial generator: K_c(g, g') for a 64 x 32 block, split into BF16 limbs.
+// Thread gt owns row gt % 64 and inner points 8 (gt / 64) .. + 7.
+template <class C, int LIMBS>
+__device__ __forceinline__ void s1_gen_radial(const S1Params& p, const S1Smem& sm, int gt,
+                                              int64_t n_tiles) {
+  const int row = gt % C::BN;
+  const int kc = (gt / C::BN) * C::COLS;
+  const int64_t n_gs = p.g_end - p.g_begin;
+  const float d = p.d;
+  uint32_t it = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t g_tile = tile % p.n_g_tiles;
+    const int64_t gl = g_tile * C::BN + row;
+    const bool gvalid = gl < n_gs;
+    const int64_t g = p.g_begin + (gvalid ? gl : 0);
+    const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t gself = gvalid ? g : -1;
+    for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+      const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+      const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
+      if (!tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err)) return;
+      const uint32_t cbase = tc::smem_u32(sm.ring + cs * p.cbytes);
+      float dx[8], dy[8], dz[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        pair_diff(gh, glo, tc::lds_f4(cbase + (kc + e) * 16),
+                  tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
+      tc::mbar_arrive(&sm.cempty[cs]);  // this thread's reads precede the next bulk copy
+      // the self pair can only fall in this block when the index ranges meet
+      const bool may_self = gself >= k0 && gself < k0 + C::BK;
+      uint32_t pk[4][LIMBS][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        float kv[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          radial_pair(dx[e + h], dy[e + h], dz[e + h], d,
+                      may_self && (k0 + kc + e + h) == gself, kv[h][0], kv[h][1], kv[h][2],
+                      kv[h][3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t w[LIMBS];
+          split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+        }
+      }
+      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err)) return;
+      s1_store_b<C, LIMBS>(sm, s, row, kc, pk);
+    }
+  }
+}
+
+// Multi-centre (Boys-Handy) generator.  With A = A_{gI}, y = A_{g'I} and the
+// terms grouped by their E exponent (group 0: o = 0; groups j = 1..NG: o_j),
+//   grad_g u = f(g) + sum_I [sum_d P0_d y^d + sum_j E^{o_j} P_j(y)] grad A_{gI}
+//              + [rho(E) + sum_j o_j E^{o_j - 1} sum_I Q_j(y)] dE/dr e_{gg'}
+// where the polynomial coefficients P_j,d and Q_j,d are functions of A_{gI}
+// and the nucleus type, tabulated per (row point, nucleus) in FP64 and held in
+// shared memory as [I][slot / 4][row] float4 for the tile's 64 rows:
+//   slots 0..2 grad A_{gI}; 3 .. 2 + DEG  P0_1 .. P0_DEG;
+//   then per group j: P_j,0 .. P_j,DEG, Q_j,0 .. Q_j,DEG.
+// f(g) collects the y-independent part P0_0 grad A_{gI}; rho(E) the cusp and
+// the pure electron-electron terms.  Lane l of generator warp w owns row
+// 8 w + l / 4 and inner points 8 (l % 4) .. + 7, so the four lanes sharing a
+// row fill its table entries together (warp-level synchronisation only); all
+// exits are warp-uniform.
+template <class C, int LIMBS, int NG, int DEG>
+__device__ __forceinline__ void s1_gen_bh(const S1Params& p, const S1Smem& sm, int gw, int lane,
+                                          int64_t n_tiles) {
+  constexpr int NS = 3 + DEG + 2 * NG * (DEG + 1);
+  constexpr int NS4 = (NS + 3) / 4;
+  const int row = gw * 8 + (lane >> 2);
+  const int kc = (lane & 3) * C::COLS;
+  const int64_t n_gs = p.g_end - p.g_begin;
+  const float d = p.d;
+  const int n_nuc = p.n_nuc;
+  const uint32_t tab = tc::smem_u32(sm.tab);
+  float4* tabp = reinterpret_cast<float4*>(sm.tab);
+  uint32_t it = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t g_tile = tile % p.n_g_tiles;
+    const int64_t gl = g_tile * C::BN + row;
+    const bool gvalid = gl < n_gs;
+    const int64_t g = p.g_begin + (gvalid ? gl : 0);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 gh = gvalid ? p.xyz_hi[g] : zero;
+    const float4 glo = gvalid ? p.xyz_lo[g] : zero;
+    const float4 fg = gvalid ? p.fvec[g] : zero;
+    const int64_t gself = gvalid ? g : -1;
+    // this warp's rows of the nucleus table (the previous tile's reads are done)
+    __syncwarp();
+    for (int idx = lane & 3; idx < n_nuc * NS4; idx += 4)
+      tabp[idx * C::BN + row] = gvalid ? p.rowslots[g * n_nuc * NS4 + idx] : zero;
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+      const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+      const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
+      const bool okc = tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, okc)) return;
+      const uint32_t cbase = tc::smem_u32(sm.ring + cs * p.cbytes);
+      float dx[8], dy[8], dz[8], fr[8], ce[8], gx[8], gy[8], gz[8];
+      float eo[NG][8], wq[NG][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        pair_diff(gh, glo, tc::lds_f4(cbase + (kc + e) * 16),
+                  tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
+        const float r2 = fmaxf(fmaf(dx[e], dx[e], fmaf(dy[e], dy[e], dz[e] * dz[e])), 1e-30f);
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float iden = rcp_approx(fmaf(d, r, 1.0f));
+        const float E = d * r * iden;
+        fr[e] = d * iden * iden * rinv;
+        ce[e] = fmaf(E, fmaf(E, fmaf(E, p.rho[3], p.rho[2]), p.rho[1]), p.rho[0]);
+#pragma unroll
+        for (int j = 0; j < NG; ++j) {
+          float pw = 1.0f;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (t < p.oexp[j] - 1) pw *= E;
+          wq[j][e] = (float)p.oexp[j] * pw;
+          eo[j][e] = pw * E;
+        }
+        gx[e] = fg.x;
+        gy[e] = fg.y;
+        gz[e] = fg.z;
+      }
+      const uint32_t abase = cbase + C::C_BASE + kc * 4;
+#pragma unroll 1
+      for (int I = 0; I < n_nuc; ++I) {
+        float sl[NS4 * 4];
+#pragma unroll
+        for (int k4 = 0; k4 < NS4; ++k4) {
+          const float4 v = tc::lds_f4(tab + ((I * NS4 + k4) * C::BN + row) * 16);
+          sl[4 * k4] = v.x;
+          sl[4 * k4 + 1] = v.y;
+          sl[4 * k4 + 2] = v.z;
+          sl[4 * k4 + 3] = v.w;
+        }
+        const float4 y0 = tc::lds_f4(abase + I * C::BK * 4);
+        const float4 y1 = tc::lds_f4(abase + I * C::BK * 4 + 16);
+        const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          float s0 = sl[2 + DEG];
+#pragma unroll
+          for (int dd = DEG - 1; dd >= 1; --dd) s0 = fmaf(s0, y[e], sl[2 + dd]);
+          float ca = s0 * y[e];
+#pragma unroll
+          for (int j = 0; j < NG; ++j) {
+            const int pb = 3 + DEG + j * 2 * (DEG + 1);
+            const int qb = pb + DEG + 1;
+            float pj = sl[pb + DEG], qj = sl[qb + DEG];
+#pragma unroll
+            for (int dd = DEG - 1; dd >= 0; --dd) {
+              pj = fmaf(pj, y[e], sl[pb + dd]);
+              qj = fmaf(qj, y[e], sl[qb + dd]);
+            }
+            ca = fmaf(eo[j][e], pj, ca);
+            ce[e] = fmaf(wq[j][e], qj, ce[e]);
+          }
+          gx[e] = fmaf(ca, sl[0], gx[e]);
+          gy[e] = fmaf(ca, sl[1], gy[e]);
+          gz[e] = fmaf(ca, sl[2], gz[e]);
+        }
+      }
+      tc::mbar_arrive(&sm.cempty[cs]);  // ring reads of this stage are done
+      const bool may_self = gself >= k0 && gself < k0 + C::BK;
+      uint32_t pk[4][LIMBS][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        float kv[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = e + h;
+          const bool self = may_self && (k0 + kc + q) == gself;
+          const float fac = ce[q] * fr[q];
+          const float kx = fmaf(fac, dx[q], gx[q]);
+          const float ky = fmaf(fac, dy[q], gy[q]);
+          const float kz = fmaf(fac, dz[q], gz[q]);
+          kv[h][0] = self ? 0.f : kx;
+          kv[h][1] = self ? 0.f : ky;
+          kv[h][2] = self ? 0.f : kz;
+          kv[h][3] = self ? 0.f : fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t w[LIMBS];
+          split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+        }
+      }
+      const bool oke = tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, oke)) return;
+      s1_store_b<C, LIMBS>(sm, s, row, kc, pk);
+    }
+  }
+}
+
+// Epilogue: fold each chunk into the running sum; write the tile at the end.
+template <class C>
+__device__ __forceinline__ void s1_epilogue(const S1Params& p, const S1Smem& sm, uint32_t tmem,
+                                            int warp, int lane, int64_t n_tiles,
+                                            int64_t n_chunks) {
+  const int quad = warp & 3;
+  const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+  const int64_t n_gs = p.g_end - p.g_begin;
+  uint32_t u = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t g_tile = tile % p.n_g_tiles;
+    const int mu = (int)(tile / p.n_g_tiles) * C::BM + 32 * quad + lane;
+    for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+      if (!tc::mbar_wait(sm.acc_full, u & 1, sm.abort_flag, p.err)) return;
+      tc::tc_fence_after();
+      const bool first = (ch == 0), last = (ch + 1 == n_chunks);
+#pragma unroll 1
+      for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
+        uint32_t r[32];
+        tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
+                            first, r);
+        if (!last) {
+          tc::tmem_st_32x32b_x32(tmem + lane_base + C::ACC_COLS + blk * 32, r);
+        } else if (mu < p.n_mu) {
+          const int c = blk / (C::BN / 32);
+          double* dst = p.calG + ((int64_t)c * p.n_mu + mu) * n_gs;
+          const int64_t gbase = g_tile * C::BN + (blk % (C::BN / 32)) * 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
+        }
+      }
+      if (!last) tc::tmem_st_wait();
+      tc::tc_fence_before();
+      tc::mbar_arrive(sm.acc_empty);
+    }
+  }
+}
+
+// Stage-1 kernel.  NG < 0: radial correlator; NG >= 1: multi-centre
+// correlator with NG pair-term groups and polynomial degree DEG in A_{g'I}.
+template <int LIMBS, int NG, int DEG>
+__global__ void __launch_bounds__(S1C<LIMBS, (NG >= 0)>::THREADS, 1)
     s1_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                 const __grid_constant__ CUtensorMap mA2, const S1Params p) {
-  using C = S1C<LIMBS>;
+                 const __grid_constant__ CUtensorMap mA2, const __grid_constant__ S1Params p) {
+  constexpr bool BH = NG >= 0;
+  using C = S1C<LIMBS, BH>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* csm = smem + C::STAGES * C::STAGE;  // coordinate ring
-  uint64_t* full = (uint64_t*)(csm + C::CSTAGES * C::C_BYTES);
-  uint64_t* empty = full + C::STAGES;
-  uint64_t* cfull = empty + C::STAGES;
-  uint64_t* cempty = cfull + C::CSTAGES;
-  uint64_t* acc_full = cempty + C::CSTAGES;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
-  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  S1Smem sm;
+  sm.stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  sm.ring = sm.stages + C::STAGES * C::STAGE;
+  sm.tab = sm.ring + C::CSTAGES * p.cbytes;
+  sm.full = (uint64_t*)(sm.tab + p.tab_bytes);
+  sm.empty = sm.full + C::STAGES;
+  sm.cfull = sm.empty + C::STAGES;
+  sm.cempty = sm.cfull + C::CSTAGES;
+  sm.acc_full = sm.cempty + C::CSTAGES;
+  sm.acc_empty = sm.acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(sm.acc_empty + 1);
+  sm.abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -249,16 +620,16 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
       // every generator thread arrives: its own shared-memory writes must be
       // ordered before the tensor core reads them (a warp-level sync followed
       // by one lane's arrive does not give that ordering)
-      tc::mbar_init(&full[s], C::NGW * 32 + 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&sm.full[s], C::NGW * 32 + 1);
+      tc::mbar_init(&sm.empty[s], 1);
     }
     for (int s = 0; s < C::CSTAGES; ++s) {
-      tc::mbar_init(&cfull[s], 1);
-      tc::mbar_init(&cempty[s], C::NGW * 32);
+      tc::mbar_init(&sm.cfull[s], 1);
+      tc::mbar_init(&sm.cempty[s], C::NGW * 32);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, C::NEW * 32);
-    *abort_flag = 0;
+    tc::mbar_init(sm.acc_full, 1);
+    tc::mbar_init(sm.acc_empty, C::NEW * 32);
+    *sm.abort_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -270,187 +641,25 @@ __global__ void __launch_bounds__(S1C<LIMBS>::THREADS, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int64_t n_gs = p.g_end - p.g_begin;
   const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
   const int64_t n_chunks = (p.n_k + p.kchunk - 1) / p.kchunk;
 
   if (warp == 0) {
-    // producer of the (w xi) limbs (TMA)
-    if (lane == 0) {
-      tc::tma_prefetch_desc(&mA0);
-      if (LIMBS > 1) tc::tma_prefetch_desc(&mA1);
-      if (LIMBS > 2) tc::tma_prefetch_desc(&mA2);
-      uint32_t it = 0;
-      bool skip = (p.debug & 1) != 0;
-      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
-        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
-          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
-          if (skip) {  // fault-path test: this stage's operand never arrives
-            skip = false;
-            continue;
-          }
-          uint8_t* st = smem + s * C::STAGE;
-          tc::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
-          tc::tma_load_2d(st, &mA0, &full[s], (int32_t)k0, mu0);
-          if (LIMBS > 1) tc::tma_load_2d(st + C::A_LIMB, &mA1, &full[s], (int32_t)k0, mu0);
-          if (LIMBS > 2) tc::tma_load_2d(st + 2 * C::A_LIMB, &mA2, &full[s], (int32_t)k0, mu0);
-        }
-      }
-    }
+    if (lane == 0) s1_load_a<C, LIMBS>(&mA0, &mA1, &mA2, p, sm, n_tiles);
   } else if (warp == C::CW) {
-    // producer of the inner-point coordinates (bulk copies, runs ahead)
-    if (lane == 0) {
-      uint32_t cit = 0;
-      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
-          const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
-          if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err)) goto done;
-          uint8_t* dst = csm + cs * C::C_BYTES;
-          tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
-          bulk_copy_g2s(dst, p.loc + k0, C::BK * 16, &cfull[cs]);
-          bulk_copy_g2s(dst + C::BK * 16, p.org + 2 * (k0 / C::BK), 32, &cfull[cs]);
-        }
-      }
-    }
+    if (lane == 0) s1_load_coords<C, BH>(p, sm, n_tiles);
   } else if (warp == 1) {
-    // MMA issuer
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16(128, 4 * C::BN, 1);
-      uint32_t it = 0, u = 0;
-      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
-          const int64_t kb = ch * p.kchunk;
-          const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto mma_out;
-          tc::tc_fence_after();
-          for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
-            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto mma_out;
-            tc::tc_fence_after();
-            const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE);
-            const uint32_t b_base = a_base + C::A_BYTES;
-            const bool first = (k0 == kb);
-            // one N = 256 MMA covers the four channels: the limb-j tiles of
-            // channels 0..3 are contiguous, so A is read once per product
-#pragma unroll
-            for (int i = 0; i < LIMBS; ++i)
-#pragma unroll
-              for (int j = 0; j < LIMBS - i; ++j)
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
-                  const uint64_t bd =
-                      tc::smem_desc(b_base + j * 4 * C::B_TILE + kk * 32, 16, 512, 4);
-                  const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                  tc::umma_f16(tmem, ad, bd, idesc, acc);
-                }
-            tc::umma_commit(&empty[s]);
-          }
-          tc::umma_commit(acc_full);
-        }
-      }
-    mma_out:;
-    }
+    if (lane == 0) s1_issue_mma<C, LIMBS>(p, sm, tmem, n_tiles, n_chunks);
   } else if (warp < 2 + C::NGW) {
-    // generators: K_c(g, g') for a 64 x 32 block, split into BF16 limbs,
-    // stored into the 64B-swizzled K-major B tiles
-    const int gt = threadIdx.x - 64;
-    const int row = gt % C::BN;
-    const int kc = (gt / C::BN) * C::COLS;
-    const float d = p.d;
-    uint32_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const int64_t g_tile = tile % p.n_g_tiles;
-      const int64_t gl = g_tile * C::BN + row;
-      const bool gvalid = gl < n_gs;
-      const int64_t g = p.g_begin + (gvalid ? gl : 0);
-      const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int64_t gself = gvalid ? g : -1;
-      for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
-        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-        const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
-        if (!tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err)) goto done;
-        const uint32_t cbase = tc::smem_u32(csm + cs * C::C_BYTES);
-        float4 l4[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) l4[e] = tc::lds_f4(cbase + (kc + e) * 16);
-        const float4 oh = tc::lds_f4(cbase + C::BK * 16);
-        const float4 ol = tc::lds_f4(cbase + C::BK * 16 + 16);
-        tc::mbar_arrive(&cempty[cs]);  // this thread's reads precede the next bulk copy
-        // row point relative to the block origin
-        const float4 m = make_float4((gh.x - oh.x) + (glo.x - ol.x), (gh.y - oh.y) + (glo.y - ol.y),
-                                     (gh.z - oh.z) + (glo.z - ol.z), 0.f);
-        // the self pair can only fall in this block when the index ranges meet
-        const bool may_self = gself >= k0 && gself < k0 + C::BK;
-        uint32_t pk[4][LIMBS][4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          float kv[2][4];
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-            radial_pair(m, l4[e + h], d, may_self && (k0 + kc + e + h) == gself, kv[h][0],
-                        kv[h][1], kv[h][2], kv[h][3]);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            uint32_t w[LIMBS];
-            split_pack<LIMBS>(kv[0][c], kv[1][c], w);
-#pragma unroll
-            for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
-          }
-        }
-        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
-        const uint32_t bsm = tc::smem_u32(smem + s * C::STAGE + C::A_BYTES) +
-                             tc::sw64_offset(row, kc >> 3);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int l = 0; l < LIMBS; ++l)
-            tc::sts_u4(bsm + (l * 4 + c) * C::B_TILE, pk[c][l][0], pk[c][l][1], pk[c][l][2],
-                       pk[c][l][3]);
-        tc::fence_proxy_async_smem();
-        tc::mbar_arrive(&full[s]);
-      }
-    }
+    if constexpr (BH)
+      s1_gen_bh<C, LIMBS, (BH ? NG : 1), (BH ? DEG : 2)>(p, sm, warp - 2, lane, n_tiles);
+    else
+      s1_gen_radial<C, LIMBS>(p, sm, threadIdx.x - 64, n_tiles);
   } else {
-    // epilogue: fold each chunk into the running sum; write the tile at the end
-    const int quad = warp & 3;
-    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-    uint32_t u = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const int64_t g_tile = tile % p.n_g_tiles;
-      const int mu = (int)(tile / p.n_g_tiles) * C::BM + 32 * quad + lane;
-      for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
-        if (!tc::mbar_wait(acc_full, u & 1, abort_flag, p.err)) goto done;
-        tc::tc_fence_after();
-        const bool first = (ch == 0), last = (ch + 1 == n_chunks);
-#pragma unroll 1
-        for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
-          uint32_t r[32];
-          tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
-                              first, r);
-          if (!last) {
-            tc::tmem_st_32x32b_x32(tmem + lane_base + C::ACC_COLS + blk * 32, r);
-          } else if (mu < p.n_mu) {
-            const int c = blk / (C::BN / 32);
-            double* dst = p.calG + ((int64_t)c * p.n_mu + mu) * n_gs;
-            const int64_t gbase = g_tile * C::BN + (blk % (C::BN / 32)) * 32;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
-          }
-        }
-        if (!last) tc::tmem_st_wait();
-        tc::tc_fence_before();
-        tc::mbar_arrive(acc_empty);
-      }
-    }
+    s1_epilogue<C>(p, sm, tmem, warp, lane, n_tiles, n_chunks);
   }
-done:
   __syncthreads();
-  if (*abort_flag) {
+  if (*sm.abort_flag) {
     // a bounded wait expired: give issued copies and MMAs time to land
     const uint64_t t0 = globaltimer_ns();
     while (globaltimer_ns() - t0 < 200000ull) {
@@ -695,6 +904,139 @@ int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, 
   return ISDF_OK;
 }
 
+// Multi-centre correlator in the form the stage-1 generator evaluates: the
+// terms with (m, n) != (0, 0) grouped by their E exponent (group 0: o = 0,
+// groups 1..ng: o = oexp[j-1]); per type, the coefficients of
+//   P_j,d(A) = sum_e kp[t][j][d][e] A^e      (d A_{gI} part, y^d)
+//   Q_j,d(A) = sum_e kq[t][j-1][d][e] A^e    (d E part, y^d)
+// from d/dr_g [A^m y^n + y^m A^n] = (m A^(m-1) y^n + n A^(n-1) y^m) grad A and
+// the E-derivative factor o E^(o-1) [A^m y^n + y^m A^n]; and rho(E), the
+// E-gradient factor of the cusp and of the pure electron-electron terms
+// (sum_I 2 c o E^(o-1)).
+struct BhTc {
+  int ng;   // groups with o > 0 in the kernel (1 or 2; unused groups are zero)
+  int deg;  // polynomial degree in A_{g'I} (2 or 3)
+  int ns4;  // float4 slots per (point, nucleus)
+  int oexp[2];
+  double kp[ISDF_MAX_TYPES][3][4][3];
+  double kq[ISDF_MAX_TYPES][2][4][4];
+  double rho[4];
+};
+
+static int bh_tc_form(const isdf_jastrow& J, BhTc& K) {
+  memset(&K, 0, sizeof(K));
+  int ng = 0, deg = 0;
+  if (J.cusp) K.rho[0] += 0.5 / J.d;
+  for (int k = 0; k < J.n_terms; ++k) {
+    const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
+    ISDF_ARG(m <= 3 && n <= 3 && o <= 4,
+             "tensor-core generator takes exponents m, n <= 3 and o <= 4 (term %d)", k);
+    if (m == 0 && n == 0) {
+      if (o > 0)
+        for (int I = 0; I < J.n_nuc; ++I) K.rho[o - 1] += 2.0 * o * J.coef[J.nuc_type[I]][k];
+      continue;
+    }
+    int j = 0;
+    if (o > 0) {
+      for (j = 1; j <= ng; ++j)
+        if (K.oexp[j - 1] == o) break;
+      if (j > ng) {
+        ISDF_ARG(ng < 2, "tensor-core generator takes at most two E exponents among the "
+                         "electron-electron-nucleus terms");
+        K.oexp[ng++] = o;
+        j = ng;
+      }
+    }
+    for (int t = 0; t < J.n_types; ++t) {
+      const double c = J.coef[t][k];
+      if (m > 0) K.kp[t][j][n][m - 1] += c * m;
+      if (n > 0) K.kp[t][j][m][n - 1] += c * n;
+      if (o > 0) {
+        K.kq[t][j - 1][n][m] += c;
+        K.kq[t][j - 1][m][n] += c;
+      }
+    }
+    if (m > 0 && n > deg) deg = n;
+    if (n > 0 && m > deg) deg = m;
+    if (o > 0 && m > deg) deg = m;
+    if (o > 0 && n > deg) deg = n;
+  }
+  for (int j = ng; j < 2; ++j) K.oexp[j] = 1;  // empty groups
+  K.ng = ng < 1 ? 1 : ng;
+  K.deg = (deg <= 2 && K.ng == 1) ? 2 : 3;
+  const int ns = 3 + K.deg + 2 * K.ng * (K.deg + 1);
+  K.ns4 = (ns + 3) / 4;
+  return ISDF_OK;
+}
+
+namespace {
+
+__device__ __forceinline__ double poly_a(const double* c, int n, const double* ap) {
+  double v = 0.0;
+  for (int e = 0; e < n; ++e) v += c[e] * ap[e];
+  return v;
+}
+
+// Per point g (padded; padding points at the origin) and nucleus I, in FP64:
+// A = b r/(1 + b r), grad A = b/(1 + b r)^2 e_gI (zero on the nucleus), the
+// slots of the stage-1 multi-centre generator, f(g) = sum_I P0,0(A) grad A and
+// the A_{gI} block table that the coordinate ring streams.
+__global__ void bh_tc_table_kernel(const double* __restrict__ grid, int64_t n_g, int64_t n_k,
+                                   const __grid_constant__ isdf_jastrow J,
+                                   const __grid_constant__ BhTc K, float* __restrict__ rowslots,
+                                   float4* __restrict__ fvec, float* __restrict__ ajtab) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_k) return;
+  double x = 0, y = 0, z = 0;
+  if (g < n_g) { x = grid[3 * g]; y = grid[3 * g + 1]; z = grid[3 * g + 2]; }
+  double fx = 0, fy = 0, fz = 0;
+  const int nslot = 4 * K.ns4;
+  for (int I = 0; I < J.n_nuc; ++I) {
+    const int t = J.nuc_type[I];
+    const double b = J.b[t];
+    const double vx = x - J.nuc_xyz[I][0], vy = y - J.nuc_xyz[I][1], vz = z - J.nuc_xyz[I][2];
+    const double r = sqrt(vx * vx + vy * vy + vz * vz);
+    const double den = 1.0 + b * r;
+    const double A = b * r / den;
+    const double dc = r > 0.0 ? b / (den * den) / r : 0.0;
+    const double ap[4] = {1.0, A, A * A, A * A * A};
+    float* sl = rowslots + (g * J.n_nuc + I) * nslot;
+    int q = 0;
+    sl[q++] = (float)(dc * vx);
+    sl[q++] = (float)(dc * vy);
+    sl[q++] = (float)(dc * vz);
+    for (int dd = 1; dd <= K.deg; ++dd) sl[q++] = (float)poly_a(K.kp[t][0][dd], 3, ap);
+    for (int j = 1; j <= K.ng; ++j) {
+      for (int dd = 0; dd <= K.deg; ++dd) sl[q++] = (float)poly_a(K.kp[t][j][dd], 3, ap);
+      for (int dd = 0; dd <= K.deg; ++dd) sl[q++] = (float)poly_a(K.kq[t][j - 1][dd], 4, ap);
+    }
+    while (q < nslot) sl[q++] = 0.f;
+    const double p00 = poly_a(K.kp[t][0][0], 3, ap);
+    fx += p00 * dc * vx;
+    fy += p00 * dc * vy;
+    fz += p00 * dc * vz;
+    ajtab[(g >> 5) * J.n_nuc * 32 + I * 32 + (g & 31)] = (float)A;
+  }
+  fvec[g] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
+}
+
+template <int LIMBS, int NG, int DEG>
+int launch_s1(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStream_t s) {
+  using C = S1C<LIMBS, (NG >= 0)>;
+  const uint32_t smem = C::FIXED + C::CSTAGES * p.cbytes + p.tab_bytes;
+  ISDF_ARG(smem <= kSmemLimit,
+           "too many centres for the tensor-core generator: %d nuclei with this term set need "
+           "%u bytes of shared memory",
+           p.n_nuc, smem);
+  ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<LIMBS, NG, DEG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  s1_tc_kernel<LIMBS, NG, DEG><<<grid1, C::THREADS, smem, s>>>(mA[0], mA[1], mA[2], p);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+}  // namespace
+
 struct TcLayout {
   int limbs, bn;
   int64_t n_k, mu_pad, gs, gs_pad;
@@ -711,17 +1053,41 @@ static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
   return L;
 }
 
-size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
+static bool tc_radial(const isdf_jastrow& J) { return J.n_terms == 0 && J.cusp; }
+
+// Multi-centre tables: nuclei x float4 slots per point (0 for the radial
+// correlator; the largest accepted layout when J is unknown).
+static void bh_tc_dims(const isdf_jastrow* J, int& nn, int& ns4) {
+  nn = 0;
+  ns4 = 0;
+  if (!J) {
+    nn = 32;
+    ns4 = 6;
+    return;
+  }
+  if (tc_radial(*J)) return;
+  BhTc K;
+  nn = J->n_nuc;
+  ns4 = bh_tc_form(*J, K) == ISDF_OK ? K.ns4 : 6;
+}
+
+size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision,
+                    const isdf_jastrow* J) {
   TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, precision);
   Carve c(nullptr, 0);
   c.take<int>(64);
   c.take<float4>(L.n_k);
   c.take<float4>(L.n_k);
-  c.take<float4>(L.n_k);
-  c.take<float4>(L.n_k / 16);
   c.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);           // S1 A
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
+  int nn, ns4;
+  bh_tc_dims(J, nn, ns4);
+  if (nn > 0) {
+    c.take<float4>((size_t)L.n_k * nn * ns4);
+    c.take<float4>(L.n_k);
+    c.take<float>((size_t)L.n_k * nn);
+  }
   return c.off;
 }
 
@@ -729,17 +1095,27 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
               int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, const isdf_jastrow& J,
               const isdf_options& opt, double* W, double* calG, void* ws, size_t ws_bytes,
               cudaStream_t s) {
-  ISDF_ARG(J.n_terms == 0 && J.cusp, "tensor-core path takes the radial correlator only");
+  const bool radial = tc_radial(J);
+  BhTc K;
+  if (!radial) ISDF_TRY(bh_tc_form(J, K));
   const TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, opt.precision);
   Carve cv(ws, ws_bytes);
   int* err = cv.take<int>(64);
   float4* hi = cv.take<float4>(L.n_k);
   float4* lo = cv.take<float4>(L.n_k);
-  float4* loc = cv.take<float4>(L.n_k);
-  float4* org = cv.take<float4>(L.n_k / 16);
   uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);
   uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
+  float4* rowslots = nullptr;
+  float4* fvec = nullptr;
+  float* ajtab = nullptr;
+  if (!radial && J.n_nuc > 0) {
+    rowslots = cv.take<float4>((size_t)L.n_k * J.n_nuc * K.ns4);
+    fvec = cv.take<float4>(L.n_k);
+    ajtab = cv.take<float>((size_t)L.n_k * J.n_nuc);
+  } else if (!radial) {
+    fvec = cv.take<float4>(L.n_k);
+  }
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   ISDF_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
 
@@ -747,8 +1123,17 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 256;
 
   // operands of stage 1
-  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo, loc, org);
+  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo);
   ISDF_LAUNCH_CHECK();
+  if (!radial) {
+    if (J.n_nuc > 0) {
+      bh_tc_table_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, J, K, (float*)rowslots,
+                                                       fvec, ajtab);
+      ISDF_LAUNCH_CHECK();
+    } else {
+      ISDF_CUDA(cudaMemsetAsync(fvec, 0, sizeof(float4) * L.n_k, s));
+    }
+  }
   ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad, L.n_k, L.limbs, A1, s));
   CUtensorMap mA[3];
   memset(mA, 0, sizeof(mA));
@@ -756,7 +1141,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad * L.n_k, L.mu_pad, L.n_k, 128));
 
   S1Params p;
-  p.xyz_hi = hi; p.xyz_lo = lo; p.loc = loc; p.org = org;
+  p.xyz_hi = hi; p.xyz_lo = lo;
   p.n_g = n_g; p.n_k = L.n_k; p.n_mu = n_mu;
   p.n_mu_tiles = (int)(L.mu_pad / 128);
   p.g_begin = g_begin; p.g_end = g_end;
@@ -766,6 +1151,15 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   p.calG = calG;
   p.err = err;
   p.debug = opt.debug_flags;
+  p.n_nuc = radial ? 0 : J.n_nuc;
+  p.cbytes = S1C<2, false>::C_BASE + 4u * S1C<2, false>::BK * (uint32_t)p.n_nuc;
+  p.tab_bytes = radial ? 0u : (uint32_t)(p.n_nuc * K.ns4 * S1C<2, false>::BN * 16);
+  p.oexp[0] = radial ? 1 : K.oexp[0];
+  p.oexp[1] = radial ? 1 : K.oexp[1];
+  for (int e = 0; e < 4; ++e) p.rho[e] = radial ? 0.f : (float)K.rho[e];
+  p.rowslots = rowslots;
+  p.fvec = fvec;
+  p.ajtab = ajtab;
   int dev = 0, nsm = 148;
   ISDF_CUDA(cudaGetDevice(&dev));
   ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -777,16 +1171,16 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     for (int i = 0; i < 4; ++i) ISDF_CUDA(cudaEventCreate(&ev[i]));
     ISDF_CUDA(cudaEventRecord(ev[0], s));
   }
-  if (L.limbs == 2) {
-    using C = S1C<2>;
-    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    s1_tc_kernel<2><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
-  } else {
-    using C = S1C<3>;
-    ISDF_CUDA(cudaFuncSetAttribute(s1_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    s1_tc_kernel<3><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
-  }
-  ISDF_LAUNCH_CHECK();
+  int rc;
+  if (radial)
+    rc = L.limbs == 2 ? launch_s1<2, -1, 0>(grid1, mA, p, s) : launch_s1<3, -1, 0>(grid1, mA, p, s);
+  else if (K.ng == 1 && K.deg == 2)
+    rc = L.limbs == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
+  else if (K.ng == 1)
+    rc = L.limbs == 2 ? launch_s1<2, 1, 3>(grid1, mA, p, s) : launch_s1<3, 1, 3>(grid1, mA, p, s);
+  else
+    rc = L.limbs == 2 ? launch_s1<2, 2, 3>(grid1, mA, p, s) : launch_s1<3, 2, 3>(grid1, mA, p, s);
+  if (rc != ISDF_OK) return rc;
   if (timed) ISDF_CUDA(cudaEventRecord(ev[1], s));
 
   // operands of stage 2: (w xi~^c) and (w xi) over the slice; calG limbs

@@ -402,7 +402,7 @@ def bh_jastrow(atoms: Sequence[str], xyz: np.ndarray, terms, rng,
 # --------------------------------------------------------------------------
 
 def _assemble(name, atoms, xyz, n_rad, n_ang, shells, n_orb, n_occ, n_mu,
-              jkind, seed, jterms=None) -> Workload:
+              jkind, seed, jterms=None, jscale: float = 0.05) -> Workload:
     rng = np.random.default_rng(seed)
     grid, w = becke_grid(xyz, n_rad, n_ang)
     basis = make_basis(atoms, xyz, shells, rng)
@@ -410,7 +410,7 @@ def _assemble(name, atoms, xyz, n_rad, n_ang, shells, n_orb, n_occ, n_mu,
     if jkind == "radial":
         jas = radial_jastrow(xyz)
     else:
-        jas = bh_jastrow(atoms, xyz, jterms, rng)
+        jas = bh_jastrow(atoms, xyz, jterms, rng, scale=jscale)
     return Workload(name=name, atoms=list(atoms), xyz=xyz, grid_xyz=grid,
                     grid_w=w, basis=basis, mo_coef=C, n_occ=n_occ, n_mu=n_mu,
                     jastrow=jas, seed=seed)
@@ -440,6 +440,17 @@ def benzene_c6h6() -> Workload:
               "H": [0] * 12 + [1] * 6 + [2] * 5 + [3] * 4}
     return _assemble("benzene", atoms, xyz, 75, 302, shells, 1200, 21, 8000,
                      "bh", 3001, BH_TERMS_C3)
+
+
+def benzene_small(n_rad: int = 6, n_ang: int = 14, n_mu: int = 64, seed: int = 3101,
+                  jscale: float = 0.05, jterms=None) -> Workload:
+    """Benzene geometry and two-type BH Jastrow of the benzene workload on a
+    small grid (12 x n_rad x n_ang points) with an s/p basis (48 functions,
+    24 orbitals, 6 occupied), for parity tests of the multi-centre kernels."""
+    atoms, xyz = benzene()
+    shells = {"C": [0, 1], "H": [0, 1]}
+    return _assemble("benzene_small", atoms, xyz, n_rad, n_ang, shells, 24, 6, n_mu,
+                     "bh", seed, BH_TERMS_C3 if jterms is None else jterms, jscale)
 
 
 def h20_chain_bh() -> Workload:

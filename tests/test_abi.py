@@ -52,8 +52,8 @@ def test_struct_layout_matches_header():
 
 def test_workspace_queries(lib):
     assert lib.isdf_points_workspace(1000, 10) >= 8 * (2 * 1000 + 2 * 10 * 1000)
-    assert lib.tc_kernel_build_workspace(100000, 2000, 0, 100000, 1) > 2 * 2048 * 100000 * 2
-    assert lib.tc_kernel_build_workspace(4800, 96, 0, 4800, 0) > 0
+    assert lib.tc_kernel_build_workspace(100000, 2000, 0, 100000, 1, None) > 2 * 2048 * 100000 * 2
+    assert lib.tc_kernel_build_workspace(4800, 96, 0, 4800, 0, None) > 0
 
 
 def test_argument_errors_need_no_gpu(lib):
@@ -71,6 +71,42 @@ def test_argument_errors_need_no_gpu(lib):
     assert st == C.ISDF_E_ARG  # null pointers
     st = lib.isdf_points(None, None, None, 10, 2, 4, 7, None, None, None, 0, None)
     assert st == C.ISDF_E_ARG
+
+
+def test_multicentre_tensor_core_form_needs_no_gpu(lib):
+    """The multi-centre tensor-core generator sizes its tables from the
+    correlator and rejects term sets outside its polynomial form before any
+    device work."""
+    from paper_2607_17314_b300 import _capi as C
+    J = C.IsdfJastrow()
+    J.n_nuc, J.n_types, J.d, J.cusp = 12, 2, 1.0, 1
+    for I in range(12):
+        J.nuc_type[I] = I % 2
+        J.nuc_xyz[I][0] = float(I)
+    J.b[0] = J.b[1] = 1.0
+    radial_ws = lib.tc_kernel_build_workspace(4096, 128, 0, 4096, 1, ctypes.byref(J))
+    terms = [(0, 0, 2), (1, 0, 0), (1, 1, 0), (1, 1, 2), (2, 2, 2)]
+    J.n_terms = len(terms)
+    for k, t in enumerate(terms):
+        J.mno[k][0], J.mno[k][1], J.mno[k][2] = t
+        J.coef[0][k] = J.coef[1][k] = 0.01
+    bh_ws = lib.tc_kernel_build_workspace(4096, 128, 0, 4096, 1, ctypes.byref(J))
+    # (point, nucleus) slots: 3 gradient + 2 + 2 x 3 polynomial = 11 -> 3 float4,
+    # plus f(g) and the A table
+    assert bh_ws - radial_ws >= 4096 * (12 * 3 * 16 + 16 + 12 * 4)
+    fake = ctypes.c_void_p(256)
+    J.mno[1][0] = 4
+    st = lib.tc_kernel_build(fake, fake, fake, fake, 4096, 128, 0, 4096, ctypes.byref(J), None,
+                             fake, fake, fake, 1 << 30, None)
+    assert st == C.ISDF_E_ARG
+    assert b"tensor-core generator" in lib.isdf_last_error()
+    J.mno[1][0] = 1
+    for k, t in enumerate([(1, 1, 2), (1, 1, 3), (1, 1, 4)]):
+        J.mno[k][0], J.mno[k][1], J.mno[k][2] = t
+    st = lib.tc_kernel_build(fake, fake, fake, fake, 4096, 128, 0, 4096, ctypes.byref(J), None,
+                             fake, fake, fake, 1 << 30, None)
+    assert st == C.ISDF_E_ARG
+    assert b"two E exponents" in lib.isdf_last_error()
 
 
 def test_product_path_has_no_oracle_import():

@@ -51,7 +51,8 @@ def test_bad_arguments_rejected_before_launch(api):
     with pytest.raises(C.IsdfError) as e:
         api.tc_kernel_build(g, wt, xi, xig, J, "bf16x6", g_begin=5, g_end=3)
     assert e.value.status == C.ISDF_E_ARG
-    Jbh = api.jastrow_from(wl.bh_jastrow(w.atoms, w.xyz, wl.BH_TERMS_C3, np.random.default_rng(0)))
+    # a term outside the tensor-core generator's polynomial form (m = 4)
+    Jbh = api.jastrow_from(wl.bh_jastrow(w.atoms, w.xyz, [(4, 0, 0)], np.random.default_rng(0)))
     with pytest.raises(C.IsdfError) as e:
         api.tc_kernel_build(g, wt, xi, xig, Jbh, "bf16x6")
-    assert e.value.status == C.ISDF_E_UNSUPPORTED
+    assert e.value.status == C.ISDF_E_ARG

@@ -223,6 +223,60 @@ def test_ragged_small_system(P):
     assert max(rel(host(W16[c]), o["W"][c]) for c in range(4)) < 1e-5
 
 
+_BENZ = {}
+
+
+def _benzene_case(jscale):
+    if jscale not in _BENZ:
+        w = wl.benzene_small(jscale=jscale)
+        _BENZ[jscale] = (w, oracle_case(w))
+    return _BENZ[jscale]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("jscale", [0.05, 0.5])
+def test_w_tensor_core_bh(P, prec, jscale):
+    """Multi-centre (e-e, e-n, e-e-n) correlator of the benzene workload on the
+    tensor-core path: 12 centres, two types, 1008 points (ragged in both grid
+    directions), N_mu = 64.  jscale = 0.5 makes the free terms dominate."""
+    w, o = _benzene_case(jscale)
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
+                                _jas(P, w), prec)
+    errs = [rel(host(W[c]), o["W"][c]) for c in range(4)]
+    gerr = [rel(host(calG[c]), o["calG"][c]) for c in range(4)]
+    print(prec, jscale, "W", errs, "calG", gerr)
+    assert max(errs) < 1e-5, errs
+    assert max(gerr) < 1e-5, gerr
+
+
+@pytest.mark.parametrize("terms", ["c4", "deg3"])
+def test_w_tensor_core_bh_forms(P, terms):
+    """The other generator forms: two E-exponent groups with degree 3 (the
+    28-term set), and one group with degree 3."""
+    jt = wl.bh_terms_c4() if terms == "c4" else [(3, 1, 2), (1, 0, 0), (0, 0, 3), (2, 1, 0)]
+    w = wl.tiny_chain(n_atom=3, n_rad=8, n_ang=14, shells=(0, 1), n_mu=20, seed=5,
+                      jkind="bh", jterms=jt)
+    w.jastrow.coef[:] *= 10.0
+    o = oracle_case(w)
+    args = (cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w))
+    W, calG = P.tc_kernel_build(*args, "bf16x6")
+    errs = [rel(host(W[c]), o["W"][c]) for c in range(4)]
+    print(terms, errs)
+    assert max(errs) < 1e-5, errs
+
+
+def test_w_tensor_core_bh_slices(P):
+    """Outer-grid slices of the multi-centre build are additive."""
+    w, o = _benzene_case(0.05)
+    args = (cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w))
+    n_g = w.grid_xyz.shape[0]
+    Wsum = 0
+    for a, b in ((0, 300), (300, 700), (700, n_g)):
+        Ws, _ = P.tc_kernel_build(*args, "bf16x3", g_begin=a, g_end=b)
+        Wsum = Wsum + host(Ws)
+    assert max(rel(Wsum[c], o["W"][c]) for c in range(4)) < 1e-5
+
+
 def test_bh_jastrow_fp64(P):
     """Multi-centre Boys-Handy correlator (e-e, e-n, e-e-n terms) on the FP64 path."""
     w = wl.tiny_chain(n_atom=3, n_rad=8, n_ang=14, shells=(0, 1), n_mu=20, seed=5,
