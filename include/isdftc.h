@@ -95,7 +95,7 @@ typedef struct {
   int32_t precision;  /* isdf_precision; default ISDF_PREC_BF16X3 */
   int32_t kchunk;     /* inner-grid points accumulated in FP32 tensor memory before
                          each FP64 flush in stage 1; 0 = default (16384) */
-  int32_t s2_kchunk;  /* same for stage 2; 0 = default (16384) */
+  int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (timeouts, non-finite values) */
   int32_t debug_flags;/* bit 0: the stage-1 producer skips its first arrival, so
