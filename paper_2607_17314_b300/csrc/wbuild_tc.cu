@@ -566,12 +566,16 @@ __device__ __forceinline__ void s1_epilogue(const S1Params& p, const S1Smem& sm,
     const int64_t g_tile = tile % p.n_g_tiles;
     const int mu = (int)(tile / p.n_g_tiles) * C::BM + 32 * quad + lane;
     for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
-      if (!tc::mbar_wait(sm.acc_full, u & 1, sm.abort_flag, p.err)) return;
+      // tcgen05.ld/st/wait are warp-collective (.sync.aligned): every lane
+      // leaves the spin-wait and the divergent stores before reaching them
+      const bool ok = tc::mbar_wait(sm.acc_full, u & 1, sm.abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) return;
       tc::tc_fence_after();
       const bool first = (ch == 0), last = (ch + 1 == n_chunks);
 #pragma unroll 1
       for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
         uint32_t r[32];
+        __syncwarp();
         tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
                             first, r);
         if (!last) {
@@ -585,6 +589,7 @@ __device__ __forceinline__ void s1_epilogue(const S1Params& p, const S1Smem& sm,
             if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
         }
       }
+      __syncwarp();
       if (!last) tc::tmem_st_wait();
       tc::tc_fence_before();
       tc::mbar_arrive(sm.acc_empty);
@@ -805,12 +810,16 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
       const int64_t m = m0 + 32 * quad + lane;
       double* dst = p.out + (int64_t)z * p.out_bs + m * p.ldo;
       for (int64_t f = 0; f < n_folds; ++f) {
-        if (!tc::mbar_wait(acc_full, f & 1, abort_flag, p.err)) break;
+        // warp-collective tcgen05.ld/st/wait: reconverge after the spin-wait
+        // and after the divergent stores
+        const bool ok = tc::mbar_wait(acc_full, f & 1, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, ok)) break;
         tc::tc_fence_after();
         const bool first = (f == 0), last = (f + 1 == n_folds);
 #pragma unroll 1
         for (int blk = 0; blk < 4; ++blk) {
           uint32_t r[32];
+          __syncwarp();
           tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + 128 + blk * 32, first, r);
           if (!last) {
             tc::tmem_st_32x32b_x32(tmem + lane_base + 128 + blk * 32, r);
@@ -822,6 +831,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
             }
           }
         }
+        __syncwarp();
         if (!last) tc::tmem_st_wait();
         tc::tc_fence_before();
         tc::mbar_arrive(acc_empty);
