@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--w-only", action="store_true",
                     help="profiling mode: time only the W build on an H50-chain grid with "
                          "--w-nrad radial shells and seeded random xi (N_mu = --w-nmu)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="adjoint dW/dtheta on the H20 chain (FP32 and FP64) instead of the main line")
     ap.add_argument("--proposer", action="store_true",
                     help="learned proposer on perturbed H30 chains (60,000 points, 240 orbitals, "
                          "N_mu = 1200): train on --n-train, report on --n-test held-out chains")
@@ -255,6 +257,56 @@ def run_w_only(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adjoint(args):
+    """The adjoint dL/dtheta on the H20-chain workload (40,000 points, N_mu = 800,
+    28-term one-type correlator + d + b = 30 parameters; seeded xi and seed
+    Wbar of the workload's shapes): the FP32 adjoint kernel, with the FP64
+    forward W build of the same correlator on a 512-point outer slice for
+    comparison (the full FP64 forward and the FP64 adjoint take minutes at this
+    size; their agreement with the FP32 adjoint is tested on smaller cases)."""
+    import numpy as np
+    import torch
+    from synth import workloads as wl
+    from paper_2607_17314_b300 import api, build
+    build.build()
+    w = wl.h20_chain_bh()
+    n_g, n_mu = w.grid_xyz.shape[0], w.n_mu
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4321)
+    g = torch.tensor(w.grid_xyz, device="cuda")
+    wt = torch.tensor(w.grid_w, device="cuda")
+    xi = torch.randn((n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    xig = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    Wbar = torch.tensor(wl.seeded_matrix((4, n_mu, n_mu), 77), device="cuda")
+    J = api.jastrow_from(w.jastrow)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, ts
+
+    d32, t32 = timed(lambda: api.tc_kernel_adjoint(g, wt, xi, xig, J, Wbar, "fp32"))
+    rows = 512
+    _, tw = timed(lambda: api.tc_kernel_build(g, wt, xi, xig, J, "fp64", g_end=rows))
+    pair_flops = 8.0 * n_mu * n_g * n_g  # the recomputed M tiles, 4 channels
+    print(json.dumps({"mode": "adjoint", "workload": "h20_chain (28-term correlator, 30 parameters)",
+                      "n_g": n_g, "n_mu": n_mu, "n_params": int(d32.numel()),
+                      "fp32_ms": t32,
+                      "fp32_m_tile_tflops": pair_flops / (min(t32) * 1e-3) / 1e12,
+                      "forward_fp64_slice": {"outer_points": rows, "ms": tw,
+                                             "tflops": 8.0 * n_mu * n_g * rows / (min(tw) * 1e-3) / 1e12},
+                      "dtheta_finite": bool(torch.isfinite(d32).all())}), flush=True)
+
+
 def _chain(k):
     from synth import workloads as wl
     return wl.perturbed_chain(k)
@@ -330,6 +382,8 @@ def main():
         return run_reference(args, rank, world)
     if args.w_only:
         return run_w_only(args)
+    if args.adjoint:
+        return run_adjoint(args)
     if args.proposer:
         return run_proposer(args)
 

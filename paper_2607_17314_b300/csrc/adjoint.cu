@@ -8,8 +8,9 @@
 //
 // Bhat is one FP64 GEMM; the pair kernel recomputes the M^c tile from the
 // factors (nothing of size N_g^2 is stored), regenerates grad_1 u and its
-// parameter derivatives for each pair, and reduces the products per block
-// into FP64 atomics.  Parameters: theta = (d, b, c_0 .. c_{K-1}) for a
+// parameter derivatives for each pair (term loops unrolled over the supported
+// exponents m, n <= 3, o <= 4, so powers come from register tables), and
+// reduces the per-thread sums per block into FP64 atomics.  Parameters: theta = (d, b, c_0 .. c_{K-1}) for a
 // correlator with one nucleus type.
 #include "linalg.cuh"
 
@@ -56,11 +57,13 @@ __global__ void adj_table_kernel(const double* grid, int64_t n_g, const __grid_c
   for (int c = 0; c < 3; ++c) o[5 + c] = (T)((1.0 - b * r) / (den * den * den) * v[c] * inv);
 }
 
-template <class T>
-__device__ __forceinline__ T pw(T x, int n) {
-  T r = (T)1;
-  for (int i = 0; i < n; ++i) r *= x;
-  return r;
+// p[e] for a warp-uniform exponent e (register arrays stay in registers)
+template <class T, int N>
+__device__ __forceinline__ T sel(const T (&p)[N], int e) {
+  T v = p[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) v = e == i ? p[i] : v;
+  return v;
 }
 
 template <class T>
@@ -102,9 +105,11 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
 
   const int K = J.n_terms;
   const T d = (T)J.d;
-  double acc[AMAXK + 2];
+  // per-thread sums of the 4 pairs (term k at index 2 + k); the term loops are
+  // unrolled so that the accumulators stay in registers
+  T acc[AMAXK + 2];
 #pragma unroll
-  for (int p = 0; p < AMAXK + 2; ++p) acc[p] = 0.0;
+  for (int p = 0; p < AMAXK + 2; ++p) acc[p] = (T)0;
   const int64_t g = g0 + tg;
   if (g < a.n_g) {
     const double* rg = a.grid + 3 * g;
@@ -120,6 +125,10 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
       const T dEdr = d / (den * den);
       const T E_d = r / (den * den);
       const T dEdr_d = ((T)1 - d * r) / (den * den * den);
+      T pE[5];
+      pE[0] = (T)1;
+#pragma unroll
+      for (int i = 1; i < 5; ++i) pE[i] = pE[i - 1] * E;
       // pass 1: grad u
       T cE = J.cusp ? (T)0.5 / d : (T)0;
       T gx = 0, gy = 0, gz = 0;
@@ -127,16 +136,21 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
         const T* ti = a.tab + (g * J.n_nuc + I) * 8;
         const T* tj = a.tab + (h * J.n_nuc + I) * 8;
         const T Ai = ti[0], Aj = tj[0];
+        const T pi[4] = {(T)1, Ai, Ai * Ai, Ai * Ai * Ai};
+        const T pj[4] = {(T)1, Aj, Aj * Aj, Aj * Aj * Aj};
         T cA = 0;
-        for (int k = 0; k < K; ++k) {
-          const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
-          const T c = (T)J.coef[0][k];
-          const T Eo = pw(E, o);
-          T Da = 0;
-          if (m > 0) Da += (T)m * pw(Ai, m - 1) * pw(Aj, n);
-          if (n > 0) Da += (T)n * pw(Aj, m) * pw(Ai, n - 1);
-          cA += c * Da * Eo;
-          if (o > 0) cE += c * (pw(Ai, m) * pw(Aj, n) + pw(Aj, m) * pw(Ai, n)) * (T)o * pw(E, o - 1);
+#pragma unroll
+        for (int k = 0; k < AMAXK; ++k) {
+          if (k < K) {
+            const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
+            const T c = (T)J.coef[0][k];
+            T Da = 0;
+            if (m > 0) Da += (T)m * sel(pi, m - 1) * sel(pj, n);
+            if (n > 0) Da += (T)n * sel(pj, m) * sel(pi, n - 1);
+            cA += c * Da * sel(pE, o);
+            if (o > 0)
+              cE += c * (sel(pi, m) * sel(pj, n) + sel(pj, m) * sel(pi, n)) * (T)o * sel(pE, o - 1);
+          }
         }
         gx += cA * ti[1];
         gy += cA * ti[2];
@@ -154,53 +168,61 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
         const T* ti = a.tab + (g * J.n_nuc + I) * 8;
         const T* tj = a.tab + (h * J.n_nuc + I) * 8;
         const T Ai = ti[0], Aj = tj[0], Ai_b = ti[4], Aj_b = tj[4];
+        const T pi[4] = {(T)1, Ai, Ai * Ai, Ai * Ai * Ai};
+        const T pj[4] = {(T)1, Aj, Aj * Aj, Aj * Aj * Aj};
         const T cg = cx * ti[1] + cy * ti[2] + cz * ti[3];        // coef . gA
         const T cgb = cx * ti[5] + cy * ti[6] + cz * ti[7];       // coef . dgA/db
         T cA = 0, cA_d = 0, cA_b = 0;
-        for (int k = 0; k < K; ++k) {
-          const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
-          const T c = (T)J.coef[0][k];
-          const T S = pw(Ai, m) * pw(Aj, n) + pw(Aj, m) * pw(Ai, n);
-          T S_b = 0, Da = 0, Da_b = 0;
-          if (m > 0) {
-            S_b += (T)m * pw(Ai, m - 1) * pw(Aj, n) * Ai_b + (T)m * pw(Aj, m - 1) * pw(Ai, n) * Aj_b;
-            Da += (T)m * pw(Ai, m - 1) * pw(Aj, n);
-            if (m > 1) Da_b += (T)(m * (m - 1)) * pw(Ai, m - 2) * pw(Aj, n) * Ai_b;
-            if (n > 0) Da_b += (T)(m * n) * pw(Ai, m - 1) * pw(Aj, n - 1) * Aj_b;
+#pragma unroll
+        for (int k = 0; k < AMAXK; ++k) {
+          if (k < K) {
+            const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
+            const T c = (T)J.coef[0][k];
+            const T S = sel(pi, m) * sel(pj, n) + sel(pj, m) * sel(pi, n);
+            T S_b = 0, Da = 0, Da_b = 0;
+            if (m > 0) {
+              S_b += (T)m * sel(pi, m - 1) * sel(pj, n) * Ai_b +
+                     (T)m * sel(pj, m - 1) * sel(pi, n) * Aj_b;
+              Da += (T)m * sel(pi, m - 1) * sel(pj, n);
+              if (m > 1) Da_b += (T)(m * (m - 1)) * sel(pi, m - 2) * sel(pj, n) * Ai_b;
+              if (n > 0) Da_b += (T)(m * n) * sel(pi, m - 1) * sel(pj, n - 1) * Aj_b;
+            }
+            if (n > 0) {
+              S_b += (T)n * sel(pi, m) * sel(pj, n - 1) * Aj_b +
+                     (T)n * sel(pj, m) * sel(pi, n - 1) * Ai_b;
+              Da += (T)n * sel(pj, m) * sel(pi, n - 1);
+              if (m > 0) Da_b += (T)(n * m) * sel(pj, m - 1) * sel(pi, n - 1) * Aj_b;
+              if (n > 1) Da_b += (T)(n * (n - 1)) * sel(pj, m) * sel(pi, n - 2) * Ai_b;
+            }
+            const T Eo = sel(pE, o);
+            const T Eo_d = o > 0 ? (T)o * sel(pE, o - 1) * E_d : (T)0;
+            T dc = Da * Eo * cg;  // d/dc_k of the cA_I gA_I part
+            if (o > 0) {
+              const T Eo1 = sel(pE, o - 1);
+              const T Eo1_d = o > 1 ? (T)(o - 1) * sel(pE, o - 2) * E_d : (T)0;
+              dc += S * (T)o * Eo1 * dEdr * ce;
+              cE_d += c * S * (T)o * Eo1_d;
+              cE_b += c * S_b * (T)o * Eo1;
+            }
+            acc[2 + k] += dc;
+            cA += c * Da * Eo;
+            cA_d += c * Da * Eo_d;
+            cA_b += c * Da_b * Eo;
           }
-          if (n > 0) {
-            S_b += (T)n * pw(Ai, m) * pw(Aj, n - 1) * Aj_b + (T)n * pw(Aj, m) * pw(Ai, n - 1) * Ai_b;
-            Da += (T)n * pw(Aj, m) * pw(Ai, n - 1);
-            if (m > 0) Da_b += (T)(n * m) * pw(Aj, m - 1) * pw(Ai, n - 1) * Aj_b;
-            if (n > 1) Da_b += (T)(n * (n - 1)) * pw(Aj, m) * pw(Ai, n - 2) * Ai_b;
-          }
-          const T Eo = pw(E, o);
-          const T Eo_d = o > 0 ? (T)o * pw(E, o - 1) * E_d : (T)0;
-          T dc = Da * Eo * cg;  // d/dc_k of the cA_I gA_I part
-          if (o > 0) {
-            const T Eo1 = pw(E, o - 1);
-            const T Eo1_d = o > 1 ? (T)(o - 1) * pw(E, o - 2) * E_d : (T)0;
-            dc += S * (T)o * Eo1 * dEdr * ce;
-            cE_d += c * S * (T)o * Eo1_d;
-            cE_b += c * S_b * (T)o * Eo1;
-          }
-          acc[2 + k] += (double)dc;
-          cA += c * Da * Eo;
-          cA_d += c * Da * Eo_d;
-          cA_b += c * Da_b * Eo;
         }
         s_d += cA_d * cg;
         s_b += cA_b * cg + cA * cgb;
       }
-      acc[0] += (double)((cE_d * dEdr + cE * dEdr_d) * ce + s_d);
-      acc[1] += (double)(cE_b * dEdr * ce + s_b);
+      acc[0] += (cE_d * dEdr + cE * dEdr_d) * ce + s_d;
+      acc[1] += cE_b * dEdr * ce + s_b;
     }
   }
   // block reduction: warp shuffles, then one row per warp in shared memory
   const int P = 2 + K;
+#pragma unroll
   for (int p = 0; p < AMAXK + 2; ++p) {
     if (p >= P) break;
-    double v = acc[p];
+    double v = (double)acc[p];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((t & 31) == 0) red[t >> 5][p] = v;
   }
@@ -286,6 +308,11 @@ int adjoint(const double* grid, const double* w, const double* xi, const double*
     set_error("the adjoint takes one nucleus type and at most %d free terms", AMAXK);
     return ISDF_E_UNSUPPORTED;
   }
+  for (int k = 0; k < J.n_terms; ++k)
+    if (J.mno[k][0] > 3 || J.mno[k][1] > 3 || J.mno[k][2] > 4) {
+      set_error("the adjoint takes exponents m, n <= 3 and o <= 4 (term %d)", k);
+      return ISDF_E_UNSUPPORTED;
+    }
   if (precision == ISDF_PREC_FP64)
     return run_adjoint<double>(grid, w, xi, xig, n_g, n_mu, J, Wbar, dtheta, ws, ws_bytes, s);
   return run_adjoint<float>(grid, w, xi, xig, n_g, n_mu, J, Wbar, dtheta, ws, ws_bytes, s);
