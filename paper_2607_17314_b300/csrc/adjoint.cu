@@ -8,9 +8,12 @@
 //
 // Bhat is one FP64 GEMM; the pair kernel recomputes the M^c tile from the
 // factors (nothing of size N_g^2 is stored), regenerates grad_1 u and its
-// parameter derivatives for each pair (term loops unrolled over the supported
-// exponents m, n <= 3, o <= 4, so powers come from register tables), and
-// reduces the per-thread sums per block into FP64 atomics.  Parameters: theta = (d, b, c_0 .. c_{K-1}) for a
+// parameter derivatives for each pair, and reduces the per-thread sums per
+// block into FP64 atomics.  The terms are folded by exponent group {m, n}
+// (m, n <= 3; 10 groups fixed at compile time) and E power o <= 4: per pair,
+// the nucleus sums of S, dS/dA, their b-derivatives and cg-weighted forms are
+// taken once per group, and the derivative of term k is the (group, power)
+// combination that it belongs to.  Parameters: theta = (d, b, c_0 .. c_{K-1}) for a
 // correlator with one nucleus type.
 #include "linalg.cuh"
 
@@ -32,8 +35,19 @@ struct AdjArgs {
   int64_t n_g;
   int n_mu;
   const T* tab;    // [n_g][n_nuc][8]: A, gA(3), A_b, gA_b(3)
-  double* dtheta;  // [2 + K]
+  double* sums;    // [2 + NGRP * 5]: d, b, then (group, E power) sums
+  T gc[10][5];     // C_G[o] = sum of c_k over the terms of group G with E power o
 };
+
+// Terms grouped by the unordered exponent pair {m, n} (m <= n <= 3): group G
+// holds (m, n) = (gm(G), gn(G)); S = A^m B^n + B^m A^n and its derivatives are
+// the same for (m, n) and (n, m).
+constexpr int NGRP = 10;
+__host__ __device__ constexpr int gm(int G) { return G < 4 ? 0 : G < 7 ? 1 : G < 9 ? 2 : 3; }
+__host__ __device__ constexpr int gn(int G) { return G < 4 ? G : G < 7 ? G - 3 : G < 9 ? G - 5 : 3; }
+__host__ __device__ constexpr int grp_of(int m, int n) {
+  return m > n ? grp_of(n, m) : m == 0 ? n : m == 1 ? 3 + n : m == 2 ? 5 + n : 9;
+}
 
 // Per-point nucleus table: A = b r/(1+br), grad A = b/(1+br)^2 e,
 // dA/db = r/(1+br)^2, d(grad A)/db = (1-br)/(1+br)^3 e.
@@ -71,7 +85,7 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
   constexpr int AMU = AMu<T>::v;
   __shared__ T As[4][AMU][AT];
   __shared__ T Bs[4][AMU][AT];
-  __shared__ double red[8][AMAXK + 2];
+  __shared__ double red[8][2 + NGRP * 5];
   const int t = threadIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * AT, h0 = (int64_t)blockIdx.x * AT;
   // each thread: g row (t / 8), g' columns (t % 8) + 8 j, j < 4
@@ -103,13 +117,11 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
     __syncthreads();
   }
 
-  const int K = J.n_terms;
   const T d = (T)J.d;
-  // per-thread sums of the 4 pairs (term k at index 2 + k); the term loops are
-  // unrolled so that the accumulators stay in registers
-  T acc[AMAXK + 2];
+  // per-thread sums over its pairs: [0] d, [1] b, [2 + 5 G + o] group G, E power o
+  T acc[2 + NGRP * 5];
 #pragma unroll
-  for (int p = 0; p < AMAXK + 2; ++p) acc[p] = (T)0;
+  for (int q = 0; q < 2 + NGRP * 5; ++q) acc[q] = (T)0;
   const int64_t g = g0 + tg;
   if (g < a.n_g) {
     const double* rg = a.grid + 3 * g;
@@ -129,9 +141,26 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
       pE[0] = (T)1;
 #pragma unroll
       for (int i = 1; i < 5; ++i) pE[i] = pE[i - 1] * E;
-      // pass 1: grad u
+      // E weights of each group: P0 = sum_o C_G[o] E^o, P1 = its E-derivative, P2 the second
+      T P0[NGRP], P1[NGRP], P2[NGRP];
+#pragma unroll
+      for (int G = 0; G < NGRP; ++G) {
+        P0[G] = (T)0;
+        P1[G] = (T)0;
+        P2[G] = (T)0;
+#pragma unroll
+        for (int o = 0; o < 5; ++o) {
+          P0[G] += a.gc[G][o] * pE[o];
+          if (o > 0) P1[G] += a.gc[G][o] * (T)o * pE[o - 1];
+          if (o > 1) P2[G] += a.gc[G][o] * (T)(o * (o - 1)) * pE[o - 2];
+        }
+      }
+      // pass 1: grad u, and Y_G = sum_I S_G
       T cE = J.cusp ? (T)0.5 / d : (T)0;
       T gx = 0, gy = 0, gz = 0;
+      T Y[NGRP];
+#pragma unroll
+      for (int G = 0; G < NGRP; ++G) Y[G] = (T)0;
       for (int I = 0; I < J.n_nuc; ++I) {
         const T* ti = a.tab + (g * J.n_nuc + I) * 8;
         const T* tj = a.tab + (h * J.n_nuc + I) * 8;
@@ -140,17 +169,15 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
         const T pj[4] = {(T)1, Aj, Aj * Aj, Aj * Aj * Aj};
         T cA = 0;
 #pragma unroll
-        for (int k = 0; k < AMAXK; ++k) {
-          if (k < K) {
-            const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
-            const T c = (T)J.coef[0][k];
-            T Da = 0;
-            if (m > 0) Da += (T)m * sel(pi, m - 1) * sel(pj, n);
-            if (n > 0) Da += (T)n * sel(pj, m) * sel(pi, n - 1);
-            cA += c * Da * sel(pE, o);
-            if (o > 0)
-              cE += c * (sel(pi, m) * sel(pj, n) + sel(pj, m) * sel(pi, n)) * (T)o * sel(pE, o - 1);
-          }
+        for (int G = 0; G < NGRP; ++G) {
+          const int m = gm(G), n = gn(G);
+          const T S = pi[m] * pj[n] + pj[m] * pi[n];
+          T Da = 0;
+          if (m > 0) Da += (T)m * pi[m > 0 ? m - 1 : 0] * pj[n];
+          if (n > 0) Da += (T)n * pi[n > 0 ? n - 1 : 0] * pj[m];
+          cA += P0[G] * Da;
+          cE += P1[G] * S;
+          Y[G] += S;
         }
         gx += cA * ti[1];
         gy += cA * ti[2];
@@ -160,10 +187,10 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
       const T msq2 = (T)2 * M[3][j];
       const T cx = M[0][j] + msq2 * Kx, cy = M[1][j] + msq2 * Ky, cz = M[2][j] + msq2 * Kz;
       const T ce = cx * ex + cy * ey + cz * ez;  // coef . e_ij
-      // pass 2: parameter derivatives contracted with coef
-      T cE_d = J.cusp ? (T)-0.5 / (d * d) : (T)0;
-      T cE_b = 0;
-      T s_d = 0, s_b = 0;  // sum_I coef . (d(cA_I gA_I)/d{d,b})
+      // pass 2: X_G = sum_I Da cg, Z_G = sum_I dS/db, V_G = sum_I (dDa/db cg + Da cgb)
+      T X[NGRP], Z[NGRP], V[NGRP];
+#pragma unroll
+      for (int G = 0; G < NGRP; ++G) X[G] = Z[G] = V[G] = (T)0;
       for (int I = 0; I < J.n_nuc; ++I) {
         const T* ti = a.tab + (g * J.n_nuc + I) * 8;
         const T* tj = a.tab + (h * J.n_nuc + I) * 8;
@@ -172,65 +199,71 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
         const T pj[4] = {(T)1, Aj, Aj * Aj, Aj * Aj * Aj};
         const T cg = cx * ti[1] + cy * ti[2] + cz * ti[3];        // coef . gA
         const T cgb = cx * ti[5] + cy * ti[6] + cz * ti[7];       // coef . dgA/db
-        T cA = 0, cA_d = 0, cA_b = 0;
 #pragma unroll
-        for (int k = 0; k < AMAXK; ++k) {
-          if (k < K) {
-            const int m = J.mno[k][0], n = J.mno[k][1], o = J.mno[k][2];
-            const T c = (T)J.coef[0][k];
-            const T S = sel(pi, m) * sel(pj, n) + sel(pj, m) * sel(pi, n);
-            T S_b = 0, Da = 0, Da_b = 0;
-            if (m > 0) {
-              S_b += (T)m * sel(pi, m - 1) * sel(pj, n) * Ai_b +
-                     (T)m * sel(pj, m - 1) * sel(pi, n) * Aj_b;
-              Da += (T)m * sel(pi, m - 1) * sel(pj, n);
-              if (m > 1) Da_b += (T)(m * (m - 1)) * sel(pi, m - 2) * sel(pj, n) * Ai_b;
-              if (n > 0) Da_b += (T)(m * n) * sel(pi, m - 1) * sel(pj, n - 1) * Aj_b;
-            }
-            if (n > 0) {
-              S_b += (T)n * sel(pi, m) * sel(pj, n - 1) * Aj_b +
-                     (T)n * sel(pj, m) * sel(pi, n - 1) * Ai_b;
-              Da += (T)n * sel(pj, m) * sel(pi, n - 1);
-              if (m > 0) Da_b += (T)(n * m) * sel(pj, m - 1) * sel(pi, n - 1) * Aj_b;
-              if (n > 1) Da_b += (T)(n * (n - 1)) * sel(pj, m) * sel(pi, n - 2) * Ai_b;
-            }
-            const T Eo = sel(pE, o);
-            const T Eo_d = o > 0 ? (T)o * sel(pE, o - 1) * E_d : (T)0;
-            T dc = Da * Eo * cg;  // d/dc_k of the cA_I gA_I part
-            if (o > 0) {
-              const T Eo1 = sel(pE, o - 1);
-              const T Eo1_d = o > 1 ? (T)(o - 1) * sel(pE, o - 2) * E_d : (T)0;
-              dc += S * (T)o * Eo1 * dEdr * ce;
-              cE_d += c * S * (T)o * Eo1_d;
-              cE_b += c * S_b * (T)o * Eo1;
-            }
-            acc[2 + k] += dc;
-            cA += c * Da * Eo;
-            cA_d += c * Da * Eo_d;
-            cA_b += c * Da_b * Eo;
+        for (int G = 0; G < NGRP; ++G) {
+          const int m = gm(G), n = gn(G);
+          T Da = 0, Db = 0, DaA = 0, DaB = 0;
+          if (m > 0) {
+            Da += (T)m * pi[m > 0 ? m - 1 : 0] * pj[n];
+            Db += (T)m * pj[m > 0 ? m - 1 : 0] * pi[n];
           }
+          if (n > 0) {
+            Da += (T)n * pi[n > 0 ? n - 1 : 0] * pj[m];
+            Db += (T)n * pj[n > 0 ? n - 1 : 0] * pi[m];
+          }
+          if (m > 1) DaA += (T)(m * (m - 1)) * pi[m > 1 ? m - 2 : 0] * pj[n];
+          if (n > 1) DaA += (T)(n * (n - 1)) * pi[n > 1 ? n - 2 : 0] * pj[m];
+          if (m > 0 && n > 0)
+            DaB += (T)(m * n) * (pi[m > 0 ? m - 1 : 0] * pj[n > 0 ? n - 1 : 0] +
+                                 pi[n > 0 ? n - 1 : 0] * pj[m > 0 ? m - 1 : 0]);
+          X[G] += Da * cg;
+          Z[G] += Da * Ai_b + Db * Aj_b;
+          V[G] += (DaA * Ai_b + DaB * Aj_b) * cg + Da * cgb;
         }
-        s_d += cA_d * cg;
-        s_b += cA_b * cg + cA * cgb;
       }
-      acc[0] += (cE_d * dEdr + cE * dEdr_d) * ce + s_d;
-      acc[1] += cE_b * dEdr * ce + s_b;
+      T sYd = 0, sXd = 0, sZb = 0, sVb = 0;
+      const T ce_dEdr = ce * dEdr;
+#pragma unroll
+      for (int G = 0; G < NGRP; ++G) {
+        sYd += P2[G] * Y[G];
+        sXd += P1[G] * X[G];
+        sZb += P1[G] * Z[G];
+        sVb += P0[G] * V[G];
+#pragma unroll
+        for (int o = 0; o < 5; ++o)
+          acc[2 + 5 * G + o] += pE[o] * X[G] + (o > 0 ? (T)o * pE[o > 0 ? o - 1 : 0] * ce_dEdr * Y[G] : (T)0);
+      }
+      const T cE_d = (J.cusp ? (T)-0.5 / (d * d) : (T)0) + E_d * sYd;
+      acc[0] += (cE_d * dEdr + cE * dEdr_d) * ce + E_d * sXd;
+      acc[1] += sZb * ce_dEdr + sVb;
     }
   }
   // block reduction: warp shuffles, then one row per warp in shared memory
-  const int P = 2 + K;
+  constexpr int P = 2 + NGRP * 5;
 #pragma unroll
-  for (int p = 0; p < AMAXK + 2; ++p) {
-    if (p >= P) break;
-    double v = (double)acc[p];
+  for (int q = 0; q < P; ++q) {
+    double v = (double)acc[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((t & 31) == 0) red[t >> 5][p] = v;
+    if ((t & 31) == 0) red[t >> 5][q] = v;
   }
   __syncthreads();
   if (t < P) {
-    double s = 0.0;
-    for (int w8 = 0; w8 < 8; ++w8) s += red[w8][t];
-    atomicAdd(a.dtheta + t, s);
+    double sum = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) sum += red[w8][t];
+    atomicAdd(a.sums + t, sum);
+  }
+}
+
+// dtheta = (d, b, c_0 .. c_{K-1}) from the (group, E power) sums
+__global__ void adj_scatter_kernel(const double* sums, const __grid_constant__ isdf_jastrow J,
+                                   double* dtheta) {
+  const int k = threadIdx.x;
+  if (k >= 2 + J.n_terms) return;
+  if (k < 2) {
+    dtheta[k] = sums[k];
+  } else {
+    const int* t = J.mno[k - 2];
+    dtheta[k] = sums[2 + 5 * grp_of(t[0], t[1]) + t[2]];
   }
 }
 
@@ -256,6 +289,7 @@ int run_adjoint(const double* grid, const double* w, const double* xi, const dou
   T* Ah = cv.take<T>(4 * plane);
   T* Bh = cv.take<T>(4 * plane);
   T* tab = cv.take<T>((size_t)n_g * J.n_nuc * 8);
+  double* sums = cv.take<double>(2 + NGRP * 5);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   // Bhat^c = Wbar^c (w xi)
   Dgemm g;
@@ -276,12 +310,19 @@ int run_adjoint(const double* grid, const double* w, const double* xi, const dou
     adj_table_kernel<T><<<nb(n_g * J.n_nuc), 256, 0, s>>>(grid, n_g, J, tab);
     ISDF_LAUNCH_CHECK();
   }
-  ISDF_CUDA(cudaMemsetAsync(dtheta, 0, sizeof(double) * (2 + J.n_terms), s));
+  ISDF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (2 + NGRP * 5), s));
   AdjArgs<T> a;
-  a.Ah = Ah; a.Bh = Bh; a.grid = grid; a.n_g = n_g; a.n_mu = n_mu; a.tab = tab; a.dtheta = dtheta;
+  a.Ah = Ah; a.Bh = Bh; a.grid = grid; a.n_g = n_g; a.n_mu = n_mu; a.tab = tab; a.sums = sums;
+  double gc[NGRP][5] = {};
+  for (int k = 0; k < J.n_terms; ++k)
+    gc[grp_of(J.mno[k][0], J.mno[k][1])][J.mno[k][2]] += J.coef[0][k];
+  for (int G = 0; G < NGRP; ++G)
+    for (int o = 0; o < 5; ++o) a.gc[G][o] = (T)gc[G][o];
   dim3 grd((unsigned)ceil_div(n_g, AT), (unsigned)ceil_div(n_g, AT));
   ISDF_ARG(grd.y < 65536u, "n_g too large for the adjoint grid");
   adj_pair_kernel<T><<<grd, 256, 0, s>>>(a, J);
+  ISDF_LAUNCH_CHECK();
+  adj_scatter_kernel<<<1, 64, 0, s>>>(sums, J, dtheta);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
@@ -296,6 +337,7 @@ size_t adjoint_ws(int64_t n_g, int n_mu, int n_nuc, int precision) {
   c.take<unsigned char>(4 * plane * el);
   c.take<unsigned char>(4 * plane * el);
   c.take<unsigned char>((size_t)n_g * n_nuc * 8 * el);
+  c.take<double>(2 + NGRP * 5);
   return c.off;
 }
 
