@@ -277,11 +277,12 @@ int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
  * calG [>=3][n_mu][n_g] FP64; D [n_mu][n_mu] FP64;
  * X_packed [n_orb_x (n_orb_x + 1) / 2][n_mu] FP64 or NULL.
  * precision: ISDF_PREC_FP64 (CUDA-core FP64 GEMMs) or ISDF_PREC_BF16X3 /
- * ISDF_PREC_BF16X6 (the D4 and D1 contractions as split-BF16 tcgen05 GEMMs
- * with FP32 accumulation folded every 256 grid points; X stays FP64).
+ * ISDF_PREC_BF16X6 (the D4 and D1 contractions and the two GEMM families of
+ * X as split-BF16 tcgen05 GEMMs with FP32 accumulation folded every 256 inner
+ * points, X always with three limbs; the element-wise parts in FP64).
  * Asynchronous for FP64.  The tensor-core precisions synchronise `stream`
- * after the D contraction to read the pipeline's wait-status word and return
- * ISDF_E_TIMEOUT if a bounded wait expired. */
+ * after the D and X contractions to read the pipeline's wait-status word and
+ * return ISDF_E_TIMEOUT if a bounded wait expired. */
 size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ,
                                       int n_orb_x, int precision);
 int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const double* xi,

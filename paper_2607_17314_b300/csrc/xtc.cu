@@ -12,6 +12,12 @@
 //   X_{qs mu}    = sum_g w_g [ xi_mu(g) Q1_{qs}(g) + sum_c calG^c_{mu g} Q2^c_{qs}(g) ]
 // for q <= s < n_orb_x, packed row s(s+1)/2 + q (the X_{qs} = X_{sq}
 // symmetry of Sec. IV.C).
+// With the split-BF16 precisions, D4, D1 and the two GEMM families of X run on
+// the tcgen05 split GEMM (FP32 accumulation folded every 256 inner points,
+// FP64 partial sums; X always with three limbs); the element-wise parts stay
+// in FP64.
+#include <cuda_bf16.h>
+
 #include "linalg.cuh"
 
 namespace isdf {
@@ -105,6 +111,35 @@ __global__ void q_kernel(const double* F, int n_occ, int n_s, int64_t nbg, int64
 }
 
 constexpr int64_t XBATCH = 4096;
+// X's GEMMs always split into three limbs: its products cancel strongly (two
+// limbs leave ~2e-5 relative error in X, three ~3e-6) and they are small.
+constexpr int kXLimbs = 3;
+
+// Transposed limb split: dst[l][r][c] = limb l of src[c * src_rs + c0 + r]
+// (r < rows, c < cols; zero in the padding), through 32 x 32 shared-memory
+// tiles so that both the reads (along r) and the writes (along c) coalesce.
+__global__ void split_t_kernel(const double* __restrict__ src, int64_t src_rs, int64_t c0,
+                               int64_t rows, int64_t cols, int64_t rows_pad, int64_t cols_pad,
+                               int limbs, __nv_bfloat16* __restrict__ dst) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, cb = (int64_t)blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t c = cb + i, r = r0 + threadIdx.x;
+    t[i][threadIdx.x] = (c < cols && r < rows) ? src[c * src_rs + c0 + r] : 0.0;
+  }
+  __syncthreads();
+  const int64_t plane = rows_pad * cols_pad;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = cb + threadIdx.x;
+    if (r >= rows_pad || c >= cols_pad) continue;
+    double v = t[threadIdx.x][i];
+    for (int l = 0; l < limbs; ++l) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      dst[l * plane + r * cols_pad + c] = h;
+      v -= (double)__bfloat162float(h);
+    }
+  }
+}
 
 }  // namespace
 
@@ -124,9 +159,17 @@ size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x, int prec
   if (n_orb_x > 0) {
     const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
     const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
-    c.take<double>((size_t)n_occ * n_orb_x * n_mu);
-    c.take<double>((size_t)4 * n_occ * n_orb_x * nbg);
+    const int64_t nas = (int64_t)n_occ * n_orb_x;
+    c.take<double>((size_t)nas * n_mu);
+    c.take<double>((size_t)4 * nas * nbg);
     c.take<double>((size_t)4 * npair * nbg);
+    if (precision != ISDF_PREC_FP64) {
+      const int64_t kmu = round_up(n_mu, 32), kg = round_up(nbg, 32);
+      c.take<uint16_t>((size_t)kXLimbs * round_up(nas, 128) * kmu);
+      c.take<uint16_t>((size_t)4 * kXLimbs * round_up(nbg, 128) * kmu);
+      c.take<uint16_t>((size_t)4 * kXLimbs * round_up(npair, 128) * kg);
+      c.take<uint16_t>((size_t)4 * kXLimbs * round_up(n_mu, 128) * kg);
+    }
   }
   return c.off;
 }
@@ -158,10 +201,19 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
   double *P = nullptr, *F = nullptr, *Q = nullptr;
   const int64_t nbg = XBATCH < n_g ? XBATCH : n_g;
   const int64_t npair = (int64_t)n_orb_x * (n_orb_x + 1) / 2;
+  uint16_t *Pl = nullptr, *Bt = nullptr, *Ql = nullptr, *Bb = nullptr;
+  const int64_t kmu = round_up(n_mu, 32), kgx = round_up(nbg, 32);
+  const int64_t nas_pad = round_up((int64_t)n_occ * n_orb_x, 128), np_pad = round_up(npair, 128);
   if (n_orb_x > 0) {
     P = cv.take<double>((size_t)n_occ * n_orb_x * n_mu);
     F = cv.take<double>((size_t)4 * n_occ * n_orb_x * nbg);
     Q = cv.take<double>((size_t)4 * npair * nbg);
+    if (precision != ISDF_PREC_FP64) {
+      Pl = cv.take<uint16_t>((size_t)kXLimbs * nas_pad * kmu);
+      Bt = cv.take<uint16_t>((size_t)4 * kXLimbs * round_up(nbg, 128) * kmu);
+      Ql = cv.take<uint16_t>((size_t)4 * kXLimbs * np_pad * kgx);
+      Bb = cv.take<uint16_t>((size_t)4 * kXLimbs * mp * kgx);
+    }
   }
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   const int64_t plane = (int64_t)n_mu * n_g;
@@ -236,6 +288,54 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
   const int64_t nas = (int64_t)n_occ * n_orb_x;
   pair_factor_kernel<<<nb(nas * n_mu), 256, 0, s>>>(phiP, n_mu, n_orb, n_occ, n_orb_x, P);
   ISDF_LAUNCH_CHECK();
+  if (precision != ISDF_PREC_FP64) {
+    // F = P [xi | calG^c](:, batch) and X += sum_f Q_f [xi | calG^c](:, batch)^T on the
+    // split-BF16 GEMM; the batch operands are split per batch (the F family transposed)
+    ISDF_TRY(split_operand(P, n_mu, 0, nullptr, nas, n_mu, nas_pad, kmu, kXLimbs, Pl, s));
+    ISDF_CUDA(cudaMemsetAsync(Xp, 0, sizeof(double) * (size_t)npair * n_mu, s));
+    const int64_t nq = npair * nbg;
+    for (int64_t g0 = 0; g0 < n_g; g0 += nbg) {
+      const int64_t bw = g0 + nbg <= n_g ? nbg : n_g - g0;
+      const int64_t bw_pad = round_up(bw, 128), kg = round_up(bw, 32);
+      const size_t tpl = (size_t)kXLimbs * bw_pad * kmu;
+      const void* A4[4];
+      const void* B4[4];
+      for (int f = 0; f < 4; ++f) {
+        const double* src = f == 0 ? xi : calG + (int64_t)(f - 1) * plane;
+        uint16_t* dst = Bt + f * tpl;
+        const dim3 grd((unsigned)ceil_div(bw_pad, 32), (unsigned)ceil_div(kmu, 32));
+        split_t_kernel<<<grd, dim3(32, 8), 0, s>>>(src, n_g, g0, bw, n_mu, bw_pad, kmu, kXLimbs,
+                                                  (__nv_bfloat16*)dst);
+        ISDF_LAUNCH_CHECK();
+        A4[f] = Pl;
+        B4[f] = dst;
+      }
+      ISDF_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * 4 * (size_t)nas * nbg, s));
+      ISDF_TRY(splitgemm(kXLimbs, 4, A4, B4, nas, bw, kmu, kmu, 256, F, nbg, nas * nbg, 1.0, err, s));
+      q_kernel<<<nb(npair * bw), 256, 0, s>>>(F, n_occ, n_orb_x, nbg, bw, w, g0, Q);
+      ISDF_LAUNCH_CHECK();
+      const size_t qpl = (size_t)kXLimbs * np_pad * kg, bpl = (size_t)kXLimbs * mp * kg;
+      for (int f = 0; f < 4; ++f) {
+        const double* src = f == 0 ? xi : calG + (int64_t)(f - 1) * plane;
+        ISDF_TRY(split_operand(Q + f * nq, nbg, 0, nullptr, npair, bw, np_pad, kg, kXLimbs,
+                               Ql + f * qpl, s));
+        ISDF_TRY(split_operand(src, n_g, g0, nullptr, n_mu, bw, mp, kg, kXLimbs, Bb + f * bpl, s));
+        A4[f] = Ql + f * qpl;
+        B4[f] = Bb + f * bpl;
+      }
+      const int64_t kr = kg < 1024 ? kg : 1024;
+      ISDF_TRY(splitgemm(kXLimbs, 4, A4, B4, npair, n_mu, kg, kr, 256, Xp, n_mu, 0, 1.0, err, s));
+    }
+    int h_err = 0;
+    ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ISDF_CUDA(cudaStreamSynchronize(s));
+    if (h_err) {
+      set_error("tensor-core pipeline wait expired in the X contraction (device error word 0x%x)",
+                h_err);
+      return ISDF_E_TIMEOUT;
+    }
+    return ISDF_OK;
+  }
   for (int64_t g0 = 0; g0 < n_g; g0 += nbg) {
     const int64_t bw = g0 + nbg <= n_g ? nbg : n_g - g0;
     // F[0] = P xi[:, batch], F[1+c] = P calG^c[:, batch]   (row stride nbg)

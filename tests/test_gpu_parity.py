@@ -155,7 +155,7 @@ def test_xtc(P, h6):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
 def test_xtc_tensor_core(P, h6, prec):
-    """D on the split-BF16 tensor-core GEMMs; X stays FP64."""
+    """D and X on the split-BF16 tensor-core GEMMs."""
     w, o = h6
     n_orb = w.n_orb
     D, Xp = P.xtc_density_contract(cu(o["phiP"]), w.n_occ, cu(o["xi"]), cu(w.grid_w),
@@ -163,7 +163,9 @@ def test_xtc_tensor_core(P, h6, prec):
     _, _, Dref = xtc.d_kernels(w.grid_w, o["xi"], o["calG"], xtc.g_nu(o["phiP"], w.n_occ))
     assert rel(host(D), Dref) < 1e-5
     Xfull = xtc.x_projector(w.grid_w, o["xi"], o["calG"], o["phiP"], w.n_occ)
-    assert rel(host(Xp), xtc.pack_upper(Xfull)) < 1e-10
+    xerr = rel(host(Xp), xtc.pack_upper(Xfull))
+    print(prec, "X rel", xerr)
+    assert xerr < 1e-5
 
 
 def test_xtc_tensor_core_chunks(P):
