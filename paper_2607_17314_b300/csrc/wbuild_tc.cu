@@ -1,17 +1,19 @@
 // Jastrow kernels u^(1),c and u^(3) (Eqs. K1-isdf, K3-isdf) on the
 // 5th-generation tensor cores (tcgen05) of sm_103a, with split-BF16 operands
-// and FP32 accumulation in tensor memory, flushed to FP64 every kchunk
-// inner-grid points.
+// and FP32 accumulation in tensor memory, folded into an FP32 running sum
+// every kchunk inner-grid points and written to FP64 once per tile.
 //
 // Stage 1 (the O(N_mu N_g^2) contraction, Sec. IV.C doubly-blocked grid sum):
 //   calG^c[nu][g] = sum_g' (w xi)[nu][g'] K_c(g, g'),  c = x, y, z, sq
 // as a GEMM D[nu][g] = A[nu][g'] B[g][g'] whose B operand is never stored:
-// eight generator warps evaluate K_c(g, g') for a 128 x 32 (g x g') block in
-// FP32 registers, split each value into BF16 limbs and write them straight
-// into the 64B-swizzled K-major shared-memory layout that the tensor core
-// reads.  A TMA warp streams the (w xi) limbs, one thread issues tcgen05.mma
-// into four 128-column FP32 accumulators in tensor memory (one per channel),
-// and the generator warps drain the accumulators into FP64 after each chunk.
+// eight generator warps evaluate K_c(g, g') for a 64 x 32 (g x g') block in
+// FP32 registers (radial or multi-centre correlator), split each value into
+// BF16 limbs and write them straight into the 64B-swizzled K-major
+// shared-memory layout that the tensor core reads.  A TMA warp streams the
+// (w xi) limbs, a bulk-copy warp the inner-point data, one thread issues one
+// N = 256 tcgen05.mma per limb product and k-step (the four channels' B tiles
+// back to back), and four epilogue warps fold each chunk accumulator into the
+// running sum held in the other half of tensor memory.
 //
 // Stage 2: W^c = (w xi~^c) calG^c^T as a split-BF16 tcgen05 GEMM with both
 // operands streamed by TMA, split-K over the grid with FP64 atomic reduction.
