@@ -165,6 +165,18 @@ def host_cores():
         return os.cpu_count()
 
 
+def run_config(args, wlw, world):
+    """The workload config shared by both arms' lines."""
+    n_mu, n_g = wlw.n_mu, wlw.n_g
+    limbs = 2 if args.precision == "bf16x3" else 3
+    return {"workload": args.workload, "n_g": n_g, "n_mu": n_mu, "n_orb": wlw.n_orb,
+            "n_occ": wlw.n_occ, "jastrow": "radial u=r/(2(1+r))",
+            "precision": args.precision,
+            "l2": f"inputs larger than L2 (w xi limbs {limbs * 2 * n_mu * n_g / 1e9:.2f} GB)",
+            "parallelism": f"replicas{world}",
+            "value_basis": "W build (stage 1 + stage 2 + operand prep) inside each full-path step"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -186,8 +198,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_g": n_g, "n_mu": n_mu,
-                       "n_orb": wlw.n_orb, "sample_outer_points": args.cpu_rows},
+            "config": run_config(args, wlw, world),
             "cpu_baseline": {"value": val, "unit": unit, "cores": host_cores(), "kind": "oracle",
                              "sample": f"W build (stages 1+2) for {args.cpu_rows} of {n_g} outer "
                                        f"grid points, all {n_g} inner points, N_mu={n_mu}; "
@@ -522,11 +533,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": args.workload, "n_g": n_g, "n_mu": n_mu, "n_orb": wlw.n_orb,
-                       "n_occ": wlw.n_occ, "jastrow": "radial u=r/(2(1+r))",
-                       "precision": args.precision, "l2": "inputs larger than L2 (w xi limbs "
-                       f"{3 * 2 * n_mu * n_g / 1e9:.2f} GB)", "parallelism": f"replicas{world}",
-                       "value_basis": "W build (stage 1 + stage 2 + operand prep) inside each full-path step"},
+            "config": run_config(args, wlw, world),
             "stages_ms": stages, "w_build_ms": a4_ms, "s1_ms": s1_ms, "s2_ms": s2_ms,
             "fp64_gpu": {"tflops": fp64_tflops, "slice_outer_points": rows,
                          "speedup_tc_over_fp64": value / fp64_tflops,
