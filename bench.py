@@ -165,6 +165,23 @@ def host_cores():
         return os.cpu_count()
 
 
+def aggregate_times(a4_ms, ms_step, world, device):
+    """Max over ranks of the per-replica W-build and step times: the slowest
+    replica sets the pace of the whole job."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([a4_ms, ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0]), float(t[1])
+    return a4_ms, ms_step
+
+
+def job_tflops(world, flops_per_replica, ms):
+    """Whole-job throughput: every replica's work over the slowest replica's time."""
+    return world * flops_per_replica / (ms * 1e-3) / 1e12
+
+
 def run_config(args, wlw, world):
     """The workload config shared by both arms' lines."""
     n_mu, n_g = wlw.n_mu, wlw.n_g
@@ -448,12 +465,9 @@ def main():
     stages = {k: statistics.mean(stage(k)) for k in ("a1", "a2", "a3", "a4", "a5", "a6")}
     a4_ms = stages["a4"]
     ms_step = total_ms / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([a4_ms, ms_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a4_ms, ms_step = float(t[0]), float(t[1])
+    a4_ms, ms_step = aggregate_times(a4_ms, ms_step, world, "cuda")
     flops = w_flops(n_mu, n_g, n_g)
-    value = world * flops / (a4_ms * 1e-3) / 1e12
+    value = job_tflops(world, flops, a4_ms)
 
     # dominant kernel: stage-1 tcgen05 contraction (device time from events
     # recorded by the library on the launching stream)
@@ -511,8 +525,8 @@ def main():
             W_host.copy_(o2["W"], non_blocking=True)
         e1.record(stream)
         barrier()
-        e2e_ms = e0.elapsed_time(e1) / max(args.steps, 1)
-        e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        e2e_ms, _ = aggregate_times(e0.elapsed_time(e1) / max(args.steps, 1), 0.0, world, "cuda")
+        e2e = {"value": job_tflops(world, flops, e2e_ms), "unit": "TFLOP/s",
                "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
