@@ -356,6 +356,49 @@ def test_particle_exchange(h6):
     assert np.max(np.abs(K - np.transpose(K, (2, 3, 0, 1)))) > 1e-6 * np.max(np.abs(K))
 
 
+def test_k_tensor_full_rank_equals_direct_double_grid_sum(tiny):
+    """At full fused rank (both channels' product spaces spanned) the ISDF
+    four-index K of Eq. K-recombine-final equals its pre-ISDF definition,
+    K1^{pq}_{rs} = sum_c sum_{g,g'} w w phi_p d_c phi_r (g) K_c(g,g') phi_q phi_s (g'),
+    K3 with K_sq and rho_pr rho_qs, combined as 1/2 P12 [K1 - K1swap + K3]."""
+    w, phi, dphi = tiny
+    n, n_g = phi.shape
+    res = pivots.select(phi, dphi, w.grid_w, 33)
+    assert res.rank_exhausted and len(res.pivots) == 30  # 6 scalar + 27 gradient, 3 shared
+    P = res.pivots
+    xi, xit, _ = fit.fit(phi, dphi, P)
+    W, _ = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, w.jastrow)
+    phiP = xtc.pivot_factors(phi, P)
+    dphiP = [dphi[c][:, P].T for c in range(3)]
+    K = energies.k_tensor(W, phiP, dphiP, np.arange(n))
+    Kc = jastrow.kernels(w.grid_xyz, w.grid_xyz, w.jastrow, np.arange(n_g), np.arange(n_g))
+    gw = w.grid_w
+    rho = phi[:, None, :] * phi[None, :, :]
+    K1 = np.zeros((n,) * 4)
+    for c in range(3):
+        grad_pr = gw * phi[:, None, :] * dphi[c][None, :, :]
+        K1 += np.einsum("prg,gh,qsh->pqrs", grad_pr, Kc[c], gw * rho)
+    K3 = np.einsum("prg,gh,qsh->pqrs", gw * rho, Kc[3], gw * rho)
+    T = K1 - np.transpose(K1, (2, 3, 0, 1)) + K3
+    direct = 0.5 * (T + np.transpose(T, (1, 0, 3, 2)))
+    assert np.max(np.abs(K - direct)) < 1e-9 * np.max(np.abs(direct))
+
+
+def test_e0_is_a_third_of_e_du(h6):
+    """With Eqs. xtc-deltah and xtc-const, sum_i Delta h_ii = -E_dU / 2, so
+    E0 = E_dU / 3 exactly (an index swap in Delta h breaks it)."""
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 40)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    W, calG = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, w.jastrow)
+    phiP = xtc.pivot_factors(phi, res.pivots)
+    dphiP = [dphi[c][:, res.pivots].T for c in range(3)]
+    _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, w.n_occ))
+    X = xtc.x_projector(w.grid_w, xi, calG, phiP, w.n_occ)
+    E = energies.energies(W, D, X, phiP, dphiP, w.n_occ)
+    assert abs(E["E0"] - E["E_dU"] / 3.0) < 1e-12 * abs(E["E_dU"])
+
+
 # ---------------------------------------------------------------- adjoint
 
 def test_dgrad_dtheta_matches_fd():
