@@ -479,7 +479,7 @@ def main():
     products = 3 if args.precision == "bf16x3" else 6
     # DRAM bytes per (mu, g) output element of stage 1 from the ncu capture in
     # profiles/s1_tc_kernel_bf16x3.md (input and output both scale with N_mu n_g)
-    traffic = 36.2 * n_mu * n_g if args.precision == "bf16x3" else None
+    traffic = 36.15 * n_mu * n_g if args.precision == "bf16x3" else None
     roofline = {"bound": "tensor", "achieved": s1_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": s1_tflops / peak, "traffic": traffic,
                 "pipe_frac": s1_tflops * products / peak,

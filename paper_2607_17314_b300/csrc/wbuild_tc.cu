@@ -219,21 +219,22 @@ __device__ __forceinline__ void pair_diff(const float4& gh, const float4& gl, co
   dz = (gh.z - h.z) + (gl.z - l.z);
 }
 
-// Radial correlator u = r / (2 (1 + d r)):  K_c = u'(r)/r (r_g - r_g')_c with
-// u' = 1/(2 (1 + d r)^2), and K_sq = u'^2.  The self pair (flagged by the
-// caller) gives zero.
-__device__ __forceinline__ void radial_pair(float dx, float dy, float dz, float d, bool self,
-                                            float& kx, float& ky, float& kz, float& ksq) {
-  const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1e-30f);
-  const float rinv = rsqrtf(r2);
+// Radial correlator u = r / (2 (1 + d r)):  K_c = f (r_g - r_g')_c with
+// f = u'(r)/r, u' = 1/(2 (1 + d r)^2), and K_sq = |K|^2 = f (f r^2).  The self
+// pair is the one pair whose hi/lo difference is exactly zero (distinct grid
+// points never coincide), and these forms give it zero without an index test:
+// r^2 is clamped only inside the square root, so f stays finite.
+__device__ __forceinline__ void radial_pair(float dx, float dy, float dz, float d, float& kx,
+                                            float& ky, float& kz, float& ksq) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
   const float iden = rcp_approx(fmaf(d, r, 1.0f));
-  const float up = 0.5f * iden * iden;
-  const float f = self ? 0.0f : up * rinv;
+  const float f = 0.5f * iden * iden * rinv;
   kx = f * dx;
   ky = f * dy;
   kz = f * dz;
-  ksq = self ? 0.0f : up * up;
+  ksq = f * (f * r2);
 }
 
 // Shared-memory carve-up and barriers common to the stage-1 roles.
@@ -371,7 +372,6 @@ __device__ __forceinline__ void s1_gen_radial(const S1Params& p, const S1Smem& s
     const int64_t g = p.g_begin + (gvalid ? gl : 0);
     const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int64_t gself = gvalid ? g : -1;
     for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
       const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
       const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
@@ -383,16 +383,13 @@ __device__ __forceinline__ void s1_gen_radial(const S1Params& p, const S1Smem& s
         pair_diff(gh, glo, tc::lds_f4(cbase + (kc + e) * 16),
                   tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
       tc::mbar_arrive(&sm.cempty[cs]);  // this thread's reads precede the next bulk copy
-      // the self pair can only fall in this block when the index ranges meet
-      const bool may_self = gself >= k0 && gself < k0 + C::BK;
       uint32_t pk[4][LIMBS][4];
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
         float kv[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-          radial_pair(dx[e + h], dy[e + h], dz[e + h], d,
-                      may_self && (k0 + kc + e + h) == gself, kv[h][0], kv[h][1], kv[h][2],
+          radial_pair(dx[e + h], dy[e + h], dz[e + h], d, kv[h][0], kv[h][1], kv[h][2],
                       kv[h][3]);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
