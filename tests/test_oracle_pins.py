@@ -237,6 +237,27 @@ def test_full_rank_reconstruction(tiny):
             assert np.max(np.abs(rec - phi[p] * phi[q])) < 1e-8 * np.max(np.abs(phi[p] * phi[q]))
 
 
+def test_jitter_schedule_on_matrices_with_known_spectra():
+    """Adaptive Tikhonov shift of the fit's Cholesky (Sec. IV.B; schedule a
+    reading: lambda = 0, then 1e-14 max diag, x10 per retry, 8 retries) on
+    2 x 2 matrices [[a, 1], [1, a]] whose eigenvalues a - 1 and a + 1 fix how
+    many retries succeed."""
+    # exactly singular: the first shift suffices
+    L, lam = fit.cholesky_with_jitter(np.array([[1.0, 1.0], [1.0, 1.0]]))
+    assert lam == 1e-14
+    assert np.allclose(L @ L.T, [[1 + 1e-14, 1.0], [1.0, 1 + 1e-14]], rtol=0, atol=1e-15)
+    # lowest eigenvalue -5e-12: shifts 1e-14 a, 1e-13 a, 1e-12 a fail, 1e-11 a succeeds
+    a = 1.0 - 5e-12
+    _, lam = fit.cholesky_with_jitter(np.array([[a, 1.0], [1.0, a]]))
+    assert abs(lam - 1e-11 * a) < 1e-12 * 1e-11
+    # positive definite: no shift
+    _, lam = fit.cholesky_with_jitter(np.array([[2.0, 1.0], [1.0, 2.0]]))
+    assert lam == 0.0
+    # indefinite (eigenvalue -1): no shift up to 1e-7 helps
+    with pytest.raises(np.linalg.LinAlgError):
+        fit.cholesky_with_jitter(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
 # ---------------------------------------------------------------- W
 
 def test_w_staged_equals_brute_force():
