@@ -389,8 +389,9 @@ __global__ void fit_error_kernel(const double* __restrict__ phi, const double* _
   }
 }
 
-__global__ void square_copy_kernel(const double* __restrict__ G, double* __restrict__ B,
-                                   double* __restrict__ X, int64_t n) {
+// B and X may be the same buffer (the Gram's saved copy), so neither is restrict.
+__global__ void square_copy_kernel(const double* __restrict__ G, double* B, double* X,
+                                   int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double g = G[i];
