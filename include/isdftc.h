@@ -208,7 +208,7 @@ int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
  * s = W3 relu(W2 relu(W1 x + b1) + b2) + b3 (8 -> 128 -> 128 -> 1) scores grid
  * points; the highest-scoring kappa N_mu points form a candidate set on which
  * the plain pivoted Cholesky (isdf_points) runs; the scalar-channel fit error
- * judges the result against the plain selection, which stays the fallback.
+ * decides between the result and the plain selection, which stays the fallback.
  * params: device FP32 [isdf_mlp_n_params()] laid out W1 [128][8], b1 [128],
  * W2 [128][128], b2 [128], W3 [128], b3; the forward uses their BF16
  * roundings with FP32 arithmetic. */

@@ -3,7 +3,7 @@
 // FP32 arithmetic) trained by weighted binary cross-entropy against the plain
 // pivoted-Cholesky selection, Adam, top-k candidate selection, the pivoted
 // Cholesky restricted to the candidates, and the scalar-channel ISDF fit error
-// that judges a selection.
+// that decides between selections.
 #include <cuda_bf16.h>
 
 #include "linalg.cuh"

@@ -2,7 +2,7 @@
 learned component).  Python driver of the libisdftc kernels: feature
 extraction, training by weighted binary cross-entropy against the plain
 pivoted-Cholesky selection, and proposal = pivoted Cholesky restricted to the
-kappa N_mu highest-scoring points, judged by the scalar-channel fit error
+kappa N_mu highest-scoring points, scored by the scalar-channel fit error
 against the plain selection (the fallback)."""
 from __future__ import annotations
 
@@ -101,7 +101,7 @@ def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
 @dataclasses.dataclass
 class Sample:
     """One training geometry: features, labels (plain selection) and the
-    arrays needed to judge a proposal."""
+    arrays needed to score a proposal."""
     feat: torch.Tensor
     labels: torch.Tensor
     phi: torch.Tensor

@@ -135,7 +135,7 @@ def test_training_and_gain(P):
     print("fit-error ratio proposal/plain", ratios, "fallbacks", fallbacks,
           "selection time plain %.4f s proposal %.4f s" % (t_plain, t_prop))
     assert np.median(ratios) < 2.0
-    # a network with scrambled weights is caught by the fit-error judge
+    # a network with scrambled weights is caught by the fit-error check
     bad = P.Proposer(seed=1)
     bad.params.mul_(-1.0)
     outs = [bad.select(smp, kappa=1.0, tolerance=1.05) for smp in test]
