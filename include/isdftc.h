@@ -93,8 +93,11 @@ typedef struct {
 /* Options of the kernel build (host struct; NULL = defaults). */
 typedef struct {
   int32_t precision;  /* isdf_precision; default ISDF_PREC_BF16X3 */
-  int32_t kchunk;     /* inner-grid points accumulated in FP32 tensor memory before
-                         each FP64 flush in stage 1; 0 = default (16384) */
+  int32_t kchunk;     /* stage 1: inner-grid points the tensor core accumulates into
+                         its FP32 chunk sum before the epilogue folds that sum into
+                         the IEEE-rounded FP32 running sum (also in tensor memory;
+                         the tile is written to FP64 once); rounded up to a multiple
+                         of 32; 0 = default (512) */
   int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (timeouts, non-finite values) */
