@@ -4,6 +4,7 @@ Every check here compares the oracle with something other than itself: a
 closed form, a finite difference, a brute-force sum, an analytic integral,
 a linear-algebra identity, or the paper's pre-ISDF definitions.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -259,6 +260,56 @@ def test_jitter_schedule_on_matrices_with_known_spectra():
 
 
 # ---------------------------------------------------------------- W
+
+def _geometry_case(seed=21, n_g=150, n_mu=5):
+    """Random points and fit functions with a two-type multi-centre
+    correlator (b != 1, d != 1), so that nuclei and both scaled distances
+    enter every kernel value."""
+    rng = np.random.default_rng(seed)
+    atoms = ["C", "H", "H"]
+    xyz = np.array([[0.0, 0.0, 0.0], [1.1, 0.9, 0.0], [-1.2, 0.4, 0.7]])
+    jas = wl.bh_jastrow(atoms, xyz, wl.bh_terms_c4(), rng, scale=0.3, d=1.2)
+    jas.b = np.array([0.8, 1.3])
+    grid = rng.normal(size=(n_g, 3)) * 1.5
+    w = rng.uniform(0.2, 1.0, size=n_g)
+    xi = rng.normal(size=(n_mu, n_g))
+    xit = rng.normal(size=(3, n_mu, n_g))
+    return grid, w, xi, xit, jas
+
+
+def _moved(jas, f):
+    return dataclasses.replace(jas, nuc_xyz=f(jas.nuc_xyz))
+
+
+def test_w_translation_and_permutation_invariant():
+    """W depends on differences of positions only, and the double grid sum
+    does not depend on the order of the points (Eqs. K1-isdf, K3-isdf)."""
+    grid, w, xi, xit, jas = _geometry_case()
+    W, _ = wbuild.build(grid, w, xi, xit, jas, batch=64)
+    t = np.array([3.7, -2.2, 0.9])
+    Wt, _ = wbuild.build(grid + t, w, xi, xit, _moved(jas, lambda x: x + t), batch=64)
+    scale = np.max(np.abs(W))
+    assert np.max(np.abs(Wt - W)) < 1e-12 * scale
+    perm = np.random.default_rng(5).permutation(grid.shape[0])
+    Wp, _ = wbuild.build(grid[perm], w[perm], xi[:, perm], xit[:, :, perm], jas, batch=37)
+    assert np.max(np.abs(Wp - W)) < 1e-12 * scale
+
+
+def test_w_rotation_covariance():
+    """Rotating points and nuclei by R rotates the kernel gradient, so with one
+    fit function for all three channels u1 turns as a vector,
+    u1'^c = sum_d R_cd u1^d, and u3 (a squared norm) is unchanged.  A channel
+    computed from the wrong coordinate fails this."""
+    grid, w, xi, _, jas = _geometry_case(seed=22)
+    xit = np.stack([xi, xi, xi])
+    q, _ = np.linalg.qr(np.random.default_rng(8).normal(size=(3, 3)))
+    R = q * np.sign(np.linalg.det(q))
+    W, _ = wbuild.build(grid, w, xi, xit, jas, batch=64)
+    Wr, _ = wbuild.build(grid @ R.T, w, xi, xit, _moved(jas, lambda x: x @ R.T), batch=64)
+    scale = np.max(np.abs(W))
+    assert np.max(np.abs(Wr[:3] - np.einsum("cd,dmn->cmn", R, W[:3]))) < 1e-12 * scale
+    assert np.max(np.abs(Wr[3] - W[3])) < 1e-12 * scale
+
 
 def test_w_staged_equals_brute_force():
     w = wl.tiny_chain(n_atom=2, n_rad=6, n_ang=10, shells=(0, 1), n_mu=10, seed=4)
