@@ -398,6 +398,80 @@ def test_xtc_full_rank_equals_pre_isdf(tiny):
     assert np.max(np.abs(dU - ref)) < 1e-7 * np.max(np.abs(ref))
 
 
+def _three_body_L(grid, gw, phi, jas):
+    """L^{pqr}_{stu} of Eq. Hbar-2nd, index order [p, q, r, s, t, u]: the
+    three-body operator of the BCH expansion (Eq. Hbar-bch), the sum over the
+    centre electron a of grad_a u(a,b) . grad_a u(a,c) with each centre counted
+    once, against phi_p phi_s (1), phi_q phi_t (2), phi_r phi_u (3).  The triple
+    grid sum runs through F^a_b(g) = sum_g' w_g' phi_a phi_b (g') grad u(g, g'),
+    an exact refactoring of it (see test_three_body_fields_equal_triple_sum)."""
+    n_g = grid.shape[0]
+    K = jastrow.kernels(grid, grid, jas, np.arange(n_g), np.arange(n_g))[:3]
+    rho = phi[:, None, :] * phi[None, :, :]
+    F = np.einsum("abh,cgh->abgc", rho * gw, K)
+    return (np.einsum("g,psg,qtgc,rugc->pqrstu", gw, rho, F, F)
+            + np.einsum("g,qtg,psgc,rugc->pqrstu", gw, rho, F, F)
+            + np.einsum("g,rug,psgc,qtgc->pqrstu", gw, rho, F, F))
+
+
+def _normal_ordered_du(L, n_occ):
+    """Normal ordering the three-body part -1/6 L a+a+a+aaa of Eq. Hbar-2nd
+    against the closed-shell determinant leaves the two-body operator
+    -1/2 v a+_p a+_q a_s a_r with
+        v^{pq}_{rs} = sum_{k occ} [2 L^{pqk}_{rsk} - L^{pqk}_{ksr} - L^{pqk}_{rks}]
+    (the third electron contracted directly, summed over both spins, minus its
+    exchange with electron 1 or 2, same spin only).  Eq. xtc-hamiltonian
+    carries the two-body part as +1/2 DeltaU, so DeltaU = -v."""
+    v = np.zeros(L.shape[:2] + L.shape[3:5])
+    for k in range(n_occ):
+        v += 2.0 * L[:, :, k, :, :, k]
+        v -= np.transpose(L[:, :, k, k, :, :], (0, 1, 3, 2))
+        v -= L[:, :, k, :, k, :]
+    return -v
+
+
+def test_three_body_fields_equal_triple_sum():
+    """The field refactoring of L against the literal triple sum over grid
+    points (g1, g2, g3) on a 48-point grid."""
+    w = wl.tiny_chain(n_atom=2, n_rad=4, n_ang=6, shells=(0,), seed=5)
+    jas = wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(4), 0.2)
+    phi, _ = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    n_g = w.n_g
+    K = jastrow.kernels(w.grid_xyz, w.grid_xyz, jas, np.arange(n_g), np.arange(n_g))[:3]
+    O = np.einsum("xab,xac->abc", K, K)               # grad_a u(a,b) . grad_a u(a,c)
+    G = O + np.transpose(O, (1, 0, 2)) + np.transpose(O, (1, 2, 0))
+    rho = phi[:, None, :] * phi[None, :, :] * w.grid_w
+    L_sum = np.einsum("psa,qtb,ruc,abc->pqrstu", rho, rho, rho, G)
+    L = _three_body_L(w.grid_xyz, w.grid_w, phi, jas)
+    assert np.max(np.abs(L - L_sum)) < 1e-12 * np.max(np.abs(L_sum))
+
+
+def test_xtc_equals_normal_ordered_three_body_term():
+    """Delta U of Eqs. deltaU-four .. deltaU-preisdf, and the oracle's ISDF
+    route at full scalar rank, against the normal-ordered three-body
+    operator L of Eq. Hbar-2nd (4 orbitals, 2 occupied; radial and
+    two-type multi-centre correlators).  Pins the signs and factors of
+    Terms 1-4 and the reading that L counts each centre electron once."""
+    w = wl.tiny_chain(n_atom=4, n_rad=12, n_ang=20, shells=(0,), n_mu=10, seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    n, n_occ = w.n_orb, w.n_occ
+    assert (n, n_occ) == (4, 2)
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    P = res.piv_s
+    xi, _, _ = fit.fit(phi, dphi, P, channels=(0,))
+    phiP = xtc.pivot_factors(phi, P)
+    bh = wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(9), 0.2)
+    for jas in (w.jastrow, bh):
+        ref = _normal_ordered_du(_three_body_L(w.grid_xyz, w.grid_w, phi, jas), n_occ)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(_pre_isdf_du(w, phi, n_occ, jas) - ref)) < 1e-12 * scale
+        calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, jas)
+        _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, n_occ))
+        X = xtc.x_projector(w.grid_w, xi, calG, phiP, n_occ)
+        dU = energies.du_tensor(D, X, phiP, np.arange(n))
+        assert np.max(np.abs(dU - ref)) < 1e-7 * scale
+
+
 def test_projector_equals_dense_and_symmetry(h6):
     w, phi, dphi = h6
     res = pivots.select(phi, dphi, w.grid_w, 30)
