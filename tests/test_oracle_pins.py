@@ -238,6 +238,24 @@ def test_full_rank_reconstruction(tiny):
             assert np.max(np.abs(rec - phi[p] * phi[q])) < 1e-8 * np.max(np.abs(phi[p] * phi[q]))
 
 
+def test_full_rank_gradient_reconstruction(tiny):
+    """With both channels run to exhaustion (the fused set spans every
+    product phi_p d_c phi_q), the gradient-channel fit reproduces those
+    products on the whole grid (Sec. II.D, gradient normal equations)."""
+    w, phi, dphi = tiny
+    n = w.n_orb
+    res = pivots.select(phi, dphi, w.grid_w, 33)
+    assert res.rank_exhausted
+    P = res.pivots
+    _, xit, _ = fit.fit(phi, dphi, P)
+    for c in range(3):
+        for p in range(n):
+            for q in range(n):
+                target = phi[p] * dphi[c][q]
+                rec = (phi[p, P] * dphi[c][q, P]) @ xit[c]
+                assert np.max(np.abs(rec - target)) < 1e-7 * np.max(np.abs(target))
+
+
 def test_jitter_schedule_on_matrices_with_known_spectra():
     """Adaptive Tikhonov shift of the fit's Cholesky (Sec. IV.B; schedule a
     reading: lambda = 0, then 1e-14 max diag, x10 per retry, 8 retries) on
