@@ -323,13 +323,28 @@ def ao_overlap_fast(basis: Basis) -> np.ndarray:
 
 
 def make_basis(atoms: Sequence[str], xyz: np.ndarray, shells: dict,
-               rng: np.random.Generator, n_prim: int = 3) -> Basis:
+               rng: np.random.Generator, n_prim: int = 3,
+               exp_bands: Optional[dict] = None) -> Basis:
     """Draw a seeded contracted Cartesian basis.  ``shells[symbol]`` lists the
-    angular momenta of the shells on that element."""
+    angular momenta of the shells on that element.  Exponents are
+    log-uniform on [0.1, 10]; with ``exp_bands = {l: (lo, hi)}`` the k-th of
+    the n_l shells of angular momentum l draws instead from the k-th of n_l
+    equal log-width bands of [lo, hi], so that many shells of one l on an atom
+    stay linearly independent."""
     centers, powers, exps, coefs, atom_of = [], [], [], [], []
     for ia, sym in enumerate(atoms):
+        seen = {}
         for l in shells[sym]:
-            alpha = np.exp(rng.uniform(math.log(0.1), math.log(10.0), size=n_prim))
+            if exp_bands is None:
+                lo, hi = math.log(0.1), math.log(10.0)
+            else:
+                k = seen.get(l, 0)
+                seen[l] = k + 1
+                n_l = shells[sym].count(l)
+                blo, bhi = (math.log(x) for x in exp_bands[l])
+                lo = blo + (bhi - blo) * k / n_l
+                hi = blo + (bhi - blo) * (k + 1) / n_l
+            alpha = np.exp(rng.uniform(lo, hi, size=n_prim))
             c = rng.uniform(0.5, 1.5, size=n_prim)
             for pw in cart_tuples(l):
                 centers.append(xyz[ia])
@@ -402,10 +417,11 @@ def bh_jastrow(atoms: Sequence[str], xyz: np.ndarray, terms, rng,
 # --------------------------------------------------------------------------
 
 def _assemble(name, atoms, xyz, n_rad, n_ang, shells, n_orb, n_occ, n_mu,
-              jkind, seed, jterms=None, jscale: float = 0.05) -> Workload:
+              jkind, seed, jterms=None, jscale: float = 0.05,
+              exp_bands: Optional[dict] = None) -> Workload:
     rng = np.random.default_rng(seed)
     grid, w = becke_grid(xyz, n_rad, n_ang)
-    basis = make_basis(atoms, xyz, shells, rng)
+    basis = make_basis(atoms, xyz, shells, rng, exp_bands=exp_bands)
     C = make_mo_coef(basis, n_orb, rng)
     if jkind == "radial":
         jas = radial_jastrow(xyz)
@@ -432,14 +448,21 @@ def h50_chain() -> Workload:
                      25, 2000, "radial", 2001)
 
 
+BENZENE_EXP_BANDS = {0: (0.1, 5000.0), 1: (0.1, 200.0), 2: (0.2, 40.0), 3: (0.4, 10.0)}
+
+
 def benzene_c6h6() -> Workload:
-    """Benzene, 100 functions per atom (s-f), 1200 orbitals, 12 x 75 x 302
-    points, N_mu = 8000, two-type BH Jastrow with 10 terms per type."""
+    """Benzene, 100 functions per atom (12 s, 6 p, 5 d, 4 f shells), 1200
+    orbitals, 12 x 75 x 302 points, N_mu = 8000, two-type BH Jastrow with 10
+    terms per type.  The shells of one angular momentum take separate exponent
+    bands: with all exponents in one common range the 1200-function overlap
+    is numerically singular (condition ~1e15) and the orbitals cannot be
+    orthonormalised; the bands bring it to ~1e9."""
     atoms, xyz = benzene()
     shells = {"C": [0] * 12 + [1] * 6 + [2] * 5 + [3] * 4,
               "H": [0] * 12 + [1] * 6 + [2] * 5 + [3] * 4}
     return _assemble("benzene", atoms, xyz, 75, 302, shells, 1200, 21, 8000,
-                     "bh", 3001, BH_TERMS_C3)
+                     "bh", 3001, BH_TERMS_C3, exp_bands=BENZENE_EXP_BANDS)
 
 
 def benzene_small(n_rad: int = 6, n_ang: int = 14, n_mu: int = 64, seed: int = 3101,
