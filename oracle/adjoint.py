@@ -1,5 +1,5 @@
 """Adjoint of the Jastrow kernels with respect to the correlator parameters --
-oracle (not in the paper; the task asks for dW/dtheta).
+oracle (not in the paper).
 
 TEST INFRASTRUCTURE (FP64 numpy, analytic derivatives written from the
 Boys-Handy form of Eqs. bh-scaled / bh-u).

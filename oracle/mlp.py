@@ -1,5 +1,5 @@
-"""Learned interpolation-point proposer -- oracle (not in the paper; the task
-asks for it).
+"""Learned interpolation-point proposer -- oracle (not in the paper, which
+selects points by pivoted Cholesky only).
 
 TEST INFRASTRUCTURE (FP64 numpy on the same BF16-rounded weights the GPU uses).
 

@@ -1,5 +1,5 @@
-// Learned interpolation-point proposer (not in the paper; the task asks for
-// it): per-point features, a small MLP (8 -> 128 -> 128 -> 1, BF16 weights,
+// Learned interpolation-point proposer (not in the paper): per-point
+// features, a small MLP (8 -> 128 -> 128 -> 1, BF16 weights,
 // FP32 arithmetic) trained by weighted binary cross-entropy against the plain
 // pivoted-Cholesky selection, Adam, top-k candidate selection, the pivoted
 // Cholesky restricted to the candidates, and the scalar-channel ISDF fit error

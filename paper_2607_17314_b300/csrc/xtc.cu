@@ -1,4 +1,5 @@
-// xTC density contraction of the three-body term (Sec. III.B) in FP64.
+// xTC density contraction of the three-body term (Sec. III.B): an FP64 path
+// and the split-BF16 tensor-core path described at the end of this comment.
 //
 // Terms 1 and 4 (factorisable):
 //   G_nu = sum_{i<n_occ} phi_i(r_nu)^2,  w~_g = w_g sum_l G_l xi_l(g)

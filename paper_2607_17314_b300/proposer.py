@@ -1,5 +1,5 @@
-"""Learned interpolation-point proposer (the task asks for it; the paper has no
-learned component).  Python driver of the libisdftc kernels: feature
+"""Learned interpolation-point proposer (the paper has no learned
+component).  Python driver of the libisdftc kernels: feature
 extraction, training by weighted binary cross-entropy against the plain
 pivoted-Cholesky selection, and proposal = pivoted Cholesky restricted to the
 kappa N_mu highest-scoring points, scored by the scalar-channel fit error
