@@ -2,6 +2,7 @@
 they stand in for, positive quadrature weights and orthonormal orbitals."""
 import numpy as np
 import pytest
+from scipy.spatial import cKDTree
 
 from synth import workloads as wl
 
@@ -23,6 +24,10 @@ def test_workload_sizes_weights_and_orthonormal_orbitals(name):
     assert (w.n_occ, w.n_mu) == (n_occ, n_mu)
     assert (w.jastrow.n_types, w.jastrow.n_terms) == (n_types, n_terms)
     assert np.all(np.isfinite(w.grid_xyz)) and np.all(w.grid_w > 0)
+    # distinct points never coincide: the tensor-core radial generator
+    # identifies the self pair by its exactly-zero difference vector
+    nn, _ = cKDTree(w.grid_xyz).query(w.grid_xyz, k=2)
+    assert nn[:, 1].min() > 1e-6
     S = wl.ao_overlap_fast(w.basis)
     assert np.allclose(np.diag(S), 1.0, rtol=0, atol=1e-12)
     C = w.mo_coef
