@@ -490,6 +490,68 @@ def test_xtc_equals_normal_ordered_three_body_term():
         assert np.max(np.abs(dU - ref)) < 1e-7 * scale
 
 
+def _normal_ordered_scalars(L, n_occ):
+    """One-body increment and constant of the plain-form Hamiltonian from
+    normal ordering -1/6 L (Eq. Hbar-2nd) against the closed-shell determinant.
+
+    The doubly and triply contracted parts take the three-electron
+    antisymmetrizer A3 = 1 - P12 - P13 - P23 + two 3-cycles, summed over the
+    spins the contracted orbitals may carry (each permutation term gets the
+    count of spin assignments it allows):
+      f_pq = -1/2 sum_{kl} [4 L^{pkl}_{qkl} - 2 L^{pkl}_{kql} - 2 L^{pkl}_{lkq}
+                            - 2 L^{pkl}_{qlk} + L^{pkl}_{klq} + L^{pkl}_{lqk}]
+      c    = -1/6 sum_{klm} [8 L^{klm}_{klm} - 4 (L^{klm}_{lkm} + L^{klm}_{mlk} + L^{klm}_{kml})
+                             + 2 (L^{klm}_{lmk} + L^{klm}_{mkl})]
+    Rewriting the normal-ordered two-body part 1/2 DeltaU {a+a+aa} in plain
+    form adds -sum_k (2 DeltaU^{pk}_{qk} - DeltaU^{pk}_{kq}) to the one-body
+    term and +E_dU to the constant, and rewriting the normal-ordered one-body
+    part adds -E_dU, so the constant is c alone.  Returns (Delta h [n][n], E0)."""
+    occ = range(n_occ)
+    dU = _normal_ordered_du(L, n_occ)
+    f = np.zeros(L.shape[:1] * 2)
+    for a in occ:
+        for b in occ:
+            f += (4 * L[:, a, b, :, a, b] - 2 * L[:, a, b, a, :, b] - 2 * L[:, a, b, b, a, :]
+                  - 2 * L[:, a, b, :, b, a] + L[:, a, b, a, b, :] + L[:, a, b, b, :, a])
+    f *= -0.5
+    conv = -sum(2 * dU[:, k, :, k] - dU[:, k, k, :] for k in occ)
+    c = 0.0
+    for k in occ:
+        for l in occ:
+            for m in occ:
+                c += (8 * L[k, l, m, k, l, m]
+                      - 4 * (L[k, l, m, l, k, m] + L[k, l, m, m, l, k] + L[k, l, m, k, m, l])
+                      + 2 * (L[k, l, m, l, m, k] + L[k, l, m, m, k, l]))
+    return f + conv, -c / 6.0
+
+
+def test_delta_h_and_e0_equal_normal_ordered_three_body_term():
+    """Eqs. xtc-deltah and xtc-const (Delta h from a partial contraction of
+    DeltaU, E0 = -2/3 sum_i Delta h_ii) against the one-body part and the
+    constant of the normal-ordered three-body operator L, through the
+    oracle's energies at full scalar rank (4 orbitals, 2 occupied)."""
+    w = wl.tiny_chain(n_atom=4, n_rad=12, n_ang=20, shells=(0,), n_mu=10, seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    n, n_occ = w.n_orb, w.n_occ
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    P = res.piv_s
+    xi, _, _ = fit.fit(phi, dphi, P, channels=(0,))
+    phiP = xtc.pivot_factors(phi, P)
+    dphiP = [dphi[c][:, P].T for c in range(3)]
+    bh = wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(9), 0.2)
+    for jas in (w.jastrow, bh):
+        dh_ref, E0_ref = _normal_ordered_scalars(_three_body_L(w.grid_xyz, w.grid_w, phi, jas),
+                                                 n_occ)
+        calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, jas)
+        _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, n_occ))
+        X = xtc.x_projector(w.grid_w, xi, calG, phiP, n_occ)
+        occ = np.arange(n_occ)
+        dh = energies.delta_h_occ(energies.du_tensor(D, X, phiP, occ))
+        assert np.max(np.abs(dh - np.diag(dh_ref)[:n_occ])) < 1e-7 * np.max(np.abs(dh_ref))
+        E = energies.energies(np.zeros((4, len(P), len(P))), D, X, phiP, dphiP, n_occ)
+        assert abs(E["E0"] - E0_ref) < 1e-7 * abs(E0_ref)
+
+
 def test_projector_equals_dense_and_symmetry(h6):
     w, phi, dphi = h6
     res = pivots.select(phi, dphi, w.grid_w, 30)
