@@ -26,14 +26,18 @@ from . import jastrow as J
 
 
 def n_params(jas) -> int:
+    """Number of parameters theta = (d, b per type, c per type and term) of
+    the correlator of Eqs. bh-scaled and bh-u."""
     return 1 + jas.n_types + jas.n_types * jas.n_terms
 
 
 def get_theta(jas) -> np.ndarray:
+    """theta = (d, b_0 .. b_{T-1}, c[type][term] row-major) of Eqs. bh-scaled, bh-u."""
     return np.concatenate([[jas.d], np.asarray(jas.b, float), np.asarray(jas.coef, float).ravel()])
 
 
 def set_theta(jas, theta):
+    """A copy of the correlator with the parameters theta (order of get_theta)."""
     import copy
     j2 = copy.deepcopy(jas)
     j2.d = float(theta[0])

@@ -19,7 +19,8 @@ import numpy as np
 
 
 def k_tensor(W, phiP, dphiP, idx):
-    """K^{pq}_{rs} for p, q, r, s in ``idx`` -> [n][n][n][n] (p, q, r, s)."""
+    """K^{pq}_{rs} for p, q, r, s in ``idx`` -> [n][n][n][n] (p, q, r, s), from
+    u^(1) and u^(3) (Eqs. K1-isdf, K3-isdf) recombined by Eq. K-recombine-final."""
     P = phiP[:, idx]
     dP = [d[:, idx] for d in dphiP]
     Cs = P[:, :, None] * P[:, None, :]                     # [mu, q, s]
@@ -34,7 +35,8 @@ def k_tensor(W, phiP, dphiP, idx):
 
 
 def du_tensor(D, X, phiP, idx):
-    """DeltaU^{pq}_{rs} for p, q, r, s in idx.  X is [n_orb][n_orb][n_mu]."""
+    """DeltaU^{pq}_{rs} for p, q, r, s in idx by the final assembly of Sec. III.B
+    (Eq. deltaU-four with the D and X kernels).  X is [n_orb][n_orb][n_mu]."""
     P = phiP[:, idx]
     Cs = P[:, :, None] * P[:, None, :]                     # [mu, p, r]
     T1 = np.einsum("mpr,mn,nqs->pqrs", Cs, D, Cs)
@@ -45,7 +47,9 @@ def du_tensor(D, X, phiP, idx):
 
 
 def closed_shell(T):
-    """sum_{ij} (2 T^{ij}_{ij} - T^{ij}_{ji}) over the given (occupied) block."""
+    """sum_{ij} (2 T^{ij}_{ij} - T^{ij}_{ji}) over the given (occupied) block: the
+    closed-shell expectation value read as the test energy (Coulomb weight 2 and
+    exchange, as in Eq. xtc-fock)."""
     n = T.shape[0]
     i = np.arange(n)
     coul = T[i[:, None], i[None, :], i[:, None], i[None, :]]
@@ -54,7 +58,7 @@ def closed_shell(T):
 
 
 def delta_h_occ(dU):
-    """Delta h_ii for i in the block (the block is the occupied space)."""
+    """Delta h_ii for i in the block (the block is the occupied space), Eq. xtc-deltah."""
     n = dU.shape[0]
     out = np.zeros(n)
     for i in range(n):
@@ -63,6 +67,8 @@ def delta_h_occ(dU):
 
 
 def energies(W, D, X, phiP, dphiP, n_occ):
+    """E_K and E_dU (closed_shell of K and DeltaU on the occupied block) and
+    E0 = -2/3 sum_i Delta h_ii (Eq. xtc-const, without nuclear repulsion)."""
     occ = np.arange(n_occ)
     K = k_tensor(W, phiP, dphiP, occ)
     dU = du_tensor(D, X, phiP, occ)

@@ -19,7 +19,8 @@ import scipy.linalg as sla
 
 
 def cholesky_with_jitter(A: np.ndarray, max_tries: int = 8):
-    """Lower Cholesky factor of A + lambda I and the lambda used."""
+    """Lower Cholesky factor of A + lambda I and the lambda used: the adaptive
+    Tikhonov retry of Sec. IV.B with the schedule read in the module docstring."""
     try:
         return sla.cholesky(A, lower=True), 0.0
     except np.linalg.LinAlgError:
@@ -34,7 +35,8 @@ def cholesky_with_jitter(A: np.ndarray, max_tries: int = 8):
 
 
 def grams(phi, dphi, piv):
-    """The four normal-equation matrices [4][n_mu][n_mu] (scalar, x, y, z)."""
+    """The four normal-equation matrices [4][n_mu][n_mu] (scalar, x, y, z) of
+    the least-squares fits of Sec. II.D."""
     phiP = phi[:, piv].T
     GPP = phiP @ phiP.T
     out = [GPP * GPP]
@@ -45,7 +47,7 @@ def grams(phi, dphi, piv):
 
 
 def rhs(phi, dphi, piv, g0=0, g1=None):
-    """Right-hand sides [4][n_mu][g1-g0]."""
+    """Right-hand sides [4][n_mu][g1-g0] of the normal equations of Sec. II.D."""
     g1 = phi.shape[1] if g1 is None else g1
     phiP = phi[:, piv].T
     G = phiP @ phi[:, g0:g1]
@@ -57,7 +59,8 @@ def rhs(phi, dphi, piv, g0=0, g1=None):
 
 
 def fit(phi, dphi, piv, channels=(0, 1, 2, 3)):
-    """xi [n_mu][n_g] and xi~ [3][n_mu][n_g] plus the jitter per channel."""
+    """xi [n_mu][n_g] and xi~ [3][n_mu][n_g] of Eq. isdf-rho and its gradient
+    analogue (Sec. II.D normal equations), plus the jitter per channel."""
     Gm = grams(phi, dphi, piv)
     B = rhs(phi, dphi, piv)
     xis = np.zeros_like(B)

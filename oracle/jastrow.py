@@ -30,7 +30,7 @@ def _unit(dv: np.ndarray, r: np.ndarray) -> np.ndarray:
 
 
 def u_value(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
-    """u(r_i, r_j) for all pairs, [n, m]."""
+    """u(r_i, r_j) of Eqs. bh-scaled and bh-u (plus the cusp term) for all pairs, [n, m]."""
     dv = ri[:, None, :] - rj[None, :, :]
     r = np.sqrt(np.sum(dv * dv, axis=2))
     E = jas.d * r / (1.0 + jas.d * r)
@@ -52,7 +52,7 @@ def u_value(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
 
 
 def grad1_u(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
-    """Analytic d u(r_i, r_j) / d r_i, [3, n, m]."""
+    """Analytic d u(r_i, r_j) / d r_i of Eqs. bh-scaled and bh-u, [3, n, m]."""
     dv = ri[:, None, :] - rj[None, :, :]
     r = np.sqrt(np.sum(dv * dv, axis=2))
     d = jas.d
@@ -95,7 +95,7 @@ def grad1_u(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
 
 def kernels(ri: np.ndarray, rj: np.ndarray, jas, gi: np.ndarray = None,
             gj: np.ndarray = None) -> np.ndarray:
-    """[K_x, K_y, K_z, K_sq] for all pairs, [4, n, m].  ``gi``/``gj`` are
+    """[K_x, K_y, K_z, K_sq] of Eqs. K1-isdf and K3-isdf for all pairs, [4, n, m].  ``gi``/``gj`` are
     the grid indices of the two point sets; pairs with gi == gj are zeroed."""
     g = grad1_u(ri, rj, jas)
     out = np.empty((4,) + g.shape[1:])

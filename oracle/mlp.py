@@ -32,6 +32,9 @@ N_PARAMS = H * F + H + H * H + H + H + 1
 
 
 def features(phi, dphi, w, grid, nuc_xyz):
+    """Per-point features [n_g][8]: log10 of the scalar and gradient pivot
+    diagonals (Alg. 1 and its gradient branch, Sec. II.D), of w, rho and tau
+    (each / 10), the two nearest-nucleus distances / 5 and log10(r_1 + 1e-3)."""
     rho = np.sum(phi * phi, axis=0)
     tau = np.sum(dphi * dphi, axis=(0, 1))
     dist = np.linalg.norm(grid[:, None, :] - nuc_xyz[None, :, :], axis=2)
@@ -73,6 +76,7 @@ def bf16_round(x):
 
 
 def init_params(seed: int = 0) -> np.ndarray:
+    """He-scaled normal initial weights and zero biases, flattened (unpack order)."""
     rng = np.random.default_rng(seed)
     W1 = rng.standard_normal((H, F)) * np.sqrt(2.0 / F)
     W2 = rng.standard_normal((H, H)) * np.sqrt(2.0 / H)
@@ -93,6 +97,7 @@ def forward(theta, x, rounding: bool = True):
 
 
 def softplus(t):
+    """log(1 + e^t) without overflow."""
     return np.maximum(t, 0.0) + np.log1p(np.exp(-np.abs(t)))
 
 
@@ -118,6 +123,7 @@ def loss_and_grad(theta, x, y, pos_w, rounding: bool = True):
 
 
 def adam(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One bias-corrected Adam step (Kingma and Ba) at 1-based step t."""
     m = b1 * m + (1.0 - b1) * g
     v = b2 * v + (1.0 - b2) * g * g
     mh = m / (1.0 - b1 ** t)

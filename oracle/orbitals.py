@@ -12,7 +12,8 @@ import numpy as np
 
 
 def eval_ao(basis, pts: np.ndarray):
-    """AO values [n_bf, n] and gradients [3, n_bf, n] at points [n, 3]."""
+    """Contracted Cartesian Gaussian values [n_bf, n] and analytic gradients
+    [3, n_bf, n] at points [n, 3] (the basis functions of Alg. 2 step 2)."""
     n = pts.shape[0]
     nbf = basis.center.shape[0]
     val = np.zeros((nbf, n))
@@ -45,7 +46,8 @@ def eval_ao(basis, pts: np.ndarray):
 
 
 def eval_orbitals(basis, mo_coef: np.ndarray, grid: np.ndarray, batch: int = 4096):
-    """phi [n_orb][n_g] and dphi [3][n_orb][n_g] in FP64."""
+    """phi [n_orb][n_g] and dphi [3][n_orb][n_g] in FP64: the orbitals and their
+    gradients on the grid (Alg. 2 step 2)."""
     n_g = grid.shape[0]
     n_orb = mo_coef.shape[1]
     phi = np.empty((n_orb, n_g))

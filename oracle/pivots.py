@@ -43,8 +43,9 @@ MODES = {"fused": 0, "scalar": 1, "gradient": 2}
 
 def select(phi: np.ndarray, dphi: np.ndarray, w: np.ndarray, n_mu: int,
            mode: str = "fused", cap: int = None, keep_L: bool = True) -> PivotResult:
-    """Pivoted-Cholesky interpolation points.  phi [n_orb][n_g], dphi
-    [3][n_orb][n_g], w [n_g]."""
+    """Pivoted-Cholesky interpolation points (Alg. 1, its gradient branch and
+    the pivot fusion of Sec. II.D, in the order-exact form of the C routine).
+    phi [n_orb][n_g], dphi [3][n_orb][n_g], w [n_g]."""
     lib = _load()
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     dphi = np.ascontiguousarray(dphi, dtype=np.float64)

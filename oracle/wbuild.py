@@ -44,6 +44,8 @@ def stage2(w, xi, xit, calG, g_rows=None):
 
 
 def build(grid, w, xi, xit, jas, batch: int = 512):
+    """W [4][n_mu][n_mu] of Eqs. K1-isdf and K3-isdf (channels x, y, z, sq) and
+    calG, by stage1 then stage2."""
     calG = stage1(grid, w, xi, jas, batch=batch)
     return stage2(w, xi, xit, calG), calG
 

@@ -27,10 +27,14 @@ import numpy as np
 
 
 def pivot_factors(phi, piv):
+    """phi_p(r_mu) [n_mu][n_orb]: the orbital values at the pivots that form the
+    pivot tensors C^p_q(r_mu) = phi_p(r_mu) phi_q(r_mu) of Eq. isdf-rho."""
     return np.ascontiguousarray(phi[:, piv].T)     # [n_mu][n_orb]
 
 
 def g_nu(phiP, n_occ):
+    """G_nu = sum_{tu} C^t_u(r_nu) gamma^u_t of Sec. III.B with gamma the
+    projector on the first n_occ orbitals: sum_{i < n_occ} phi_i(r_nu)^2."""
     return np.sum(phiP[:, :n_occ] ** 2, axis=1)
 
 
