@@ -95,8 +95,9 @@ def grad1_u(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
 
 def kernels(ri: np.ndarray, rj: np.ndarray, jas, gi: np.ndarray = None,
             gj: np.ndarray = None) -> np.ndarray:
-    """[K_x, K_y, K_z, K_sq] of Eqs. K1-isdf and K3-isdf for all pairs, [4, n, m].  ``gi``/``gj`` are
-    the grid indices of the two point sets; pairs with gi == gj are zeroed."""
+    """[K_x, K_y, K_z, K_sq] of Eqs. K1-isdf and K3-isdf for all pairs,
+    [4, n, m].  ``gi``/``gj`` are the grid indices of the two point sets;
+    pairs with gi == gj are zeroed."""
     g = grad1_u(ri, rj, jas)
     out = np.empty((4,) + g.shape[1:])
     out[:3] = g
