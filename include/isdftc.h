@@ -76,7 +76,9 @@ typedef struct {
  * with A_iI = b_I r_iI / (1 + b_I r_iI), E_ij = d r_ij / (1 + d r_ij) and
  * (m,n,o) = mno[k].  The cusp line is the cusp-normalised (0,0,1) term
  * (slope du/dr_ij -> 1/2).  n_terms = 0 with cusp = 1 is the radial
- * electron-electron correlator u(r) = r / (2 (1 + d r)).  Host struct. */
+ * electron-electron correlator u(r) = r / (2 (1 + d r)).  Host struct.  Calls
+ * return ISDF_E_ARG for d <= 0, counts or exponents out of range, non-finite
+ * positions, d or coefficients, and b_t <= 0 when n_terms > 0. */
 typedef struct {
   int32_t n_nuc;
   int32_t n_types;

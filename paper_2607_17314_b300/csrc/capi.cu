@@ -1,6 +1,8 @@
 // extern "C" entry points of libisdftc (declared in include/isdftc.h).
 #include <stdarg.h>
 
+#include <cmath>
+
 #include <atomic>
 
 #include "common.cuh"
@@ -69,12 +71,21 @@ static int check_jastrow(const isdf_jastrow* J) {
   ISDF_ARG(J->n_nuc >= 0 && J->n_nuc <= ISDF_MAX_NUC, "n_nuc out of range");
   ISDF_ARG(J->n_types >= 1 && J->n_types <= ISDF_MAX_TYPES, "n_types out of range");
   ISDF_ARG(J->n_terms >= 0 && J->n_terms <= ISDF_MAX_TERMS, "n_terms out of range");
-  ISDF_ARG(J->d > 0.0, "d must be positive");
-  for (int I = 0; I < J->n_nuc; ++I)
+  ISDF_ARG(J->d > 0.0 && std::isfinite(J->d), "d must be positive");
+  for (int I = 0; I < J->n_nuc; ++I) {
     ISDF_ARG(J->nuc_type[I] >= 0 && J->nuc_type[I] < J->n_types, "nucleus type out of range");
+    for (int c = 0; c < 3; ++c)
+      ISDF_ARG(std::isfinite(J->nuc_xyz[I][c]), "nucleus position not finite");
+  }
   for (int k = 0; k < J->n_terms; ++k)
     for (int e = 0; e < 3; ++e)
       ISDF_ARG(J->mno[k][e] >= 0 && J->mno[k][e] <= 8, "exponent out of range");
+  // b_I enters only through the free terms (Eq. bh-scaled needs b_I > 0)
+  for (int t = 0; t < J->n_types && J->n_terms > 0; ++t) {
+    ISDF_ARG(J->b[t] > 0.0 && std::isfinite(J->b[t]), "b must be positive");
+    for (int k = 0; k < J->n_terms; ++k)
+      ISDF_ARG(std::isfinite(J->coef[t][k]), "Jastrow coefficient not finite");
+  }
   return ISDF_OK;
 }
 

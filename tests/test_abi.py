@@ -73,6 +73,43 @@ def test_argument_errors_need_no_gpu(lib):
     assert st == C.ISDF_E_ARG
 
 
+def test_correlator_parameters_checked_before_launch(lib):
+    """Scale parameters b_I > 0 (Eq. bh-scaled) and finite d, positions and
+    coefficients are required before any device work; b is not used, and not
+    checked, when the correlator has no free terms."""
+    from paper_2607_17314_b300 import _capi as C
+    fake = ctypes.c_void_p(256)
+
+    def build(J):
+        return lib.tc_kernel_build(fake, fake, fake, fake, 64, 4, 0, 64, ctypes.byref(J), None,
+                                   fake, fake, fake, 0, None)
+
+    J = C.IsdfJastrow()
+    J.n_nuc, J.n_types, J.d, J.cusp = 1, 1, 1.0, 1
+    J.b[0] = 0.0                       # radial correlator: b unused
+    assert build(J) == C.ISDF_E_ARG    # the zero-byte workspace fails later
+    assert b"b must be positive" not in lib.isdf_last_error()
+    J.n_terms = 1
+    J.mno[0][0], J.mno[0][1], J.mno[0][2] = 1, 0, 0
+    J.coef[0][0] = 0.1
+    for b in (0.0, -1.0, float("inf"), float("nan")):
+        J.b[0] = b
+        assert build(J) == C.ISDF_E_ARG
+        assert b"b must be positive" in lib.isdf_last_error()
+    J.b[0] = 1.0
+    J.coef[0][0] = float("nan")
+    assert build(J) == C.ISDF_E_ARG
+    assert b"coefficient not finite" in lib.isdf_last_error()
+    J.coef[0][0] = 0.1
+    J.nuc_xyz[0][2] = float("inf")
+    assert build(J) == C.ISDF_E_ARG
+    assert b"position not finite" in lib.isdf_last_error()
+    J.nuc_xyz[0][2] = 0.0
+    J.d = float("inf")
+    assert build(J) == C.ISDF_E_ARG
+    assert b"d must be positive" in lib.isdf_last_error()
+
+
 def test_multicentre_tensor_core_form_needs_no_gpu(lib):
     """The multi-centre tensor-core generator sizes its tables from the
     correlator and rejects term sets outside its polynomial form before any
