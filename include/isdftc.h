@@ -155,8 +155,10 @@ int isdf_points(const double* phi, const double* dphi, const double* w, int64_t 
  * FP64 Cholesky with adaptive Tikhonov retry (Sec. IV.B): lambda = 0, then
  * 1e-14 max(diag) times 10 per retry, at most 8 retries; the lambda used per
  * system is written to jitter_used (host [4], may be NULL).
- * pivots [n_mu]; xi [n_mu][n_g]; xi_grad [3][n_mu][n_g].  Synchronises
- * `stream`; ISDF_E_NOT_PD if a system stays indefinite. */
+ * pivots [n_mu] (distinct grid indices in [0, n_g), as isdf_points returns
+ * them; the device array is read as given, not range-checked); xi [n_mu][n_g];
+ * xi_grad [3][n_mu][n_g].  Synchronises `stream`; ISDF_E_NOT_PD if a system
+ * stays indefinite. */
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu);
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
              const int32_t* pivots, int n_mu, double* xi, double* xi_grad,
@@ -249,8 +251,9 @@ int isdf_mlp_adam(float* params, const float* grad, float* m, float* v, int step
  * Asynchronous. */
 int isdf_mlp_topk(const float* scores, int64_t n, int k, int32_t* out, isdf_stream_t stream);
 
-/* isdf_points (fused mode) on the candidate points cand[n_cand] only; pivots
- * receive grid indices.  Synchronises `stream`; ISDF_E_RANK as isdf_points. */
+/* isdf_points (fused mode) on the candidate points cand[n_cand] only (distinct
+ * grid indices in [0, n_g); the device array is read as given, not
+ * range-checked); pivots receive grid indices.  Synchronises `stream`; ISDF_E_RANK as isdf_points. */
 size_t isdf_points_restricted_workspace(int n_cand, int n_orb, int n_mu);
 int isdf_points_restricted(const double* phi, const double* dphi, const double* w, int64_t n_g,
                            int n_orb, const int32_t* cand, int n_cand, int n_mu, int32_t* pivots,
@@ -259,7 +262,8 @@ int isdf_points_restricted(const double* phi, const double* dphi, const double* 
 /* Scalar-channel ISDF fit error of a pivot set over the whole grid:
  *   *eps = sum_g w_g^2 [(sum_p phi_p^2)^2 - sum_mu xi_mu(g) G_{mu g}^2] / sum_g w_g^2 (sum_p phi_p^2)^2
  * with xi from the FP64 normal equations of Eq. isdf-rho (the weighted
- * Frobenius residual).  eps host.  Synchronises `stream`. */
+ * Frobenius residual).  pivots: device [n_mu], distinct indices in [0, n_g)
+ * (read as given, not range-checked).  eps host.  Synchronises `stream`. */
 size_t isdf_fit_error_workspace(int64_t n_g, int n_orb, int n_mu);
 int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
                    const int32_t* pivots, int n_mu, double* eps, void* ws, size_t ws_bytes,
@@ -328,7 +332,8 @@ int tc_energies_noalloc(const double* W, const double* D, const double* X_packed
                         int n_occ, double* out, isdf_stream_t stream);
 
 /* Gather phi_p(r_mu) and d_c phi_p(r_mu): phi_piv [n_mu][n_orb],
- * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL).  Asynchronous. */
+ * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL); pivots: device [n_mu],
+ * indices in [0, n_g) (read as given, not range-checked).  Asynchronous. */
 int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
                        const int32_t* pivots, int n_mu, double* phi_piv, double* dphi_piv,
                        isdf_stream_t stream);
