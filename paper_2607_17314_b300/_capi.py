@@ -31,11 +31,13 @@ INT = ctypes.c_int
 
 
 class IsdfBasis(ctypes.Structure):
+    """ctypes mirror of isdf_basis (device pointers to the contracted Gaussians)."""
     _fields_ = [("n_bf", I32), ("n_prim", I32), ("center", P), ("powers", P), ("exps", P),
                 ("coefs", P)]
 
 
 class IsdfJastrow(ctypes.Structure):
+    """ctypes mirror of isdf_jastrow (Boys-Handy correlator, Eqs. bh-scaled, bh-u)."""
     _fields_ = [("n_nuc", I32), ("n_types", I32), ("n_terms", I32), ("cusp", I32),
                 ("d", ctypes.c_double),
                 ("nuc_xyz", (ctypes.c_double * 3) * ISDF_MAX_NUC),
@@ -46,6 +48,7 @@ class IsdfJastrow(ctypes.Structure):
 
 
 class IsdfOptions(ctypes.Structure):
+    """ctypes mirror of isdf_options (precision, fold intervals, checks, timing)."""
     _fields_ = [("precision", I32), ("kchunk", I32), ("s2_kchunk", I32), ("sync_check", I32),
                 ("debug_flags", I32), ("stage_ms", ctypes.POINTER(ctypes.c_float))]
 
@@ -106,6 +109,8 @@ def load() -> ctypes.CDLL:
 
 
 class IsdfError(RuntimeError):
+    """A libisdftc call returned a failure status; ``status`` holds it."""
+
     def __init__(self, func: str, status: int, msg: str):
         self.status = status
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -113,6 +118,8 @@ class IsdfError(RuntimeError):
 
 
 def check(func: str, status: int, allow=()):
+    """Raise IsdfError with the library's message unless status is ISDF_OK or in
+    ``allow``; return the status."""
     if status != ISDF_OK and status not in allow:
         raise IsdfError(func, status, load().isdf_last_error().decode(errors="replace"))
     return status

@@ -118,6 +118,8 @@ def isdf_fit(phi, dphi, pivots):
 
 
 def isdf_gather_pivots(phi, dphi, pivots):
+    """phi_p(r_mu) [n_mu][n_orb] and d_c phi_p(r_mu) [3][n_mu][n_orb] at the
+    pivots: the factors of the pivot tensors C^p_q(r_mu) of Eq. isdf-rho."""
     lib = C.load()
     n_orb, n_g = phi.shape
     n_mu = pivots.numel()
@@ -130,6 +132,7 @@ def isdf_gather_pivots(phi, dphi, pivots):
 
 def options(precision="bf16x3", kchunk: int = 0, s2_kchunk: int = 0, sync_check: bool = True,
             debug_flags: int = 0, stage_ms=None) -> C.IsdfOptions:
+    """isdf_options for the W build; 0 selects the library defaults."""
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return C.IsdfOptions(prec, kchunk, s2_kchunk, int(sync_check), debug_flags, stage_ms)
 

@@ -43,6 +43,8 @@ def _compile(src: str, force: bool) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every CUDA source for sm_103a (in parallel, skipping up-to-date
+    objects unless ``force``) and link libisdftc.so next to this file."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:

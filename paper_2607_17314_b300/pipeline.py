@@ -19,6 +19,8 @@ from . import api
 
 @dataclasses.dataclass
 class Inputs:
+    """Device-resident inputs of one pass: the basis, MO coefficients, grid and
+    weights, N_mu, N_occ and the correlator struct."""
     center: torch.Tensor   # [n_bf][3]
     powers: torch.Tensor   # [n_bf][3] int32
     exps: torch.Tensor     # [n_bf][n_prim]

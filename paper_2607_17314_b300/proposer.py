@@ -20,10 +20,13 @@ f32, f64 = torch.float32, torch.float64
 
 
 def n_params() -> int:
+    """Number of FP32 parameters of the 8 -> 128 -> 128 -> 1 network."""
     return int(C.load().isdf_mlp_n_params())
 
 
 def features(phi, dphi, w, grid_xyz, nuc_xyz) -> torch.Tensor:
+    """Per-point features [n_g][8] (pivot diagonals of Alg. 1 and its gradient
+    branch, weights, densities, nucleus distances) on the device."""
     lib = C.load()
     n_orb, n_g = phi.shape
     nuc = np.ascontiguousarray(np.asarray(nuc_xyz, dtype=np.float64).reshape(-1, 3))
@@ -35,6 +38,7 @@ def features(phi, dphi, w, grid_xyz, nuc_xyz) -> torch.Tensor:
 
 
 def forward(params, feat) -> torch.Tensor:
+    """Scores [n] of the network with BF16-rounded weights."""
     lib = C.load()
     scores = torch.empty(feat.shape[0], dtype=f32, device=feat.device)
     C.check("isdf_mlp_forward", lib.isdf_mlp_forward(_ptr(params), _ptr(feat), feat.shape[0],
@@ -43,6 +47,8 @@ def forward(params, feat) -> torch.Tensor:
 
 
 def backward(params, feat, labels, pos_w: float, n_total: int, grad, loss):
+    """Add the weighted-BCE gradient (normalised by n_total) to grad and the
+    unnormalised loss sum to loss (device FP64 [1])."""
     lib = C.load()
     C.check("isdf_mlp_backward", lib.isdf_mlp_backward(
         _ptr(params), _ptr(feat), _ptr(labels), feat.shape[0], float(pos_w), int(n_total),
@@ -50,12 +56,14 @@ def backward(params, feat, labels, pos_w: float, n_total: int, grad, loss):
 
 
 def adam(params, grad, m, v, step: int, lr: float):
+    """One bias-corrected Adam step on params (1-based step)."""
     lib = C.load()
     C.check("isdf_mlp_adam", lib.isdf_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v),
                                                int(step), float(lr), _stream()))
 
 
 def topk(scores, k: int) -> torch.Tensor:
+    """Indices of the k highest scores, ties by the lower index, ascending."""
     lib = C.load()
     out = torch.empty(k, dtype=torch.int32, device=scores.device)
     C.check("isdf_mlp_topk", lib.isdf_mlp_topk(_ptr(scores), scores.shape[0], int(k), _ptr(out),
@@ -64,6 +72,8 @@ def topk(scores, k: int) -> torch.Tensor:
 
 
 def points_restricted(phi, dphi, w, cand, n_mu: int) -> torch.Tensor:
+    """Fused pivoted Cholesky (Alg. 1 and Sec. II.D) on the candidate points
+    only; grid indices of the selected points (fewer if the rank runs out)."""
     lib = C.load()
     n_orb, n_g = phi.shape
     piv = torch.empty(n_mu, dtype=torch.int32, device=phi.device)
@@ -77,6 +87,7 @@ def points_restricted(phi, dphi, w, cand, n_mu: int) -> torch.Tensor:
 
 
 def fit_error(phi, w, pivots) -> float:
+    """Scalar-channel weighted ISDF fit error of a pivot set (Eq. isdf-rho)."""
     lib = C.load()
     n_orb, n_g = phi.shape
     eps = ctypes.c_double(0.0)
@@ -112,6 +123,9 @@ class Sample:
 
 
 class Proposer:
+    """The network, its Adam state, training on plain selections and proposals
+    with the plain selection as fallback."""
+
     def __init__(self, seed: int = 0, lr: float = 1e-3, device="cuda"):
         self.params = init_params(seed, device)
         self.m = torch.zeros_like(self.params)
@@ -137,6 +151,7 @@ class Proposer:
         return tot / npts
 
     def propose(self, smp: Sample, kappa: float = 3.0) -> torch.Tensor:
+        """Pivots from the kappa N_mu highest-scoring candidates."""
         scores = forward(self.params, smp.feat)
         k = min(int(kappa * smp.n_mu), smp.feat.shape[0])
         cand = topk(scores, k)
