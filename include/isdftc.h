@@ -282,8 +282,8 @@ int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
  *   X_{qs mu} = sum_g w_g [ xi_mu(g) sum_{a,c} A^s_{a,c} A^q_{a,c}
  *                          + sum_c calG^c_{mu g} sum_a (rho~^s_a A^q_{a,c} + A^s_{a,c} rho~^q_a) ]
  *   for q <= s < n_orb_x, packed row s(s+1)/2 + q.
- * phi_piv [n_mu][n_orb] = phi_p(r_mu); xi [n_mu][n_g]; w [n_g];
- * calG [>=3][n_mu][n_g] FP64; D [n_mu][n_mu] FP64;
+ * phi_piv [n_mu][n_orb] = phi_p(r_mu); 1 <= n_occ <= n_orb; xi [n_mu][n_g];
+ * w [n_g]; calG [>=3][n_mu][n_g] FP64; D [n_mu][n_mu] FP64;
  * X_packed [n_orb_x (n_orb_x + 1) / 2][n_mu] FP64 or NULL.
  * precision: ISDF_PREC_FP64 (CUDA-core FP64 GEMMs) or ISDF_PREC_BF16X3 /
  * ISDF_PREC_BF16X6 (the D4 and D1 contractions and the two GEMM families of

@@ -182,7 +182,8 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
                precision == ISDF_PREC_BF16X6,
            "xtc precision must be FP64, BF16X3 or BF16X6");
   ISDF_ARG(phiP && xi && w && calG && D, "null pointer argument");
-  ISDF_ARG(n_occ >= 0 && n_occ <= n_orb && n_mu > 0 && n_g > 0, "bad sizes");
+  ISDF_ARG(n_occ >= 1 && n_occ <= n_orb && n_mu > 0 && n_g > 0,
+           "bad sizes (n_occ must be in [1, n_orb], n_mu and n_g positive)");
   ISDF_ARG(!Xp || (n_orb_x >= 1 && n_orb_x <= n_orb), "n_orb_x out of range");
   if (!Xp) n_orb_x = 0;
   Carve cv(ws, ws_bytes);

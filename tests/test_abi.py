@@ -110,6 +110,17 @@ def test_correlator_parameters_checked_before_launch(lib):
     assert b"d must be positive" in lib.isdf_last_error()
 
 
+def test_xtc_sizes_checked_before_launch(lib):
+    """No occupied orbitals, n_occ > n_orb or an X width beyond n_orb are
+    argument errors, reported before any device work."""
+    from paper_2607_17314_b300 import _capi as C
+    fake = ctypes.c_void_p(256)
+    for n_occ, n_orb_x in ((0, 4), (9, 4), (2, 9)):
+        st = lib.xtc_density_contract(fake, 8, n_occ, fake, fake, fake, 64, 16, fake, fake,
+                                      n_orb_x, 0, fake, 1 << 30, None)
+        assert st == C.ISDF_E_ARG, (n_occ, n_orb_x)
+
+
 def test_multicentre_tensor_core_form_needs_no_gpu(lib):
     """The multi-centre tensor-core generator sizes its tables from the
     correlator and rejects term sets outside its polynomial form before any
