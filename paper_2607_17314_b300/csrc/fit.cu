@@ -68,6 +68,7 @@ inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t
 int gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
                   const int32_t* piv, int n_mu, double* phiP, double* dphiP, cudaStream_t s) {
   ISDF_ARG(phi && piv && phiP, "null pointer argument");
+  ISDF_ARG(n_orb > 0 && n_g > 0, "empty sizes");
   if (n_mu <= 0) return ISDF_OK;
   int64_t per = (int64_t)n_mu * n_orb;
   gather_pivots_kernel<<<nblocks(per), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP, 1);

@@ -119,6 +119,8 @@ def test_xtc_sizes_checked_before_launch(lib):
         st = lib.xtc_density_contract(fake, 8, n_occ, fake, fake, fake, 64, 16, fake, fake,
                                       n_orb_x, 0, fake, 1 << 30, None)
         assert st == C.ISDF_E_ARG, (n_occ, n_orb_x)
+    st = lib.isdf_gather_pivots(fake, None, 64, 0, fake, 4, fake, None, None)
+    assert st == C.ISDF_E_ARG
 
 
 def test_multicentre_tensor_core_form_needs_no_gpu(lib):
