@@ -744,3 +744,20 @@ def test_candidates_and_fit_error():
     res3 = pivots.select(phi, dphi, w.grid_w, 3, mode="scalar")
     e3 = mlp.fit_error(phi, w.grid_w, res3.piv_s)
     assert 0 < e3 < 1
+
+
+def test_features_carry_the_pivot_diagonals(h6):
+    """Features 0 and 1 are monotone in the scalar and gradient pivot
+    diagonals d^(0) of Alg. 1 (Sec. II.D), so their argmax is each channel's
+    first pivot; features 5 and 6 are the sorted nearest-nucleus distances."""
+    from oracle import mlp
+    w, phi, dphi = h6
+    f = mlp.features(phi, dphi, w.grid_w, w.grid_xyz, w.xyz)
+    assert f.shape == (w.n_g, 8) and np.all(np.isfinite(f))
+    first_s = pivots.select(phi, dphi, w.grid_w, 1, mode="scalar").piv_s[0]
+    first_v = pivots.select(phi, dphi, w.grid_w, 1, mode="gradient").piv_v[0]
+    assert int(np.argmax(f[:, 0])) == first_s
+    assert int(np.argmax(f[:, 1])) == first_v
+    assert np.all(f[:, 5] <= f[:, 6])
+    d = np.linalg.norm(w.grid_xyz[:, None, :] - w.xyz[None, :, :], axis=2)
+    assert np.allclose(f[:, 5], d.min(axis=1) / 5.0, rtol=0, atol=1e-15)
