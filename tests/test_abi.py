@@ -164,3 +164,37 @@ def test_product_path_has_no_oracle_import():
     for f in glob.glob(os.path.join(ROOT, "paper_2607_17314_b300", "**", "*.py"), recursive=True):
         src = open(f).read()
         assert not re.search(r"^\s*(from|import)\s+(oracle|synth)\b", src, flags=re.M), f
+
+
+def test_undersized_workspace_rejected_before_launch(lib):
+    """Every call that takes a workspace rejects one that is too small with
+    ISDF_E_ARG and a message naming the bytes needed, before any device work."""
+    from paper_2607_17314_b300 import _capi as C
+    f = ctypes.c_void_p(256)
+    n = C.INT(0)
+    eps = ctypes.c_double(0.0)
+    basis = C.IsdfBasis(4, 3, f, f, f, f)
+    J = C.IsdfJastrow()
+    J.n_types, J.d, J.cusp, J.b[0] = 1, 1.0, 1, 1.0
+    calls = {
+        "isdf_eval_orbitals": lambda: lib.isdf_eval_orbitals(ctypes.byref(basis), f, 4, f, 64, f,
+                                                             f, f, 16, None),
+        "isdf_points": lambda: lib.isdf_points(f, f, f, 64, 4, 8, 0, f, ctypes.byref(n), f, 16,
+                                               None),
+        "isdf_fit": lambda: lib.isdf_fit(f, f, 64, 4, f, 8, f, f, None, f, 16, None),
+        "tc_kernel_build": lambda: lib.tc_kernel_build(f, f, f, f, 64, 8, 0, 64, ctypes.byref(J),
+                                                       None, f, f, f, 16, None),
+        "tc_kernel_adjoint": lambda: lib.tc_kernel_adjoint(f, f, f, f, 64, 8, ctypes.byref(J), f,
+                                                           C.PRECISIONS["fp64"], f, f, 16, None),
+        "xtc_density_contract": lambda: lib.xtc_density_contract(f, 4, 2, f, f, f, 64, 8, f, f, 4,
+                                                                 0, f, 16, None),
+        "tc_energies": lambda: lib.tc_energies(f, f, f, f, f, 8, 4, 2, f, f, 16, None),
+        "isdf_points_restricted": lambda: lib.isdf_points_restricted(f, f, f, 64, 4, f, 32, 8, f,
+                                                                     ctypes.byref(n), f, 16, None),
+        "isdf_fit_error": lambda: lib.isdf_fit_error(f, f, 64, 4, f, 8, ctypes.byref(eps), f, 16,
+                                                     None),
+    }
+    for name, call in calls.items():
+        st = call()
+        assert st == C.ISDF_E_ARG, (name, st, lib.isdf_last_error())
+        assert b"workspace too small" in lib.isdf_last_error(), (name, lib.isdf_last_error())
