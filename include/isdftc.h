@@ -41,7 +41,8 @@ typedef enum {
   ISDF_E_ARG = 1,        /* invalid argument, size or workspace */
   ISDF_E_NOT_PD = 2,     /* Gram Cholesky failed after the last jitter retry */
   ISDF_E_RANK = 3,       /* numerical rank exhausted before n_mu points (informational) */
-  ISDF_E_NONFINITE = 4,  /* NaN/Inf detected in an input or result */
+  ISDF_E_NONFINITE = 4,  /* reserved for NaN/Inf detection; no call returns it yet:
+                            non-finite device inputs propagate to the outputs */
   ISDF_E_TIMEOUT = 5,    /* a bounded device wait expired; the kernel returned early */
   ISDF_E_CUDA = 6,       /* CUDA runtime error */
   ISDF_E_UNSUPPORTED = 7 /* option combination not implemented */
@@ -102,7 +103,7 @@ typedef struct {
                          of 32; 0 = default (512) */
   int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
-                         device-side errors (timeouts, non-finite values) */
+                         device-side errors (expired bounded waits, CUDA errors) */
   int32_t debug_flags;/* bit 0: the stage-1 producer skips its first arrival, so
                          the consumer's bounded wait expires (fault-path test) */
   float* stage_ms;    /* host [2] or NULL: when set (with sync_check), the device
