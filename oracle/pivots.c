@@ -197,3 +197,59 @@ int oracle_pivots(const double* phi, const double* dphi, const double* w,
   for (int i = 0; i < 4; ++i) free(own[i]);
   return nu < n_mu ? 1 : 0;
 }
+
+/*
+ * The paper's own fusion (Sec. II.D, pivot-fusion paragraph): each channel runs
+ * on its own to a fixed rank -- n_phi scalar steps, then n_grad gradient steps,
+ * fewer where a channel stops -- and the interpolation set is their union, the
+ * scalar list in its order followed by each gradient pivot not already in it.
+ * The union size is an outcome (at most n_phi + n_grad).
+ * Outputs as oracle_pivots; piv_union needs n_phi + n_grad entries.
+ * Returns 0 when both channels reached their ranks, 1 when either stopped
+ * early (rank exhausted).
+ */
+int oracle_pivots_ranks(const double* phi, const double* dphi, const double* w,
+                        long n_g, int n_orb, int n_phi, int n_grad,
+                        int* piv_union, int* n_union, int* piv_s, int* n_s,
+                        int* piv_v, int* n_v) {
+  pv_in in = {phi, dphi, w, n_g, n_orb};
+  const int rank[2] = {n_phi, n_grad};
+  int* piv[2] = {piv_s, piv_v};
+  int* nk[2] = {n_s, n_v};
+  char* in_union = (char*)calloc(n_g, 1);
+  double* t1 = (double*)malloc(n_g * sizeof(double));
+  double* t2 = (double*)malloc(n_g * sizeof(double));
+  int nu = 0;
+  int short_rank = 0;
+  for (int c = 0; c < 2; ++c) {
+    pv_chan ch;
+    ch.grad = c;
+    ch.d = (double*)malloc(n_g * sizeof(double));
+    ch.L = (double*)malloc((size_t)(rank[c] > 0 ? rank[c] : 1) * n_g * sizeof(double));
+    ch.piv = piv[c];
+    ch.k = 0;
+    ch.cap = rank[c];
+    ch.done = rank[c] <= 0;
+    diag_init(&in, c, ch.d);
+    double mx = 0.0;
+    for (long g = 0; g < n_g; ++g) if (ch.d[g] > mx) mx = ch.d[g];
+    ch.tol = 64.0 * DBL_EPSILON * mx;
+    for (;;) {
+      long gs = chan_step(&in, &ch, t1, t2);
+      if (gs < 0) break;
+      if (!in_union[gs]) {
+        in_union[gs] = 1;
+        piv_union[nu++] = (int)gs;
+      }
+    }
+    if (ch.k < rank[c]) short_rank = 1;
+    *nk[c] = ch.k;
+    free(ch.d);
+    free(ch.L);
+  }
+  *n_union = nu;
+  free(in_union);
+  free(t1);
+  free(t2);
+  return short_rank;
+}

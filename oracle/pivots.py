@@ -23,6 +23,10 @@ def _load():
         P = ctypes.c_void_p
         f.argtypes = [P, P, P, ctypes.c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                       ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
+        f = _lib.oracle_pivots_ranks
+        f.restype = ctypes.c_int
+        f.argtypes = [P, P, P, ctypes.c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                      P, P, P, P, P, P]
     return _lib
 
 
@@ -71,4 +75,28 @@ def select(phi: np.ndarray, dphi: np.ndarray, w: np.ndarray, n_mu: int,
                        piv_v=pv[:nv.value].copy(), d_s=ds, d_v=dv,
                        L_s=None if Ls is None else Ls[:ns.value],
                        L_v=None if Lv is None else Lv[:nv.value],
+                       rank_exhausted=bool(rc))
+
+
+def select_ranks(phi: np.ndarray, dphi: np.ndarray, w: np.ndarray, n_phi: int,
+                 n_grad: int) -> PivotResult:
+    """The paper's pivot fusion (Sec. II.D): the scalar channel run to rank
+    n_phi and the gradient channel to rank n_grad, each on its own (Alg. 1 and
+    its gradient branch), then their union -- the scalar list followed by the
+    gradient pivots not already in it.  L and d are not kept."""
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    dphi = np.ascontiguousarray(dphi, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n_orb, n_g = phi.shape
+    pu = np.zeros(max(n_phi + n_grad, 1), np.int32)
+    ps = np.zeros(max(n_phi, 1), np.int32)
+    pv = np.zeros(max(n_grad, 1), np.int32)
+    nu, ns, nv = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib.oracle_pivots_ranks(phi.ctypes.data, dphi.ctypes.data, w.ctypes.data, n_g, n_orb,
+                                 n_phi, n_grad, pu.ctypes.data, ctypes.byref(nu),
+                                 ps.ctypes.data, ctypes.byref(ns), pv.ctypes.data,
+                                 ctypes.byref(nv))
+    return PivotResult(pivots=pu[:nu.value].copy(), piv_s=ps[:ns.value].copy(),
+                       piv_v=pv[:nv.value].copy(), d_s=None, d_v=None, L_s=None, L_v=None,
                        rank_exhausted=bool(rc))

@@ -135,3 +135,55 @@ def test_w_two_points_against_hand_fractions():
     W, _ = wbuild.build(grid, w, xi, xit, jas)
     assert np.max(np.abs(W - W_exp)) <= 1e-17
     assert np.max(np.abs(wbuild.brute_force(grid, w, xi, xit, jas) - W_exp)) <= 1e-17
+
+
+@pytest.mark.parametrize("case", _blocks("pivots_fixed_rank.txt"),
+                         ids=lambda c: f"{c['n_phi']}-{c['n_grad']}")
+def test_fixed_rank_fusion_against_hand_steps(case):
+    """The paper's fusion: each channel to its own rank, then the union."""
+    dphi = np.zeros((3, 2, 3))
+    dphi[0] = _rows("0 2 0 | 0 0 1")
+    res = pivots.select_ranks(PHI, dphi, np.ones(3), int(case["n_phi"]), int(case["n_grad"]))
+    assert res.pivots.tolist() == [int(x) for x in case["pivots"].split()]
+    assert res.rank_exhausted == bool(int(case["exhausted"]))
+
+
+def _sparse(s, shape):
+    a = np.zeros(shape)
+    for item in s.split():
+        parts = item.split(",")
+        idx = tuple(int(x) for x in parts[:-1])
+        a[idx] = _frac(parts[-1])
+    return a
+
+
+def test_mlp_forward_against_hand_fractions():
+    """Oracle forward pass of the proposer network on a sparse dyadic network
+    whose activations were worked by hand (some ReLUs on, some off)."""
+    from oracle import mlp
+    f = _blocks("mlp_forward.txt")[0]
+    H, F = mlp.H, mlp.F
+    theta = np.concatenate([_sparse(f["W1"], (H, F)).ravel(), _sparse(f["b1"], (H,)),
+                            _sparse(f["W2"], (H, H)).ravel(), _sparse(f["b2"], (H,)),
+                            _sparse(f["W3"], (H,)), [_frac(f["b3"])]])
+    assert theta.size == mlp.N_PARAMS
+    x = _rows(f["x"])
+    for rounding in (True, False):   # dyadic weights are exact in BF16
+        s, (_, _, h1, _, h2) = mlp.forward(theta, x, rounding=rounding)
+        assert s.tolist() == [_frac(v) for v in f["s"].split()]
+        for r, (e1, e2) in enumerate(zip(f["h1"].split("|"), f["h2"].split("|"))):
+            assert np.array_equal(h1[r], _sparse(e1, (H,)))
+            assert np.array_equal(h2[r], _sparse(e2, (H,)))
+
+
+def test_mlp_features_against_hand_values():
+    from oracle import mlp
+    f = _blocks("mlp_features.txt")[0]
+    phi = np.array([[_frac(v)] for v in f["phi"].split()])            # [n_orb][1]
+    dphi = np.stack([np.array([[_frac(v)] for v in f[k].split()])
+                     for k in ("dphi_x", "dphi_y", "dphi_z")])         # [3][n_orb][1]
+    w = np.array([_frac(f["w"])])
+    nuc = _rows(f["nuclei"])
+    got = mlp.features(phi, dphi, w, np.zeros((1, 3)), nuc)[0]
+    exp = np.array([_frac(v) for v in f["features"].split()])
+    assert np.max(np.abs(got - exp)) <= 1e-15
