@@ -41,8 +41,8 @@ typedef enum {
   ISDF_E_ARG = 1,        /* invalid argument, size or workspace */
   ISDF_E_NOT_PD = 2,     /* Gram Cholesky failed after the last jitter retry */
   ISDF_E_RANK = 3,       /* numerical rank exhausted before n_mu points (informational) */
-  ISDF_E_NONFINITE = 4,  /* reserved for NaN/Inf detection; no call returns it yet:
-                            non-finite device inputs propagate to the outputs */
+  ISDF_E_NONFINITE = 4,  /* NaN or Inf found by a call that synchronises (stated per
+                            call); the asynchronous calls propagate them */
   ISDF_E_TIMEOUT = 5,    /* a bounded device wait expired; the kernel returned early */
   ISDF_E_CUDA = 6,       /* CUDA runtime error */
   ISDF_E_UNSUPPORTED = 7 /* option combination not implemented */
@@ -141,12 +141,28 @@ int isdf_eval_orbitals(const isdf_basis* basis, const double* mo_coef, int n_orb
  * mode 1 = scalar channel only; mode 2 = gradient channel only.
  * A channel stops when its pivot d_g* <= 64 eps max_g d_g(initial).
  * pivots [n_mu] int32 (append order) receives *n_mu_out entries.  Returns
- * ISDF_E_RANK (with *n_mu_out < n_mu) when both channels stopped early.
+ * ISDF_E_RANK (with *n_mu_out < n_mu) when both channels stopped early, and
+ * ISDF_E_NONFINITE (before any step) when phi, dphi or w hold a NaN or Inf.
  * Synchronises `stream`. */
 size_t isdf_points_workspace(int64_t n_g, int n_mu);
 int isdf_points(const double* phi, const double* dphi, const double* w, int64_t n_g,
                 int n_orb, int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws,
                 size_t ws_bytes, isdf_stream_t stream);
+
+/* The paper's pivot fusion (Sec. II.D, pivot-fusion paragraph): the scalar
+ * channel runs to rank n_ch_phi, then the gradient channel to rank n_ch_grad,
+ * each on its own with the arithmetic and tie rule of isdf_points, and the
+ * interpolation set is their union -- the scalar pivots in order, then each
+ * gradient pivot not already present.  The union size is an outcome:
+ * *n_mu_out <= n_ch_phi + n_ch_grad.  pivots: device int32 with room for
+ * n_ch_phi + n_ch_grad entries.  n_ch_phi, n_ch_grad >= 0 with a positive
+ * sum.  Returns ISDF_E_RANK (pivots still valid) when a channel stopped before
+ * its rank, ISDF_E_NONFINITE (before any step) when phi, dphi or w hold a NaN
+ * or Inf.  Synchronises `stream`. */
+size_t isdf_points_fixed_rank_workspace(int64_t n_g, int n_ch_phi, int n_ch_grad);
+int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                           int n_orb, int n_ch_phi, int n_ch_grad, int32_t* pivots,
+                           int* n_mu_out, void* ws, size_t ws_bytes, isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Least-squares ISDF fit (Eq. isdf-rho and the normal equations of Sec. II.D).
@@ -157,9 +173,11 @@ int isdf_points(const double* phi, const double* dphi, const double* w, int64_t 
  * 1e-14 max(diag) times 10 per retry, at most 8 retries; the lambda used per
  * system is written to jitter_used (host [4], may be NULL).
  * pivots [n_mu] (distinct grid indices in [0, n_g), as isdf_points returns
- * them; the device array is read as given, not range-checked); xi [n_mu][n_g];
- * xi_grad [3][n_mu][n_g].  Synchronises `stream`; ISDF_E_NOT_PD if a system
- * stays indefinite. */
+ * them); xi [n_mu][n_g]; xi_grad [3][n_mu][n_g].  Synchronises `stream`.
+ * Errors: ISDF_E_ARG when a pivot index lies outside [0, n_g) (checked on the
+ * device before any solve; such an index is never dereferenced);
+ * ISDF_E_NONFINITE when phi or dphi hold a NaN or Inf, or the solutions
+ * overflow; ISDF_E_NOT_PD if a system stays indefinite. */
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu);
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
              const int32_t* pivots, int n_mu, double* xi, double* xi_grad,
@@ -176,7 +194,9 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * The outer-grid slice [g_begin, g_end) gives additive partial kernels.
  * grid_xyz [n_g][3]; w [n_g]; xi [n_mu][n_g]; xi_grad [3][n_mu][n_g];
  * W [4][n_mu][n_mu] FP64 (overwritten); calG [4][n_mu][g_end-g_begin] FP64
- * (overwritten; required).  ISDF_PREC_FP64 takes any correlator.  The
+ * (overwritten; required).  With sync_check (default) the call returns
+ * ISDF_E_NONFINITE when W holds a NaN or Inf (every input value reaches W).
+ * ISDF_PREC_FP64 takes any correlator.  The
  * tensor-core precisions take the radial correlator (n_terms = 0, cusp = 1)
  * and multi-centre correlators whose terms have m, n <= 3, o <= 4 and at most
  * two distinct E exponents o among the terms with (m, n) != (0, 0), with the
@@ -253,8 +273,10 @@ int isdf_mlp_adam(float* params, const float* grad, float* m, float* v, int step
 int isdf_mlp_topk(const float* scores, int64_t n, int k, int32_t* out, isdf_stream_t stream);
 
 /* isdf_points (fused mode) on the candidate points cand[n_cand] only (distinct
- * grid indices in [0, n_g); the device array is read as given, not
- * range-checked); pivots receive grid indices.  Synchronises `stream`; ISDF_E_RANK as isdf_points. */
+ * grid indices in [0, n_g)); pivots receive grid indices.  Synchronises
+ * `stream`; ISDF_E_RANK and ISDF_E_NONFINITE as isdf_points; ISDF_E_ARG when
+ * a candidate index lies outside [0, n_g) (checked on the device before any
+ * step; such an index is never dereferenced). */
 size_t isdf_points_restricted_workspace(int n_cand, int n_orb, int n_mu);
 int isdf_points_restricted(const double* phi, const double* dphi, const double* w, int64_t n_g,
                            int n_orb, const int32_t* cand, int n_cand, int n_mu, int32_t* pivots,
@@ -264,7 +286,9 @@ int isdf_points_restricted(const double* phi, const double* dphi, const double* 
  *   *eps = sum_g w_g^2 [(sum_p phi_p^2)^2 - sum_mu xi_mu(g) G_{mu g}^2] / sum_g w_g^2 (sum_p phi_p^2)^2
  * with xi from the FP64 normal equations of Eq. isdf-rho (the weighted
  * Frobenius residual).  pivots: device [n_mu], distinct indices in [0, n_g)
- * (read as given, not range-checked).  eps host.  Synchronises `stream`. */
+ * (ISDF_E_ARG otherwise, checked on the device; such an index is never
+ * dereferenced).  eps host.  ISDF_E_NONFINITE when phi or w hold a NaN or Inf
+ * or eps is not finite.  Synchronises `stream`. */
 size_t isdf_fit_error_workspace(int64_t n_g, int n_orb, int n_mu);
 int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
                    const int32_t* pivots, int n_mu, double* eps, void* ws, size_t ws_bytes,
@@ -292,7 +316,8 @@ int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
  * points, X always with three limbs; the element-wise parts in FP64).
  * Asynchronous for FP64.  The tensor-core precisions synchronise `stream`
  * after the D and X contractions to read the pipeline's wait-status word and
- * return ISDF_E_TIMEOUT if a bounded wait expired. */
+ * return ISDF_E_TIMEOUT if a bounded wait expired, or ISDF_E_NONFINITE if D
+ * or X holds a NaN or Inf. */
 size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ,
                                       int n_orb_x, int precision);
 int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const double* xi,
@@ -309,7 +334,7 @@ int xtc_density_contract(const double* phi_piv, int n_orb, int n_occ, const doub
  *   out[2] = E0   = -2/3 sum_i Delta h_ii   (without nuclear repulsion)
  * W [4][n_mu][n_mu]; D [n_mu][n_mu]; X_packed as above with n_orb_x >= n_occ;
  * phi_piv [n_mu][n_orb]; dphi_piv [3][n_mu][n_orb]; out host [3].  FP64.
- * Synchronises `stream`. */
+ * Synchronises `stream`; ISDF_E_NONFINITE when an energy is NaN or Inf. */
 size_t tc_energies_workspace(int n_mu, int n_occ);
 int tc_energies(const double* W, const double* D, const double* X_packed,
                 const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
@@ -324,17 +349,20 @@ int tc_energies(const double* W, const double* D, const double* X_packed,
  * fixed 16 MiB device array inside the library (held by every GPU that loads
  * the library until exit); sizes needing more (6 n_mu n_occ^2 + 4 n_occ^4
  * doubles plus alignment) return ISDF_E_ARG.  The first call on a device looks
- * up the array's device address with that device current; make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams or host threads) race.  No device memory is allocated.
- * Synchronises `stream`. */
+ * up the array's device address with that device current, and looks it up
+ * again in a new context of the device (after a cudaDeviceReset); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams or host threads) race.  No device
+ * memory is allocated.  Synchronises `stream`. */
 int tc_energies_noalloc(const double* W, const double* D, const double* X_packed,
                         const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
                         int n_occ, double* out, isdf_stream_t stream);
 
 /* Gather phi_p(r_mu) and d_c phi_p(r_mu): phi_piv [n_mu][n_orb],
  * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL); pivots: device [n_mu],
- * indices in [0, n_g) (read as given, not range-checked).  Asynchronous. */
+ * indices in [0, n_g).  Asynchronous, so an index outside [0, n_g) cannot be
+ * reported: it is never dereferenced and its rows are written as quiet NaN,
+ * which the synchronising calls downstream report as ISDF_E_NONFINITE. */
 int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
                        const int32_t* pivots, int n_mu, double* phi_piv, double* dphi_piv,
                        isdf_stream_t stream);

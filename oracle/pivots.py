@@ -100,3 +100,22 @@ def select_ranks(phi: np.ndarray, dphi: np.ndarray, w: np.ndarray, n_phi: int,
     return PivotResult(pivots=pu[:nu.value].copy(), piv_s=ps[:ns.value].copy(),
                        piv_v=pv[:nv.value].copy(), d_s=None, d_v=None, L_s=None, L_v=None,
                        rank_exhausted=bool(rc))
+
+
+def tie_margin(phi, dphi, w, piv_a, piv_b, channel: str):
+    """Near-tie check for two pivot lists of one channel ("scalar" or
+    "gradient") obtained from inputs equal up to rounding (e.g. orbitals
+    evaluated on two machines).  Returns (j, gap): the first step j where the
+    lists differ and the relative gap (d(a_j) - d(b_j)) / d(a_j) of this
+    oracle's residual diagonal (Alg. 1) on (phi, dphi, w) just before step j,
+    a_j being the point the oracle picks there.  (None, 0.0) when the lists
+    agree over their common length."""
+    n = min(len(piv_a), len(piv_b))
+    diff = [j for j in range(n) if piv_a[j] != piv_b[j]]
+    if not diff:
+        return None, 0.0
+    j = diff[0]
+    st = select(phi, dphi, w, j, mode=channel, keep_L=False)   # the state after j steps
+    d = st.d_s if channel == "scalar" else st.d_v
+    a, b = int(piv_a[j]), int(piv_b[j])
+    return j, float((d[a] - d[b]) / d[a])

@@ -63,3 +63,23 @@ def brute_force(grid, w, xi, xit, jas):
                 W[c] += ww * K[c, g, h] * np.outer(xit[c][:, g], xi[:, h])
             W[3] += ww * K[3, g, h] * np.outer(xi[:, g], xi[:, h])
     return W
+
+
+def stage1_bounded(grid, w, xi, jas, g_rows, batch: int = 128):
+    """calG of ``stage1`` for the rows in g_rows together with the normwise
+    bound sum_g' |w_g' xi_nu(g')| |K_c(g, g')| of each of its sums (the scale
+    of a dot product's rounding error); both [4][n_nu][len(g_rows)]."""
+    n_g = grid.shape[0]
+    rows = np.asarray(g_rows)
+    wxi = xi * w[None, :]
+    awxi = np.abs(wxi)
+    out = np.zeros((4, wxi.shape[0], rows.shape[0]))
+    bound = np.zeros_like(out)
+    allg = np.arange(n_g)
+    for b0 in range(0, rows.shape[0], batch):
+        r = rows[b0:b0 + batch]
+        K = J.kernels(grid[r], grid, jas, r, allg)
+        for c in range(4):
+            out[c][:, b0:b0 + batch] = wxi @ K[c].T
+            bound[c][:, b0:b0 + batch] = awxi @ np.abs(K[c]).T
+    return out, bound

@@ -62,6 +62,9 @@ SIGNATURES = {
     "isdf_eval_orbitals": (INT, [ctypes.POINTER(IsdfBasis), P, INT, P, I64, P, P, P, SZ, P]),
     "isdf_points_workspace": (SZ, [I64, INT]),
     "isdf_points": (INT, [P, P, P, I64, INT, INT, INT, P, ctypes.POINTER(INT), P, SZ, P]),
+    "isdf_points_fixed_rank_workspace": (SZ, [I64, INT, INT]),
+    "isdf_points_fixed_rank": (INT, [P, P, P, I64, INT, INT, INT, P, ctypes.POINTER(INT), P, SZ,
+                                     P]),
     "isdf_fit_workspace": (SZ, [I64, INT, INT]),
     "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, SZ, P]),
     "isdf_gather_pivots": (INT, [P, P, I64, INT, P, INT, P, P, P]),

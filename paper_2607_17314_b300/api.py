@@ -101,6 +101,24 @@ def isdf_points(phi, dphi, w, n_mu: int, mode: int = 0, allow_rank: bool = False
     return piv[:out.value]
 
 
+def isdf_points_fixed_rank(phi, dphi, w, n_ch_phi: int, n_ch_grad: int,
+                           allow_rank: bool = False):
+    """The paper's pivot fusion (Sec. II.D): each channel to its own rank, then
+    the union (scalar pivots first).  int32 tensor of length n_mu_out."""
+    lib = C.load()
+    dev = phi.device
+    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(w, f64, "w")
+    n_orb, n_g = phi.shape
+    piv = torch.empty(max(n_ch_phi + n_ch_grad, 1), dtype=torch.int32, device=dev)
+    out = C.INT(0)
+    ws = _ws(lib.isdf_points_fixed_rank_workspace(n_g, n_ch_phi, n_ch_grad), dev)
+    st = lib.isdf_points_fixed_rank(_ptr(phi), _ptr(dphi), _ptr(w), n_g, n_orb, n_ch_phi,
+                                    n_ch_grad, _ptr(piv), ctypes.byref(out), _ptr(ws), ws.numel(),
+                                    _stream())
+    C.check("isdf_points_fixed_rank", st, allow=(C.ISDF_E_RANK,) if allow_rank else ())
+    return piv[:out.value]
+
+
 def isdf_fit(phi, dphi, pivots):
     """xi [n_mu][n_g], xi~ [3][n_mu][n_g] and the jitter per system."""
     lib = C.load()

@@ -28,6 +28,9 @@ int eval_orbitals(const isdf_basis*, const double*, int, const double*, int64_t,
 size_t points_ws(int64_t n_g, int n_mu);
 int points(const double*, const double*, const double*, int64_t, int, int, int, int32_t*, int*,
            void*, size_t, cudaStream_t);
+size_t points_ranks_ws(int64_t n_g, int n_phi, int n_grad);
+int points_ranks(const double*, const double*, const double*, int64_t, int, int, int, int32_t*,
+                 int*, void*, size_t, cudaStream_t);
 size_t fit_ws(int64_t, int, int);
 int fit(const double*, const double*, int64_t, int, const int32_t*, int, double*, double*,
         double*, void*, size_t, cudaStream_t);
@@ -35,7 +38,7 @@ int gather_pivots(const double*, const double*, int64_t, int, const int32_t*, in
                   double*, cudaStream_t);
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J);
 int wbuild_fp64(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
-                int64_t, const isdf_jastrow&, double*, double*, void*, size_t, cudaStream_t);
+                int64_t, const isdf_jastrow&, double*, double*, int, void*, size_t, cudaStream_t);
 size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int, const isdf_jastrow*);
 int wbuild_tc(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
               int64_t, const isdf_jastrow&, const isdf_options&, double*, double*, void*, size_t,
@@ -117,6 +120,17 @@ int isdf_points(const double* phi, const double* dphi, const double* w, int64_t 
                 (cudaStream_t)stream);
 }
 
+size_t isdf_points_fixed_rank_workspace(int64_t n_g, int n_ch_phi, int n_ch_grad) {
+  return points_ranks_ws(n_g, n_ch_phi, n_ch_grad);
+}
+
+int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                           int n_orb, int n_ch_phi, int n_ch_grad, int32_t* pivots,
+                           int* n_mu_out, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  return points_ranks(phi, dphi, w, n_g, n_orb, n_ch_phi, n_ch_grad, pivots, n_mu_out, ws,
+                      ws_bytes, (cudaStream_t)stream);
+}
+
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu) { return fit_ws(n_g, n_orb, n_mu); }
 
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* pivots,
@@ -152,10 +166,8 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
   if (options) opt = *options;
   cudaStream_t s = (cudaStream_t)stream;
   if (opt.precision == ISDF_PREC_FP64) {
-    int rc = wbuild_fp64(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, W, calG, ws,
-                         ws_bytes, s);
-    if (rc == ISDF_OK && opt.sync_check) ISDF_CUDA(cudaStreamSynchronize(s));
-    return rc;
+    return wbuild_fp64(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, W, calG,
+                       opt.sync_check, ws, ws_bytes, s);
   }
   if (opt.precision != ISDF_PREC_BF16X3 && opt.precision != ISDF_PREC_BF16X6) {
     set_error("unknown precision %d", opt.precision);

@@ -6,6 +6,9 @@
 //   K1[(p,r),(q,s)] = sum_c Ct^c^T W^c Cs,  K3 = Cs^T W^3 Cs
 //   T = K1 - K1swap + K3,  K^{pq}_{rs} = (T^{pq}_{rs} + T^{qp}_{sr}) / 2
 //   DeltaU^{pq}_{rs} = -(U^{pq}_{rs} + U^{qp}_{sr}),  U = Cs^T D Cs - Cs^T X
+#include <cuda.h>
+
+#include <cmath>
 #include <mutex>
 
 #include "linalg.cuh"
@@ -154,6 +157,11 @@ int energies(const double* W, const double* D, const double* Xp, const double* p
   ISDF_LAUNCH_CHECK();
   ISDF_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ISDF_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(out_host[i])) {
+      set_error("energy %d is not finite (NaN or Inf in W, D, X or the pivot factors)", i);
+      return ISDF_E_NONFINITE;
+    }
   return ISDF_OK;
 }
 
@@ -166,12 +174,14 @@ int energies(const double* W, const double* D, const double* Xp, const double* p
 // block on an allocator.  For them the scratch of the energies call lives in
 // one fixed device array of this library instead of a caller workspace.  The
 // array is kEnergiesScratchBytes large and every GPU that loads the library
-// holds it until the process exits.  Its device address is looked up once per
-// device, with that device current, on the first call made on that device;
-// make that first call before any stream capture.  All calls share the array
-// and it keeps the last call's contents: every region the energies path reads
-// is written earlier in the same call, so nothing needs clearing, but calls
-// that overlap on the GPU (other streams, other host threads) race on it.
+// holds it until the process exits.  Its device address is looked up with the
+// device current on the first call in each CUDA context of that device: once
+// per device, and once more after a cudaDeviceReset, which ends the context
+// that held the array (the module is loaded again, possibly elsewhere); make
+// that first call before any stream capture.  All calls share the array and
+// it keeps the last call's contents: every region the energies path reads is
+// written earlier in the same call, so nothing needs clearing, but calls that
+// overlap on the GPU (other streams, other host threads) race on it.
 
 namespace {
 
@@ -181,13 +191,40 @@ static __device__ __align__(256) unsigned char g_energies_scratch[kEnergiesScrat
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if unavailable).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx) get_id(ctx, &id);
+  return id;
+}
 
 int scratch_address(void** out) {
   int dev = 0;
   ISDF_CUDA(cudaGetDevice(&dev));
   ISDF_ARG(dev >= 0 && dev < kMaxDevices, "device ordinal %d beyond the scratch table", dev);
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_energies_scratch);
     if (e != cudaSuccess || !p) {
@@ -196,6 +233,7 @@ int scratch_address(void** out) {
       return ISDF_E_CUDA;
     }
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return ISDF_OK;

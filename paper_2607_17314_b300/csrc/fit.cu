@@ -13,14 +13,15 @@ namespace {
 
 __global__ void gather_pivots_kernel(const double* __restrict__ src, int64_t n_g, int n_orb,
                                      const int32_t* __restrict__ piv, int n_mu,
-                                     double* __restrict__ dst, int nplanes) {
+                                     double* __restrict__ dst, int nplanes, int* err) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t per = (int64_t)n_mu * n_orb;
   if (e >= per * nplanes) return;
   int c = (int)(e / per);
   int64_t r = e % per;
   int mu = (int)(r / n_orb), p = (int)(r % n_orb);
-  dst[e] = src[((int64_t)c * n_orb + p) * n_g + piv[mu]];
+  const int64_t g = piv[mu];
+  dst[e] = index_ok(g, n_g, err) ? src[((int64_t)c * n_orb + p) * n_g + g] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // x[i] = a[i] * b[i]
@@ -65,24 +66,32 @@ inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t
 
 }  // namespace
 
-int gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
-                  const int32_t* piv, int n_mu, double* phiP, double* dphiP, cudaStream_t s) {
+static int gather_pivots_err(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+                             const int32_t* piv, int n_mu, double* phiP, double* dphiP, int* err,
+                             cudaStream_t s) {
   ISDF_ARG(phi && piv && phiP, "null pointer argument");
   ISDF_ARG(n_orb > 0 && n_g > 0, "empty sizes");
   if (n_mu <= 0) return ISDF_OK;
   int64_t per = (int64_t)n_mu * n_orb;
-  gather_pivots_kernel<<<nblocks(per), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP, 1);
+  gather_pivots_kernel<<<nblocks(per), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP, 1, err);
   ISDF_LAUNCH_CHECK();
   if (dphi && dphiP) {
-    gather_pivots_kernel<<<nblocks(3 * per), 256, 0, s>>>(dphi, n_g, n_orb, piv, n_mu, dphiP, 3);
+    gather_pivots_kernel<<<nblocks(3 * per), 256, 0, s>>>(dphi, n_g, n_orb, piv, n_mu, dphiP, 3,
+                                                          err);
     ISDF_LAUNCH_CHECK();
   }
   return ISDF_OK;
 }
 
+int gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
+                  const int32_t* piv, int n_mu, double* phiP, double* dphiP, cudaStream_t s) {
+  return gather_pivots_err(phi, dphi, n_g, n_orb, piv, n_mu, phiP, dphiP, nullptr, s);
+}
+
 size_t fit_ws(int64_t n_g, int n_orb, int n_mu) {
   (void)n_g;
   Carve c(nullptr, 0);
+  c.take<int>(64);
   c.take<double>((size_t)4 * n_mu * n_orb);
   c.take<double>((size_t)3 * n_mu * n_mu);
   c.take<double>(2);
@@ -96,6 +105,7 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
   ISDF_ARG(phi && dphi && piv && xi && xig, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
   Carve cv(ws, ws_bytes);
+  int* err = cv.take<int>(64);
   double* phiP = cv.take<double>((size_t)n_mu * n_orb);
   double* dphiP = cv.take<double>((size_t)3 * n_mu * n_orb);
   double* GPP = cv.take<double>((size_t)n_mu * n_mu);
@@ -105,7 +115,20 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
   int* info = cv.take<int>(1);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
 
-  ISDF_TRY(gather_pivots(phi, dphi, n_g, n_orb, piv, n_mu, phiP, dphiP, s));
+  ISDF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  ISDF_TRY(gather_pivots_err(phi, dphi, n_g, n_orb, piv, n_mu, phiP, dphiP, err, s));
+  ISDF_TRY(scan_nonfinite(phi, (int64_t)n_orb * n_g, err, s));
+  ISDF_TRY(scan_nonfinite(dphi, (int64_t)3 * n_orb * n_g, err, s));
+  int h_err = 0;
+  ISDF_TRY(read_error_word(err, &h_err, s));
+  if (h_err & DEV_ERR_ARG) {
+    set_error("a pivot index lies outside [0, n_g = %lld)", (long long)n_g);
+    return ISDF_E_ARG;
+  }
+  if (h_err & DEV_ERR_NONFINITE) {
+    set_error("non-finite phi or dphi (NaN or Inf)");
+    return ISDF_E_NONFINITE;
+  }
   const int64_t nn = (int64_t)n_mu * n_mu;
   const int64_t ng = (int64_t)n_mu * n_g;
 
@@ -173,7 +196,14 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
     double* rhs = ch == 0 ? xi : xig + (int64_t)(ch - 1) * ng;
     ISDF_TRY(dpotrs_lower(Gram, n_mu, rhs, n_g, n_g, s));
   }
-  ISDF_CUDA(cudaStreamSynchronize(s));
+  // overflow in the solves
+  ISDF_TRY(scan_nonfinite(xi, ng, err, s));
+  ISDF_TRY(scan_nonfinite(xig, 3 * ng, err, s));
+  ISDF_TRY(read_error_word(err, &h_err, s));
+  if (h_err & DEV_ERR_NONFINITE) {
+    set_error("non-finite values in the fitted xi (overflow in the solves)");
+    return ISDF_E_NONFINITE;
+  }
   return ISDF_OK;
 }
 

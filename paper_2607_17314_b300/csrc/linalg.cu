@@ -256,4 +256,36 @@ int dpotrs_lower(const double* L, int n, double* B, int64_t nrhs, int64_t ldb, c
   return ISDF_OK;
 }
 
+// ---------------------------------------------------------------- input checks
+
+namespace {
+
+__global__ void scan_nonfinite_kernel(const double* __restrict__ x, int64_t n, int* err) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
+}  // namespace
+
+int scan_nonfinite(const double* x, int64_t n, int* err, cudaStream_t s) {
+  if (n <= 0) return ISDF_OK;
+  int dev = 0, nsm = 148;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t want = ceil_div(n, 256);
+  const unsigned blocks = (unsigned)(want < 8 * nsm ? want : 8 * nsm);
+  scan_nonfinite_kernel<<<blocks, 256, 0, s>>>(x, n, err);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+int read_error_word(const int* err, int* h_err, cudaStream_t s) {
+  ISDF_CUDA(cudaMemcpyAsync(h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  return ISDF_OK;
+}
+
 }  // namespace isdf

@@ -33,4 +33,20 @@ int dpotrf_lower(double* A, int n, int* info_dev, cudaStream_t s);
 int dpotrs_lower(const double* L, int n, double* B, int64_t nrhs, int64_t ldb,
                  cudaStream_t s);
 
+// OR DEV_ERR_NONFINITE into the device word *err when any of x[0..n) is NaN
+// or Inf.  Asynchronous.
+int scan_nonfinite(const double* x, int64_t n, int* err, cudaStream_t s);
+
+// Copy the device error word to *h_err and synchronise `s`.
+int read_error_word(const int* err, int* h_err, cudaStream_t s);
+
+// A device index that a kernel finds outside [0, n) is never dereferenced: the
+// gathered value becomes a quiet NaN and DEV_ERR_ARG is OR-ed into the error
+// word when the call has one.
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int* err) {
+  if (i >= 0 && i < n) return true;
+  if (err) atomicOr(err, DEV_ERR_ARG);
+  return false;
+}
+
 }  // namespace isdf

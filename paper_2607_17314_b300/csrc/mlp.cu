@@ -6,6 +6,8 @@
 // that decides between selections.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "linalg.cuh"
 
 namespace isdf {
@@ -348,12 +350,13 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ s,
 
 __global__ void gather_cols_kernel(const double* __restrict__ src, int64_t n_g, int64_t rows,
                                    const int32_t* __restrict__ idx, int n_idx,
-                                   double* __restrict__ dst) {
+                                   double* __restrict__ dst, int* err) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * n_idx) return;
   const int64_t r = e / n_idx;
   const int c = (int)(e % n_idx);
-  dst[e] = src[r * n_g + idx[c]];
+  const int64_t g = idx[c];
+  dst[e] = index_ok(g, n_g, err) ? src[r * n_g + g] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 __global__ void map_idx_kernel(const int32_t* __restrict__ sub, const int32_t* __restrict__ cand,
@@ -422,9 +425,10 @@ __global__ void add_diag_copy_kernel(double* A, const double* S, int n, double l
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)ceil_div(n, t); }
 
 int gather_pivot_rows(const double* phi, int64_t n_g, int n_orb, const int32_t* piv, int n_mu,
-                      double* phiP, cudaStream_t s) {
-  // phiP[mu][p] = phi[p][piv[mu]]
-  gather_cols_kernel<<<nb((int64_t)n_orb * n_mu), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP);
+                      double* phiP, int* err, cudaStream_t s) {
+  // phiP[p][mu] = phi[p][piv[mu]]
+  gather_cols_kernel<<<nb((int64_t)n_orb * n_mu), 256, 0, s>>>(phi, n_g, n_orb, piv, n_mu, phiP,
+                                                              err);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
@@ -490,6 +494,7 @@ int mlp_topk(const float* scores, int64_t n, int k, int32_t* out, cudaStream_t s
 
 size_t points_restricted_ws(int n_cand, int n_orb, int n_mu) {
   Carve c(nullptr, 0);
+  c.take<int>(64);
   c.take<double>((size_t)4 * n_orb * n_cand + n_cand);
   c.take<int32_t>(n_mu);
   c.take<unsigned char>(points_ws(n_cand, n_mu));
@@ -502,6 +507,7 @@ int points_restricted(const double* phi, const double* dphi, const double* w, in
   ISDF_ARG(phi && dphi && w && cand && pivots && n_mu_out, "null pointer argument");
   ISDF_ARG(n_cand > 0 && n_mu > 0 && n_orb > 0, "bad sizes");
   Carve cv(ws, ws_bytes);
+  int* err = cv.take<int>(64);
   double* sub = cv.take<double>((size_t)4 * n_orb * n_cand + n_cand);
   int32_t* spiv = cv.take<int32_t>(n_mu);
   const size_t pws = points_ws(n_cand, n_mu);
@@ -510,13 +516,21 @@ int points_restricted(const double* phi, const double* dphi, const double* w, in
   double* sphi = sub;
   double* sdphi = sub + (int64_t)n_orb * n_cand;
   double* sw = sub + (int64_t)4 * n_orb * n_cand;
-  gather_cols_kernel<<<nb((int64_t)n_orb * n_cand), 256, 0, s>>>(phi, n_g, n_orb, cand, n_cand, sphi);
+  ISDF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  gather_cols_kernel<<<nb((int64_t)n_orb * n_cand), 256, 0, s>>>(phi, n_g, n_orb, cand, n_cand, sphi,
+                                                                 err);
   ISDF_LAUNCH_CHECK();
   gather_cols_kernel<<<nb((int64_t)3 * n_orb * n_cand), 256, 0, s>>>(dphi, n_g, 3 * n_orb, cand,
-                                                                     n_cand, sdphi);
+                                                                     n_cand, sdphi, err);
   ISDF_LAUNCH_CHECK();
-  gather_cols_kernel<<<nb(n_cand), 256, 0, s>>>(w, n_g, 1, cand, n_cand, sw);
+  gather_cols_kernel<<<nb(n_cand), 256, 0, s>>>(w, n_g, 1, cand, n_cand, sw, err);
   ISDF_LAUNCH_CHECK();
+  int h_err = 0;
+  ISDF_TRY(read_error_word(err, &h_err, s));
+  if (h_err & DEV_ERR_ARG) {
+    set_error("a candidate index lies outside [0, n_g = %lld)", (long long)n_g);
+    return ISDF_E_ARG;
+  }
   const int rc = points(sphi, sdphi, sw, n_cand, n_orb, n_mu, 0, spiv, n_mu_out, pw, pws, s);
   if (rc != ISDF_OK && rc != ISDF_E_RANK) return rc;
   if (*n_mu_out > 0) {
@@ -529,6 +543,7 @@ int points_restricted(const double* phi, const double* dphi, const double* w, in
 
 size_t fit_error_ws(int64_t n_g, int n_orb, int n_mu) {
   Carve c(nullptr, 0);
+  c.take<int>(64);
   c.take<double>((size_t)n_mu * n_orb);
   for (int i = 0; i < 2; ++i) c.take<double>((size_t)n_mu * n_mu);
   for (int i = 0; i < 3; ++i) c.take<double>((size_t)n_mu * n_g);
@@ -541,6 +556,7 @@ int fit_error(const double* phi, const double* w, int64_t n_g, int n_orb, const 
               int n_mu, double* eps, void* ws, size_t ws_bytes, cudaStream_t s) {
   ISDF_ARG(phi && w && piv && eps && n_g > 0 && n_orb > 0 && n_mu > 0, "bad arguments");
   Carve cv(ws, ws_bytes);
+  int* err = cv.take<int>(64);
   double* phiP = cv.take<double>((size_t)n_mu * n_orb);  // [n_orb][n_mu]
   double* Gram = cv.take<double>((size_t)n_mu * n_mu);
   double* Save = cv.take<double>((size_t)n_mu * n_mu);
@@ -550,7 +566,20 @@ int fit_error(const double* phi, const double* w, int64_t n_g, int n_orb, const 
   double* acc = cv.take<double>(2);
   int* info = cv.take<int>(1);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
-  ISDF_TRY(gather_pivot_rows(phi, n_g, n_orb, piv, n_mu, phiP, s));  // phiP [n_orb][n_mu]
+  ISDF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  ISDF_TRY(gather_pivot_rows(phi, n_g, n_orb, piv, n_mu, phiP, err, s));  // phiP [n_orb][n_mu]
+  ISDF_TRY(scan_nonfinite(phi, (int64_t)n_orb * n_g, err, s));
+  ISDF_TRY(scan_nonfinite(w, n_g, err, s));
+  int h_err = 0;
+  ISDF_TRY(read_error_word(err, &h_err, s));
+  if (h_err & DEV_ERR_ARG) {
+    set_error("a pivot index lies outside [0, n_g = %lld)", (long long)n_g);
+    return ISDF_E_ARG;
+  }
+  if (h_err & DEV_ERR_NONFINITE) {
+    set_error("non-finite phi or w (NaN or Inf)");
+    return ISDF_E_NONFINITE;
+  }
   // G_PP = phiP^T phiP, G = phiP^T phi
   Dgemm g;
   g.M = n_mu; g.N = n_mu; g.K = n_orb;
@@ -600,6 +629,10 @@ int fit_error(const double* phi, const double* w, int64_t n_g, int n_orb, const 
   ISDF_CUDA(cudaMemcpyAsync(h, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ISDF_CUDA(cudaStreamSynchronize(s));
   *eps = h[0] / h[1];
+  if (!std::isfinite(*eps)) {
+    set_error("fit error is not finite");
+    return ISDF_E_NONFINITE;
+  }
   return ISDF_OK;
 }
 

@@ -32,7 +32,8 @@ struct PivArgs {
   int64_t n_g;
   int n_orb;
   int n_mu;
-  int cap;
+  int cap;             // columns per channel in L
+  int rank[2];         // mode 3: steps per channel
   double* d;           // [2][n_g]
   double* L;           // [2][cap][n_g]
   double* part_v;      // [2 ch][2 buf][nblk]
@@ -42,6 +43,7 @@ struct PivArgs {
   double* tol;         // [2]
   unsigned char* in_union;  // [n_g]
   int* union_piv;      // [n_mu]
+  int* err;            // device error word
 };
 
 __device__ __forceinline__ void better(double& bv, int& bi, double v, int i) {
@@ -91,6 +93,8 @@ __global__ void __launch_bounds__(PT) diag_init_kernel(PivArgs a) {
     d1 = __dmul_rn(ww, __dmul_rn(t1, t2));
     a.d[g] = d0;
     a.d[a.n_g + g] = d1;
+    // a NaN or Inf in phi, dphi or w reaches both diagonals
+    if (!isfinite(d0) || !isfinite(d1)) atomicOr(a.err, DEV_ERR_NONFINITE);
   }
   int i0 = g < a.n_g ? (int)g : 0x7fffffff, i1 = i0;
   block_argmax(d0, i0);
@@ -142,13 +146,15 @@ __global__ void __launch_bounds__(PT) pivot_step_kernel(PivArgs a, int parity, i
   if (active && s.done[c]) c = 1 - c;
   if (mode == 1) c = 0;
   if (mode == 2) c = 1;
+  if (mode == 3) c = s.done[0] ? 1 : 0;  // the scalar channel to its rank, then the gradient one
   double dgs = 0.0;
   int gs = 0;
   if (active) {
     reduce_partials(a, c, s.k[c] & 1, dgs, gs);
-    if (s.k[c] >= a.cap || !(dgs > a.tol[c])) {
+    const int cap = mode == 3 ? a.rank[c] : a.cap;
+    if (s.k[c] >= cap || !(dgs > a.tol[c])) {
       ns.done[c] = 1;
-      if (mode != 0) ns.done[1 - c] = 1;
+      if (mode == 1 || mode == 2) ns.done[1 - c] = 1;
       ns.turn = 1 - s.turn;
       active = false;
     }
@@ -216,11 +222,14 @@ __global__ void __launch_bounds__(PT) pivot_step_kernel(PivArgs a, int parity, i
 
 }  // namespace
 
-size_t points_ws(int64_t n_g, int n_mu) {
+// Workspace of a selection with `cap` Cholesky columns per channel and at most
+// n_mu union points.
+static size_t points_ws_cap(int64_t n_g, int n_mu, int cap) {
   Carve c(nullptr, 0);
   int nblk = (int)ceil_div(n_g, PT);
+  c.take<int>(64);
   c.take<double>(2 * (size_t)n_g);
-  c.take<double>(2 * (size_t)n_mu * n_g);
+  c.take<double>(2 * (size_t)cap * n_g);
   c.take<double>(4 * (size_t)nblk);
   c.take<int>(4 * (size_t)nblk);
   c.take<PivState>(2);
@@ -230,20 +239,32 @@ size_t points_ws(int64_t n_g, int n_mu) {
   return c.off;
 }
 
-int points(const double* phi, const double* dphi, const double* w, int64_t n_g, int n_orb,
-           int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws, size_t ws_bytes,
-           cudaStream_t s) {
+size_t points_ws(int64_t n_g, int n_mu) { return points_ws_cap(n_g, n_mu, n_mu); }
+
+size_t points_ranks_ws(int64_t n_g, int n_phi, int n_grad) {
+  return points_ws_cap(n_g, n_phi + n_grad, n_phi > n_grad ? n_phi : n_grad);
+}
+
+// Modes 0-2 (fused alternating, scalar, gradient) select n_mu points; mode 3
+// (the paper's fusion) runs the scalar channel to rank n_phi and the gradient
+// channel to rank n_grad, with n_mu = n_phi + n_grad bounding the union.
+static int points_run(const double* phi, const double* dphi, const double* w, int64_t n_g,
+                      int n_orb, int n_mu, int mode, int n_phi, int n_grad, int32_t* pivots,
+                      int* n_mu_out, void* ws, size_t ws_bytes, cudaStream_t s) {
   ISDF_ARG(phi && dphi && w && pivots && n_mu_out, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
   ISDF_ARG(n_g < 0x7fffffff, "n_g must fit in int32");
-  ISDF_ARG(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
+  ISDF_ARG(mode >= 0 && mode <= 3, "mode must be 0, 1, 2 or 3");
   PivArgs a;
   a.phi = phi; a.dphi = dphi; a.w = w; a.n_g = n_g; a.n_orb = n_orb; a.n_mu = n_mu;
-  a.cap = n_mu;
+  a.cap = mode == 3 ? (n_phi > n_grad ? n_phi : n_grad) : n_mu;
+  a.rank[0] = n_phi;
+  a.rank[1] = n_grad;
   a.nblk = (int)ceil_div(n_g, PT);
   Carve cv(ws, ws_bytes);
+  a.err = cv.take<int>(64);
   a.d = cv.take<double>(2 * (size_t)n_g);
-  a.L = cv.take<double>(2 * (size_t)n_mu * n_g);
+  a.L = cv.take<double>(2 * (size_t)a.cap * n_g);
   a.part_v = cv.take<double>(4 * (size_t)a.nblk);
   a.part_i = cv.take<int>(4 * (size_t)a.nblk);
   a.st = cv.take<PivState>(2);
@@ -252,16 +273,23 @@ int points(const double* phi, const double* dphi, const double* w, int64_t n_g, 
   a.union_piv = cv.take<int>(n_mu);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   ISDF_CUDA(cudaMemsetAsync(a.in_union, 0, n_g, s));
+  ISDF_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), s));
   diag_init_kernel<<<a.nblk, PT, 0, s>>>(a);
   ISDF_LAUNCH_CHECK();
   tol_init_kernel<<<1, PT, 0, s>>>(a);
   ISDF_LAUNCH_CHECK();
+  int h_err = 0;
+  ISDF_CUDA(cudaMemcpyAsync(&h_err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  if (h_err & DEV_ERR_NONFINITE) {
+    set_error("non-finite phi, dphi or w: a pivot diagonal is NaN or Inf");
+    return ISDF_E_NONFINITE;
+  }
   const int max_iter = 2 * n_mu + 4;
   // Steps run in batches of 32 launches replayed from a CUDA graph on a private
   // stream (the launch cost dominates the short steps of small grids); the host
   // reads the step state between batches to stop.  Steps past the end are no-ops.
   constexpr int kBatch = 32;
-  ISDF_CUDA(cudaStreamSynchronize(s));
   cudaStream_t ps = nullptr;
   ISDF_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -309,11 +337,36 @@ int points(const double* phi, const double* dphi, const double* w, int64_t n_g, 
   if (h.nu > 0)
     ISDF_CUDA(cudaMemcpyAsync(pivots, a.union_piv, sizeof(int) * h.nu, cudaMemcpyDeviceToDevice, s));
   ISDF_CUDA(cudaStreamSynchronize(s));
+  if (mode == 3) {
+    if (h.k[0] < n_phi || h.k[1] < n_grad) {
+      set_error("rank exhausted: %d of %d scalar and %d of %d gradient steps", h.k[0], n_phi,
+                h.k[1], n_grad);
+      return ISDF_E_RANK;
+    }
+    return ISDF_OK;
+  }
   if (h.nu < n_mu) {
     set_error("rank exhausted: %d of %d points", h.nu, n_mu);
     return ISDF_E_RANK;
   }
   return ISDF_OK;
+}
+
+int points(const double* phi, const double* dphi, const double* w, int64_t n_g, int n_orb,
+           int n_mu, int mode, int32_t* pivots, int* n_mu_out, void* ws, size_t ws_bytes,
+           cudaStream_t s) {
+  ISDF_ARG(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
+  return points_run(phi, dphi, w, n_g, n_orb, n_mu, mode, 0, 0, pivots, n_mu_out, ws, ws_bytes,
+                    s);
+}
+
+int points_ranks(const double* phi, const double* dphi, const double* w, int64_t n_g, int n_orb,
+                 int n_phi, int n_grad, int32_t* pivots, int* n_mu_out, void* ws,
+                 size_t ws_bytes, cudaStream_t s) {
+  ISDF_ARG(n_phi >= 0 && n_grad >= 0 && n_phi + n_grad > 0, "channel ranks must be >= 0 with a "
+           "positive sum");
+  return points_run(phi, dphi, w, n_g, n_orb, n_phi + n_grad, 3, n_phi, n_grad, pivots, n_mu_out,
+                    ws, ws_bytes, s);
 }
 
 }  // namespace isdf

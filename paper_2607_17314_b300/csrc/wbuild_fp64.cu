@@ -109,7 +109,8 @@ __global__ void bh_table_kernel(const double* grid, int64_t n_g, const __grid_co
 
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J) {
   Carve c(nullptr, 0);
-  int nn = J ? J->n_nuc : ISDF_MAX_NUC;
+  c.take<int>(64);
+  int nn = J ? (J->n_terms == 0 ? 0 : J->n_nuc) : ISDF_MAX_NUC;
   c.take<double>((size_t)n_g * nn);
   c.take<double>((size_t)3 * n_g * nn);
   return c.off;
@@ -126,17 +127,19 @@ int bh_table(const double* grid, int64_t n_g, const isdf_jastrow& J, double* A, 
 
 int wbuild_fp64(const double* grid, const double* w, const double* xi, const double* xig,
                 int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, const isdf_jastrow& J,
-                double* W, double* calG, void* ws, size_t ws_bytes, cudaStream_t s) {
+                double* W, double* calG, int sync_check, void* ws, size_t ws_bytes,
+                cudaStream_t s) {
   const bool radial = J.n_terms == 0;
   S1F64 a;
   a.grid = grid; a.w = w; a.xi = xi; a.n_g = n_g; a.n_mu = n_mu;
   a.g_begin = g_begin; a.g_end = g_end; a.calG = calG;
   a.tab.A = nullptr; a.tab.dA = nullptr;
+  Carve cv(ws, ws_bytes);
+  int* err = cv.take<int>(64);
+  double* A = radial ? nullptr : cv.take<double>((size_t)n_g * J.n_nuc);
+  double* dA = radial ? nullptr : cv.take<double>((size_t)3 * n_g * J.n_nuc);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   if (!radial) {
-    Carve cv(ws, ws_bytes);
-    double* A = cv.take<double>((size_t)n_g * J.n_nuc);
-    double* dA = cv.take<double>((size_t)3 * n_g * J.n_nuc);
-    ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
     ISDF_TRY(bh_table(grid, n_g, J, A, dA, s));
     a.tab.A = A; a.tab.dA = dA;
   }
@@ -159,6 +162,17 @@ int wbuild_fp64(const double* grid, const double* w, const double* xi, const dou
   g.C = W + 3 * (int64_t)n_mu * n_mu;
   g.batch = 1;
   ISDF_TRY(dgemm(g, s));
+  if (sync_check) {
+    // every input value reaches W: a NaN or Inf there leaves a non-finite W
+    ISDF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    ISDF_TRY(scan_nonfinite(W, (int64_t)4 * n_mu * n_mu, err, s));
+    int h_err = 0;
+    ISDF_TRY(read_error_word(err, &h_err, s));
+    if (h_err & DEV_ERR_NONFINITE) {
+      set_error("W is not finite (NaN or Inf in the grid, weights or xi)");
+      return ISDF_E_NONFINITE;
+    }
+  }
   return ISDF_OK;
 }
 

@@ -1211,6 +1211,8 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
                      (int64_t)n_mu * n_mu, 1.0, err, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[3], s));
   if (opt.sync_check) {
+    // every input value reaches W: a NaN or Inf there leaves a non-finite W
+    ISDF_TRY(scan_nonfinite(W, (int64_t)4 * n_mu * n_mu, err, s));
     int h_err = 0;
     ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ISDF_CUDA(cudaStreamSynchronize(s));
@@ -1222,6 +1224,10 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     if (h_err & DEV_ERR_TIMEOUT) {
       set_error("tensor-core pipeline wait expired (device error word 0x%x)", h_err);
       return ISDF_E_TIMEOUT;
+    }
+    if (h_err & DEV_ERR_NONFINITE) {
+      set_error("W is not finite (NaN or Inf in the grid, weights or xi)");
+      return ISDF_E_NONFINITE;
     }
   }
   return ISDF_OK;

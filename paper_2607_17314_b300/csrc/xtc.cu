@@ -276,13 +276,19 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
       const void* B1[1] = {b};
       ISDF_TRY(splitgemm(limbs, 1, A1, B1, n_mu, n_mu, kp, kp, 256, D, n_mu, 0, 2.0, err, s));
     }
+    // every input value reaches D: a NaN or Inf there leaves a non-finite D
+    ISDF_TRY(scan_nonfinite(D, (int64_t)n_mu * n_mu, err, s));
     int h_err = 0;
     ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ISDF_CUDA(cudaStreamSynchronize(s));
-    if (h_err) {
+    if (h_err & DEV_ERR_TIMEOUT) {
       set_error("tensor-core pipeline wait expired in the D contraction (device error word 0x%x)",
                 h_err);
       return ISDF_E_TIMEOUT;
+    }
+    if (h_err & DEV_ERR_NONFINITE) {
+      set_error("D is not finite (NaN or Inf in phi_piv, xi, w or calG)");
+      return ISDF_E_NONFINITE;
     }
   }
   if (n_orb_x == 0) return ISDF_OK;
@@ -328,13 +334,18 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
       const int64_t kr = kg < 1024 ? kg : 1024;
       ISDF_TRY(splitgemm(kXLimbs, 4, A4, B4, npair, n_mu, kg, kr, 256, Xp, n_mu, 0, 1.0, err, s));
     }
+    ISDF_TRY(scan_nonfinite(Xp, npair * n_mu, err, s));
     int h_err = 0;
     ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ISDF_CUDA(cudaStreamSynchronize(s));
-    if (h_err) {
+    if (h_err & DEV_ERR_TIMEOUT) {
       set_error("tensor-core pipeline wait expired in the X contraction (device error word 0x%x)",
                 h_err);
       return ISDF_E_TIMEOUT;
+    }
+    if (h_err & DEV_ERR_NONFINITE) {
+      set_error("X is not finite (NaN or Inf in phi_piv, xi, w or calG)");
+      return ISDF_E_NONFINITE;
     }
     return ISDF_OK;
   }

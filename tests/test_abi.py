@@ -71,6 +71,12 @@ def test_argument_errors_need_no_gpu(lib):
     assert st == C.ISDF_E_ARG  # null pointers
     st = lib.isdf_points(None, None, None, 10, 2, 4, 7, None, None, None, 0, None)
     assert st == C.ISDF_E_ARG
+    fake = ctypes.c_void_p(256)
+    n = C.INT(0)
+    for ranks in ((0, 0), (-1, 4), (4, -1)):
+        st = lib.isdf_points_fixed_rank(fake, fake, fake, 64, 4, *ranks, fake, ctypes.byref(n),
+                                        fake, 1 << 30, None)
+        assert st == C.ISDF_E_ARG, ranks
 
 
 def test_correlator_parameters_checked_before_launch(lib):
@@ -176,14 +182,19 @@ def test_undersized_workspace_rejected_before_launch(lib):
     basis = C.IsdfBasis(4, 3, f, f, f, f)
     J = C.IsdfJastrow()
     J.n_types, J.d, J.cusp, J.b[0] = 1, 1.0, 1, 1.0
+    opt64 = C.IsdfOptions(C.ISDF_PREC_FP64, 0, 0, 1, 0, None)
     calls = {
         "isdf_eval_orbitals": lambda: lib.isdf_eval_orbitals(ctypes.byref(basis), f, 4, f, 64, f,
                                                              f, f, 16, None),
         "isdf_points": lambda: lib.isdf_points(f, f, f, 64, 4, 8, 0, f, ctypes.byref(n), f, 16,
                                                None),
+        "isdf_points_fixed_rank": lambda: lib.isdf_points_fixed_rank(
+            f, f, f, 64, 4, 4, 4, f, ctypes.byref(n), f, 16, None),
         "isdf_fit": lambda: lib.isdf_fit(f, f, 64, 4, f, 8, f, f, None, f, 16, None),
         "tc_kernel_build": lambda: lib.tc_kernel_build(f, f, f, f, 64, 8, 0, 64, ctypes.byref(J),
                                                        None, f, f, f, 16, None),
+        "tc_kernel_build (fp64)": lambda: lib.tc_kernel_build(
+            f, f, f, f, 64, 8, 0, 64, ctypes.byref(J), ctypes.byref(opt64), f, f, f, 16, None),
         "tc_kernel_adjoint": lambda: lib.tc_kernel_adjoint(f, f, f, f, 64, 8, ctypes.byref(J), f,
                                                            C.PRECISIONS["fp64"], f, f, 16, None),
         "xtc_density_contract": lambda: lib.xtc_density_contract(f, 4, 2, f, f, f, 64, 8, f, f, 4,

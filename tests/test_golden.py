@@ -187,3 +187,13 @@ def test_mlp_features_against_hand_values():
     got = mlp.features(phi, dphi, w, np.zeros((1, 3)), nuc)[0]
     exp = np.array([_frac(v) for v in f["features"].split()])
     assert np.max(np.abs(got - exp)) <= 1e-15
+
+
+def test_tie_margin_on_hand_case():
+    """The near-tie measure used when two machines' pivot lists differ: in the
+    unit case points 0 and 1 tie at step 1 (d = 3/4 each), while at step 0
+    point 0 trails point 2 by (4 - 1)/4."""
+    dphi = np.zeros((3, 2, 3))
+    assert pivots.tie_margin(PHI, dphi, np.ones(3), [2, 0, 1], [2, 1, 0], "scalar") == (1, 0.0)
+    assert pivots.tie_margin(PHI, dphi, np.ones(3), [2, 0, 1], [0, 1, 2], "scalar") == (0, 0.75)
+    assert pivots.tie_margin(PHI, dphi, np.ones(3), [2, 0, 1], [2, 0, 1], "scalar") == (None, 0.0)

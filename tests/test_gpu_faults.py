@@ -56,3 +56,92 @@ def test_bad_arguments_rejected_before_launch(api):
     with pytest.raises(C.IsdfError) as e:
         api.tc_kernel_build(g, wt, xi, xig, Jbh, "bf16x6")
     assert e.value.status == C.ISDF_E_ARG
+
+
+# ---------------------------------------------------------------- host-injected bad inputs
+# Each case plants a NaN, an Inf or an out-of-range index in an input on the
+# host.  The kernels never dereference an out-of-range index (the gather
+# writes a quiet NaN instead), so nothing faults; the calls that synchronise
+# report the problem by status.
+
+def _orbital_case():
+    from oracle import orbitals
+    w = wl.tiny_chain(n_atom=2, n_rad=10, n_ang=14, shells=(0, 1), n_mu=16, seed=7)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    return w, c(phi), c(dphi), c(w.grid_w)
+
+
+def _status(fn):
+    from paper_2607_17314_b300 import _capi as C
+    try:
+        fn()
+    except C.IsdfError as e:
+        return e.status
+    return C.ISDF_OK
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_pivot_inputs(api, bad):
+    from paper_2607_17314_b300 import _capi as C
+    w, phi, dphi, wt = _orbital_case()
+    wt2 = wt.clone()
+    wt2[17] = bad
+    assert _status(lambda: api.isdf_points(phi, dphi, wt2, w.n_mu)) == C.ISDF_E_NONFINITE
+    assert _status(lambda: api.isdf_points_fixed_rank(phi, dphi, wt2, 4, 4)) == C.ISDF_E_NONFINITE
+    dphi2 = dphi.clone()
+    dphi2[2, 1, 5] = bad
+    assert _status(lambda: api.isdf_points(phi, dphi2, wt, w.n_mu)) == C.ISDF_E_NONFINITE
+    # the same context keeps working
+    assert api.isdf_points(phi, dphi, wt, w.n_mu).numel() == w.n_mu
+
+
+def test_nonfinite_fit_and_kernel_build(api):
+    from paper_2607_17314_b300 import _capi as C
+    w, phi, dphi, wt = _orbital_case()
+    piv = api.isdf_points(phi, dphi, wt, w.n_mu)
+    phi2 = phi.clone()
+    phi2[0, 3] = float("nan")
+    assert _status(lambda: api.isdf_fit(phi2, dphi, piv)) == C.ISDF_E_NONFINITE
+    xi, xig, _ = api.isdf_fit(phi, dphi, piv)
+    J = api.jastrow_from(w.jastrow)
+    g = torch.as_tensor(w.grid_xyz).cuda()
+    xi2 = xi.clone()
+    xi2[1, 9] = float("inf")
+    for prec in ("fp64", "bf16x3", "bf16x6"):
+        assert _status(lambda: api.tc_kernel_build(g, wt, xi2, xig, J, prec)) == \
+            C.ISDF_E_NONFINITE, prec
+    W, calG = api.tc_kernel_build(g, wt, xi, xig, J, "bf16x3")
+    phiP, dphiP = api.isdf_gather_pivots(phi, dphi, piv)
+    calG2 = calG.clone()
+    calG2[0, 2, 11] = float("nan")
+    for prec in ("bf16x3", "bf16x6"):
+        assert _status(lambda: api.xtc_density_contract(phiP, w.n_occ, xi, wt, calG2, w.n_occ,
+                                                        precision=prec)) == C.ISDF_E_NONFINITE
+    D, Xp = api.xtc_density_contract(phiP, w.n_occ, xi, wt, calG, w.n_occ)
+    W2 = W.clone()
+    W2[3, 0, 0] = float("nan")
+    assert _status(lambda: api.tc_energies(W2, D, Xp, phiP, dphiP, w.n_occ)) == C.ISDF_E_NONFINITE
+    assert all(np.isfinite(api.tc_energies(W, D, Xp, phiP, dphiP, w.n_occ)))
+
+
+@pytest.mark.parametrize("bad_index", [-1, "n_g", 1 << 30])
+def test_out_of_range_indices(api, bad_index):
+    from paper_2607_17314_b300 import _capi as C, proposer
+    w, phi, dphi, wt = _orbital_case()
+    n_g = phi.shape[1]
+    bad = n_g if bad_index == "n_g" else bad_index
+    piv = api.isdf_points(phi, dphi, wt, w.n_mu)
+    piv2 = piv.clone()
+    piv2[5] = bad
+    assert _status(lambda: api.isdf_fit(phi, dphi, piv2)) == C.ISDF_E_ARG
+    assert _status(lambda: proposer.fit_error(phi, wt, piv2)) == C.ISDF_E_ARG
+    # the asynchronous gather cannot report: the bad row becomes NaN
+    phiP, dphiP = api.isdf_gather_pivots(phi, dphi, piv2)
+    assert bool(torch.isnan(phiP[5]).all()) and bool(torch.isnan(dphiP[:, 5]).all())
+    good = torch.cat([torch.arange(0, 5), torch.arange(6, phiP.shape[0])]).cuda()
+    ref, _ = api.isdf_gather_pivots(phi, dphi, piv)
+    assert torch.equal(phiP[good], ref[good])
+    cand = torch.arange(0, n_g, 3, dtype=torch.int32, device="cuda")
+    cand[2] = bad
+    assert _status(lambda: proposer.points_restricted(phi, dphi, wt, cand, 8)) == C.ISDF_E_ARG

@@ -1,0 +1,89 @@
+"""Stage 1 and stage 2 of the tensor-core W build compared with the FP64 oracle
+element by element where every persistent CTA runs several tiles.
+
+Radial correlator on an H10-chain grid: 10 x 40 x 50 = 20,000 points (312.5
+tiles of 64 outer points) and N_mu = 300 (three 128-row tiles, the last one
+ragged): 939 tiles on 148 CTAs.  Two-type multi-centre correlator on the
+benzene geometry: 12 x 14 x 50 = 8400 points (131.25 tiles), N_mu = 300:
+396 tiles.  Every calG and W element is checked against the oracle within
+1e-5 of its normwise bound: sum_g' |w_g' xi_nu(g')| |K_c(g, g')| for calG,
+and that bound carried through stage 2, sum_g |w_g xi~^c_mu(g)| bound_nu(g),
+plus the stage-2 sum's own scale sum_g |w_g xi~^c_mu(g)| |calG_nu(g)|, for W.
+xi and xi~ are seeded normal samples (the oracle's cost does not depend on
+their values).  The oracle runs in a process pool started with spawn.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from synth import workloads as wl
+from oracle import wbuild
+
+pytestmark = pytest.mark.gpu
+
+_CASES = {}
+
+
+def _geometry(name):
+    if name == "radial":
+        _, xyz = wl.h_chain(10, 1.8)
+        grid, w = wl.becke_grid(xyz, 40, 50)
+        return grid, w, wl.radial_jastrow(xyz)
+    atoms, xyz = wl.benzene()
+    grid, w = wl.becke_grid(xyz, 14, 50)
+    return grid, w, wl.bh_jastrow(atoms, xyz, wl.BH_TERMS_C3, np.random.default_rng(3001))
+
+
+def _oracle(name, n_mu=300):
+    if name in _CASES:
+        return _CASES[name]
+    grid, w, jas = _geometry(name)
+    n_g = grid.shape[0]
+    xi = wl.seeded_matrix((n_mu, n_g), 901, 1e-3)
+    xit = wl.seeded_matrix((3, n_mu, n_g), 902, 1e-3)
+    chunks = np.array_split(np.arange(n_g), 64)
+    procs = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.starmap(wbuild.stage1_bounded, [(grid, w, xi, jas, c) for c in chunks])
+    calG = np.concatenate([p[0] for p in parts], axis=2)
+    bound = np.concatenate([p[1] for p in parts], axis=2)
+    W = wbuild.stage2(w, xi, xit, calG)
+    src = [xit[0], xit[1], xit[2], xi]
+    Wb = np.stack([np.abs(s * w[None, :]) @ (bound[c] + np.abs(calG[c])).T
+                   for c, s in enumerate(src)])
+    _CASES[name] = (grid, w, jas, xi, xit, calG, bound, W, Wb)
+    return _CASES[name]
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_17314_b300 import build
+    build.build()
+    from paper_2607_17314_b300 import api
+    return api
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("name", ["radial", "benzene"])
+def test_stage1_and_w_every_element(api, name, prec):
+    grid, w, jas, xi, xit, calG, bound, W, Wb = _oracle(name)
+    n_g = grid.shape[0]
+    c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    Wg, Gg = api.tc_kernel_build(c(grid), c(w), c(xi), c(xit), api.jastrow_from(jas), prec)
+    Gg = Gg.cpu().numpy()
+    Wg = Wg.cpu().numpy()
+    n_tiles = int(np.ceil(xi.shape[0] / 128)) * int(np.ceil(n_g / 64))
+    assert n_tiles > 2 * 148          # every CTA runs more than one tile
+    gerr = np.abs(Gg - calG) / bound
+    werr = np.abs(Wg - W) / Wb
+    print(name, prec, "tiles", n_tiles, "max calG err / bound %.2e" % gerr.max(),
+          "max W err / bound %.2e" % werr.max(),
+          "W rel Frobenius", [float(np.linalg.norm(Wg[k] - W[k]) / np.linalg.norm(W[k]))
+                              for k in range(4)])
+    assert gerr.max() < 1e-5, np.unravel_index(np.argmax(gerr), gerr.shape)
+    assert werr.max() < 1e-5, np.unravel_index(np.argmax(werr), werr.shape)
