@@ -15,10 +15,11 @@ OUT = os.path.join(HERE, "_pivots.so")
 def build(force: bool = False) -> str:
     """Compile the order-exact pivot routine (Alg. 1) with gcc, with FMA
     contraction and fast math off so that every product and sum is the
-    correctly rounded operation the source writes; returns the library path."""
+    correctly rounded operation the source writes (OpenMP splits loops over
+    grid points only); returns the library path."""
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
         return OUT
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
            "-o", OUT + ".tmp", SRC, "-lm"]
     # use the hardware fused multiply-add when the host has one (the result
     # of fma() is the same correctly rounded value either way)

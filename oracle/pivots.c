@@ -1,9 +1,11 @@
 /*
  * Order-exact weighted pivoted Cholesky with pivot fusion -- oracle.
  *
- * TEST INFRASTRUCTURE: plain single-threaded C, FP64, built with
- * -ffp-contract=off so that every product and sum below is rounded exactly as
- * written (fma() is an explicit, correctly rounded fused multiply-add).
+ * TEST INFRASTRUCTURE: plain C, FP64, built with -ffp-contract=off so that
+ * every product and sum below is rounded exactly as written (fma() is an
+ * explicit, correctly rounded fused multiply-add).  Loops over grid points may
+ * be split across OpenMP threads; each point's sums keep the stated order, so
+ * the results do not depend on the thread count.
  *
  * Follows Alg. 1 (scalar branch) and the gradient branch of Sec. II.D:
  *   t1(g,h) = sum_p phi_p(g) phi_p(h)                         (p ascending)
@@ -37,26 +39,37 @@ typedef struct {
   int n_orb;
 } pv_in;
 
-/* column t1(., h) into out[g] */
+/* column t1(., h) into out[g].  The loops over g may run on several threads
+ * (OpenMP, static partition): each point's sum keeps its order, p ascending. */
 static void col_t1(const pv_in* in, long h, double* out) {
   long n_g = in->n_g;
-  for (long g = 0; g < n_g; ++g) out[g] = 0.0;
-  for (int p = 0; p < in->n_orb; ++p) {
-    const double* row = in->phi + (long)p * n_g;
-    double b = row[h];
-    for (long g = 0; g < n_g; ++g) out[g] = fma(row[g], b, out[g]);
+#pragma omp parallel
+  {
+#pragma omp for schedule(static)
+    for (long g = 0; g < n_g; ++g) out[g] = 0.0;
+    for (int p = 0; p < in->n_orb; ++p) {
+      const double* row = in->phi + (long)p * n_g;
+      double b = row[h];
+#pragma omp for schedule(static)
+      for (long g = 0; g < n_g; ++g) out[g] = fma(row[g], b, out[g]);
+    }
   }
 }
 
 static void col_t2(const pv_in* in, long h, double* out) {
   long n_g = in->n_g;
-  for (long g = 0; g < n_g; ++g) out[g] = 0.0;
-  for (int c = 0; c < 3; ++c)
-    for (int p = 0; p < in->n_orb; ++p) {
-      const double* row = in->dphi + ((long)c * in->n_orb + p) * n_g;
-      double b = row[h];
-      for (long g = 0; g < n_g; ++g) out[g] = fma(row[g], b, out[g]);
-    }
+#pragma omp parallel
+  {
+#pragma omp for schedule(static)
+    for (long g = 0; g < n_g; ++g) out[g] = 0.0;
+    for (int c = 0; c < 3; ++c)
+      for (int p = 0; p < in->n_orb; ++p) {
+        const double* row = in->dphi + ((long)c * in->n_orb + p) * n_g;
+        double b = row[h];
+#pragma omp for schedule(static)
+        for (long g = 0; g < n_g; ++g) out[g] = fma(row[g], b, out[g]);
+      }
+  }
 }
 
 /* diagonal: t(g,g) computed in the same order as a column */
@@ -114,22 +127,28 @@ static long chan_step(const pv_in* in, pv_chan* ch, double* t1, double* t2) {
   if (ch->grad) col_t2(in, gs, t2);
   double* Lk = ch->L + (long)ch->k * n_g;
   double wg = in->w[gs];
-  for (long g = 0; g < n_g; ++g) {
-    double s = ch->grad ? (in->w[g] * wg) * (t1[g] * t2[g])
-                        : (in->w[g] * wg) * (t1[g] * t1[g]);
-    Lk[g] = s;
-  }
-  for (int l = 0; l < ch->k; ++l) {
-    const double* Ll = ch->L + (long)l * n_g;
-    double b = Ll[gs];
-    for (long g = 0; g < n_g; ++g) Lk[g] = fma(-Ll[g], b, Lk[g]);
-  }
   double sq = sqrt(dgs);
-  for (long g = 0; g < n_g; ++g) {
-    double v = Lk[g] / sq;
-    Lk[g] = v;
-    double nd = fma(-v, v, ch->d[g]);
-    ch->d[g] = nd > 0.0 ? nd : 0.0;
+#pragma omp parallel
+  {
+#pragma omp for schedule(static)
+    for (long g = 0; g < n_g; ++g) {
+      double s = ch->grad ? (in->w[g] * wg) * (t1[g] * t2[g])
+                          : (in->w[g] * wg) * (t1[g] * t1[g]);
+      Lk[g] = s;
+    }
+    for (int l = 0; l < ch->k; ++l) {
+      const double* Ll = ch->L + (long)l * n_g;
+      double b = Ll[gs];
+#pragma omp for schedule(static)
+      for (long g = 0; g < n_g; ++g) Lk[g] = fma(-Ll[g], b, Lk[g]);
+    }
+#pragma omp for schedule(static)
+    for (long g = 0; g < n_g; ++g) {
+      double v = Lk[g] / sq;
+      Lk[g] = v;
+      double nd = fma(-v, v, ch->d[g]);
+      ch->d[g] = nd > 0.0 ? nd : 0.0;
+    }
   }
   ch->d[gs] = 0.0;
   ch->piv[ch->k] = (int)gs;
