@@ -46,6 +46,10 @@ def parse():
                     help="outer grid points of the FP64 GPU comparison slice")
     ap.add_argument("--cpu-rows", type=int, default=64,
                     help="outer grid points of the CPU oracle sample")
+    ap.add_argument("--validate", action="store_true",
+                    help="instead of the bench line: the whole workload once on the tensor-core "
+                         "path and once on the FP64 GPU path from the same orbitals, pivots and "
+                         "fit; full W, D, X and energy differences (minutes at the H50 size)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--w-only", action="store_true",
@@ -77,6 +81,13 @@ def w_flops(n_mu, n_rows, n_g):
 
 
 FALLBACK_BF16_SUSTAINED_TFLOPS = 1400.0
+
+# ncu counters of the current stage-1 kernel, from its small-case capture
+# (H50-chain geometry, 40,000 points, N_mu = 1024, one launch):
+# dram__bytes_read.sum + dram__bytes_write.sum divided by N_mu x n_g (the
+# launch's compulsory traffic scales with it), and sm__pipe_tensor_cycles_active
+# as a fraction of elapsed cycles.  Empty for a kernel not yet captured.
+S1_NCU = {"bf16x3": {"dram_bytes_per_mu_g": 36.15, "tensor_pipe_active": 0.465}}
 
 
 def tensor_peak(root=None):
@@ -162,6 +173,43 @@ def make_workload(name):
     return fn()
 
 
+def sampled_energy_error(api, inp, out, J, precision, n_slices=8, width=128):
+    """Error of the tensor-core energies against the FP64 GPU path, estimated
+    from outer-grid slices.  W, D and X are sums over outer grid points and the
+    energies are linear in them, so each slice's error contribution is exact:
+    both paths build W, calG, D and X over the slice (same xi, pivots and
+    orbitals) and the energies of the partial sums are differenced.  The total
+    is extrapolated by n_g / (n_slices width), with the standard error of that
+    extrapolation from the spread over the slices."""
+    import torch
+    n_g, n_occ = inp.n_g, inp.n_occ
+    xi, xig, phiP, dphiP = out["xi"], out["xig"], out["phiP"], out["dphiP"]
+    diffs = []
+    for i in range(n_slices):
+        g0 = max(0, min(n_g - width, int((i + 0.5) * n_g / n_slices) - width // 2))
+        g1 = min(n_g, g0 + width)
+        xs = xi[:, g0:g1].contiguous()
+        ws = inp.w[g0:g1].contiguous()
+        E = {}
+        for prec in ("fp64", precision):
+            W, calG = api.tc_kernel_build(inp.grid, inp.w, xi, xig, J, prec, g_begin=g0, g_end=g1)
+            D, Xp = api.xtc_density_contract(phiP, n_occ, xs, ws, calG, n_occ, precision=prec)
+            E[prec] = api.tc_energies(W, D, Xp, phiP, dphiP, n_occ)
+            del W, calG, D, Xp
+        diffs.append([a - b for a, b in zip(E[precision], E["fp64"])])
+    torch.cuda.empty_cache()
+    d = np.array(diffs)
+    scale = n_g / (n_slices * width)
+    est = scale * d.sum(axis=0)
+    se = scale * np.sqrt(n_slices) * d.std(axis=0, ddof=1)
+    keys = ("E_K", "E_dU", "E0")
+    return {"estimate": dict(zip(keys, map(float, est))),
+            "std_error": dict(zip(keys, map(float, se))),
+            "sample": f"{n_slices} outer slices x {width} points spread over the grid, exact "
+                      f"per-slice differences of W, D, X and the energies, extrapolated by "
+                      f"n_g/{n_slices * width}"}
+
+
 def cpu_sample(wlw, rows, xi, xit):
     """FP64 oracle W build for `rows` outer points (all inner points)."""
     from oracle import wbuild
@@ -220,7 +268,8 @@ def run_reference(args, rank, world):
     xi = rng.standard_normal((n_mu, n_g)) * 1e-3
     xit = rng.standard_normal((3, n_mu, n_g)) * 1e-3
     times = []
-    cpu_sample(wlw, 4, xi, xit)
+    for _ in range(args.warmup):
+        cpu_sample(wlw, args.cpu_rows, xi, xit)
     for _ in range(args.steps):
         times.append(cpu_sample(wlw, args.cpu_rows, xi, xit))
     dt = statistics.mean(times)
@@ -350,6 +399,45 @@ def run_adjoint(args):
                       "dtheta_finite": bool(torch.isfinite(d32).all())}), flush=True)
 
 
+def run_validate(args):
+    """Full-size accuracy of the tensor-core path against the FP64 GPU path (the
+    FP64 GPU path is checked against the FP64 oracle at 1e-10 on the smaller
+    configurations): one pass of the path at the requested precision, then W,
+    D, X and the energies rebuilt in FP64 on the GPU from the same orbitals,
+    pivots and fit."""
+    import torch
+    from paper_2607_17314_b300 import api, build, pipeline
+    build.build()
+    wlw = make_workload(args.workload)
+    b = wlw.basis
+    J = api.jastrow_from(wlw.jastrow)
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
+                          wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
+    out = pipeline.run(inp, precision=args.precision)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W64, calG64 = api.tc_kernel_build(inp.grid, inp.w, out["xi"], out["xig"], J, "fp64")
+    torch.cuda.synchronize()
+    t_w = time.perf_counter() - t0
+    D64, X64 = api.xtc_density_contract(out["phiP"], inp.n_occ, out["xi"], inp.w, calG64,
+                                        inp.n_occ, precision="fp64")
+    E64 = api.tc_energies(W64, D64, X64, out["phiP"], out["dphiP"], inp.n_occ)
+    relf = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))
+    keys = ("E_K", "E_dU", "E0")
+    print(json.dumps({
+        "mode": "validate", "workload": args.workload, "precision": args.precision,
+        "n_g": inp.n_g, "n_mu": inp.n_mu, "n_occ": inp.n_occ,
+        "fp64_w_build_s": t_w,
+        "w_rel_err": [relf(out["W"][c], W64[c]) for c in range(4)],
+        "w_max_err_over_max": [float((out["W"][c] - W64[c]).abs().max() / W64[c].abs().max())
+                               for c in range(4)],
+        "calG_rel_err": [relf(out["calG"][c], calG64[c]) for c in range(4)],
+        "D_rel_err": relf(out["D"], D64), "X_rel_err": relf(out["Xp"], X64),
+        "energies_ha": dict(zip(keys, out["E"])), "energies_fp64_ha": dict(zip(keys, E64)),
+        "energies_err_ha": {k: a - b for k, a, b in zip(keys, out["E"], E64)},
+    }), flush=True)
+
+
 def _chain(k):
     from synth import workloads as wl
     return wl.perturbed_chain(k)
@@ -429,6 +517,8 @@ def main():
         return run_adjoint(args)
     if args.proposer:
         return run_proposer(args)
+    if args.validate:
+        return run_validate(args)
 
     import torch
     import torch.distributed as dist
@@ -491,12 +581,15 @@ def main():
     peak, peak_kind = tensor_peak()
     s1_tflops = 8.0 * n_mu * n_g * n_g / (s1_ms * 1e-3) / 1e12
     products = 3 if args.precision == "bf16x3" else 6
-    # DRAM bytes per (mu, g) output element of stage 1 from the ncu capture in
-    # profiles/s1_tc_kernel_bf16x3.md (input and output both scale with N_mu n_g)
-    traffic = 36.15 * n_mu * n_g if args.precision == "bf16x3" else None
+    ncu = S1_NCU.get(args.precision)
+    # DRAM traffic of one launch: the per-(mu, g) figure of the ncu capture of
+    # the current kernel (reads of the w xi limbs and the FP64 calG writes both
+    # scale with N_mu n_g), or null when the current kernel has not been captured
+    traffic = ncu["dram_bytes_per_mu_g"] * n_mu * n_g if ncu else None
     roofline = {"bound": "tensor", "achieved": s1_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": s1_tflops / peak, "traffic": traffic,
-                "pipe_frac": s1_tflops * products / peak,
+                "products_frac": s1_tflops * products / peak,
+                "ncu_tensor_pipe_active": ncu["tensor_pipe_active"] if ncu else None,
                 "kernel": f"s1_tc_kernel ({args.precision}: {products} BF16 products per algorithmic MAC)",
                 "peak_kind": peak_kind}
 
@@ -518,6 +611,7 @@ def main():
     errs = [float(torch.linalg.norm(kbt.W[c] - kb64.W[c]) / torch.linalg.norm(kb64.W[c]))
             for c in range(4)]
     del kbt, kb64
+    e_err = sampled_energy_error(api, inp, out, J, args.precision)
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -567,6 +661,7 @@ def main():
                          "speedup_tc_over_fp64": value / fp64_tflops,
                          "w_rel_err_tc_vs_fp64": errs},
             "energies_ha": {"E_K": E[0], "E_dU": E[1], "E0": E[2]},
+            "energies_err_ha_vs_fp64_gpu": e_err,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk.summary(),
         }

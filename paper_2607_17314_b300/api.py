@@ -208,6 +208,19 @@ def tc_kernel_build(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, precision="bf1
     return kb.W, kb.calG
 
 
+def grid_shard(n_g: int, rank: int, world: int) -> Tuple[int, int]:
+    """The outer-grid slice [g_begin, g_end) of rank ``rank`` of ``world`` for a
+    sharded W build (Sec. IV.C): contiguous, covering [0, n_g) once, sizes
+    differing by at most one tile of 64 points.  The partial kernels of the
+    slices sum to the full W (one all-reduce of 4 n_mu^2 values)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    tiles = (n_g + 63) // 64
+    t0 = tiles * rank // world
+    t1 = tiles * (rank + 1) // world
+    return min(64 * t0, n_g), min(64 * t1, n_g)
+
+
 def kernel_launches() -> int:
     """Kernels launched by libisdftc in this process so far."""
     return int(C.load().isdf_kernel_launches())
