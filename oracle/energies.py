@@ -9,6 +9,7 @@ TEST INFRASTRUCTURE (FP64 numpy).
   P12 T^{pq}_{rs} = T^{pq}_{rs} + T^{qp}_{sr}                               (Eq. K-recombine-final)
   DeltaU = -P12 [ sum C^p_r(mu) D_{mu nu} C^q_s(nu) - sum_mu C^p_r(mu) X_{qs mu} ]
   Delta h_pq = -1/2 sum_o (2 DeltaU^{po}_{qo} - DeltaU^{po}_{oq})          (Eq. xtc-deltah)
+  f^xTC_pq = Delta h_pq + sum_i (2 W^{pi}_{qi} - W^{pi}_{iq}),  W = -K + DeltaU  (Eq. xtc-fock)
   E0 = -2/3 sum_i Delta h_ii   (nuclear repulsion omitted)                  (Eq. xtc-const)
 Closed-shell test functionals (reading of "TC energy"):
   E_K = sum_{ij occ} (2 K^{ij}_{ij} - K^{ij}_{ji}),  E_dU likewise with DeltaU.
@@ -75,3 +76,23 @@ def energies(W, D, X, phiP, dphiP, n_occ):
     dh = delta_h_occ(dU)
     return {"E_K": closed_shell(K), "E_dU": closed_shell(dU),
             "E0": -2.0 / 3.0 * float(np.sum(dh))}
+
+
+def delta_h(dU, occ):
+    """Delta h_pq of Eq. xtc-deltah for every p, q: dU is the full four-index
+    DeltaU [n][n][n][n] (index order p, q, r, s of DeltaU^{pq}_{rs}) and occ the
+    occupied orbital indices."""
+    return -0.5 * sum(2.0 * dU[:, o, :, o] - dU[:, o, o, :] for o in occ)
+
+
+def fock_xtc(K, dU, occ):
+    """f^xTC_pq of Eq. xtc-fock for every p, q: Delta h plus the closed-shell
+    Coulomb (weight 2) and exchange contractions of W = -K + DeltaU over the
+    occupied orbitals.  Not symmetrised (K and DeltaU are non-Hermitian)."""
+    Wt = -K + dU
+    return delta_h(dU, occ) + sum(2.0 * Wt[:, i, :, i] - Wt[:, i, i, :] for i in occ)
+
+
+def e0_xtc(dh, occ):
+    """E0 of Eq. xtc-const without the nuclear repulsion: -2/3 sum_i Delta h_ii."""
+    return -2.0 / 3.0 * float(sum(dh[i, i] for i in occ))

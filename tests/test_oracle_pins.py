@@ -761,3 +761,65 @@ def test_features_carry_the_pivot_diagonals(h6):
     assert np.all(f[:, 5] <= f[:, 6])
     d = np.linalg.norm(w.grid_xyz[:, None, :] - w.xyz[None, :, :], axis=2)
     assert np.allclose(f[:, 5], d.min(axis=1) / 5.0, rtol=0, atol=1e-15)
+
+
+def test_delta_h_all_orbitals_equals_normal_ordered_three_body_term():
+    """Eq. xtc-deltah over every (p, q), not only the occupied diagonal, from
+    the full four-index DeltaU at full scalar rank, against the one-body part
+    of the normal-ordered three-body operator (4 orbitals, 2 occupied)."""
+    w = wl.tiny_chain(n_atom=4, n_rad=12, n_ang=20, shells=(0,), n_mu=10, seed=11)
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    n, n_occ = w.n_orb, w.n_occ
+    res = pivots.select(phi, dphi, w.grid_w, n * (n + 1) // 2, mode="scalar")
+    P = res.piv_s
+    xi, _, _ = fit.fit(phi, dphi, P, channels=(0,))
+    phiP = xtc.pivot_factors(phi, P)
+    occ = np.arange(n_occ)
+    bh = wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(9), 0.2)
+    for jas in (w.jastrow, bh):
+        dh_ref, E0_ref = _normal_ordered_scalars(_three_body_L(w.grid_xyz, w.grid_w, phi, jas),
+                                                 n_occ)
+        calG = wbuild.stage1(w.grid_xyz, w.grid_w, xi, jas)
+        _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, n_occ))
+        X = xtc.x_projector(w.grid_w, xi, calG, phiP, n_occ)
+        dU = energies.du_tensor(D, X, phiP, np.arange(n))
+        dh = energies.delta_h(dU, occ)
+        assert np.max(np.abs(dh - dh_ref)) < 1e-7 * np.max(np.abs(dh_ref))
+        assert abs(energies.e0_xtc(dh, occ) - E0_ref) < 1e-7 * abs(E0_ref)
+
+
+def test_fock_closed_form_for_separable_two_body():
+    """Eq. xtc-fock on a two-body correction of product form
+    W^{pq}_{rs} = u_p u_r v_q v_s (K = -W, DeltaU = 0): the Coulomb sum is
+    sum_i W^{pi}_{qi} = u_p u_q sum_i v_i^2 and the exchange sum is
+    sum_i W^{pi}_{iq} = u_p v_q sum_i u_i v_i, so
+    f_pq = 2 u_p u_q S_vv - u_p v_q S_uv (worked by hand; a Coulomb or
+    exchange index in the wrong slot gives another matrix)."""
+    rng = np.random.default_rng(12)
+    n, occ = 5, np.arange(2)
+    u, v = rng.standard_normal(n), rng.standard_normal(n)
+    Wt = np.einsum("p,r,q,s->pqrs", u, u, v, v)
+    f = energies.fock_xtc(-Wt, np.zeros_like(Wt), occ)
+    Svv, Suv = float(np.sum(v[occ] ** 2)), float(np.sum(u[occ] * v[occ]))
+    assert np.max(np.abs(f - (2.0 * np.outer(u, u) * Svv - np.outer(u, v) * Suv))) < 1e-14
+
+
+def test_fock_trace_matches_closed_shell_energies(h6):
+    """sum_i f^xTC_ii = sum_i Delta h_ii - E_K + E_dU = E_dU / 2 - E_K on the
+    occupied block (Eq. xtc-fock traced against the closed-shell functionals)."""
+    w, phi, dphi = h6
+    res = pivots.select(phi, dphi, w.grid_w, 30)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    W, calG = wbuild.build(w.grid_xyz, w.grid_w, xi, xit, w.jastrow)
+    phiP = xtc.pivot_factors(phi, res.pivots)
+    dphiP = [dphi[c][:, res.pivots].T for c in range(3)]
+    _, _, D = xtc.d_kernels(w.grid_w, xi, calG, xtc.g_nu(phiP, w.n_occ))
+    X = xtc.x_projector(w.grid_w, xi, calG, phiP, w.n_occ)
+    idx = np.arange(6)
+    occ = np.arange(w.n_occ)
+    K = energies.k_tensor(W, phiP, dphiP, idx)
+    dU = energies.du_tensor(D, X, phiP, idx)
+    f = energies.fock_xtc(K, dU, occ)
+    E = energies.energies(W, D, X, phiP, dphiP, w.n_occ)
+    tr = float(np.trace(f[np.ix_(occ, occ)]))
+    assert abs(tr - (E["E_dU"] / 2.0 - E["E_K"])) < 1e-12 * (abs(E["E_K"]) + abs(E["E_dU"]))
