@@ -358,6 +358,53 @@ int tc_energies_noalloc(const double* W, const double* D, const double* X_packed
                         const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
                         int n_occ, double* out, isdf_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Assembly of the xTC Hamiltonian's corrections over every orbital index
+ * (final assembly of Sec. III.B and the assembly subsection after it).
+ *
+ * Two-body panels (Eqs. K-recombine-final and deltaU-four): with the
+ * composite indices (p,r) = p n_orb + r and (q,s) = q n_orb + s,
+ *   K_panel [pr_end - pr_begin][n_orb^2]:  K_panel[(p,r) - pr_begin][(q,s)] = K^{pq}_{rs}
+ *   dU_panel (same shape):                 DeltaU^{pq}_{rs}
+ * for the rows pr_begin <= (p,r) < pr_end (either output may be NULL), from
+ *   K  = 1/2 P12 [K1 - K1swap + K3],  K1^{pq}_{rs} = sum_c sum_{mu nu} phi_p(mu) d_c phi_r(mu)
+ *        u1^c_{mu nu} phi_q(nu) phi_s(nu),  K3 with u3 and C^p_r(mu) = phi_p(mu) phi_r(mu),
+ *   DeltaU = -P12 [ sum C^p_r(mu) D_{mu nu} C^q_s(nu) - sum_mu C^p_r(mu) X_{qs mu} ],
+ *   P12 T^{pq}_{rs} = T^{pq}_{rs} + T^{qp}_{sr}.
+ * A panel is two GEMMs of inner dimension 4 n_mu and 2 n_mu over all n_orb^2
+ * columns, streamed panel by panel as in the paper's cost analysis (Sec. IV.C).
+ * W [4][n_mu][n_mu]; D [n_mu][n_mu]; X_packed [n_orb (n_orb + 1) / 2][n_mu] (the
+ * full X, n_orb_x = n_orb); phi_piv [n_mu][n_orb]; dphi_piv [3][n_mu][n_orb].
+ * precision: ISDF_PREC_FP64 (CUDA-core FP64 GEMMs) or ISDF_PREC_BF16X3 /
+ * ISDF_PREC_BF16X6 (the two panel GEMMs as split-BF16 tcgen05 GEMMs with FP32
+ * accumulation folded every 256 terms; the left factors in FP64).  FP64 is
+ * asynchronous; the tensor-core precisions synchronise `stream` and return
+ * ISDF_E_TIMEOUT if a bounded wait expired.  0 <= pr_begin < pr_end <= n_orb^2. */
+size_t tc_two_body_panel_workspace(int n_mu, int n_orb, int64_t rows, int precision);
+int tc_two_body_panel(const double* W, const double* D, const double* X_packed,
+                      const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
+                      int64_t pr_begin, int64_t pr_end, int precision, double* K_panel,
+                      double* dU_panel, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* One-body increment, xTC Fock correction and constant for every orbital pair
+ * (Eqs. xtc-deltah, xtc-fock, xtc-const), closed shell with the first n_occ
+ * orbitals occupied:
+ *   delta_h[p][q] = -1/2 sum_{o<n_occ} (2 DeltaU^{po}_{qo} - DeltaU^{po}_{oq})
+ *   fock[p][q]    = delta_h[p][q] + sum_{i<n_occ} (2 W^{pi}_{qi} - W^{pi}_{iq}),
+ *                   W = -K + DeltaU (not symmetrised)
+ *   *e0           = -2/3 sum_{i<n_occ} delta_h[i][i]   (nuclear repulsion not included)
+ * computed without forming four-index tensors (contractions of the occupied
+ * projector on the pivots with W, D and X: O(n_mu^2 n_orb) work, FP64).
+ * Inputs as tc_two_body_panel (X_packed is the full X); delta_h, fock: device
+ * [n_orb][n_orb] FP64; e0: host scalar or NULL.  Asynchronous when e0 is
+ * NULL; otherwise synchronises `stream` and returns ISDF_E_NONFINITE for a
+ * NaN or Inf E0. */
+size_t tc_xtc_one_body_workspace(int n_mu, int n_orb);
+int tc_xtc_one_body(const double* W, const double* D, const double* X_packed,
+                    const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb, int n_occ,
+                    double* delta_h, double* fock, double* e0, void* ws, size_t ws_bytes,
+                    isdf_stream_t stream);
+
 /* Gather phi_p(r_mu) and d_c phi_p(r_mu): phi_piv [n_mu][n_orb],
  * dphi_piv [3][n_mu][n_orb] (dphi_piv may be NULL); pivots: device [n_mu],
  * indices in [0, n_g).  Asynchronous, so an index outside [0, n_g) cannot be

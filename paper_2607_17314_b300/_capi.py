@@ -90,6 +90,11 @@ SIGNATURES = {
     "tc_energies_workspace": (SZ, [INT, INT]),
     "tc_energies": (INT, [P, P, P, P, P, INT, INT, INT, P, P, SZ, P]),
     "tc_energies_noalloc": (INT, [P, P, P, P, P, INT, INT, INT, P, P]),
+    "tc_two_body_panel_workspace": (SZ, [INT, INT, I64, INT]),
+    "tc_two_body_panel": (INT, [P, P, P, P, P, INT, INT, I64, I64, INT, P, P, P, SZ, P]),
+    "tc_xtc_one_body_workspace": (SZ, [INT, INT]),
+    "tc_xtc_one_body": (INT, [P, P, P, P, P, INT, INT, INT, P, P,
+                              ctypes.POINTER(ctypes.c_double), P, SZ, P]),
 }
 
 _lib = None

@@ -254,6 +254,40 @@ def tc_energies(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
     return tuple(out)
 
 
+def tc_two_body_panel(W, D, Xp, phi_piv, dphi_piv, pr_begin: int, pr_end: int,
+                      precision="fp64", want_k: bool = True, want_du: bool = True):
+    """Rows [pr_begin, pr_end) of the four-index K and DeltaU in composite form
+    (row (p,r) = p n_orb + r, column (q,s)); Xp is the full packed X."""
+    lib = C.load()
+    n_mu, n_orb = phi_piv.shape
+    rows = pr_end - pr_begin
+    prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dev = phi_piv.device
+    K = torch.empty((rows, n_orb * n_orb), dtype=f64, device=dev) if want_k else None
+    U = torch.empty((rows, n_orb * n_orb), dtype=f64, device=dev) if want_du else None
+    ws = _ws(lib.tc_two_body_panel_workspace(n_mu, n_orb, rows, prec), dev)
+    C.check("tc_two_body_panel", lib.tc_two_body_panel(
+        _ptr(W), _ptr(D), _ptr(Xp), _ptr(phi_piv), _ptr(dphi_piv), n_mu, n_orb, pr_begin, pr_end,
+        prec, _ptr(K), _ptr(U), _ptr(ws), ws.numel(), _stream()))
+    return K, U
+
+
+def tc_xtc_one_body(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
+    """Delta h [n_orb][n_orb], f^xTC [n_orb][n_orb] and E0 (Eqs. xtc-deltah,
+    xtc-fock, xtc-const); Xp is the full packed X."""
+    lib = C.load()
+    n_mu, n_orb = phi_piv.shape
+    dev = phi_piv.device
+    dh = torch.empty((n_orb, n_orb), dtype=f64, device=dev)
+    f = torch.empty((n_orb, n_orb), dtype=f64, device=dev)
+    e0 = ctypes.c_double(0.0)
+    ws = _ws(lib.tc_xtc_one_body_workspace(n_mu, n_orb), dev)
+    C.check("tc_xtc_one_body", lib.tc_xtc_one_body(
+        _ptr(W), _ptr(D), _ptr(Xp), _ptr(phi_piv), _ptr(dphi_piv), n_mu, n_orb, n_occ, _ptr(dh),
+        _ptr(f), ctypes.byref(e0), _ptr(ws), ws.numel(), _stream()))
+    return dh, f, e0.value
+
+
 def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precision="fp32"):
     """dL/dtheta for L = sum_c <Wbar^c, W^c>, theta = (d, b, c_0 .. c_{K-1})."""
     lib = C.load()

@@ -68,6 +68,12 @@ int fit_error(const double*, const double*, int64_t, int, const int32_t*, int, d
               size_t, cudaStream_t);
 int energies_noalloc(const double*, const double*, const double*, const double*, const double*,
                      int, int, int, double*, cudaStream_t);
+size_t xtc_one_body_ws(int, int);
+int xtc_one_body(const double*, const double*, const double*, const double*, const double*, int, int,
+                 int, double*, double*, double*, void*, size_t, cudaStream_t);
+size_t xtc_panel_ws(int, int, int64_t, int);
+int xtc_panel(const double*, const double*, const double*, const double*, const double*, int, int,
+              int64_t, int64_t, int, double*, double*, void*, size_t, cudaStream_t);
 
 static int check_jastrow(const isdf_jastrow* J) {
   ISDF_ARG(J, "null Jastrow");
@@ -269,6 +275,28 @@ int tc_energies_noalloc(const double* W, const double* D, const double* X_packed
                         int n_occ, double* out, isdf_stream_t stream) {
   return energies_noalloc(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, n_occ, out,
                           (cudaStream_t)stream);
+}
+
+size_t tc_xtc_one_body_workspace(int n_mu, int n_orb) { return xtc_one_body_ws(n_mu, n_orb); }
+
+int tc_xtc_one_body(const double* W, const double* D, const double* X_packed,
+                    const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb, int n_occ,
+                    double* delta_h, double* fock, double* e0, void* ws, size_t ws_bytes,
+                    isdf_stream_t stream) {
+  return xtc_one_body(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, n_occ, delta_h, fock, e0,
+                      ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t tc_two_body_panel_workspace(int n_mu, int n_orb, int64_t rows, int precision) {
+  return xtc_panel_ws(n_mu, n_orb, rows, precision);
+}
+
+int tc_two_body_panel(const double* W, const double* D, const double* X_packed,
+                      const double* phi_piv, const double* dphi_piv, int n_mu, int n_orb,
+                      int64_t pr_begin, int64_t pr_end, int precision, double* K_panel,
+                      double* dU_panel, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  return xtc_panel(W, D, X_packed, phi_piv, dphi_piv, n_mu, n_orb, pr_begin, pr_end, precision,
+                   K_panel, dU_panel, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -359,3 +359,59 @@ def test_zero_jastrow_fp64(P, h6):
     J.cusp = 0
     W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), J, "fp64")
     assert float(W.abs().max()) == 0.0 and float(calG.abs().max()) == 0.0
+
+
+@pytest.fixture(scope="module")
+def h6_four_index(h6):
+    """The oracle's K and DeltaU over every orbital index of the H6 case."""
+    w, o = h6
+    idx = np.arange(w.n_orb)
+    K = energies.k_tensor(o["W"], o["phiP"], list(o["dphiP"]), idx)
+    dU = energies.du_tensor(o["D"], o["X"], o["phiP"], idx)
+    return K, dU
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_two_body_panels(P, h6, h6_four_index, prec):
+    """K and DeltaU over all n_orb^2 x n_orb^2 composite entries, built panel by
+    panel (three panels, the last ragged), against the oracle's four-index
+    tensors (Eqs. K-recombine-final, deltaU-four)."""
+    from paper_2607_17314_b300 import api
+    w, o = h6
+    K, dU = h6_four_index
+    n = w.n_orb
+    Kref = K.transpose(0, 2, 1, 3).reshape(n * n, n * n)      # [(p,r)][(q,s)]
+    Uref = dU.transpose(0, 2, 1, 3).reshape(n * n, n * n)
+    args = (cu(o["W"]), cu(o["D"]), cu(xtc.pack_upper(o["X"])), cu(o["phiP"]), cu(o["dphiP"]))
+    cuts = [0, 250, 500, n * n]
+    Kg, Ug = [], []
+    for a, b in zip(cuts, cuts[1:]):
+        kp, up = api.tc_two_body_panel(*args, a, b, precision=prec)
+        Kg.append(host(kp))
+        Ug.append(host(up))
+    Kg, Ug = np.concatenate(Kg), np.concatenate(Ug)
+    ek = float(np.max(np.abs(Kg - Kref)) / np.max(np.abs(Kref)))
+    eu = float(np.max(np.abs(Ug - Uref)) / np.max(np.abs(Uref)))
+    print(prec, "K max err / max %.2e" % ek, "DeltaU %.2e" % eu,
+          "rel Frobenius", rel(Kg, Kref), rel(Ug, Uref))
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert ek < tol and eu < tol
+
+
+def test_xtc_one_body(P, h6, h6_four_index):
+    """Delta h, f^xTC and E0 over every orbital pair (Eqs. xtc-deltah, xtc-fock,
+    xtc-const) against the oracle's contractions of the four-index tensors."""
+    from paper_2607_17314_b300 import api
+    w, o = h6
+    K, dU = h6_four_index
+    occ = np.arange(w.n_occ)
+    dh_ref = energies.delta_h(dU, occ)
+    f_ref = energies.fock_xtc(K, dU, occ)
+    e0_ref = energies.e0_xtc(dh_ref, occ)
+    dh, f, e0 = api.tc_xtc_one_body(cu(o["W"]), cu(o["D"]), cu(xtc.pack_upper(o["X"])),
+                                    cu(o["phiP"]), cu(o["dphiP"]), w.n_occ)
+    assert rel(host(dh), dh_ref) < 1e-10
+    assert rel(host(f), f_ref) < 1e-10
+    assert abs(e0 - e0_ref) <= 1e-10 * abs(e0_ref)
+    # and E0 agrees with the occupied-block energies call
+    assert abs(e0 - o["E"]["E0"]) <= 1e-10 * abs(e0_ref)
