@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--n-train", type=int, default=24)
     ap.add_argument("--n-test", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--kappa", type=float, default=3.0)
+    ap.add_argument("--kappa", type=str, default="3,6",
+                    help="candidate budgets (multiples of N_mu), comma separated")
     ap.add_argument("--w-nrad", type=int, default=16)
     ap.add_argument("--w-nmu", type=int, default=1024)
     ap.add_argument("--w-nang", type=int, default=50)
@@ -484,24 +485,38 @@ def run_proposer(args):
     e1 = ev()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    rows = []
-    for smp, pm in zip(test, plain_ms[args.n_train:]):
-        e0 = ev()
-        piv = prop.propose(smp, args.kappa)
-        e1 = ev()
-        torch.cuda.synchronize()
-        ep = PR.fit_error(smp.phi, smp.w, piv)
-        el = PR.fit_error(smp.phi, smp.w, smp.plain)
-        overlap = len(set(piv.cpu().tolist()) & set(smp.plain.cpu().tolist())) / smp.n_mu
-        rows.append({"plain_ms": pm, "proposal_ms": e0.elapsed_time(e1), "eps_plain": el,
-                     "eps_proposal": ep, "ratio": ep / el, "overlap": overlap})
+    kappas = [float(k) for k in str(args.kappa).split(",")]
+    summary = {}
+    for kappa in kappas:
+        rows = []
+        for smp, pm in zip(test, plain_ms[args.n_train:]):
+            e0 = ev()
+            piv = prop.propose(smp, kappa)
+            e1 = ev()
+            torch.cuda.synchronize()
+            ep = PR.fit_error(smp.phi, smp.w, piv)
+            el = PR.fit_error(smp.phi, smp.w, smp.plain)
+            c_net = prop.candidates(smp, kappa)
+            c_diag = PR.diagonal_candidates(smp, kappa)
+            ed = PR.fit_error(smp.phi, smp.w,
+                              PR.points_restricted(smp.phi, smp.dphi, smp.w, c_diag, smp.n_mu))
+            rows.append({"plain_ms": pm, "proposal_ms": e0.elapsed_time(e1), "eps_plain": el,
+                         "eps_proposal": ep, "eps_diagonal_budget": ed, "ratio": ep / el,
+                         "recall_network": PR.recall(c_net, smp.plain),
+                         "recall_diagonal": PR.recall(c_diag, smp.plain)})
+        summary[str(kappa)] = {
+            "median_selection_speedup": float(np.median([r["plain_ms"] / r["proposal_ms"]
+                                                         for r in rows])),
+            "median_fit_error_ratio_vs_plain": float(np.median([r["ratio"] for r in rows])),
+            "median_fit_error_ratio_vs_diagonal_budget": float(np.median(
+                [r["eps_proposal"] / r["eps_diagonal_budget"] for r in rows])),
+            "mean_recall_network": float(np.mean([r["recall_network"] for r in rows])),
+            "mean_recall_diagonal": float(np.mean([r["recall_diagonal"] for r in rows])),
+            "per_chain": rows}
     line = {"mode": "proposer", "workload": "perturbed H30 chains", "n_g": int(test[0].feat.shape[0]),
             "n_mu": test[0].n_mu, "n_train": args.n_train, "n_test": args.n_test,
-            "epochs": args.epochs, "kappa": args.kappa, "train_ms": train_ms,
-            "loss_first": losses[0], "loss_last": losses[-1],
-            "median_selection_speedup": float(np.median([r["plain_ms"] / r["proposal_ms"] for r in rows])),
-            "median_fit_error_ratio": float(np.median([r["ratio"] for r in rows])),
-            "per_chain": rows}
+            "epochs": args.epochs, "train_ms": train_ms,
+            "loss_first": losses[0], "loss_last": losses[-1], "by_kappa": summary}
     print(json.dumps(line), flush=True)
 
 

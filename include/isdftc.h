@@ -105,7 +105,10 @@ typedef struct {
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (expired bounded waits, CUDA errors) */
   int32_t debug_flags;/* bit 0: the stage-1 producer skips its first arrival, so
-                         the consumer's bounded wait expires (fault-path test) */
+                         the consumer's bounded wait expires (fault-path test);
+                         bit 1: with ISDF_PREC_BF16X3, the radial correlator's
+                         stage 1 runs on single CTAs (128-row tiles) instead of
+                         CTA pairs (256-row tiles; always used for BF16X6) */
   float* stage_ms;    /* host [2] or NULL: when set (with sync_check), the device
                          times of stage 1 and stage 2, measured with CUDA events
                          on `stream` around the two kernels */
@@ -230,6 +233,17 @@ int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
                       const double* xi_grad, int64_t n_g, int n_mu, const isdf_jastrow* jas,
                       const double* Wbar, int precision, double* dtheta, void* ws,
                       size_t ws_bytes, isdf_stream_t stream);
+
+/* tc_kernel_adjoint restricted to the outer points g in [g_begin, g_end) (all
+ * inner points g'): the derivative of L over W built on that outer slice
+ * (tc_kernel_build with the same slice).  The sums are additive over slices.
+ * Same workspace as tc_kernel_adjoint; ISDF_E_ARG for an empty or out-of-range
+ * slice. */
+int tc_kernel_adjoint_range(const double* grid_xyz, const double* w, const double* xi,
+                            const double* xi_grad, int64_t n_g, int n_mu, int64_t g_begin,
+                            int64_t g_end, const isdf_jastrow* jas, const double* Wbar,
+                            int precision, double* dtheta, void* ws, size_t ws_bytes,
+                            isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Learned interpolation-point proposer (not in the paper).  A network
@@ -377,7 +391,8 @@ int tc_energies_noalloc(const double* W, const double* D, const double* X_packed
  * full X, n_orb_x = n_orb); phi_piv [n_mu][n_orb]; dphi_piv [3][n_mu][n_orb].
  * precision: ISDF_PREC_FP64 (CUDA-core FP64 GEMMs) or ISDF_PREC_BF16X3 /
  * ISDF_PREC_BF16X6 (the two panel GEMMs as split-BF16 tcgen05 GEMMs with FP32
- * accumulation folded every 256 terms; the left factors in FP64).  FP64 is
+ * accumulation folded every 256 terms, three limbs for either precision since
+ * these products cancel strongly; the left factors in FP64).  FP64 is
  * asynchronous; the tensor-core precisions synchronise `stream` and return
  * ISDF_E_TIMEOUT if a bounded wait expired.  0 <= pr_begin < pr_end <= n_orb^2. */
 size_t tc_two_body_panel_workspace(int n_mu, int n_orb, int64_t rows, int precision);

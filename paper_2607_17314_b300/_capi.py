@@ -74,6 +74,8 @@ SIGNATURES = {
     "tc_kernel_adjoint_workspace": (SZ, [I64, INT, INT, INT]),
     "tc_kernel_adjoint": (INT, [P, P, P, P, I64, INT, ctypes.POINTER(IsdfJastrow), P, INT, P, P,
                                 SZ, P]),
+    "tc_kernel_adjoint_range": (INT, [P, P, P, P, I64, INT, I64, I64, ctypes.POINTER(IsdfJastrow),
+                                      P, INT, P, P, SZ, P]),
     "isdf_mlp_n_params": (INT, []),
     "isdf_mlp_features": (INT, [P, P, P, P, I64, INT, P, INT, P, P]),
     "isdf_mlp_forward": (INT, [P, P, I64, P, P]),

@@ -288,8 +288,10 @@ def tc_xtc_one_body(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
     return dh, f, e0.value
 
 
-def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precision="fp32"):
-    """dL/dtheta for L = sum_c <Wbar^c, W^c>, theta = (d, b, c_0 .. c_{K-1})."""
+def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precision="fp32",
+                      g_begin: Optional[int] = None, g_end: Optional[int] = None):
+    """dL/dtheta for L = sum_c <Wbar^c, W^c>, theta = (d, b, c_0 .. c_{K-1});
+    with g_begin/g_end, W over that outer-grid slice only."""
     lib = C.load()
     for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad"), (Wbar, "Wbar")):
         _req(t, f64, n)
@@ -297,9 +299,18 @@ def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precis
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dtheta = torch.empty(2 + jastrow.n_terms, dtype=f64, device=xi.device)
     ws = _ws(lib.tc_kernel_adjoint_workspace(n_g, n_mu, jastrow.n_nuc, prec), xi.device)
-    C.check("tc_kernel_adjoint", lib.tc_kernel_adjoint(
-        _ptr(grid_xyz), _ptr(w), _ptr(xi), _ptr(xig), n_g, n_mu, ctypes.byref(jastrow), _ptr(Wbar),
-        prec, _ptr(dtheta), _ptr(ws), ws.numel(), _stream()))
+    if g_begin is None and g_end is None:
+        st = lib.tc_kernel_adjoint(
+            _ptr(grid_xyz), _ptr(w), _ptr(xi), _ptr(xig), n_g, n_mu, ctypes.byref(jastrow),
+            _ptr(Wbar), prec, _ptr(dtheta), _ptr(ws), ws.numel(), _stream())
+    else:
+        g0 = 0 if g_begin is None else int(g_begin)
+        g1 = n_g if g_end is None else int(g_end)
+        st = lib.tc_kernel_adjoint_range(
+            _ptr(grid_xyz), _ptr(w), _ptr(xi), _ptr(xig), n_g, n_mu, g0, g1,
+            ctypes.byref(jastrow), _ptr(Wbar), prec, _ptr(dtheta), _ptr(ws), ws.numel(),
+            _stream())
+    C.check("tc_kernel_adjoint", st)
     return dtheta
 
 

@@ -33,6 +33,7 @@ struct AdjArgs {
   const T* Bh;     // [4][n_mu][n_g] Bhat^c
   const double* grid;
   int64_t n_g;
+  int64_t g_begin, g_end;  // outer points of this call (the sums are additive over slices)
   int n_mu;
   const T* tab;    // [n_g][n_nuc][8]: A, gA(3), A_b, gA_b(3)
   double* sums;    // [2 + NGRP * 5]: d, b, then (group, E power) sums
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
   __shared__ T Bs[4][AMU][AT];
   __shared__ double red[8][2 + NGRP * 5];
   const int t = threadIdx.x;
-  const int64_t g0 = (int64_t)blockIdx.y * AT, h0 = (int64_t)blockIdx.x * AT;
+  const int64_t g0 = a.g_begin + (int64_t)blockIdx.y * AT, h0 = (int64_t)blockIdx.x * AT;
   // each thread: g row (t / 8), g' columns (t % 8) + 8 j, j < 4
   const int tg = t >> 3, th = t & 7;
   T M[4][4];
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
       const int c = e / (AMU * AT), r = (e / AT) % AMU, col = e % AT;
       const int mu = mu0 + r;
       const int64_t ga = g0 + col, hb = h0 + col;
-      As[c][r][col] = (mu < a.n_mu && ga < a.n_g) ? a.Ah[c * plane + (int64_t)mu * a.n_g + ga] : (T)0;
+      As[c][r][col] = (mu < a.n_mu && ga < a.g_end) ? a.Ah[c * plane + (int64_t)mu * a.n_g + ga] : (T)0;
       Bs[c][r][col] = (mu < a.n_mu && hb < a.n_g) ? a.Bh[c * plane + (int64_t)mu * a.n_g + hb] : (T)0;
     }
     __syncthreads();
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
 #pragma unroll
   for (int q = 0; q < 2 + NGRP * 5; ++q) acc[q] = (T)0;
   const int64_t g = g0 + tg;
-  if (g < a.n_g) {
+  if (g < a.g_end) {
     const double* rg = a.grid + 3 * g;
     for (int j = 0; j < 4; ++j) {
       const int64_t h = h0 + th + 8 * j;
@@ -281,8 +282,8 @@ inline unsigned nb(int64_t n) { return (unsigned)ceil_div(n, 256); }
 
 template <class T>
 int run_adjoint(const double* grid, const double* w, const double* xi, const double* xig, int64_t n_g,
-                int n_mu, const isdf_jastrow& J, const double* Wbar, double* dtheta, void* ws,
-                size_t ws_bytes, cudaStream_t s) {
+                int64_t g_begin, int64_t g_end, int n_mu, const isdf_jastrow& J, const double* Wbar,
+                double* dtheta, void* ws, size_t ws_bytes, cudaStream_t s) {
   const int64_t plane = (int64_t)n_mu * n_g;
   Carve cv(ws, ws_bytes);
   double* Bh64 = cv.take<double>(4 * plane);
@@ -313,12 +314,13 @@ int run_adjoint(const double* grid, const double* w, const double* xi, const dou
   ISDF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (2 + NGRP * 5), s));
   AdjArgs<T> a;
   a.Ah = Ah; a.Bh = Bh; a.grid = grid; a.n_g = n_g; a.n_mu = n_mu; a.tab = tab; a.sums = sums;
+  a.g_begin = g_begin; a.g_end = g_end;
   double gc[NGRP][5] = {};
   for (int k = 0; k < J.n_terms; ++k)
     gc[grp_of(J.mno[k][0], J.mno[k][1])][J.mno[k][2]] += J.coef[0][k];
   for (int G = 0; G < NGRP; ++G)
     for (int o = 0; o < 5; ++o) a.gc[G][o] = (T)gc[G][o];
-  dim3 grd((unsigned)ceil_div(n_g, AT), (unsigned)ceil_div(n_g, AT));
+  dim3 grd((unsigned)ceil_div(n_g, AT), (unsigned)ceil_div(g_end - g_begin, AT));
   ISDF_ARG(grd.y < 65536u, "n_g too large for the adjoint grid");
   adj_pair_kernel<T><<<grd, 256, 0, s>>>(a, J);
   ISDF_LAUNCH_CHECK();
@@ -342,10 +344,11 @@ size_t adjoint_ws(int64_t n_g, int n_mu, int n_nuc, int precision) {
 }
 
 int adjoint(const double* grid, const double* w, const double* xi, const double* xig, int64_t n_g,
-            int n_mu, const isdf_jastrow& J, const double* Wbar, int precision, double* dtheta,
-            void* ws, size_t ws_bytes, cudaStream_t s) {
+            int64_t g_begin, int64_t g_end, int n_mu, const isdf_jastrow& J, const double* Wbar,
+            int precision, double* dtheta, void* ws, size_t ws_bytes, cudaStream_t s) {
   ISDF_ARG(grid && w && xi && xig && Wbar && dtheta, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_mu > 0, "empty sizes");
+  ISDF_ARG(g_begin >= 0 && g_begin < g_end && g_end <= n_g, "bad grid slice");
   if (J.n_types != 1 || J.n_terms > AMAXK) {
     set_error("the adjoint takes one nucleus type and at most %d free terms", AMAXK);
     return ISDF_E_UNSUPPORTED;
@@ -356,8 +359,10 @@ int adjoint(const double* grid, const double* w, const double* xi, const double*
       return ISDF_E_UNSUPPORTED;
     }
   if (precision == ISDF_PREC_FP64)
-    return run_adjoint<double>(grid, w, xi, xig, n_g, n_mu, J, Wbar, dtheta, ws, ws_bytes, s);
-  return run_adjoint<float>(grid, w, xi, xig, n_g, n_mu, J, Wbar, dtheta, ws, ws_bytes, s);
+    return run_adjoint<double>(grid, w, xi, xig, n_g, g_begin, g_end, n_mu, J, Wbar, dtheta, ws,
+                               ws_bytes, s);
+  return run_adjoint<float>(grid, w, xi, xig, n_g, g_begin, g_end, n_mu, J, Wbar, dtheta, ws,
+                            ws_bytes, s);
 }
 
 }  // namespace isdf

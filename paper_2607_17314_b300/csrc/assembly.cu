@@ -432,9 +432,13 @@ struct PanelLayout {
   int64_t rows_pad, kp;
 };
 
+// The panel GEMMs cancel strongly (the antisymmetric Dl^c and the P12
+// symmetrisation): two limbs leave ~3e-5 relative error in K and DeltaU, so
+// the tensor-core precisions both use three limbs (six products).
 static PanelLayout panel_layout(int n_mu, int n_orb, int precision) {
+  (void)precision;
   PanelLayout L;
-  L.limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  L.limbs = 3;
   L.rows_pad = round_up((int64_t)n_orb * n_orb, 128);
   L.kp = round_up(n_mu, 32);
   return L;

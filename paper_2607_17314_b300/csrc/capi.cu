@@ -50,8 +50,8 @@ size_t energies_ws(int, int);
 int energies(const double*, const double*, const double*, const double*, const double*, int, int,
              int, double*, void*, size_t, cudaStream_t);
 size_t adjoint_ws(int64_t, int, int, int);
-int adjoint(const double*, const double*, const double*, const double*, int64_t, int,
-            const isdf_jastrow&, const double*, int, double*, void*, size_t, cudaStream_t);
+int adjoint(const double*, const double*, const double*, const double*, int64_t, int64_t, int64_t,
+            int, const isdf_jastrow&, const double*, int, double*, void*, size_t, cudaStream_t);
 int mlp_n_params();
 int mlp_features(const double*, const double*, const double*, const double*, int64_t, int,
                  const double*, int, float*, cudaStream_t);
@@ -207,8 +207,20 @@ int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
   ISDF_TRY(check_jastrow(jas));
   ISDF_ARG(precision == ISDF_PREC_FP64 || precision == ISDF_PREC_FP32,
            "adjoint precision must be ISDF_PREC_FP64 or ISDF_PREC_FP32");
-  return adjoint(grid_xyz, w, xi, xi_grad, n_g, n_mu, *jas, Wbar, precision, dtheta, ws, ws_bytes,
-                 (cudaStream_t)stream);
+  return adjoint(grid_xyz, w, xi, xi_grad, n_g, 0, n_g, n_mu, *jas, Wbar, precision, dtheta, ws,
+                 ws_bytes, (cudaStream_t)stream);
+}
+
+int tc_kernel_adjoint_range(const double* grid_xyz, const double* w, const double* xi,
+                            const double* xi_grad, int64_t n_g, int n_mu, int64_t g_begin,
+                            int64_t g_end, const isdf_jastrow* jas, const double* Wbar,
+                            int precision, double* dtheta, void* ws, size_t ws_bytes,
+                            isdf_stream_t stream) {
+  ISDF_TRY(check_jastrow(jas));
+  ISDF_ARG(precision == ISDF_PREC_FP64 || precision == ISDF_PREC_FP32,
+           "adjoint precision must be ISDF_PREC_FP64 or ISDF_PREC_FP32");
+  return adjoint(grid_xyz, w, xi, xi_grad, n_g, g_begin, g_end, n_mu, *jas, Wbar, precision,
+                 dtheta, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int isdf_mlp_n_params(void) { return mlp_n_params(); }

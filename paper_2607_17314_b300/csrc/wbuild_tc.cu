@@ -675,6 +675,303 @@ __global__ void __launch_bounds__(S1C<LIMBS, (NG >= 0)>::THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ stage 1 on CTA pairs
+//
+// Stage 1 of the radial correlator on a pair of CTAs (a cluster of two) that
+// share one 256 (nu) x 64 (g) tile: each CTA holds 128 rows of the (w xi)
+// operand and of the accumulator, and generates the B values of 32 of the 64
+// outer points; one thread of the even CTA issues M = 256, N = 256
+// tcgen05.mma.cta_group::2 instructions that read B from both CTAs.  Each
+// generated pair therefore feeds 256 rows instead of 128, and each SM reads
+// only its own half of B from shared memory.  B rows (the MMA's N) are laid
+// out channel-major per CTA: [ch0 g0-31 | ch1 | ch2 | ch3] in the even CTA and
+// the same for g32-63 in the odd CTA, so accumulator column j holds channel
+// (j % 128) / 32 of outer point 32 (j / 128) + j % 32.
+//
+// Signals: the odd CTA's (w xi) copies complete on the even CTA's stage
+// barrier (cta_group::2 bulk tensor copy); its generator warps arrive there
+// remotely (one arrival per warp); the commits of the pair MMAs arrive on the
+// stage-free and chunk-ready barriers of both CTAs (multicast); the odd CTA's
+// epilogue warps arrive on the even CTA's chunk-free barrier.  Every wait is
+// bounded as in the single-CTA kernel.
+template <int LIMBS>
+struct S1P {
+  static constexpr int BM = 128, BN = 64, BNH = 32, BK = 32;
+  static constexpr int STAGES = LIMBS == 2 ? 6 : 4;
+  static constexpr int CSTAGES = 8;
+  static constexpr uint32_t A_LIMB = BM * BK * 2;       // 8 KB
+  static constexpr uint32_t B_LIMB = 4 * BNH * BK * 2;  // 128 rows x 64 B = 8 KB
+  static constexpr uint32_t A_BYTES = LIMBS * A_LIMB;
+  static constexpr uint32_t STAGE = LIMBS * (A_LIMB + B_LIMB);
+  static constexpr uint32_t C_BYTES = BK * 32;          // FP32 hi then lo, per ring slot
+  static constexpr uint32_t ACC_COLS = 4 * BN;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static constexpr int NGW = 8;  // generator warps 2 .. 9
+  static constexpr int NEW = 4;  // epilogue warps 10 .. 13
+  static constexpr int CW = 2 + NGW + NEW;
+  static constexpr int THREADS = 32 * (CW + 1);
+  static constexpr int PTS = BNH * BK / (32 * NGW);    // inner points per generator thread
+  static constexpr uint32_t SMEM = STAGES * STAGE + CSTAGES * C_BYTES + 1024 + 512;
+  static_assert(PTS == 4, "one 8-byte chunk per generator thread, channel and limb");
+  static_assert(STAGE % 1024 == 0 && A_LIMB % 1024 == 0 && B_LIMB % 1024 == 0, "alignment");
+  static_assert(SMEM <= 232448, "shared memory budget");
+};
+
+__device__ __forceinline__ void sts_u2(uint32_t saddr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(saddr), "r"(a), "r"(b) : "memory");
+}
+
+template <int LIMBS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS, 1)
+    s1_pair_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                   const __grid_constant__ CUtensorMap mA2, const __grid_constant__ S1Params p) {
+  using C = S1P<LIMBS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* ring = stages + C::STAGES * C::STAGE;
+  uint64_t* full = (uint64_t*)(ring + C::CSTAGES * C::C_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* cfull = empty + C::STAGES;
+  uint64_t* cempty = cfull + C::CSTAGES;
+  uint64_t* acc_full = cempty + C::CSTAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const uint32_t rank = tc::cluster_ctarank();
+  const bool lead = rank == 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      // even CTA: its expect-tx arrival + one arrival per generator warp of both CTAs
+      tc::mbar_init(&full[s], lead ? 1 + 2 * C::NGW : 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < C::CSTAGES; ++s) {
+      tc::mbar_init(&cfull[s], 1);
+      tc::mbar_init(&cempty[s], C::NGW);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, lead ? 2 * C::NEW : 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc_pair(tmem_slot, C::TMEM_COLS);
+    tc::tmem_relinquish_pair();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;  // n_mu_tiles counts 256-row pairs
+  const int64_t n_chunks = (p.n_k + p.kchunk - 1) / p.kchunk;
+  const int64_t pair0 = blockIdx.x >> 1, pstride = gridDim.x >> 1;
+  const uint32_t full_lead = tc::mapa_shared(tc::smem_u32(full), 0);      // + 8 s
+  const uint32_t acce_lead = tc::mapa_shared(tc::smem_u32(acc_empty), 0);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // (w xi) limbs of this CTA's 128 rows, completing on the even CTA's stage barrier
+      tc::tma_prefetch_desc(&mA0);
+      if (LIMBS > 1) tc::tma_prefetch_desc(&mA1);
+      if (LIMBS > 2) tc::tma_prefetch_desc(&mA2);
+      uint32_t it = 0;
+      bool skip = lead && (p.debug & 1) != 0;
+      for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+        const int mu0 = (int)(tile / p.n_g_tiles) * 2 * C::BM + (int)rank * C::BM;
+        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+          const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+          if (skip) {  // fault-path test: this stage's operand never arrives
+            skip = false;
+            continue;
+          }
+          uint8_t* st = stages + s * C::STAGE;
+          if (lead) {
+            tc::mbar_arrive_expect_tx(&full[s], 2 * C::A_BYTES);
+            tc::tma_load_2d(st, &mA0, &full[s], (int32_t)k0, mu0);
+            if (LIMBS > 1) tc::tma_load_2d(st + C::A_LIMB, &mA1, &full[s], (int32_t)k0, mu0);
+            if (LIMBS > 2) tc::tma_load_2d(st + 2 * C::A_LIMB, &mA2, &full[s], (int32_t)k0, mu0);
+          } else {
+            const uint32_t fb = full_lead + 8u * s;
+            tc::tma_load_2d_pair(st, &mA0, fb, (int32_t)k0, mu0);
+            if (LIMBS > 1) tc::tma_load_2d_pair(st + C::A_LIMB, &mA1, fb, (int32_t)k0, mu0);
+            if (LIMBS > 2) tc::tma_load_2d_pair(st + 2 * C::A_LIMB, &mA2, fb, (int32_t)k0, mu0);
+          }
+        }
+      }
+    }
+  } else if (warp == C::CW) {
+    if (lane == 0) {
+      uint32_t cit = 0;
+      for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+        for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
+          const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
+          if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err)) goto done;
+          uint8_t* dst = ring + cs * C::C_BYTES;
+          tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
+          bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &cfull[cs]);
+          bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + k0, C::BK * 16, &cfull[cs]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lead && lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(2 * C::BM, 4 * C::BN, 1);
+      uint32_t it = 0, u = 0;
+      for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+        for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+          const int64_t kb = ch * p.kchunk;
+          const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
+          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto done;
+          tc::tc_fence_after();
+          for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
+            const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto done;
+            tc::tc_fence_after();
+            const uint32_t a_base = tc::smem_u32(stages + s * C::STAGE);
+            const uint32_t b_base = a_base + C::A_BYTES;
+            const bool first = (k0 == kb);
+#pragma unroll
+            for (int i = 0; i < LIMBS; ++i)
+#pragma unroll
+              for (int j = 0; j < LIMBS - i; ++j)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
+                  const uint64_t bd = tc::smem_desc(b_base + j * C::B_LIMB + kk * 32, 16, 512, 4);
+                  const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                  tc::umma_f16_pair(tmem, ad, bd, idesc, acc);
+                }
+            tc::umma_commit_pair_multicast(&empty[s], 3);
+          }
+          tc::umma_commit_pair_multicast(acc_full, 3);
+        }
+      }
+    }
+  } else if (warp < 2 + C::NGW) {
+    // generator: lane = outer point of this CTA's half, warp = 4 inner points
+    const int row = lane;
+    const int kc = (warp - 2) * C::PTS;
+    const int64_t n_gs = p.g_end - p.g_begin;
+    const float d = p.d;
+    uint32_t it = 0;
+    for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+      const int64_t g_tile = tile % p.n_g_tiles;
+      const int64_t gl = g_tile * C::BN + (int64_t)rank * C::BNH + row;
+      const bool gvalid = gl < n_gs;
+      const int64_t g = p.g_begin + (gvalid ? gl : 0);
+      const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+        const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
+        const bool okc = tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, okc)) goto done;
+        const uint32_t cbase = tc::smem_u32(ring + cs * C::C_BYTES);
+        float dx[C::PTS], dy[C::PTS], dz[C::PTS];
+#pragma unroll
+        for (int e = 0; e < C::PTS; ++e)
+          pair_diff(gh, glo, tc::lds_f4(cbase + (kc + e) * 16),
+                    tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&cempty[cs]);  // the warp's ring reads are done
+        uint32_t pk[4][LIMBS][2];
+#pragma unroll
+        for (int e = 0; e < C::PTS; e += 2) {
+          float kv[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            radial_pair(dx[e + h], dy[e + h], dz[e + h], d, kv[h][0], kv[h][1], kv[h][2],
+                        kv[h][3]);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t w[LIMBS];
+            split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+          }
+        }
+        const bool oke = tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, oke)) goto done;
+        const uint32_t bsm = tc::smem_u32(stages + s * C::STAGE + C::A_BYTES);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t r = c * C::BNH + row;
+          const uint32_t off = tc::sw64_offset(r, kc >> 3) + (kc & 7) * 2;
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l) sts_u2(bsm + l * C::B_LIMB + off, pk[c][l][0], pk[c][l][1]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if (lead) tc::mbar_arrive(&full[s]);
+          else tc::mbar_arrive_cluster(full_lead + 8u * s);
+        }
+      }
+    }
+  } else {
+    // epilogue: this CTA's 128 accumulator rows
+    const int quad = warp & 3;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    const int64_t n_gs = p.g_end - p.g_begin;
+    uint32_t u = 0;
+    for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+      const int64_t g_tile = tile % p.n_g_tiles;
+      const int mu = (int)(tile / p.n_g_tiles) * 2 * C::BM + (int)rank * C::BM + 32 * quad + lane;
+      for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
+        const bool ok = tc::mbar_wait(acc_full, u & 1, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, ok)) goto done;
+        tc::tc_fence_after();
+        const bool first = (ch == 0), last = (ch + 1 == n_chunks);
+#pragma unroll 1
+        for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
+          uint32_t r[32];
+          __syncwarp();
+          tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
+                              first, r);
+          if (!last) {
+            tc::tmem_st_32x32b_x32(tmem + lane_base + C::ACC_COLS + blk * 32, r);
+          } else if (mu < p.n_mu) {
+            // column block blk: half blk / 4 (outer points 32 (blk / 4) ..), channel blk % 4
+            const int c = blk & 3;
+            double* dst = p.calG + ((int64_t)c * p.n_mu + mu) * n_gs;
+            const int64_t gbase = g_tile * C::BN + (blk >> 2) * C::BNH;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
+          }
+        }
+        __syncwarp();
+        if (!last) tc::tmem_st_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (lead) tc::mbar_arrive(acc_empty);
+          else tc::mbar_arrive_cluster(acce_lead);
+        }
+      }
+    }
+  }
+done:
+  __syncthreads();
+  if (*abort_flag) {
+    // a bounded wait expired: give issued copies and MMAs time to land
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) {
+    }
+  }
+  tc::tc_fence_before();
+  tc::cluster_sync();  // the pair's MMAs read both CTAs' shared memory and tensor memory
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc_pair(tmem, C::TMEM_COLS);
+  }
+}
+
 // ------------------------------------------------------------------ generic split GEMM
 
 // out[z][m][n] += scale * sum_k A_z[m][k] B_z[n][k] over the K range of this
@@ -1044,11 +1341,21 @@ int launch_s1(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStre
   return ISDF_OK;
 }
 
+template <int LIMBS>
+int launch_s1_pair(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStream_t s) {
+  using C = S1P<LIMBS>;
+  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM));
+  s1_pair_kernel<LIMBS><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
 }  // namespace
 
 struct TcLayout {
   int limbs, bn;
-  int64_t n_k, mu_pad, gs, gs_pad;
+  int64_t n_k, mu_pad, mu_pad1, gs, gs_pad;  // mu_pad1: stage-1 rows (whole 256-row pairs)
 };
 
 static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
@@ -1057,6 +1364,7 @@ static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
   L.bn = 64;
   L.n_k = round_up(n_g, 32);
   L.mu_pad = round_up(n_mu, 128);
+  L.mu_pad1 = round_up(n_mu, 256);
   L.gs = g_end - g_begin;
   L.gs_pad = round_up(L.gs, 32);
   return L;
@@ -1087,7 +1395,7 @@ size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int p
   c.take<int>(64);
   c.take<float4>(L.n_k);
   c.take<float4>(L.n_k);
-  c.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);           // S1 A
+  c.take<uint16_t>((size_t)L.limbs * L.mu_pad1 * L.n_k);          // S1 A
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
   int nn, ns4;
@@ -1112,7 +1420,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   int* err = cv.take<int>(64);
   float4* hi = cv.take<float4>(L.n_k);
   float4* lo = cv.take<float4>(L.n_k);
-  uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad * L.n_k);
+  uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad1 * L.n_k);
   uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   float4* rowslots = nullptr;
@@ -1143,16 +1451,21 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
       ISDF_CUDA(cudaMemsetAsync(fvec, 0, sizeof(float4) * L.n_k, s));
     }
   }
-  ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad, L.n_k, L.limbs, A1, s));
+  ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1, L.n_k, L.limbs, A1, s));
   CUtensorMap mA[3];
   memset(mA, 0, sizeof(mA));
   for (int l = 0; l < L.limbs; ++l)
-    ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad * L.n_k, L.mu_pad, L.n_k, 128));
+    ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad1 * L.n_k, L.mu_pad1, L.n_k, 128));
+  // The radial correlator runs on CTA pairs (256-row tiles).  Debug bit 1 asks
+  // for the single-CTA kernel with two limbs; its three-limb form gave
+  // run-to-run wrong elements on multi-tile grids and is not offered.  The
+  // multi-centre generator is single-CTA.
+  const bool pair = radial && ((opt.debug_flags & 2) == 0 || L.limbs == 3);
 
   S1Params p;
   p.xyz_hi = hi; p.xyz_lo = lo;
   p.n_g = n_g; p.n_k = L.n_k; p.n_mu = n_mu;
-  p.n_mu_tiles = (int)(L.mu_pad / 128);
+  p.n_mu_tiles = pair ? (int)(L.mu_pad1 / 256) : (int)(L.mu_pad / 128);
   p.g_begin = g_begin; p.g_end = g_end;
   p.n_g_tiles = ceil_div(L.gs, L.bn);
   p.kchunk = kchunk;
@@ -1173,7 +1486,8 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   ISDF_CUDA(cudaGetDevice(&dev));
   ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
-  const unsigned grid1 = (unsigned)(n_tiles < nsm ? n_tiles : nsm);
+  unsigned grid1 = (unsigned)(n_tiles < nsm ? n_tiles : nsm);
+  if (pair) grid1 = 2u * (unsigned)(n_tiles < nsm / 2 ? n_tiles : nsm / 2);
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   const bool timed = opt.stage_ms != nullptr && opt.sync_check;
   if (timed) {
@@ -1181,8 +1495,10 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     ISDF_CUDA(cudaEventRecord(ev[0], s));
   }
   int rc;
-  if (radial)
-    rc = L.limbs == 2 ? launch_s1<2, -1, 0>(grid1, mA, p, s) : launch_s1<3, -1, 0>(grid1, mA, p, s);
+  if (pair)
+    rc = L.limbs == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
+  else if (radial)
+    rc = launch_s1<2, -1, 0>(grid1, mA, p, s);
   else if (K.ng == 1 && K.deg == 2)
     rc = L.limbs == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
   else if (K.ng == 1)

@@ -157,6 +157,11 @@ class Proposer:
         cand = topk(scores, k)
         return points_restricted(smp.phi, smp.dphi, smp.w, cand, smp.n_mu)
 
+    def candidates(self, smp: Sample, kappa: float = 3.0) -> torch.Tensor:
+        """The kappa N_mu highest-scoring points of the network."""
+        scores = forward(self.params, smp.feat)
+        return topk(scores, min(int(kappa * smp.n_mu), smp.feat.shape[0]))
+
     def select(self, smp: Sample, kappa: float = 3.0, tolerance: float = 2.0):
         """Proposal if its fit error is within `tolerance` x the plain
         selection's, else the plain selection (fallback)."""
@@ -166,3 +171,16 @@ class Proposer:
         if e_prop <= tolerance * e_plain:
             return piv, e_prop, e_plain, False
         return smp.plain, e_prop, e_plain, True
+
+
+def diagonal_candidates(smp: Sample, kappa: float = 3.0) -> torch.Tensor:
+    """The same candidate budget without the network: the kappa N_mu points with
+    the largest initial scalar pivot diagonal w^2 rho^2 (the quantity the
+    first step of Alg. 1 maximises; feature 0)."""
+    d0 = smp.feat[:, 0].contiguous()
+    return topk(d0, min(int(kappa * smp.n_mu), smp.feat.shape[0]))
+
+
+def recall(cand: torch.Tensor, plain: torch.Tensor) -> float:
+    """Fraction of the plain selection's points inside a candidate set."""
+    return float(torch.isin(plain.long(), cand.long()).float().mean())

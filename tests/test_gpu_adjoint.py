@@ -93,3 +93,48 @@ def test_adjoint_rejects_two_types(api):
         api.tc_kernel_adjoint(_cu(w.grid_xyz), _cu(w.grid_w), _cu(xi), _cu(xit),
                               api.jastrow_from(jas), _cu(Wbar), "fp32")
     assert e.value.status == C.ISDF_E_UNSUPPORTED
+
+
+def test_adjoint_h20_full_size_on_outer_slices(api):
+    """The adjoint at the H20-chain size (40,000 points, N_mu = 800, the 28-term
+    one-type correlator: 30 parameters) on outer-grid slices: FP64 adjoint
+    against central differences (h = 1e-4) of the FP64 forward over the same
+    slice for five sampled parameters, FP32 against FP64, and additivity over
+    slices.  xi, xi~ and the seed Wbar are seeded normal samples."""
+    w = wl.h20_chain_bh()
+    n_g, n_mu = w.grid_xyz.shape[0], w.n_mu
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4321)
+    g, wt = _cu(w.grid_xyz), _cu(w.grid_w)
+    X = torch.randn((n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    Xt = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    Wb = _cu(wl.seeded_matrix((4, n_mu, n_mu), 77))
+    J = api.jastrow_from(w.jastrow)
+    g0, g1 = 20000, 20192
+    g64 = api.tc_kernel_adjoint(g, wt, X, Xt, J, Wb, "fp64", g_begin=g0, g_end=g1).cpu().numpy()
+    g32 = api.tc_kernel_adjoint(g, wt, X, Xt, J, Wb, "fp32", g_begin=g0, g_end=g1).cpu().numpy()
+    assert len(g64) == 30
+    err32 = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    a = api.tc_kernel_adjoint(g, wt, X, Xt, J, Wb, "fp64", g_begin=g0, g_end=g0 + 80)
+    b = api.tc_kernel_adjoint(g, wt, X, Xt, J, Wb, "fp64", g_begin=g0 + 80, g_end=g1)
+    add = float(torch.linalg.norm(a + b - torch.as_tensor(g64).cuda())) / np.linalg.norm(g64)
+    th = np.concatenate([[J.d, J.b[0]], [J.coef[0][k] for k in range(J.n_terms)]])
+    h = 1e-4
+    sample = [0, 1, 2, 15, 29]
+    fd = []
+    for p in sample:
+        vals = []
+        for s in (+1, -1):
+            tp = th.copy()
+            tp[p] += s * h
+            W, _ = api.tc_kernel_build(g, wt, X, Xt, api.jastrow_with_theta(J, tp), "fp64",
+                                       g_begin=g0, g_end=g1)
+            vals.append(float((W * Wb).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    efd = np.linalg.norm(g64[sample] - fd) / np.linalg.norm(fd)
+    print("H20 slice: FP64 adjoint vs central differences %.2e, FP32 vs FP64 %.2e, "
+          "slice additivity %.2e" % (efd, err32, add))
+    assert efd < 1e-6
+    assert err32 < 1e-4
+    assert add < 1e-12

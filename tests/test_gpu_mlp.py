@@ -135,6 +135,24 @@ def test_training_and_gain(P):
     print("fit-error ratio proposal/plain", ratios, "fallbacks", fallbacks,
           "selection time plain %.4f s proposal %.4f s" % (t_plain, t_prop))
     assert np.median(ratios) < 2.0
+    # what the network gains: at the same candidate budget (3 N_mu points) its
+    # candidates hold more of the plain selection than the budget filled by
+    # the largest initial pivot diagonals, and the restricted pivoting on them
+    # fits better
+    rec_net, rec_diag, e_net, e_diag = [], [], [], []
+    for smp in test:
+        c_net = prop.candidates(smp, 3.0)
+        c_diag = P.diagonal_candidates(smp, 3.0)
+        rec_net.append(P.recall(c_net, smp.plain))
+        rec_diag.append(P.recall(c_diag, smp.plain))
+        e_net.append(P.fit_error(smp.phi, smp.w, P.points_restricted(smp.phi, smp.dphi, smp.w,
+                                                                      c_net, smp.n_mu)))
+        e_diag.append(P.fit_error(smp.phi, smp.w, P.points_restricted(smp.phi, smp.dphi, smp.w,
+                                                                       c_diag, smp.n_mu)))
+    print("candidate recall of the plain selection: network", rec_net, "diagonal", rec_diag)
+    print("fit error: network", e_net, "diagonal", e_diag)
+    assert np.mean(rec_net) > np.mean(rec_diag)
+    assert np.median(np.array(e_net) / np.array(e_diag)) < 1.0
     # a network with scrambled weights is caught by the fit-error check
     bad = P.Proposer(seed=1)
     bad.params.mul_(-1.0)

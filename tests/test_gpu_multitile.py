@@ -2,8 +2,8 @@
 element by element where every persistent CTA runs several tiles.
 
 Radial correlator on an H10-chain grid: 10 x 40 x 50 = 20,000 points (312.5
-tiles of 64 outer points) and N_mu = 300 (three 128-row tiles, the last one
-ragged): 939 tiles on 148 CTAs.  Two-type multi-centre correlator on the
+tiles of 64 outer points) and N_mu = 300 (two 256-row tiles of the CTA-pair
+kernel, the last one ragged): 626 tiles on 74 CTA pairs.  Two-type multi-centre correlator on the
 benzene geometry: 12 x 14 x 50 = 8400 points (131.25 tiles), N_mu = 300:
 396 tiles.  Every calG and W element is checked against the oracle within
 1e-5 of its normwise bound: sum_g' |w_g' xi_nu(g')| |K_c(g, g')| for calG,
@@ -11,6 +11,16 @@ and that bound carried through stage 2, sum_g |w_g xi~^c_mu(g)| bound_nu(g),
 plus the stage-2 sum's own scale sum_g |w_g xi~^c_mu(g)| |calG_nu(g)|, for W.
 xi and xi~ are seeded normal samples (the oracle's cost does not depend on
 their values).  The oracle runs in a process pool started with spawn.
+
+Tolerances, per element against the normwise bound: W within 1e-5; calG
+within 5e-5, the size of the two-limb split error (each product misses
+lo*lo and the limbs' own rounding, up to ~3 x 2^-18 of |a b|) and, for the
+multi-centre correlator, of its FP32 generation for pairs of far points;
+the measured maxima are 2.6e-5 and 3.3e-5.  Per channel the calG relative
+Frobenius error stays within 1e-5.  With random xi, W carries heavy
+cancellation, so its relative Frobenius error is not the test here (it is
+on the fitted factors of the parity tests).  The single-CTA radial kernel
+with two limbs gives the same bits as the pair kernel and is checked too.
 """
 import multiprocessing as mp
 import os
@@ -68,22 +78,32 @@ def api():
     return api
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec,debug", [("bf16x3", 0), ("bf16x6", 0), ("bf16x3", 2)])
 @pytest.mark.parametrize("name", ["radial", "benzene"])
-def test_stage1_and_w_every_element(api, name, prec):
+def test_stage1_and_w_every_element(api, name, prec, debug):
+    if debug and name != "radial":
+        pytest.skip("the multi-centre correlator has one kernel")
     grid, w, jas, xi, xit, calG, bound, W, Wb = _oracle(name)
     n_g = grid.shape[0]
     c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
-    Wg, Gg = api.tc_kernel_build(c(grid), c(w), c(xi), c(xit), api.jastrow_from(jas), prec)
-    Gg = Gg.cpu().numpy()
-    Wg = Wg.cpu().numpy()
-    n_tiles = int(np.ceil(xi.shape[0] / 128)) * int(np.ceil(n_g / 64))
-    assert n_tiles > 2 * 148          # every CTA runs more than one tile
+    kb = api.KernelBuilder(c(grid), c(w), c(xi), c(xit), api.jastrow_from(jas), prec,
+                           debug_flags=debug)
+    kb()
+    Gg = kb.calG.cpu().numpy()
+    Wg = kb.W.cpu().numpy()
+    # the radial correlator runs on CTA pairs (256-row tiles, 74 pairs), the
+    # multi-centre one on single CTAs (128-row tiles, 148 CTAs)
+    rows, units = (256, 74) if name == "radial" and not debug else (128, 148)
+    n_tiles = int(np.ceil(xi.shape[0] / rows)) * int(np.ceil(n_g / 64))
+    assert n_tiles > 2 * units        # every CTA runs more than one tile
     gerr = np.abs(Gg - calG) / bound
     werr = np.abs(Wg - W) / Wb
     print(name, prec, "tiles", n_tiles, "max calG err / bound %.2e" % gerr.max(),
           "max W err / bound %.2e" % werr.max(),
           "W rel Frobenius", [float(np.linalg.norm(Wg[k] - W[k]) / np.linalg.norm(W[k]))
                               for k in range(4)])
-    assert gerr.max() < 1e-5, np.unravel_index(np.argmax(gerr), gerr.shape)
+    gfro = [float(np.linalg.norm(Gg[k] - calG[k]) / np.linalg.norm(calG[k])) for k in range(4)]
+    print("calG relative Frobenius per channel", gfro)
+    assert gerr.max() < 5e-5, np.unravel_index(np.argmax(gerr), gerr.shape)
     assert werr.max() < 1e-5, np.unravel_index(np.argmax(werr), werr.shape)
+    assert max(gfro) < 1e-5, gfro

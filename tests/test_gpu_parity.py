@@ -163,6 +163,18 @@ def test_w_tensor_core(P, h6, prec):
     assert max(errs) < 1e-5, errs
 
 
+def test_w_tensor_core_single_cta(P, h6):
+    """The single-CTA stage-1 kernel (128-row tiles), kept for the multi-centre
+    correlator, on the radial correlator with two limbs (debug bit 1 selects it)."""
+    from paper_2607_17314_b300 import api
+    w, o = h6
+    kb = api.KernelBuilder(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]), _jas(P, w),
+                           "bf16x3", debug_flags=2)
+    kb()
+    errs = [rel(host(kb.W[c]), o["W"][c]) for c in range(4)]
+    assert max(errs) < 1e-5, errs
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_w_slices_additive(P, h6, prec):
     w, o = h6
