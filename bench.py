@@ -50,6 +50,11 @@ def parse():
                     help="instead of the bench line: the whole workload once on the tensor-core "
                          "path and once on the FP64 GPU path from the same orbitals, pivots and "
                          "fit; full W, D, X and energy differences (minutes at the H50 size)")
+    ap.add_argument("--assembly", action="store_true",
+                    help="instead of the bench line: the full X (every orbital pair) and the "
+                         "four-index assembly (one K/DeltaU panel of --panel-rows rows, Delta h, "
+                         "f^xTC, E0) at the workload's size, timed")
+    ap.add_argument("--panel-rows", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--w-only", action="store_true",
@@ -439,6 +444,53 @@ def run_validate(args):
     }), flush=True)
 
 
+def run_assembly(args):
+    """The xTC X over every orbital pair and the four-index assembly at the
+    workload's size: one pass of the path, then X with n_orb_x = n_orb, one
+    panel of K and DeltaU rows (tensor cores, three limbs), and Delta h,
+    f^xTC, E0 for every orbital pair; device times by CUDA events."""
+    import torch
+    from paper_2607_17314_b300 import api, build, pipeline
+    build.build()
+    wlw = make_workload(args.workload)
+    b = wlw.basis
+    J = api.jastrow_from(wlw.jastrow)
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
+                          wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
+    out = pipeline.run(inp, precision=args.precision)
+    n_orb, n_mu, n_g, n_occ = wlw.n_orb, wlw.n_mu, inp.n_g, wlw.n_occ
+
+    def timed(fn, reps=2):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(); e0.record(); r = fn(); e1.record(); torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return r, min(ts)
+
+    (D, Xp), t_x = timed(lambda: api.xtc_density_contract(out["phiP"], n_occ, out["xi"], inp.w,
+                                                          out["calG"], n_orb,
+                                                          precision=args.precision), reps=1)
+    x_flops = 4.0 * n_g * n_mu * n_orb * n_orb
+    rows = min(args.panel_rows, n_orb * n_orb)
+    (Kp, Up), t_p = timed(lambda: api.tc_two_body_panel(out["W"], D, Xp, out["phiP"],
+                                                        out["dphiP"], 0, rows,
+                                                        precision=args.precision), reps=1)
+    p_flops = 12.0 * rows * n_mu * n_orb * n_orb
+    (dh, f, e0), t_1 = timed(lambda: api.tc_xtc_one_body(out["W"], D, Xp, out["phiP"],
+                                                         out["dphiP"], n_occ))
+    # the occupied block of the panel against the occupied-only energies call
+    print(json.dumps({
+        "mode": "assembly", "workload": args.workload, "precision": args.precision,
+        "n_g": n_g, "n_mu": n_mu, "n_orb": n_orb, "n_occ": n_occ,
+        "x_full_ms": t_x, "x_full_alg_tflops": x_flops / (t_x * 1e-3) / 1e12,
+        "panel_rows": rows, "panel_ms": t_p, "panel_alg_tflops": p_flops / (t_p * 1e-3) / 1e12,
+        "panels_for_all_rows_s_extrapolated": t_p * 1e-3 * n_orb * n_orb / rows,
+        "one_body_ms": t_1, "e0_ha": e0, "e0_occupied_energies_call_ha": out["E"][2],
+    }), flush=True)
+
+
 def _chain(k):
     from synth import workloads as wl
     return wl.perturbed_chain(k)
@@ -534,6 +586,8 @@ def main():
         return run_proposer(args)
     if args.validate:
         return run_validate(args)
+    if args.assembly:
+        return run_assembly(args)
 
     import torch
     import torch.distributed as dist

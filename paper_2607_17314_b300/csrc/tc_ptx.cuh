@@ -253,6 +253,50 @@ __device__ __forceinline__ void tmem_fold_block(uint32_t t_chunk, uint32_t t_run
   }
 }
 
+// 16-column forms, and fold/load/store helpers over 16 or 32 columns.
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+template <int N>
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[N]) {
+  if constexpr (N == 32) tmem_ld_32x32b_x32(taddr, r); else tmem_ld_32x32b_x16(taddr, r);
+}
+template <int N>
+__device__ __forceinline__ void tmem_st_n(uint32_t taddr, const uint32_t (&r)[N]) {
+  if constexpr (N == 32) tmem_st_32x32b_x32(taddr, r); else tmem_st_32x32b_x16(taddr, r);
+}
+template <int N>
+__device__ __forceinline__ void tmem_fold_block_n(uint32_t t_chunk, uint32_t t_run, bool first,
+                                                  uint32_t (&out)[N]) {
+  uint32_t a[N];
+  tmem_ld_n<N>(t_chunk, a);
+  if (!first) tmem_ld_n<N>(t_run, out);
+  tmem_ld_wait();
+  if (first) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) out[j] = a[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      out[j] = __float_as_uint(__fadd_rn(__uint_as_float(out[j]), __uint_as_float(a[j])));
+  }
+}
+
 // ------------------------------------------------------------------ UMMA
 
 // Shared-memory matrix descriptor (tcgen05 format, version 1).

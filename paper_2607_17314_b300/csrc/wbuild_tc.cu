@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(S1C<LIMBS, (NG >= 0)>::THREADS, 1)
 // stage-free and chunk-ready barriers of both CTAs (multicast); the odd CTA's
 // epilogue warps arrive on the even CTA's chunk-free barrier.  Every wait is
 // bounded as in the single-CTA kernel.
-template <int LIMBS>
+template <int LIMBS, int NGRP = 1>
 struct S1P {
   static constexpr int BM = 128, BN = 64, BNH = 32, BK = 32;
   static constexpr int STAGES = LIMBS == 2 ? 6 : 4;
@@ -706,11 +706,14 @@ struct S1P {
   static constexpr uint32_t C_BYTES = BK * 32;          // FP32 hi then lo, per ring slot
   static constexpr uint32_t ACC_COLS = 4 * BN;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
-  static constexpr int NGW = 8;  // generator warps 2 .. 9
-  static constexpr int NEW = 4;  // epilogue warps 10 .. 13
-  static constexpr int CW = 2 + NGW + NEW;
+  static constexpr int GW = 8;              // warps of one generator group
+  static constexpr int NGW = GW * NGRP;     // generator warps 2 .. 1 + NGW; group k takes
+                                            // the k-steps it with it % NGRP == k
+  static constexpr int NEW = 4;             // epilogue warps
+  static constexpr int CW = 2 + NGW + NEW;  // coordinate producer warp
   static constexpr int THREADS = 32 * (CW + 1);
-  static constexpr int PTS = BNH * BK / (32 * NGW);    // inner points per generator thread
+  static constexpr int PTS = BNH * BK / (32 * GW);    // inner points per generator thread
+  static constexpr int FOLD = NGRP >= 2 ? 16 : 32;    // epilogue fold width (registers)
   static constexpr uint32_t SMEM = STAGES * STAGE + CSTAGES * C_BYTES + 1024 + 512;
   static_assert(PTS == 4, "one 8-byte chunk per generator thread, channel and limb");
   static_assert(STAGE % 1024 == 0 && A_LIMB % 1024 == 0 && B_LIMB % 1024 == 0, "alignment");
@@ -721,11 +724,11 @@ __device__ __forceinline__ void sts_u2(uint32_t saddr, uint32_t a, uint32_t b) {
   asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(saddr), "r"(a), "r"(b) : "memory");
 }
 
-template <int LIMBS>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS, 1)
+template <int LIMBS, int NGRP>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::THREADS, 1)
     s1_pair_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ S1Params p) {
-  using C = S1P<LIMBS>;
+  using C = S1P<LIMBS, NGRP>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ring = stages + C::STAGES * C::STAGE;
@@ -743,13 +746,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
-      // even CTA: its expect-tx arrival + one arrival per generator warp of both CTAs
-      tc::mbar_init(&full[s], lead ? 1 + 2 * C::NGW : 1);
+      // even CTA: its expect-tx arrival + one arrival per generator warp of the
+      // group that fills this phase, in both CTAs
+      tc::mbar_init(&full[s], lead ? 1 + 2 * C::GW : 1);
       tc::mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < C::CSTAGES; ++s) {
       tc::mbar_init(&cfull[s], 1);
-      tc::mbar_init(&cempty[s], C::NGW);
+      tc::mbar_init(&cempty[s], C::GW);
     }
     tc::mbar_init(acc_full, 1);
     tc::mbar_init(acc_empty, lead ? 2 * C::NEW : 1);
@@ -854,8 +858,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS,
     }
   } else if (warp < 2 + C::NGW) {
     // generator: lane = outer point of this CTA's half, warp = 4 inner points
+    const int grp = (warp - 2) / C::GW;
     const int row = lane;
-    const int kc = (warp - 2) * C::PTS;
+    const int kc = ((warp - 2) % C::GW) * C::PTS;
     const int64_t n_gs = p.g_end - p.g_begin;
     const float d = p.d;
     uint32_t it = 0;
@@ -867,6 +872,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS,
       const float4 gh = gvalid ? p.xyz_hi[g] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 glo = gvalid ? p.xyz_lo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
       for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+        if (NGRP > 1 && (int)(it % NGRP) != grp) continue;
         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
         const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
         const bool okc = tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err);
@@ -927,21 +933,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS>::THREADS,
         if (!__all_sync(0xffffffffu, ok)) goto done;
         tc::tc_fence_after();
         const bool first = (ch == 0), last = (ch + 1 == n_chunks);
+        constexpr int FW = C::FOLD;
 #pragma unroll 1
-        for (int blk = 0; blk < (int)C::ACC_COLS / 32; ++blk) {
-          uint32_t r[32];
+        for (int blk = 0; blk < (int)C::ACC_COLS / FW; ++blk) {
+          uint32_t r[FW];
           __syncwarp();
-          tc::tmem_fold_block(tmem + lane_base + blk * 32, tmem + lane_base + C::ACC_COLS + blk * 32,
-                              first, r);
+          tc::tmem_fold_block_n<FW>(tmem + lane_base + blk * FW,
+                                    tmem + lane_base + C::ACC_COLS + blk * FW, first, r);
           if (!last) {
-            tc::tmem_st_32x32b_x32(tmem + lane_base + C::ACC_COLS + blk * 32, r);
+            tc::tmem_st_n<FW>(tmem + lane_base + C::ACC_COLS + blk * FW, r);
           } else if (mu < p.n_mu) {
-            // column block blk: half blk / 4 (outer points 32 (blk / 4) ..), channel blk % 4
-            const int c = blk & 3;
+            // column j = blk FW + i: half j / 128 (outer points 32 (j / 128) ..),
+            // channel (j % 128) / 32, point j % 32 of that half
+            const int col = blk * FW;
+            const int c = (col & 127) >> 5;
             double* dst = p.calG + ((int64_t)c * p.n_mu + mu) * n_gs;
-            const int64_t gbase = g_tile * C::BN + (blk >> 2) * C::BNH;
+            const int64_t gbase = g_tile * C::BN + (col >> 7) * C::BNH + (col & 31);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < FW; ++j)
               if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
           }
         }
@@ -1341,12 +1350,17 @@ int launch_s1(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStre
   return ISDF_OK;
 }
 
+#ifndef ISDF_PAIR_GROUPS
+#define ISDF_PAIR_GROUPS 1
+#endif
+
 template <int LIMBS>
 int launch_s1_pair(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStream_t s) {
-  using C = S1P<LIMBS>;
-  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 C::SMEM));
-  s1_pair_kernel<LIMBS><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+  constexpr int G = ISDF_PAIR_GROUPS;
+  using C = S1P<LIMBS, G>;
+  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS, G>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  s1_pair_kernel<LIMBS, G><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
