@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6", "tf32x3"])
     ap.add_argument("--workload", default="h50_chain")
     ap.add_argument("--fp64-rows", type=int, default=1024,
                     help="outer grid points of the FP64 GPU comparison slice")
@@ -88,12 +88,13 @@ def w_flops(n_mu, n_rows, n_g):
 
 FALLBACK_BF16_SUSTAINED_TFLOPS = 1400.0
 
-# ncu counters of the current stage-1 kernel, from its small-case capture
-# (H50-chain geometry, 40,000 points, N_mu = 1024, one launch):
-# dram__bytes_read.sum + dram__bytes_write.sum divided by N_mu x n_g (the
-# launch's compulsory traffic scales with it), and sm__pipe_tensor_cycles_active
-# as a fraction of elapsed cycles.  Empty for a kernel not yet captured.
-S1_NCU = {"bf16x3": {"dram_bytes_per_mu_g": 36.15, "tensor_pipe_active": 0.465}}
+# ncu counters of the current stage-1 kernel (the CTA-pair kernel), from its
+# small-case capture (H50-chain geometry, 40,000 points, N_mu = 1024, one
+# launch): dram__bytes_read.sum + dram__bytes_write.sum divided by N_mu x n_g
+# (the launch's compulsory traffic, FP64 calG writes and the (w xi) limb reads,
+# scales with it), and sm__pipe_tensor_cycles_active as a fraction of elapsed
+# cycles.  Empty for a kernel not yet captured.
+S1_NCU = {"bf16x3": {"dram_bytes_per_mu_g": 48.3, "tensor_pipe_active": 0.606}}
 
 
 def tensor_peak(root=None):
@@ -428,6 +429,10 @@ def run_validate(args):
     D64, X64 = api.xtc_density_contract(out["phiP"], inp.n_occ, out["xi"], inp.w, calG64,
                                         inp.n_occ, precision="fp64")
     E64 = api.tc_energies(W64, D64, X64, out["phiP"], out["dphiP"], inp.n_occ)
+    # the xTC arithmetic alone: FP64 D and X from the tensor-core calG
+    D6c, X6c = api.xtc_density_contract(out["phiP"], inp.n_occ, out["xi"], inp.w, out["calG"],
+                                        inp.n_occ, precision="fp64")
+    E_xtc_arith = api.tc_energies(out["W"], D6c, X6c, out["phiP"], out["dphiP"], inp.n_occ)
     relf = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))
     keys = ("E_K", "E_dU", "E0")
     print(json.dumps({
@@ -441,6 +446,9 @@ def run_validate(args):
         "D_rel_err": relf(out["D"], D64), "X_rel_err": relf(out["Xp"], X64),
         "energies_ha": dict(zip(keys, out["E"])), "energies_fp64_ha": dict(zip(keys, E64)),
         "energies_err_ha": {k: a - b for k, a, b in zip(keys, out["E"], E64)},
+        "energies_err_ha_from_xtc_arithmetic": {k: a - b for k, a, b in
+                                                zip(keys, out["E"], E_xtc_arith)},
+        "energies_err_ha_from_w_and_calG": {k: a - b for k, a, b in zip(keys, E_xtc_arith, E64)},
     }), flush=True)
 
 
@@ -648,8 +656,11 @@ def main():
     s1_ms = statistics.mean(x[0] for x in stage_ms)
     s2_ms = statistics.mean(x[1] for x in stage_ms)
     peak, peak_kind = tensor_peak()
+    if args.precision == "tf32x3":
+        # dense TF32 runs at half the BF16 rate (1.1 vs 2.25 PFLOP/s nominal)
+        peak, peak_kind = peak * 0.5, peak_kind + " x 0.5 (nominal TF32/BF16 ratio)"
     s1_tflops = 8.0 * n_mu * n_g * n_g / (s1_ms * 1e-3) / 1e12
-    products = 3 if args.precision == "bf16x3" else 6
+    products = 6 if args.precision == "bf16x6" else 3
     ncu = S1_NCU.get(args.precision)
     # DRAM traffic of one launch: the per-(mu, g) figure of the ncu capture of
     # the current kernel (reads of the w xi limbs and the FP64 calG writes both
@@ -659,7 +670,8 @@ def main():
                 "frac": s1_tflops / peak, "traffic": traffic,
                 "products_frac": s1_tflops * products / peak,
                 "ncu_tensor_pipe_active": ncu["tensor_pipe_active"] if ncu else None,
-                "kernel": f"s1_tc_kernel ({args.precision}: {products} BF16 products per algorithmic MAC)",
+                "kernel": f"s1_pair_kernel ({args.precision}: {products} tensor-core products per "
+                          f"algorithmic MAC)",
                 "peak_kind": peak_kind}
 
     # FP64 GPU path on an outer-grid slice (same inner sum), and accuracy of
@@ -679,6 +691,25 @@ def main():
     kbt()
     errs = [float(torch.linalg.norm(kbt.W[c] - kb64.W[c]) / torch.linalg.norm(kb64.W[c]))
             for c in range(4)]
+    # the TF32 tensor-core arm of the same build (stage 1 kind::tf32 with two
+    # TF32 limbs), timed over the whole grid and checked on the FP64 slice
+    tf32_arm = None
+    if args.precision != "tf32x3":
+        kb32 = api.KernelBuilder(inp.grid, inp.w, xi, xig, J, "tf32x3", time_stages=True)
+        kb32()
+        t32 = []
+        for _ in range(2):
+            kb32()
+            t32.append(float(kb32.stage_ms[0]) + float(kb32.stage_ms[1]))
+        del kb32
+        kbs = api.KernelBuilder(inp.grid, inp.w, xi, xig, J, "tf32x3", 0, rows)
+        kbs()
+        e32 = [float(torch.linalg.norm(kbs.W[c] - kb64.W[c]) / torch.linalg.norm(kb64.W[c]))
+               for c in range(4)]
+        del kbs
+        tf32_arm = {"w_build_ms_stages": min(t32),
+                    "tflops": w_flops(n_mu, n_g, n_g) / (min(t32) * 1e-3) / 1e12,
+                    "w_rel_err_vs_fp64": e32}
     del kbt, kb64
     e_err = sampled_energy_error(api, inp, out, J, args.precision)
 
@@ -729,6 +760,7 @@ def main():
             "fp64_gpu": {"tflops": fp64_tflops, "slice_outer_points": rows,
                          "speedup_tc_over_fp64": value / fp64_tflops,
                          "w_rel_err_tc_vs_fp64": errs},
+            "tf32x3_arm": tf32_arm,
             "energies_ha": {"E_K": E[0], "E_dU": E[1], "E0": E[2]},
             "energies_err_ha_vs_fp64_gpu": e_err,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

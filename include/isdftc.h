@@ -52,7 +52,10 @@ typedef enum {
   ISDF_PREC_FP64 = 0,   /* FP64 on CUDA cores (the FP64 GPU path) */
   ISDF_PREC_BF16X3 = 1, /* tcgen05 BF16, 2-limb split (hi*hi + hi*lo + lo*hi), FP32 accumulation */
   ISDF_PREC_BF16X6 = 2, /* tcgen05 BF16, 3-limb split (6 products), FP32 accumulation */
-  ISDF_PREC_FP32 = 3    /* FP32 on CUDA cores (adjoint) */
+  ISDF_PREC_FP32 = 3,   /* FP32 on CUDA cores (adjoint) */
+  ISDF_PREC_TF32X3 = 4  /* W build, radial correlator: stage 1 on tcgen05 kind::tf32 with
+                           2-limb TF32 operands (3 products), FP32 accumulation; stage 2 as
+                           ISDF_PREC_BF16X6 */
 } isdf_precision;
 
 /* Contracted Cartesian Gaussian basis (device arrays).  Function f is
@@ -100,7 +103,7 @@ typedef struct {
                          its FP32 chunk sum before the epilogue folds that sum into
                          the IEEE-rounded FP32 running sum (also in tensor memory;
                          the tile is written to FP64 once); rounded up to a multiple
-                         of 32; 0 = default (512) */
+                         of 32; 0 = default (1024) */
   int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (expired bounded waits, CUDA errors) */

@@ -17,9 +17,9 @@ ISDF_OK, ISDF_E_ARG, ISDF_E_NOT_PD, ISDF_E_RANK, ISDF_E_NONFINITE, ISDF_E_TIMEOU
 STATUS_NAMES = ["ISDF_OK", "ISDF_E_ARG", "ISDF_E_NOT_PD", "ISDF_E_RANK", "ISDF_E_NONFINITE",
                 "ISDF_E_TIMEOUT", "ISDF_E_CUDA", "ISDF_E_UNSUPPORTED"]
 
-ISDF_PREC_FP64, ISDF_PREC_BF16X3, ISDF_PREC_BF16X6, ISDF_PREC_FP32 = 0, 1, 2, 3
+ISDF_PREC_FP64, ISDF_PREC_BF16X3, ISDF_PREC_BF16X6, ISDF_PREC_FP32, ISDF_PREC_TF32X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": ISDF_PREC_FP64, "bf16x3": ISDF_PREC_BF16X3, "bf16x6": ISDF_PREC_BF16X6,
-              "fp32": ISDF_PREC_FP32}
+              "fp32": ISDF_PREC_FP32, "tf32x3": ISDF_PREC_TF32X3}
 
 ISDF_MAX_NUC, ISDF_MAX_TYPES, ISDF_MAX_TERMS = 64, 4, 32
 

@@ -175,7 +175,8 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
     return wbuild_fp64(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, W, calG,
                        opt.sync_check, ws, ws_bytes, s);
   }
-  if (opt.precision != ISDF_PREC_BF16X3 && opt.precision != ISDF_PREC_BF16X6) {
+  if (opt.precision != ISDF_PREC_BF16X3 && opt.precision != ISDF_PREC_BF16X6 &&
+      opt.precision != ISDF_PREC_TF32X3) {
     set_error("unknown precision %d", opt.precision);
     return ISDF_E_ARG;
   }

@@ -72,9 +72,56 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols
   return ISDF_OK;
 }
 
+// Tensor map over an FP32 (TF32 limbs) matrix [rows][cols] with a box of 32
+// columns x box_rows rows and the 128-byte swizzle.
+static int make_map_f32(CUtensorMap* m, const void* base, int64_t rows, int64_t cols,
+                        int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return ISDF_E_CUDA;
+  }
+  ISDF_ARG(((uintptr_t)base & 15) == 0 && (cols * 4) % 16 == 0, "TMA base/stride alignment");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ISDF_E_CUDA;
+  }
+  return ISDF_OK;
+}
+
 namespace {
 
 // ------------------------------------------------------------------ prep kernels
+
+// As split_kernel with TF32 limbs in 32-bit words: each limb is the TF32
+// rounding (to nearest, ties away) of the FP32 rounding of the remainder.
+__global__ void split_tf32_kernel(const double* __restrict__ src, int64_t src_rs, int64_t c0,
+                                  const double* __restrict__ colw, int64_t rows, int64_t cols,
+                                  int64_t rows_pad, int64_t cols_pad, int limbs,
+                                  uint32_t* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t plane = rows_pad * cols_pad;
+  if (e >= plane) return;
+  int64_t r = e / cols_pad, c = e % cols_pad;
+  double v = 0.0;
+  if (r < rows && c < cols) {
+    v = src[r * src_rs + c0 + c];
+    if (colw) v *= colw[c0 + c];
+  }
+  for (int l = 0; l < limbs; ++l) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"((float)v));
+    dst[l * plane + e] = h;
+    v -= (double)__uint_as_float(h);
+  }
+}
 
 // dst[l][r][c] (rows_pad x cols_pad per limb) = limb l of
 // src[r * src_rs + c0 + c] * colw[c0 + c]; zero outside rows x cols.
@@ -95,6 +142,40 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int
     __nv_bfloat16 h = __double2bfloat16(v);
     dst[l * plane + e] = h;
     v -= (double)__bfloat162float(h);
+  }
+}
+
+// The same split over a 2-D grid (blockIdx.y = row), four columns per thread
+// written as one 8-byte word per limb; cols_pad must be a multiple of 4.
+__global__ void split_rows_kernel(const double* __restrict__ src, int64_t src_rs, int64_t c0,
+                                  const double* __restrict__ colw, int64_t rows, int64_t cols,
+                                  int64_t cols_pad, int64_t plane, int limbs,
+                                  __nv_bfloat16* __restrict__ dst) {
+  const int64_t r = blockIdx.y;
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (c >= cols_pad) return;
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t cc = c + q;
+    double x = 0.0;
+    if (r < rows && cc < cols) {
+      x = src[r * src_rs + c0 + cc];
+      if (colw) x *= colw[c0 + cc];
+    }
+    v[q] = x;
+  }
+  __nv_bfloat16* out = dst + r * cols_pad + c;
+  for (int l = 0; l < limbs; ++l) {
+    uint32_t bits[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 h = __double2bfloat16(v[q]);
+      bits[q] = (uint32_t)__bfloat16_as_ushort(h);
+      v[q] -= (double)__bfloat162float(h);
+    }
+    *reinterpret_cast<uint2*>(out + l * plane) =
+        make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
   }
 }
 
@@ -694,13 +775,22 @@ __global__ void __launch_bounds__(S1C<LIMBS, (NG >= 0)>::THREADS, 1)
 // stage-free and chunk-ready barriers of both CTAs (multicast); the odd CTA's
 // epilogue warps arrive on the even CTA's chunk-free barrier.  Every wait is
 // bounded as in the single-CTA kernel.
-template <int LIMBS, int NGRP = 1>
+// TF32: operands are TF32 limbs in 32-bit words (128-byte rows of the 32
+// inner points, 128-byte swizzle, kind::tf32 MMAs of K = 8); otherwise BF16
+// limbs (64-byte rows, 64-byte swizzle, kind::f16 MMAs of K = 16).  Both
+// advance 32 bytes of K per MMA.
+template <int LIMBS, int NGRP = 1, bool TF32 = false>
 struct S1P {
   static constexpr int BM = 128, BN = 64, BNH = 32, BK = 32;
-  static constexpr int STAGES = LIMBS == 2 ? 6 : 4;
+  static constexpr int EB = TF32 ? 4 : 2;               // operand bytes
+  static constexpr uint32_t ROWB = BK * EB;             // bytes of one operand row
+  static constexpr int KSUB = ROWB / 32;                // MMAs per limb product and k-step
+  static constexpr uint32_t SBO = 8 * ROWB;             // 8-row core-matrix stride
+  static constexpr uint32_t SWZ = TF32 ? 2 : 4;         // descriptor layout: 128B / 64B swizzle
+  static constexpr int STAGES = TF32 ? 3 : (LIMBS == 2 ? 6 : 4);
   static constexpr int CSTAGES = 8;
-  static constexpr uint32_t A_LIMB = BM * BK * 2;       // 8 KB
-  static constexpr uint32_t B_LIMB = 4 * BNH * BK * 2;  // 128 rows x 64 B = 8 KB
+  static constexpr uint32_t A_LIMB = BM * ROWB;         // 8 KB (BF16), 16 KB (TF32)
+  static constexpr uint32_t B_LIMB = 4 * BNH * ROWB;    // 128 rows
   static constexpr uint32_t A_BYTES = LIMBS * A_LIMB;
   static constexpr uint32_t STAGE = LIMBS * (A_LIMB + B_LIMB);
   static constexpr uint32_t C_BYTES = BK * 32;          // FP32 hi then lo, per ring slot
@@ -715,7 +805,7 @@ struct S1P {
   static constexpr int PTS = BNH * BK / (32 * GW);    // inner points per generator thread
   static constexpr int FOLD = NGRP >= 2 ? 16 : 32;    // epilogue fold width (registers)
   static constexpr uint32_t SMEM = STAGES * STAGE + CSTAGES * C_BYTES + 1024 + 512;
-  static_assert(PTS == 4, "one 8-byte chunk per generator thread, channel and limb");
+  static_assert(PTS == 4, "one 4-point chunk per generator thread, channel and limb");
   static_assert(STAGE % 1024 == 0 && A_LIMB % 1024 == 0 && B_LIMB % 1024 == 0, "alignment");
   static_assert(SMEM <= 232448, "shared memory budget");
 };
@@ -724,11 +814,34 @@ __device__ __forceinline__ void sts_u2(uint32_t saddr, uint32_t a, uint32_t b) {
   asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(saddr), "r"(a), "r"(b) : "memory");
 }
 
-template <int LIMBS, int NGRP>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::THREADS, 1)
+// TF32 limbs of a value: l0 = TF32 rounding (to nearest, ties away) of v,
+// l1 = TF32 rounding of the remainder v - l0 (exact in FP32), ...
+__device__ __forceinline__ uint32_t tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+template <int LIMBS>
+__device__ __forceinline__ void split_tf32(float v, uint32_t (&out)[LIMBS]) {
+#pragma unroll
+  for (int l = 0; l < LIMBS; ++l) {
+    const uint32_t h = tf32_rna(v);
+    out[l] = h;
+    if (l + 1 < LIMBS) v -= __uint_as_float(h);
+  }
+}
+
+// Byte offset of the 16-byte chunk `chunk16` of row `row` in a K-major tile
+// with 128-byte rows in the 128-byte-swizzle layout (chunk index XOR row % 8).
+__device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t chunk16) {
+  return row * 128u + ((chunk16 ^ (row & 7u)) << 4);
+}
+
+template <int LIMBS, int NGRP, bool TF32>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF32>::THREADS, 1)
     s1_pair_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ S1Params p) {
-  using C = S1P<LIMBS, NGRP>;
+  using C = S1P<LIMBS, NGRP, TF32>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ring = stages + C::STAGES * C::STAGE;
@@ -824,7 +937,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::TH
     }
   } else if (warp == 1) {
     if (lead && lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16(2 * C::BM, 4 * C::BN, 1);
+      // A and B formats: BF16 (1) for kind::f16, TF32 (2) for kind::tf32
+      constexpr uint32_t idesc = tc::idesc_f16(2 * C::BM, 4 * C::BN, TF32 ? 2 : 1);
       uint32_t it = 0, u = 0;
       for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
         for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
@@ -844,11 +958,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::TH
 #pragma unroll
               for (int j = 0; j < LIMBS - i; ++j)
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const uint64_t ad = tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, 512, 4);
-                  const uint64_t bd = tc::smem_desc(b_base + j * C::B_LIMB + kk * 32, 16, 512, 4);
+                for (int kk = 0; kk < C::KSUB; ++kk) {
+                  const uint64_t ad =
+                      tc::smem_desc(a_base + i * C::A_LIMB + kk * 32, 16, C::SBO, C::SWZ);
+                  const uint64_t bd =
+                      tc::smem_desc(b_base + j * C::B_LIMB + kk * 32, 16, C::SBO, C::SWZ);
                   const uint32_t acc = (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                  tc::umma_f16_pair(tmem, ad, bd, idesc, acc);
+                  if constexpr (TF32) tc::umma_tf32_pair(tmem, ad, bd, idesc, acc);
+                  else tc::umma_f16_pair(tmem, ad, bd, idesc, acc);
                 }
             tc::umma_commit_pair_multicast(&empty[s], 3);
           }
@@ -885,7 +1002,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::TH
                     tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&cempty[cs]);  // the warp's ring reads are done
-        uint32_t pk[4][LIMBS][2];
+        // limbs of the 4 points per channel: BF16 pairs in 2 words, TF32 in 4
+        constexpr int NW = TF32 ? 4 : 2;
+        uint32_t pk[4][LIMBS][NW];
 #pragma unroll
         for (int e = 0; e < C::PTS; e += 2) {
           float kv[2][4];
@@ -895,10 +1014,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::TH
                         kv[h][3]);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            uint32_t w[LIMBS];
-            split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+            if constexpr (TF32) {
 #pragma unroll
-            for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+              for (int h = 0; h < 2; ++h) {
+                uint32_t w[LIMBS];
+                split_tf32<LIMBS>(kv[h][c], w);
+#pragma unroll
+                for (int l = 0; l < LIMBS; ++l) pk[c][l][(e + h) % NW] = w[l];
+              }
+            } else {
+              uint32_t w[LIMBS];
+              split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+              for (int l = 0; l < LIMBS; ++l) pk[c][l][(e >> 1) % NW] = w[l];
+            }
           }
         }
         const bool oke = tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err);
@@ -907,9 +1036,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP>::TH
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const uint32_t r = c * C::BNH + row;
-          const uint32_t off = tc::sw64_offset(r, kc >> 3) + (kc & 7) * 2;
+          if constexpr (TF32) {
+            const uint32_t off = sw128_offset(r, kc >> 2);  // 4 points = one 16-byte chunk
 #pragma unroll
-          for (int l = 0; l < LIMBS; ++l) sts_u2(bsm + l * C::B_LIMB + off, pk[c][l][0], pk[c][l][1]);
+            for (int l = 0; l < LIMBS; ++l)
+              tc::sts_u4(bsm + l * C::B_LIMB + off, pk[c][l][0], pk[c][l][1], pk[c][l][2],
+                         pk[c][l][3]);
+          } else {
+            const uint32_t off = tc::sw64_offset(r, kc >> 3) + (kc & 7) * 2;
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l)
+              sts_u2(bsm + l * C::B_LIMB + off, pk[c][l][0], pk[c][l][1]);
+          }
         }
         tc::fence_proxy_async_smem();
         __syncwarp();
@@ -1158,9 +1296,9 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
 
 inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
 
-// Inner points per tensor-core accumulation run before each fold into the
-// running sum (both stages), and grid points per stage-2 CTA.
-constexpr int64_t kDefaultChunk = 512;
+// Inner points per stage-1 tensor-core accumulation run before each fold into
+// the running sum (stage 2 folds every 256), and grid points per stage-2 CTA.
+constexpr int64_t kDefaultChunk = 1024;
 constexpr int64_t kS2Range = 8192;
 
 }  // namespace
@@ -1171,9 +1309,15 @@ constexpr int64_t kS2Range = 8192;
 int split_operand(const double* src, int64_t src_rs, int64_t c0, const double* colw, int64_t rows,
                   int64_t cols, int64_t rows_pad, int64_t cols_pad, int limbs, void* dst,
                   cudaStream_t s) {
-  split_kernel<<<nb256(rows_pad * cols_pad), 256, 0, s>>>(src, src_rs, c0, colw, rows, cols,
-                                                        rows_pad, cols_pad, limbs,
-                                                        (__nv_bfloat16*)dst);
+  if (cols_pad % 4 == 0 && rows_pad < 65536) {
+    const dim3 grd((unsigned)ceil_div(cols_pad, 1024), (unsigned)rows_pad);
+    split_rows_kernel<<<grd, 256, 0, s>>>(src, src_rs, c0, colw, rows, cols, cols_pad,
+                                          rows_pad * cols_pad, limbs, (__nv_bfloat16*)dst);
+  } else {
+    split_kernel<<<nb256(rows_pad * cols_pad), 256, 0, s>>>(src, src_rs, c0, colw, rows, cols,
+                                                          rows_pad, cols_pad, limbs,
+                                                          (__nv_bfloat16*)dst);
+  }
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
@@ -1354,13 +1498,13 @@ int launch_s1(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStre
 #define ISDF_PAIR_GROUPS 1
 #endif
 
-template <int LIMBS>
+template <int LIMBS, bool TF32 = false>
 int launch_s1_pair(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStream_t s) {
   constexpr int G = ISDF_PAIR_GROUPS;
-  using C = S1P<LIMBS, G>;
-  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS, G>,
+  using C = S1P<LIMBS, G, TF32>;
+  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS, G, TF32>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  s1_pair_kernel<LIMBS, G><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
+  s1_pair_kernel<LIMBS, G, TF32><<<grid1, C::THREADS, C::SMEM, s>>>(mA[0], mA[1], mA[2], p);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
@@ -1368,13 +1512,19 @@ int launch_s1_pair(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cud
 }  // namespace
 
 struct TcLayout {
-  int limbs, bn;
+  int limbs;    // stage-2 limbs (and stage-1 limbs for the BF16 precisions)
+  int limbs1;   // stage-1 limbs
+  int eb1;      // stage-1 operand bytes (2: BF16, 4: TF32)
+  int bn;
   int64_t n_k, mu_pad, mu_pad1, gs, gs_pad;  // mu_pad1: stage-1 rows (whole 256-row pairs)
 };
 
 static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision) {
   TcLayout L;
-  L.limbs = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  // TF32X3: stage 1 in two TF32 limbs, stage 2 in three BF16 limbs
+  L.limbs = (precision == ISDF_PREC_BF16X6 || precision == ISDF_PREC_TF32X3) ? 3 : 2;
+  L.limbs1 = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  L.eb1 = precision == ISDF_PREC_TF32X3 ? 4 : 2;
   L.bn = 64;
   L.n_k = round_up(n_g, 32);
   L.mu_pad = round_up(n_mu, 128);
@@ -1409,7 +1559,7 @@ size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int p
   c.take<int>(64);
   c.take<float4>(L.n_k);
   c.take<float4>(L.n_k);
-  c.take<uint16_t>((size_t)L.limbs * L.mu_pad1 * L.n_k);          // S1 A
+  c.take<uint8_t>((size_t)L.limbs1 * L.eb1 * L.mu_pad1 * L.n_k);  // S1 A
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
   c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
   int nn, ns4;
@@ -1427,6 +1577,8 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
               const isdf_options& opt, double* W, double* calG, void* ws, size_t ws_bytes,
               cudaStream_t s) {
   const bool radial = tc_radial(J);
+  const bool tf32 = opt.precision == ISDF_PREC_TF32X3;
+  ISDF_ARG(!tf32 || radial, "the TF32 stage 1 takes the radial correlator only");
   BhTc K;
   if (!radial) ISDF_TRY(bh_tc_form(J, K));
   const TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, opt.precision);
@@ -1434,7 +1586,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   int* err = cv.take<int>(64);
   float4* hi = cv.take<float4>(L.n_k);
   float4* lo = cv.take<float4>(L.n_k);
-  uint16_t* A1 = cv.take<uint16_t>((size_t)L.limbs * L.mu_pad1 * L.n_k);
+  uint8_t* A1 = cv.take<uint8_t>((size_t)L.limbs1 * L.eb1 * L.mu_pad1 * L.n_k);
   uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   float4* rowslots = nullptr;
@@ -1465,16 +1617,25 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
       ISDF_CUDA(cudaMemsetAsync(fvec, 0, sizeof(float4) * L.n_k, s));
     }
   }
-  ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1, L.n_k, L.limbs, A1, s));
   CUtensorMap mA[3];
   memset(mA, 0, sizeof(mA));
-  for (int l = 0; l < L.limbs; ++l)
-    ISDF_TRY(make_map(&mA[l], A1 + (size_t)l * L.mu_pad1 * L.n_k, L.mu_pad1, L.n_k, 128));
+  const size_t a1_plane = (size_t)L.eb1 * L.mu_pad1 * L.n_k;
+  if (tf32) {
+    split_tf32_kernel<<<nb256(L.mu_pad1 * L.n_k), 256, 0, s>>>(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1,
+                                                              L.n_k, L.limbs1, (uint32_t*)A1);
+    ISDF_LAUNCH_CHECK();
+    for (int l = 0; l < L.limbs1; ++l)
+      ISDF_TRY(make_map_f32(&mA[l], A1 + l * a1_plane, L.mu_pad1, L.n_k, 128));
+  } else {
+    ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1, L.n_k, L.limbs1, A1, s));
+    for (int l = 0; l < L.limbs1; ++l)
+      ISDF_TRY(make_map(&mA[l], A1 + l * a1_plane, L.mu_pad1, L.n_k, 128));
+  }
   // The radial correlator runs on CTA pairs (256-row tiles).  Debug bit 1 asks
   // for the single-CTA kernel with two limbs; its three-limb form gave
   // run-to-run wrong elements on multi-tile grids and is not offered.  The
   // multi-centre generator is single-CTA.
-  const bool pair = radial && ((opt.debug_flags & 2) == 0 || L.limbs == 3);
+  const bool pair = radial && ((opt.debug_flags & 2) == 0 || L.limbs1 == 3 || tf32);
 
   S1Params p;
   p.xyz_hi = hi; p.xyz_lo = lo;
@@ -1509,16 +1670,18 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
     ISDF_CUDA(cudaEventRecord(ev[0], s));
   }
   int rc;
-  if (pair)
-    rc = L.limbs == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
+  if (tf32)
+    rc = launch_s1_pair<2, true>(grid1, mA, p, s);
+  else if (pair)
+    rc = L.limbs1 == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
   else if (radial)
     rc = launch_s1<2, -1, 0>(grid1, mA, p, s);
   else if (K.ng == 1 && K.deg == 2)
-    rc = L.limbs == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
+    rc = L.limbs1 == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
   else if (K.ng == 1)
-    rc = L.limbs == 2 ? launch_s1<2, 1, 3>(grid1, mA, p, s) : launch_s1<3, 1, 3>(grid1, mA, p, s);
+    rc = L.limbs1 == 2 ? launch_s1<2, 1, 3>(grid1, mA, p, s) : launch_s1<3, 1, 3>(grid1, mA, p, s);
   else
-    rc = L.limbs == 2 ? launch_s1<2, 2, 3>(grid1, mA, p, s) : launch_s1<3, 2, 3>(grid1, mA, p, s);
+    rc = L.limbs1 == 2 ? launch_s1<2, 2, 3>(grid1, mA, p, s) : launch_s1<3, 2, 3>(grid1, mA, p, s);
   if (rc != ISDF_OK) return rc;
   if (timed) ISDF_CUDA(cudaEventRecord(ev[1], s));
 

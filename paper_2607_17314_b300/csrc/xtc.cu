@@ -111,6 +111,79 @@ __global__ void q_kernel(const double* F, int n_occ, int n_s, int64_t nbg, int64
   for (int c = 0; c < 3; ++c) Q[((1 + c) * npair + pr) * nbg + g] = wg * q2[c];
 }
 
+// The same products for the tensor-core precisions, in FP32 arithmetic (the
+// X GEMMs that consume them carry ~3e-6 relative error, the FP32 sums of
+// 3 n_occ terms ~1e-7): one block per (q tile, s tile) pair of QT x QT orbital
+// indices (q tile <= s tile) and QG batch points, the F values of both tiles
+// staged through shared memory QA occupied orbitals at a time; thread: one
+// point (lane) and one q (warp), all QT values of s.  Writes along g coalesce.
+constexpr int QT = 8, QG = 32, QA = 5;
+__global__ void __launch_bounds__(256) q_tile_kernel(const double* __restrict__ F, int n_occ,
+                                                     int n_s, int64_t nbg, int64_t bw,
+                                                     const double* __restrict__ w, int64_t g0,
+                                                     double* __restrict__ Q) {
+  __shared__ float sA[4][QA][QT][QG];
+  __shared__ float qA[4][QA][QT][QG];
+  const int64_t tp = blockIdx.y;
+  int st = (int)((sqrt(8.0 * (double)tp + 1.0) - 1.0) / 2.0);
+  while ((int64_t)(st + 1) * (st + 2) / 2 <= tp) ++st;
+  while ((int64_t)st * (st + 1) / 2 > tp) --st;
+  const int qt = (int)(tp - (int64_t)st * (st + 1) / 2);
+  const int64_t gb = (int64_t)blockIdx.x * QG;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t fpl = (int64_t)n_occ * n_s * nbg;
+  float acc[4][QT];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int j = 0; j < QT; ++j) acc[f][j] = 0.f;
+  for (int a0 = 0; a0 < n_occ; a0 += QA) {
+    for (int e = threadIdx.x; e < 4 * QA * QT * QG; e += 256) {
+      const int gg = e % QG;
+      int r = e / QG;
+      const int ss = r % QT;
+      r /= QT;
+      const int aa = r % QA, f = r / QA;
+      const int a = a0 + aa;
+      const int64_t gi = gb + gg;
+      const bool ok = a < n_occ && gi < bw;
+      const int si = st * QT + ss, qi = qt * QT + ss;
+      const int64_t base = f * fpl + (int64_t)a * n_s * nbg + gi;
+      sA[f][aa][ss][gg] = (ok && si < n_s) ? (float)F[base + (int64_t)si * nbg] : 0.f;
+      qA[f][aa][ss][gg] = (ok && qi < n_s) ? (float)F[base + (int64_t)qi * nbg] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int aa = 0; aa < QA; ++aa) {
+      const float rq = qA[0][aa][wq][lane];
+      const float ax = qA[1][aa][wq][lane], ay = qA[2][aa][wq][lane], az = qA[3][aa][wq][lane];
+#pragma unroll
+      for (int j = 0; j < QT; ++j) {
+        const float rs = sA[0][aa][j][lane];
+        const float bx = sA[1][aa][j][lane], by = sA[2][aa][j][lane], bz = sA[3][aa][j][lane];
+        acc[0][j] = fmaf(bx, ax, fmaf(by, ay, fmaf(bz, az, acc[0][j])));
+        acc[1][j] = fmaf(rs, ax, fmaf(bx, rq, acc[1][j]));
+        acc[2][j] = fmaf(rs, ay, fmaf(by, rq, acc[2][j]));
+        acc[3][j] = fmaf(rs, az, fmaf(bz, rq, acc[3][j]));
+      }
+    }
+    __syncthreads();
+  }
+  const int q = qt * QT + wq;
+  const int64_t g = gb + lane;
+  if (g >= bw || q >= n_s) return;
+  const int64_t npair = (int64_t)n_s * (n_s + 1) / 2;
+  const double wg = w[g0 + g];
+#pragma unroll
+  for (int j = 0; j < QT; ++j) {
+    const int sj = st * QT + j;
+    if (sj >= n_s || q > sj) continue;
+    const int64_t pr = (int64_t)sj * (sj + 1) / 2 + q;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) Q[((int64_t)f * npair + pr) * nbg + g] = wg * (double)acc[f][j];
+  }
+}
+
 constexpr int64_t XBATCH = 4096;
 // X's GEMMs always split into three limbs: its products cancel strongly (two
 // limbs leave ~2e-5 relative error in X, three ~3e-6) and they are small.
@@ -320,8 +393,12 @@ int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double
       }
       ISDF_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * 4 * (size_t)nas * nbg, s));
       ISDF_TRY(splitgemm(kXLimbs, 4, A4, B4, nas, bw, kmu, kmu, 256, F, nbg, nas * nbg, 1.0, err, s));
-      q_kernel<<<nb(npair * bw), 256, 0, s>>>(F, n_occ, n_orb_x, nbg, bw, w, g0, Q);
-      ISDF_LAUNCH_CHECK();
+      {
+        const int64_t nt = ceil_div(n_orb_x, QT);
+        const dim3 grd((unsigned)ceil_div(bw, QG), (unsigned)(nt * (nt + 1) / 2));
+        q_tile_kernel<<<grd, 256, 0, s>>>(F, n_occ, n_orb_x, nbg, bw, w, g0, Q);
+        ISDF_LAUNCH_CHECK();
+      }
       const size_t qpl = (size_t)kXLimbs * np_pad * kg, bpl = (size_t)kXLimbs * mp * kg;
       for (int f = 0; f < 4; ++f) {
         const double* src = f == 0 ? xi : calG + (int64_t)(f - 1) * plane;

@@ -78,11 +78,12 @@ def api():
     return api
 
 
-@pytest.mark.parametrize("prec,debug", [("bf16x3", 0), ("bf16x6", 0), ("bf16x3", 2)])
+@pytest.mark.parametrize("prec,debug", [("bf16x3", 0), ("bf16x6", 0), ("bf16x3", 2),
+                                        ("tf32x3", 0)])
 @pytest.mark.parametrize("name", ["radial", "benzene"])
 def test_stage1_and_w_every_element(api, name, prec, debug):
-    if debug and name != "radial":
-        pytest.skip("the multi-centre correlator has one kernel")
+    if (debug or prec == "tf32x3") and name != "radial":
+        pytest.skip("the multi-centre correlator has one kernel (BF16 limbs)")
     grid, w, jas, xi, xit, calG, bound, W, Wb = _oracle(name)
     n_g = grid.shape[0]
     c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()

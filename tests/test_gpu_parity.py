@@ -149,7 +149,7 @@ def test_w_fp64(P, h6):
         assert rel(host(calG[c]), o["calG"][c]) < 1e-10, c
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6", "tf32x3"])
 def test_w_tensor_core(P, h6, prec):
     w, o = h6
     W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
