@@ -17,6 +17,15 @@ The kernels that enter u^(1) and u^(3) (Eqs. K1-isdf, K3-isdf) are
 Reading: the self pair g = g' has no defined gradient direction; K_c and
 K_sq are set to 0 there (mask by index).  A point on a nucleus gets a zero
 direction for that nucleus.
+
+One-body nuclear-cusp term (Eq. tau-def): u = u2 + [chi(r_i) + chi(r_j)]/(N-1),
+so that sum_{i<j} u = sum_i chi(r_i) + sum_{i<j} u2 for N electrons, and each
+ordered pair carries grad chi(r_i)/(N-1) in its electron-1 gradient.  The paper
+takes chi from a cited work without stating it; the reading used here is
+   chi(r) = sum_I a_t r_iI / (1 + beta_t r_iI),   t = type(I),
+whose slope at nucleus I is a_t (a_t = -Z_t imposes the electron-nucleus
+cusp) and which tends to a_t/beta_t far away.  chi is off when the object
+has no chi_a or all chi_a are zero.
 """
 from __future__ import annotations
 
@@ -29,8 +38,37 @@ def _unit(dv: np.ndarray, r: np.ndarray) -> np.ndarray:
     return np.where(r[..., None] > 0, u, 0.0)
 
 
+def chi_on(jas) -> bool:
+    a = getattr(jas, "chi_a", None)
+    return a is not None and bool(np.any(np.asarray(a) != 0.0))
+
+
+def chi_value(r: np.ndarray, jas) -> np.ndarray:
+    """chi(r) = sum_I a_t r_I / (1 + beta_t r_I) at points r [n, 3] -> [n]."""
+    out = np.zeros(r.shape[0])
+    for I in range(jas.n_nuc):
+        t = jas.nuc_type[I]
+        rI = np.linalg.norm(r - jas.nuc_xyz[I], axis=1)
+        out += jas.chi_a[t] * rI / (1.0 + jas.chi_b[t] * rI)
+    return out
+
+
+def chi_grad(r: np.ndarray, jas) -> np.ndarray:
+    """grad chi at points r [n, 3] -> [3, n]: a_t / (1 + beta_t r_I)^2 e_I,
+    with a zero direction on a nucleus."""
+    out = np.zeros((3, r.shape[0]))
+    for I in range(jas.n_nuc):
+        t = jas.nuc_type[I]
+        dv = r - jas.nuc_xyz[I]
+        rI = np.linalg.norm(dv, axis=1)
+        s = jas.chi_a[t] / (1.0 + jas.chi_b[t] * rI) ** 2
+        out += (s[:, None] * _unit(dv, rI)).T
+    return out
+
+
 def u_value(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
-    """u(r_i, r_j) of Eqs. bh-scaled and bh-u (plus the cusp term) for all pairs, [n, m]."""
+    """u(r_i, r_j) of Eqs. bh-scaled and bh-u (plus the cusp term and the
+    one-body term of Eq. tau-def) for all pairs, [n, m]."""
     dv = ri[:, None, :] - rj[None, :, :]
     r = np.sqrt(np.sum(dv * dv, axis=2))
     E = jas.d * r / (1.0 + jas.d * r)
@@ -48,11 +86,14 @@ def u_value(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
             m, n, o = (int(x) for x in jas.mno[k])
             c = jas.coef[t, k]
             u += c * (Ai ** m * Aj ** n + Aj ** m * Ai ** n) * E ** o
+    if chi_on(jas):
+        u += (chi_value(ri, jas)[:, None] + chi_value(rj, jas)[None, :]) / (jas.n_elec - 1)
     return u
 
 
 def grad1_u(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
-    """Analytic d u(r_i, r_j) / d r_i of Eqs. bh-scaled and bh-u, [3, n, m]."""
+    """Analytic d u(r_i, r_j) / d r_i of Eqs. bh-scaled and bh-u (and of the
+    one-body term of Eq. tau-def), [3, n, m]."""
     dv = ri[:, None, :] - rj[None, :, :]
     r = np.sqrt(np.sum(dv * dv, axis=2))
     d = jas.d
@@ -90,6 +131,8 @@ def grad1_u(ri: np.ndarray, rj: np.ndarray, jas) -> np.ndarray:
             g[ax] += cA * dAi[:, ax][:, None]
     for ax in range(3):
         g[ax] += cE * dEdr * eij[:, :, ax]
+    if chi_on(jas):
+        g += chi_grad(ri, jas)[:, :, None] / (jas.n_elec - 1)
     return g
 
 

@@ -84,6 +84,11 @@ class Jastrow:
     b: np.ndarray          # [n_types]
     d: float
     cusp: bool = True
+    # one-body nuclear-cusp term chi(r) = sum_I chi_a[t] r_I / (1 + chi_b[t] r_I),
+    # entering every pair as [chi(r_i) + chi(r_j)] / (n_elec - 1); off when None
+    chi_a: Optional[np.ndarray] = None   # [n_types]
+    chi_b: Optional[np.ndarray] = None   # [n_types]
+    n_elec: int = 0
 
     @property
     def n_nuc(self) -> int:
@@ -97,9 +102,22 @@ class Jastrow:
     def n_types(self) -> int:
         return int(self.b.shape[0])
 
+    def has_chi(self) -> bool:
+        return self.chi_a is not None and bool(np.any(self.chi_a != 0.0))
+
     def is_radial(self) -> bool:
         """True when only the cusp term is present (u depends on r12 only)."""
-        return self.cusp and (self.n_terms == 0 or not np.any(self.coef))
+        return (self.cusp and (self.n_terms == 0 or not np.any(self.coef))
+                and not self.has_chi())
+
+
+def with_chi(jas: Jastrow, charges, n_elec: int, beta: float = 1.0) -> Jastrow:
+    """A copy of ``jas`` with the one-body cusp term: chi_a[t] = -Z_t (the
+    electron-nucleus cusp slope), chi_b[t] = beta, for N = n_elec electrons."""
+    a = -np.asarray(charges, dtype=np.float64).reshape(-1)
+    assert a.shape[0] == jas.n_types
+    return dataclasses.replace(jas, chi_a=a, chi_b=np.full(jas.n_types, float(beta)),
+                               n_elec=int(n_elec))
 
 
 @dataclasses.dataclass

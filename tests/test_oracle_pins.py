@@ -124,6 +124,75 @@ def test_bh_symmetry_and_cusp():
     assert abs(slope - 0.5) < 1e-5
 
 
+def _chi_jastrow(n_elec=6):
+    atoms, xyz = wl.h_chain(3, 1.8)
+    jas = wl.bh_jastrow(atoms, xyz, wl.bh_terms_c4()[:6], np.random.default_rng(8), scale=0.3)
+    return wl.with_chi(jas, [1.0], n_elec, beta=1.3)
+
+
+def test_chi_one_body_closed_forms():
+    """chi(r) = sum_I a r_I/(1 + beta r_I) (the reading of the one-body cusp
+    factor): zero on a nucleus of a lone centre, slope a = -Z there (the
+    electron-nucleus cusp), limit a/beta far away, and grad chi by central
+    differences."""
+    jas = wl.with_chi(wl.radial_jastrow(np.zeros((1, 3))), [2.0], 4, beta=0.7)
+    e = np.array([[0.3, -0.4, 0.8660254037844386]])
+    e /= np.linalg.norm(e)
+    assert jastrow.chi_value(np.zeros((1, 3)), jas)[0] == 0.0
+    h = 1e-7
+    assert abs(jastrow.chi_value(h * e, jas)[0] / h - (-2.0)) < 1e-6
+    assert abs(jastrow.chi_value(1e9 * e, jas)[0] - (-2.0 / 0.7)) < 1e-7
+    r = 1.7
+    assert abs(jastrow.chi_value(r * e, jas)[0] - (-2.0 * r / (1.0 + 0.7 * r))) < 1e-15
+    jas3 = _chi_jastrow()
+    pts = np.random.default_rng(4).normal(size=(6, 3)) * 2
+    g = jastrow.chi_grad(pts, jas3)
+    for ax in range(3):
+        d = np.zeros(3)
+        d[ax] = 1e-6
+        fd = (jastrow.chi_value(pts + d, jas3) - jastrow.chi_value(pts - d, jas3)) / 2e-6
+        assert np.max(np.abs(fd - g[ax])) < 1e-8
+
+
+def test_chi_pair_kernel_resums_one_body_term():
+    """Eq. tau-def: for N electrons, sum_i chi(r_i) + sum_{i<j} u2(r_i, r_j)
+    equals sum_{i<j} u(r_i, r_j) with u = u2 + [chi_i + chi_j]/(N-1); and the
+    chi part of grad_1 u summed over the N-1 partners j != i gives grad chi(r_i)
+    (the ordered-pair evaluation of the numerical implementation notes)."""
+    N = 6
+    jas = _chi_jastrow(N)
+    import dataclasses
+    u2 = dataclasses.replace(jas, chi_a=None, chi_b=None, n_elec=0)
+    R = np.random.default_rng(11).normal(size=(N, 3)) * 1.5
+    iu = np.triu_indices(N, 1)
+    lhs = np.sum(jastrow.chi_value(R, jas)) + np.sum(jastrow.u_value(R, R, u2)[iu])
+    rhs = np.sum(jastrow.u_value(R, R, jas)[iu])
+    assert abs(lhs - rhs) < 1e-13 * max(1.0, abs(lhs))
+    gchi = jastrow.grad1_u(R, R, jas) - jastrow.grad1_u(R, R, u2)   # [3, N, N]
+    off = ~np.eye(N, dtype=bool)
+    summed = np.stack([np.sum(np.where(off, gchi[ax], 0.0), axis=1) for ax in range(3)])
+    h = 1e-6
+    for ax in range(3):
+        d = np.zeros(3)
+        d[ax] = h
+        fd = (jastrow.chi_value(R + d, jas) - jastrow.chi_value(R - d, jas)) / (2 * h)
+        assert np.max(np.abs(summed[ax] - fd)) < 1e-8
+
+
+def test_chi_gradient_fd_of_u():
+    jas = _chi_jastrow()
+    rng = np.random.default_rng(12)
+    ri = rng.normal(size=(5, 3)) * 2
+    rj = rng.normal(size=(4, 3)) * 2
+    g = jastrow.grad1_u(ri, rj, jas)
+    h = 1e-6
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        fd = (jastrow.u_value(ri + e, rj, jas) - jastrow.u_value(ri - e, rj, jas)) / (2 * h)
+        assert np.max(np.abs(fd - g[ax])) < 1e-8
+
+
 def test_self_pair_masked():
     jas = wl.radial_jastrow(np.zeros((1, 3)))
     pts = np.random.default_rng(0).normal(size=(5, 3))
@@ -660,6 +729,30 @@ def test_adjoint_gradient_matches_fd_of_loss():
     jas = w.jastrow
     jas.coef = jas.coef * 4.0
     g = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, jas, Wbar, batch=37)
+    th = adjoint.get_theta(jas)
+    h = 1e-5
+    for p in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (adjoint.loss(w.grid_xyz, w.grid_w, xi, xit, adjoint.set_theta(jas, tp), Wbar)
+              - adjoint.loss(w.grid_xyz, w.grid_w, xi, xit, adjoint.set_theta(jas, tm), Wbar)) / (2 * h)
+        assert abs(fd - g[p]) < 1e-6 * max(1.0, abs(g[p])), (p, fd, g[p])
+
+
+def test_adjoint_with_chi_matches_fd_of_loss():
+    """The adjoint with the one-body term present: chi carries no parameter of
+    theta, but it enters K_c and so the M^sq K_c factor of the gradient."""
+    from oracle import adjoint
+    w = wl.tiny_chain(n_atom=2, n_rad=5, n_ang=8, shells=(0, 1), n_mu=6, seed=3,
+                      jkind="bh", jterms=wl.bh_terms_c4()[:5])
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, w.n_mu)
+    xi, xit, _ = fit.fit(phi, dphi, res.pivots)
+    Wbar = wl.seeded_matrix((4, w.n_mu, w.n_mu), 5)
+    jas = wl.with_chi(w.jastrow, [1.0], 2 * w.n_occ, beta=1.1)
+    jas.coef = jas.coef * 4.0
+    g = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, jas, Wbar, batch=29)
     th = adjoint.get_theta(jas)
     h = 1e-5
     for p in range(len(th)):
