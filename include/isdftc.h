@@ -80,9 +80,16 @@ typedef struct {
  * with A_iI = b_I r_iI / (1 + b_I r_iI), E_ij = d r_ij / (1 + d r_ij) and
  * (m,n,o) = mno[k].  The cusp line is the cusp-normalised (0,0,1) term
  * (slope du/dr_ij -> 1/2).  n_terms = 0 with cusp = 1 is the radial
- * electron-electron correlator u(r) = r / (2 (1 + d r)).  Host struct.  Calls
- * return ISDF_E_ARG for d <= 0, counts or exponents out of range, non-finite
- * positions, d or coefficients, and b_t <= 0 when n_terms > 0. */
+ * electron-electron correlator u(r) = r / (2 (1 + d r)).
+ * One-body nuclear-cusp term (Eq. tau-def): when some chi_a[t] != 0,
+ *   u(i,j) += [chi(r_i) + chi(r_j)] / (n_elec - 1),
+ *   chi(r) = sum_I chi_a[t] r_iI / (1 + chi_b[t] r_iI),  t = nuc_type[I]
+ * (the paper cites chi's form without stating it; chi_a[t] = -Z_t gives the
+ * electron-nucleus cusp slope).  It adds grad chi(r_g)/(n_elec - 1) to K_c(g,g')
+ * for every g' != g; the self pair stays 0.  Host struct.  Calls return
+ * ISDF_E_ARG for d <= 0, counts or exponents out of range, non-finite
+ * positions, d or coefficients, b_t <= 0 when n_terms > 0, and, with chi on,
+ * n_elec < 2, n_nuc = 0 or chi_b[t] <= 0. */
 typedef struct {
   int32_t n_nuc;
   int32_t n_types;
@@ -94,9 +101,13 @@ typedef struct {
   double b[ISDF_MAX_TYPES];
   int32_t mno[ISDF_MAX_TERMS][3];
   double coef[ISDF_MAX_TYPES][ISDF_MAX_TERMS];
+  double chi_a[ISDF_MAX_TYPES];  /* one-body term amplitude per type (0 = off) */
+  double chi_b[ISDF_MAX_TYPES];  /* its scale beta per type */
+  int32_t n_elec;                /* electrons N of Eq. tau-def (used with chi on) */
 } isdf_jastrow;
 
-/* Options of the kernel build (host struct; NULL = defaults). */
+/* Options of the kernel build and the fit (host struct; NULL = defaults;
+ * a zero field takes its default). */
 typedef struct {
   int32_t precision;  /* isdf_precision; default ISDF_PREC_BF16X3 */
   int32_t kchunk;     /* stage 1: inner-grid points the tensor core accumulates into
@@ -115,6 +126,16 @@ typedef struct {
   float* stage_ms;    /* host [2] or NULL: when set (with sync_check), the device
                          times of stage 1 and stage 2, measured with CUDA events
                          on `stream` around the two kernels */
+  double jitter_init; /* isdf_fit: Tikhonov shift of the first retry, relative to
+                         max(diag) of the Gram (the first attempt has none);
+                         0 = default 1e-14 (Sec. IV.B leaves it unstated) */
+  double jitter_growth;   /* factor per further retry; 0 = default 10 */
+  int32_t max_jitter_tries; /* retries after the unshifted attempt; 0 = default 8,
+                               negative = none (an indefinite Gram returns
+                               ISDF_E_NOT_PD at once) */
+  int32_t wait_limit_ms;  /* tc_kernel_build: bound of every device-side wait of
+                             its tensor-core kernels, in ms; 0 = default 2000;
+                             larger values are clamped to 60000 */
 } isdf_options;
 
 const char* isdf_last_error(void);
@@ -176,8 +197,9 @@ int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* 
  *   scalar:     (G_PP o G_PP) xi = G o G
  *   gradient c: (dG^c_PP o G_PP) xi~^c = dG^c o G,  dG^c[mu][g] = sum_p d_c phi_p(r_mu) d_c phi_p(r_g)
  * FP64 Cholesky with adaptive Tikhonov retry (Sec. IV.B): lambda = 0, then
- * 1e-14 max(diag) times 10 per retry, at most 8 retries; the lambda used per
- * system is written to jitter_used (host [4], may be NULL).
+ * jitter_init max(diag) times jitter_growth per retry, at most
+ * max_jitter_tries retries (options; NULL = 1e-14, 10, 8); the lambda used
+ * per system is written to jitter_used (host [4], may be NULL).
  * pivots [n_mu] (distinct grid indices in [0, n_g), as isdf_points returns
  * them); xi [n_mu][n_g]; xi_grad [3][n_mu][n_g].  Synchronises `stream`.
  * Errors: ISDF_E_ARG when a pivot index lies outside [0, n_g) (checked on the
@@ -187,7 +209,8 @@ int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* 
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu);
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
              const int32_t* pivots, int n_mu, double* xi, double* xi_grad,
-             double* jitter_used, void* ws, size_t ws_bytes, isdf_stream_t stream);
+             double* jitter_used, const isdf_options* options, void* ws, size_t ws_bytes,
+             isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Jastrow kernels of the ISDF K integrals (Eqs. K1-isdf and K3-isdf):
@@ -203,8 +226,9 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * (overwritten; required).  With sync_check (default) the call returns
  * ISDF_E_NONFINITE when W holds a NaN or Inf (every input value reaches W).
  * ISDF_PREC_FP64 takes any correlator.  The
- * tensor-core precisions take the radial correlator (n_terms = 0, cusp = 1)
- * and multi-centre correlators whose terms have m, n <= 3, o <= 4 and at most
+ * tensor-core precisions take the radial correlator (n_terms = 0, cusp = 1,
+ * no one-body term; CTA-pair kernel) and, on the multi-centre generator,
+ * correlators with the one-body term and those whose terms have m, n <= 3, o <= 4 and at most
  * two distinct E exponents o among the terms with (m, n) != (0, 0), with the
  * nucleus count limited by shared memory (ISDF_E_ARG beyond it; 12 centres
  * with three E-exponent-2 electron-electron-nucleus terms use 198 KB).
@@ -227,6 +251,8 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
  *   dL/dtheta_j = sum_{g != g'} sum_{c<3} (M^c + 2 M^sq K_c)(g,g') dK_c(g,g')/dtheta_j
  *   M^c(g,g') = [(w xi~^c)^T Wbar^c (w xi)]_{g g'},  M^sq with w xi and Wbar^sq,
  * recomputing the M tiles from the factors (nothing of size n_g^2 is stored).
+ * The one-body term (isdf_jastrow chi) has no parameter in theta; it enters
+ * through K_c in the M^sq factor.
  * One nucleus type and at most 30 free terms (else ISDF_E_UNSUPPORTED);
  * precision ISDF_PREC_FP64 or ISDF_PREC_FP32 (pair arithmetic; the
  * reduction is FP64).  dtheta: device [2 + n_terms] FP64 (overwritten).

@@ -44,13 +44,19 @@ class IsdfJastrow(ctypes.Structure):
                 ("nuc_type", I32 * ISDF_MAX_NUC),
                 ("b", ctypes.c_double * ISDF_MAX_TYPES),
                 ("mno", (I32 * 3) * ISDF_MAX_TERMS),
-                ("coef", (ctypes.c_double * ISDF_MAX_TERMS) * ISDF_MAX_TYPES)]
+                ("coef", (ctypes.c_double * ISDF_MAX_TERMS) * ISDF_MAX_TYPES),
+                ("chi_a", ctypes.c_double * ISDF_MAX_TYPES),
+                ("chi_b", ctypes.c_double * ISDF_MAX_TYPES),
+                ("n_elec", I32)]
 
 
 class IsdfOptions(ctypes.Structure):
-    """ctypes mirror of isdf_options (precision, fold intervals, checks, timing)."""
+    """ctypes mirror of isdf_options (precision, fold intervals, checks, timing,
+    jitter policy of the fit, wait limit)."""
     _fields_ = [("precision", I32), ("kchunk", I32), ("s2_kchunk", I32), ("sync_check", I32),
-                ("debug_flags", I32), ("stage_ms", ctypes.POINTER(ctypes.c_float))]
+                ("debug_flags", I32), ("stage_ms", ctypes.POINTER(ctypes.c_float)),
+                ("jitter_init", ctypes.c_double), ("jitter_growth", ctypes.c_double),
+                ("max_jitter_tries", I32), ("wait_limit_ms", I32)]
 
 
 # name -> (restype, argtypes)
@@ -66,7 +72,7 @@ SIGNATURES = {
     "isdf_points_fixed_rank": (INT, [P, P, P, I64, INT, INT, INT, P, ctypes.POINTER(INT), P, SZ,
                                      P]),
     "isdf_fit_workspace": (SZ, [I64, INT, INT]),
-    "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, SZ, P]),
+    "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, P, SZ, P]),
     "isdf_gather_pivots": (INT, [P, P, I64, INT, P, INT, P, P, P]),
     "tc_kernel_build_workspace": (SZ, [I64, INT, I64, I64, INT, ctypes.POINTER(IsdfJastrow)]),
     "tc_kernel_build": (INT, [P, P, P, P, I64, INT, I64, I64, ctypes.POINTER(IsdfJastrow),

@@ -35,8 +35,10 @@ def _req(t: torch.Tensor, dtype, name: str):
     return t
 
 
-def jastrow_struct(nuc_xyz, nuc_type, mno, coef, b, d: float, cusp: bool = True) -> C.IsdfJastrow:
-    """Fill the host isdf_jastrow struct from arrays (see include/isdftc.h)."""
+def jastrow_struct(nuc_xyz, nuc_type, mno, coef, b, d: float, cusp: bool = True,
+                   chi_a=None, chi_b=None, n_elec: int = 0) -> C.IsdfJastrow:
+    """Fill the host isdf_jastrow struct from arrays (see include/isdftc.h);
+    chi_a/chi_b (per type) and n_elec give the one-body term of Eq. tau-def."""
     import numpy as np
     J = C.IsdfJastrow()
     nuc_xyz = np.asarray(nuc_xyz, dtype=np.float64).reshape(-1, 3)
@@ -57,12 +59,24 @@ def jastrow_struct(nuc_xyz, nuc_type, mno, coef, b, d: float, cusp: bool = True)
     for k in range(mno.shape[0]):
         for c in range(3):
             J.mno[k][c] = int(mno[k, c])
+    if chi_a is not None:
+        ca = np.atleast_1d(np.asarray(chi_a, dtype=np.float64))
+        cb = np.atleast_1d(np.asarray(chi_b, dtype=np.float64))
+        if ca.shape[0] != b.shape[0] or cb.shape[0] != b.shape[0]:
+            raise ValueError("chi_a and chi_b need one value per nucleus type")
+        for t in range(b.shape[0]):
+            J.chi_a[t] = float(ca[t])
+            J.chi_b[t] = float(cb[t])
+        J.n_elec = int(n_elec)
     return J
 
 
 def jastrow_from(obj) -> C.IsdfJastrow:
-    """isdf_jastrow from any object with nuc_xyz, nuc_type, mno, coef, b, d, cusp."""
-    return jastrow_struct(obj.nuc_xyz, obj.nuc_type, obj.mno, obj.coef, obj.b, obj.d, obj.cusp)
+    """isdf_jastrow from any object with nuc_xyz, nuc_type, mno, coef, b, d, cusp
+    (and optionally chi_a, chi_b, n_elec)."""
+    return jastrow_struct(obj.nuc_xyz, obj.nuc_type, obj.mno, obj.coef, obj.b, obj.d, obj.cusp,
+                          getattr(obj, "chi_a", None), getattr(obj, "chi_b", None),
+                          getattr(obj, "n_elec", 0))
 
 
 def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz) -> Tuple[torch.Tensor, torch.Tensor]:
@@ -119,8 +133,11 @@ def isdf_points_fixed_rank(phi, dphi, w, n_ch_phi: int, n_ch_grad: int,
     return piv[:out.value]
 
 
-def isdf_fit(phi, dphi, pivots):
-    """xi [n_mu][n_g], xi~ [3][n_mu][n_g] and the jitter per system."""
+def isdf_fit(phi, dphi, pivots, jitter_init: float = 0.0, jitter_growth: float = 0.0,
+             max_jitter_tries: int = 0):
+    """xi [n_mu][n_g], xi~ [3][n_mu][n_g] and the jitter per system.  The
+    jitter policy (Sec. IV.B): 0 selects the library defaults (1e-14 of the
+    largest diagonal, x10 per retry, 8 retries); max_jitter_tries < 0 allows none."""
     lib = C.load()
     dev = phi.device
     _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(pivots, torch.int32, "pivots")
@@ -130,8 +147,11 @@ def isdf_fit(phi, dphi, pivots):
     xig = torch.empty((3, n_mu, n_g), dtype=f64, device=dev)
     jit = (ctypes.c_double * 4)()
     ws = _ws(lib.isdf_fit_workspace(n_g, n_orb, n_mu), dev)
+    opt = options(jitter_init=jitter_init, jitter_growth=jitter_growth,
+                  max_jitter_tries=max_jitter_tries)
     C.check("isdf_fit", lib.isdf_fit(_ptr(phi), _ptr(dphi), n_g, n_orb, _ptr(pivots), n_mu,
-                                     _ptr(xi), _ptr(xig), jit, _ptr(ws), ws.numel(), _stream()))
+                                     _ptr(xi), _ptr(xig), jit, ctypes.byref(opt), _ptr(ws),
+                                     ws.numel(), _stream()))
     return xi, xig, list(jit)
 
 
@@ -149,10 +169,14 @@ def isdf_gather_pivots(phi, dphi, pivots):
 
 
 def options(precision="bf16x3", kchunk: int = 0, s2_kchunk: int = 0, sync_check: bool = True,
-            debug_flags: int = 0, stage_ms=None) -> C.IsdfOptions:
-    """isdf_options for the W build; 0 selects the library defaults."""
+            debug_flags: int = 0, stage_ms=None, jitter_init: float = 0.0,
+            jitter_growth: float = 0.0, max_jitter_tries: int = 0,
+            wait_limit_ms: int = 0) -> C.IsdfOptions:
+    """isdf_options for the W build and the fit; 0 selects the library defaults."""
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return C.IsdfOptions(prec, kchunk, s2_kchunk, int(sync_check), debug_flags, stage_ms)
+    return C.IsdfOptions(prec, kchunk, s2_kchunk, int(sync_check), debug_flags, stage_ms,
+                         float(jitter_init), float(jitter_growth), int(max_jitter_tries),
+                         int(wait_limit_ms))
 
 
 class KernelBuilder:
@@ -162,7 +186,7 @@ class KernelBuilder:
     def __init__(self, grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, precision="bf16x3",
                  g_begin: int = 0, g_end: Optional[int] = None, kchunk: int = 0,
                  s2_kchunk: int = 0, sync_check: bool = True, debug_flags: int = 0,
-                 time_stages: bool = False):
+                 time_stages: bool = False, wait_limit_ms: int = 0):
         lib = C.load()
         for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad")):
             _req(t, f64, n)
@@ -176,7 +200,7 @@ class KernelBuilder:
         self.stage_ms = (ctypes.c_float * 2)() if time_stages else None
         self.opt = options(precision, kchunk, s2_kchunk, sync_check, debug_flags,
                            ctypes.cast(self.stage_ms, ctypes.POINTER(ctypes.c_float))
-                           if time_stages else None)
+                           if time_stages else None, wait_limit_ms=wait_limit_ms)
         n_gs = max(self.g_end - self.g_begin, 0)  # an empty slice is rejected by the library
         self.W = torch.empty((4, self.n_mu, self.n_mu), dtype=f64, device=self.dev)
         self.calG = torch.empty((4, self.n_mu, n_gs), dtype=f64, device=self.dev)

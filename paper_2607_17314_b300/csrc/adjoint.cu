@@ -15,6 +15,7 @@
 // taken once per group, and the derivative of term k is the (group, power)
 // combination that it belongs to.  Parameters: theta = (d, b, c_0 .. c_{K-1}) for a
 // correlator with one nucleus type.
+#include "jastrow.cuh"
 #include "linalg.cuh"
 
 namespace isdf {
@@ -36,6 +37,7 @@ struct AdjArgs {
   int64_t g_begin, g_end;  // outer points of this call (the sums are additive over slices)
   int n_mu;
   const T* tab;    // [n_g][n_nuc][8]: A, gA(3), A_b, gA_b(3)
+  const double* chi;  // [g_end - g_begin][3] grad chi / (N - 1) (one-body term), or null
   double* sums;    // [2 + NGRP * 5]: d, b, then (group, E power) sums
   T gc[10][5];     // C_G[o] = sum of c_k over the terms of group G with E power o
 };
@@ -184,7 +186,13 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
         gy += cA * ti[2];
         gz += cA * ti[3];
       }
-      const T Kx = gx + cE * dEdr * ex, Ky = gy + cE * dEdr * ey, Kz = gz + cE * dEdr * ez;
+      T Kx = gx + cE * dEdr * ex, Ky = gy + cE * dEdr * ey, Kz = gz + cE * dEdr * ez;
+      if (a.chi) {  // parameter-free, so it enters only through K_c in the M^sq factor
+        const double* hc = a.chi + 3 * (g - a.g_begin);
+        Kx += (T)hc[0];
+        Ky += (T)hc[1];
+        Kz += (T)hc[2];
+      }
       const T msq2 = (T)2 * M[3][j];
       const T cx = M[0][j] + msq2 * Kx, cy = M[1][j] + msq2 * Ky, cz = M[2][j] + msq2 * Kz;
       const T ce = cx * ex + cy * ey + cz * ez;  // coef . e_ij
@@ -291,6 +299,7 @@ int run_adjoint(const double* grid, const double* w, const double* xi, const dou
   T* Bh = cv.take<T>(4 * plane);
   T* tab = cv.take<T>((size_t)n_g * J.n_nuc * 8);
   double* sums = cv.take<double>(2 + NGRP * 5);
+  double* chi = cv.take<double>((size_t)3 * n_g);
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   // Bhat^c = Wbar^c (w xi)
   Dgemm g;
@@ -315,6 +324,11 @@ int run_adjoint(const double* grid, const double* w, const double* xi, const dou
   AdjArgs<T> a;
   a.Ah = Ah; a.Bh = Bh; a.grid = grid; a.n_g = n_g; a.n_mu = n_mu; a.tab = tab; a.sums = sums;
   a.g_begin = g_begin; a.g_end = g_end;
+  a.chi = nullptr;
+  if (chi_on(J)) {
+    ISDF_TRY(chi_table(grid, g_begin, g_end - g_begin, J, chi, s));
+    a.chi = chi;
+  }
   double gc[NGRP][5] = {};
   for (int k = 0; k < J.n_terms; ++k)
     gc[grp_of(J.mno[k][0], J.mno[k][1])][J.mno[k][2]] += J.coef[0][k];
@@ -340,6 +354,7 @@ size_t adjoint_ws(int64_t n_g, int n_mu, int n_nuc, int precision) {
   c.take<unsigned char>(4 * plane * el);
   c.take<unsigned char>((size_t)n_g * n_nuc * 8 * el);
   c.take<double>(2 + NGRP * 5);
+  c.take<double>((size_t)3 * n_g);
   return c.off;
 }
 

@@ -6,6 +6,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "jastrow.cuh"
 
 namespace isdf {
 
@@ -33,7 +34,7 @@ int points_ranks(const double*, const double*, const double*, int64_t, int, int,
                  int*, void*, size_t, cudaStream_t);
 size_t fit_ws(int64_t, int, int);
 int fit(const double*, const double*, int64_t, int, const int32_t*, int, double*, double*,
-        double*, void*, size_t, cudaStream_t);
+        double*, double, double, int, void*, size_t, cudaStream_t);
 int gather_pivots(const double*, const double*, int64_t, int, const int32_t*, int, double*,
                   double*, cudaStream_t);
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J);
@@ -95,6 +96,13 @@ static int check_jastrow(const isdf_jastrow* J) {
     for (int k = 0; k < J->n_terms; ++k)
       ISDF_ARG(std::isfinite(J->coef[t][k]), "Jastrow coefficient not finite");
   }
+  if (chi_on(*J)) {
+    ISDF_ARG(J->n_elec >= 2, "the one-body term needs n_elec >= 2");
+    ISDF_ARG(J->n_nuc >= 1, "the one-body term needs nuclei");
+    for (int t = 0; t < J->n_types; ++t)
+      ISDF_ARG(std::isfinite(J->chi_a[t]) && std::isfinite(J->chi_b[t]) && J->chi_b[t] > 0.0,
+               "one-body term: chi_a finite and chi_b positive");
+  }
   return ISDF_OK;
 }
 
@@ -105,7 +113,7 @@ using namespace isdf;
 extern "C" {
 
 const char* isdf_last_error(void) { return g_err; }
-int isdf_abi_version(void) { return 1; }
+int isdf_abi_version(void) { return 2; }
 uint64_t isdf_kernel_launches(void) { return g_launches.load(); }
 
 size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g) { return eval_orbitals_ws(n_bf, n_g); }
@@ -140,10 +148,19 @@ int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* 
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu) { return fit_ws(n_g, n_orb, n_mu); }
 
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* pivots,
-             int n_mu, double* xi, double* xi_grad, double* jitter_used, void* ws,
-             size_t ws_bytes, isdf_stream_t stream) {
-  return fit(phi, dphi, n_g, n_orb, pivots, n_mu, xi, xi_grad, jitter_used, ws, ws_bytes,
-             (cudaStream_t)stream);
+             int n_mu, double* xi, double* xi_grad, double* jitter_used,
+             const isdf_options* options, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  double j0 = 1e-14, growth = 10.0;
+  int tries = 8;
+  if (options) {
+    ISDF_ARG(options->jitter_init >= 0.0 && options->jitter_growth >= 0.0,
+             "negative jitter policy");
+    if (options->jitter_init > 0.0) j0 = options->jitter_init;
+    if (options->jitter_growth > 0.0) growth = options->jitter_growth;
+    if (options->max_jitter_tries != 0) tries = options->max_jitter_tries < 0 ? 0 : options->max_jitter_tries;
+  }
+  return fit(phi, dphi, n_g, n_orb, pivots, n_mu, xi, xi_grad, jitter_used, j0, growth, tries,
+             ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
@@ -168,8 +185,10 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
   ISDF_ARG(n_g > 0 && n_mu > 0, "empty sizes");
   ISDF_ARG(g_begin >= 0 && g_begin < g_end && g_end <= n_g, "bad grid slice");
   ISDF_ARG(n_g < (1ll << 31) - 64, "n_g too large");
-  isdf_options opt = {ISDF_PREC_BF16X3, 0, 0, 1, 0, nullptr};
+  isdf_options opt = {ISDF_PREC_BF16X3, 0, 0, 1, 0, nullptr, 0.0, 0.0, 0, 0};
   if (options) opt = *options;
+  ISDF_ARG(opt.wait_limit_ms >= 0, "negative wait limit");
+  const WaitLimitScope wait_scope(opt.wait_limit_ms);
   cudaStream_t s = (cudaStream_t)stream;
   if (opt.precision == ISDF_PREC_FP64) {
     return wbuild_fp64(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, W, calG,

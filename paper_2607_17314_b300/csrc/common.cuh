@@ -83,7 +83,24 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Wait limit for every spin in this library (nanoseconds).
+// Default limit of every device-side spin in this library (nanoseconds), and
+// the range a caller may set through isdf_options.wait_limit_ms.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr int kWaitLimitMaxMs = 60000;
+
+// Limit the kernels launched by the calling host thread use: the default,
+// or the caller's option for the duration of one call (WaitLimitScope).
+inline uint64_t& wait_limit_ns() {
+  static thread_local uint64_t v = kWaitLimitNs;
+  return v;
+}
+
+struct WaitLimitScope {
+  uint64_t saved;
+  explicit WaitLimitScope(int ms) : saved(wait_limit_ns()) {
+    if (ms > 0) wait_limit_ns() = (uint64_t)(ms < kWaitLimitMaxMs ? ms : kWaitLimitMaxMs) * 1000000ull;
+  }
+  ~WaitLimitScope() { wait_limit_ns() = saved; }
+};
 
 }  // namespace isdf

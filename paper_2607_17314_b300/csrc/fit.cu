@@ -100,8 +100,8 @@ size_t fit_ws(int64_t n_g, int n_orb, int n_mu) {
 }
 
 int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* piv,
-        int n_mu, double* xi, double* xig, double* jitter_used, void* ws, size_t ws_bytes,
-        cudaStream_t s) {
+        int n_mu, double* xi, double* xig, double* jitter_used, double jitter_init,
+        double jitter_growth, int max_tries, void* ws, size_t ws_bytes, cudaStream_t s) {
   ISDF_ARG(phi && dphi && piv && xi && xig, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
   Carve cv(ws, ws_bytes);
@@ -183,12 +183,12 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
         ISDF_LAUNCH_CHECK();
         ISDF_CUDA(cudaMemcpyAsync(&maxd, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
         ISDF_CUDA(cudaStreamSynchronize(s));
-        lam = 1e-14 * maxd;
+        lam = jitter_init * maxd;
       } else {
-        lam *= 10.0;
+        lam *= jitter_growth;
       }
-      if (++tries > 8) {
-        set_error("Gram matrix %d not positive definite after %d jitter retries", ch, 8);
+      if (++tries > max_tries) {
+        set_error("Gram matrix %d not positive definite after %d jitter retries", ch, max_tries);
         return ISDF_E_NOT_PD;
       }
     }

@@ -62,6 +62,39 @@ __device__ __forceinline__ void bh_grad(const isdf_jastrow& J, const BhTable& T,
   out[2] = gz + s * dz;
 }
 
+// One-body term of Eq. tau-def: on when some type has chi_a != 0.
+__host__ __device__ inline bool chi_on(const isdf_jastrow& J) {
+  for (int t = 0; t < J.n_types && t < ISDF_MAX_TYPES; ++t)
+    if (J.chi_a[t] != 0.0) return true;
+  return false;
+}
+
+// grad chi(r) / (N - 1) at the point (x, y, z): the one-body part of every
+// ordered pair's electron-1 gradient, chi(r) = sum_I a_t r_I / (1 + beta_t r_I)
+// (zero direction on a nucleus).
+__device__ __forceinline__ void chi_grad_pair(const isdf_jastrow& J, double x, double y, double z,
+                                              double out[3]) {
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int I = 0; I < J.n_nuc; ++I) {
+    const int t = J.nuc_type[I];
+    const double vx = x - J.nuc_xyz[I][0], vy = y - J.nuc_xyz[I][1], vz = z - J.nuc_xyz[I][2];
+    const double r = sqrt(vx * vx + vy * vy + vz * vz);
+    const double den = 1.0 + J.chi_b[t] * r;
+    const double s = r > 0.0 ? J.chi_a[t] / (den * den * r) : 0.0;
+    gx += s * vx;
+    gy += s * vy;
+    gz += s * vz;
+  }
+  const double inv = 1.0 / (double)(J.n_elec - 1);
+  out[0] = gx * inv;
+  out[1] = gy * inv;
+  out[2] = gz * inv;
+}
+
+// grad chi / (N - 1) of the points g0 .. g0 + n - 1 into out [n][3] (FP64).
+int chi_table(const double* grid, int64_t g0, int64_t n, const isdf_jastrow& J, double* out,
+              cudaStream_t s);
+
 // Radial correlator u = r / (2 (1 + d r)): grad u = 1 / (2 (1 + d r)^2) e_ij.
 __device__ __forceinline__ void radial_grad(double d, const double* ri, const double* rj,
                                             double out[3]) {

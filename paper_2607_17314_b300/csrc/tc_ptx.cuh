@@ -48,17 +48,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: returns false (and sets *abort and the error word) when the
-// barrier phase did not complete within kWaitLimitNs or another role already
+// barrier phase did not complete within limit_ns or another role already
 // aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          volatile int* abort_flag, int* err) {
+                                          volatile int* abort_flag, int* err, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   uint64_t t0 = globaltimer_ns();
   uint32_t n = 0;
   while (!mbar_try_wait(bar, parity)) {
     if ((++n & 255u) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicOr(err, DEV_ERR_TIMEOUT);
         return false;
@@ -105,14 +105,15 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
 // Bounded wait with acquire at cluster scope (the phase may include arrivals
 // from the peer CTA); same exit rules as mbar_wait.
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort_flag, int* err) {
+                                                  volatile int* abort_flag, int* err,
+                                                  uint64_t limit_ns) {
   if (mbar_try_wait_cluster(bar, parity)) return true;
   uint64_t t0 = globaltimer_ns();
   uint32_t n = 0;
   while (!mbar_try_wait_cluster(bar, parity)) {
     if ((++n & 255u) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicOr(err, DEV_ERR_TIMEOUT);
         return false;

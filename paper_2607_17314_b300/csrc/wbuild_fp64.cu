@@ -18,6 +18,7 @@ struct S1F64 {
   int64_t g_begin, g_end;
   double* calG;        // [4][n_mu][n_gs]
   BhTable tab;
+  const double* chi;   // [n_gs][3] grad chi / (N - 1) of the outer points, or null
 };
 
 template <bool RADIAL>
@@ -50,6 +51,11 @@ __global__ void __launch_bounds__(256) s1_fp64_kernel(S1F64 a, const __grid_cons
             if (J.cusp) radial_grad(J.d, a.grid + 3 * g, a.grid + 3 * gp, K);
           }
           else bh_grad(J, a.tab, g, gp, a.grid + 3 * g, a.grid + 3 * gp, K);
+          if (a.chi) {
+            K[0] += a.chi[3 * gl];
+            K[1] += a.chi[3 * gl + 1];
+            K[2] += a.chi[3 * gl + 2];
+          }
         }
       }
       Ks[0][kk][gg] = K[0];
@@ -105,7 +111,23 @@ __global__ void bh_table_kernel(const double* grid, int64_t n_g, const __grid_co
   for (int c = 0; c < 3; ++c) dA[3 * e + c] = s * v[c];
 }
 
+__global__ void chi_table_kernel(const double* grid, int64_t g0, int64_t n,
+                                 const __grid_constant__ isdf_jastrow J, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double* r = grid + 3 * (g0 + e);
+  chi_grad_pair(J, r[0], r[1], r[2], out + 3 * e);
+}
+
 }  // namespace
+
+int chi_table(const double* grid, int64_t g0, int64_t n, const isdf_jastrow& J, double* out,
+              cudaStream_t s) {
+  if (n <= 0) return ISDF_OK;
+  chi_table_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(grid, g0, n, J, out);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
 
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J) {
   Carve c(nullptr, 0);
@@ -113,6 +135,7 @@ size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J) {
   int nn = J ? (J->n_terms == 0 ? 0 : J->n_nuc) : ISDF_MAX_NUC;
   c.take<double>((size_t)n_g * nn);
   c.take<double>((size_t)3 * n_g * nn);
+  if (!J || chi_on(*J)) c.take<double>((size_t)3 * n_g);
   return c.off;
 }
 
@@ -138,12 +161,15 @@ int wbuild_fp64(const double* grid, const double* w, const double* xi, const dou
   int* err = cv.take<int>(64);
   double* A = radial ? nullptr : cv.take<double>((size_t)n_g * J.n_nuc);
   double* dA = radial ? nullptr : cv.take<double>((size_t)3 * n_g * J.n_nuc);
+  const int64_t n_gs = g_end - g_begin;
+  double* chi = chi_on(J) ? cv.take<double>((size_t)3 * n_g) : nullptr;
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   if (!radial) {
     ISDF_TRY(bh_table(grid, n_g, J, A, dA, s));
     a.tab.A = A; a.tab.dA = dA;
   }
-  const int64_t n_gs = g_end - g_begin;
+  a.chi = chi;
+  if (chi) ISDF_TRY(chi_table(grid, g_begin, n_gs, J, chi, s));
   dim3 grd((unsigned)ceil_div(n_gs, FBG), (unsigned)ceil_div(n_mu, FBM));
   if (radial) s1_fp64_kernel<true><<<grd, 256, 0, s>>>(a, J);
   else s1_fp64_kernel<false><<<grd, 256, 0, s>>>(a, J);

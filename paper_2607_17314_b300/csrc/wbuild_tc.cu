@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "jastrow.cuh"
 #include "linalg.cuh"
 #include "tc_ptx.cuh"
 
@@ -249,6 +250,7 @@ struct S1Params {
   uint32_t tab_bytes;    // bytes of the per-row nucleus table
   double* calG;          // [4][n_mu][g_end - g_begin]
   int* err;
+  uint64_t wait_ns;      // bound of every mbarrier wait
   int debug;
   // multi-centre correlator (BH kernels only)
   int n_nuc;
@@ -346,7 +348,7 @@ __device__ __forceinline__ void s1_load_a(const CUtensorMap* mA0, const CUtensor
     const int mu0 = (int)(tile / p.n_g_tiles) * C::BM;
     for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
       const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err)) return;
+      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err, p.wait_ns)) return;
       if (skip) {  // fault-path test: this stage's operand never arrives
         skip = false;
         continue;
@@ -369,7 +371,7 @@ __device__ __forceinline__ void s1_load_coords(const S1Params& p, const S1Smem& 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
       const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
-      if (!tc::mbar_wait(&sm.cempty[cs], ph ^ 1, sm.abort_flag, p.err)) return;
+      if (!tc::mbar_wait(&sm.cempty[cs], ph ^ 1, sm.abort_flag, p.err, p.wait_ns)) return;
       uint8_t* dst = sm.ring + cs * p.cbytes;
       tc::mbar_arrive_expect_tx(&sm.cfull[cs], p.cbytes);
       bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &sm.cfull[cs]);
@@ -392,11 +394,11 @@ __device__ __forceinline__ void s1_issue_mma(const S1Params& p, const S1Smem& sm
     for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
       const int64_t kb = ch * p.kchunk;
       const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-      if (!tc::mbar_wait(sm.acc_empty, (u & 1) ^ 1, sm.abort_flag, p.err)) return;
+      if (!tc::mbar_wait(sm.acc_empty, (u & 1) ^ 1, sm.abort_flag, p.err, p.wait_ns)) return;
       tc::tc_fence_after();
       for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-        if (!tc::mbar_wait(&sm.full[s], ph, sm.abort_flag, p.err)) return;
+        if (!tc::mbar_wait(&sm.full[s], ph, sm.abort_flag, p.err, p.wait_ns)) return;
         tc::tc_fence_after();
         const uint32_t a_base = tc::smem_u32(sm.stages + s * C::STAGE);
         const uint32_t b_base = a_base + C::A_BYTES;
@@ -456,7 +458,7 @@ __device__ __forceinline__ void s1_gen_radial(const S1Params& p, const S1Smem& s
     for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
       const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
       const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
-      if (!tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err)) return;
+      if (!tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err, p.wait_ns)) return;
       const uint32_t cbase = tc::smem_u32(sm.ring + cs * p.cbytes);
       float dx[8], dy[8], dz[8];
 #pragma unroll
@@ -480,7 +482,7 @@ __device__ __forceinline__ void s1_gen_radial(const S1Params& p, const S1Smem& s
           for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
         }
       }
-      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err)) return;
+      if (!tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err, p.wait_ns)) return;
       s1_store_b<C, LIMBS>(sm, s, row, kc, pk);
     }
   }
@@ -531,7 +533,7 @@ __device__ __forceinline__ void s1_gen_bh(const S1Params& p, const S1Smem& sm, i
     for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
       const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
       const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
-      const bool okc = tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err);
+      const bool okc = tc::mbar_wait(&sm.cfull[cs], cph, sm.abort_flag, p.err, p.wait_ns);
       if (!__all_sync(0xffffffffu, okc)) return;
       const uint32_t cbase = tc::smem_u32(sm.ring + cs * p.cbytes);
       float dx[8], dy[8], dz[8], fr[8], ce[8], gx[8], gy[8], gz[8];
@@ -626,7 +628,7 @@ __device__ __forceinline__ void s1_gen_bh(const S1Params& p, const S1Smem& sm, i
           for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
         }
       }
-      const bool oke = tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err);
+      const bool oke = tc::mbar_wait(&sm.empty[s], ph ^ 1, sm.abort_flag, p.err, p.wait_ns);
       if (!__all_sync(0xffffffffu, oke)) return;
       s1_store_b<C, LIMBS>(sm, s, row, kc, pk);
     }
@@ -648,7 +650,7 @@ __device__ __forceinline__ void s1_epilogue(const S1Params& p, const S1Smem& sm,
     for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
       // tcgen05.ld/st/wait are warp-collective (.sync.aligned): every lane
       // leaves the spin-wait and the divergent stores before reaching them
-      const bool ok = tc::mbar_wait(sm.acc_full, u & 1, sm.abort_flag, p.err);
+      const bool ok = tc::mbar_wait(sm.acc_full, u & 1, sm.abort_flag, p.err, p.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) return;
       tc::tc_fence_after();
       const bool first = (ch == 0), last = (ch + 1 == n_chunks);
@@ -901,7 +903,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         const int mu0 = (int)(tile / p.n_g_tiles) * 2 * C::BM + (int)rank * C::BM;
         for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
           const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) goto done;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) goto done;
           if (skip) {  // fault-path test: this stage's operand never arrives
             skip = false;
             continue;
@@ -927,7 +929,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
       for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
         for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
           const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
-          if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err)) goto done;
+          if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err, p.wait_ns)) goto done;
           uint8_t* dst = ring + cs * C::C_BYTES;
           tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
           bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &cfull[cs]);
@@ -944,11 +946,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
           const int64_t kb = ch * p.kchunk;
           const int64_t ke = kb + p.kchunk < p.n_k ? kb + p.kchunk : p.n_k;
-          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err)) goto done;
+          if (!tc::mbar_wait(acc_empty, (u & 1) ^ 1, abort_flag, p.err, p.wait_ns)) goto done;
           tc::tc_fence_after();
           for (int64_t k0 = kb; k0 < ke; k0 += C::BK, ++it) {
             const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) goto done;
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err, p.wait_ns)) goto done;
             tc::tc_fence_after();
             const uint32_t a_base = tc::smem_u32(stages + s * C::STAGE);
             const uint32_t b_base = a_base + C::A_BYTES;
@@ -992,7 +994,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         if (NGRP > 1 && (int)(it % NGRP) != grp) continue;
         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
         const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
-        const bool okc = tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err);
+        const bool okc = tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err, p.wait_ns);
         if (!__all_sync(0xffffffffu, okc)) goto done;
         const uint32_t cbase = tc::smem_u32(ring + cs * C::C_BYTES);
         float dx[C::PTS], dy[C::PTS], dz[C::PTS];
@@ -1030,7 +1032,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
             }
           }
         }
-        const bool oke = tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err);
+        const bool oke = tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns);
         if (!__all_sync(0xffffffffu, oke)) goto done;
         const uint32_t bsm = tc::smem_u32(stages + s * C::STAGE + C::A_BYTES);
 #pragma unroll
@@ -1067,7 +1069,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
       const int64_t g_tile = tile % p.n_g_tiles;
       const int mu = (int)(tile / p.n_g_tiles) * 2 * C::BM + (int)rank * C::BM + 32 * quad + lane;
       for (int64_t ch = 0; ch < n_chunks; ++ch, ++u) {
-        const bool ok = tc::mbar_wait(acc_full, u & 1, abort_flag, p.err);
+        const bool ok = tc::mbar_wait(acc_full, u & 1, abort_flag, p.err, p.wait_ns);
         if (!__all_sync(0xffffffffu, ok)) goto done;
         tc::tc_fence_after();
         const bool first = (ch == 0), last = (ch + 1 == n_chunks);
@@ -1143,6 +1145,7 @@ struct GemmParams {
   int64_t ldo, out_bs;
   double scale;
   int* err;
+  uint64_t wait_ns;       // bound of every mbarrier wait
 };
 
 template <int LIMBS>
@@ -1203,7 +1206,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
         uint32_t it = 0;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
           const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err)) break;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) break;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
           uint8_t* base = smem + s * C::STAGE;
           const int32_t x = (int32_t)(kt * C::BK);
@@ -1221,12 +1224,12 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
         for (int64_t f = 0; f < n_folds; ++f) {
           const int64_t fb = kt0 + f * p.fold_tiles;
           const int64_t fe = fb + p.fold_tiles < kt1 ? fb + p.fold_tiles : kt1;
-          if (!tc::mbar_wait(acc_empty, (f & 1) ^ 1, abort_flag, p.err)) break;
+          if (!tc::mbar_wait(acc_empty, (f & 1) ^ 1, abort_flag, p.err, p.wait_ns)) break;
           tc::tc_fence_after();
           bool ok = true;
           for (int64_t kt = fb; kt < fe; ++kt, ++it) {
             const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
-            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+            if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
             tc::tc_fence_after();
             const uint32_t base = tc::smem_u32(smem + s * C::STAGE);
 #pragma unroll
@@ -1255,7 +1258,7 @@ __global__ void __launch_bounds__(GC<LIMBS>::THREADS, 1)
       for (int64_t f = 0; f < n_folds; ++f) {
         // warp-collective tcgen05.ld/st/wait: reconverge after the spin-wait
         // and after the divergent stores
-        const bool ok = tc::mbar_wait(acc_full, f & 1, abort_flag, p.err);
+        const bool ok = tc::mbar_wait(acc_full, f & 1, abort_flag, p.err, p.wait_ns);
         if (!__all_sync(0xffffffffu, ok)) break;
         tc::tc_fence_after();
         const bool first = (f == 0), last = (f + 1 == n_folds);
@@ -1350,6 +1353,7 @@ int splitgemm(int limbs, int batch, const void* const* A, const void* const* B, 
   p.kchunks = (int)ceil_div(p.k_tiles, p.kchunk_tiles);
   p.batch = batch;
   p.out = out; p.ldo = ldo; p.out_bs = out_bs; p.scale = scale; p.err = err;
+  p.wait_ns = wait_limit_ns();
   int64_t units = (int64_t)p.m_tiles * p.n_tiles * p.kchunks * batch;
   ISDF_ARG(units < (1ll << 31), "too many GEMM work units");
   if (limbs == 2) {
@@ -1438,8 +1442,9 @@ __device__ __forceinline__ double poly_a(const double* c, int n, const double* a
 
 // Per point g (padded; padding points at the origin) and nucleus I, in FP64:
 // A = b r/(1 + b r), grad A = b/(1 + b r)^2 e_gI (zero on the nucleus), the
-// slots of the stage-1 multi-centre generator, f(g) = sum_I P0,0(A) grad A and
-// the A_{gI} block table that the coordinate ring streams.
+// slots of the stage-1 multi-centre generator, f(g) = sum_I P0,0(A) grad A
+// (plus grad chi(r_g)/(N-1) with the one-body term) and the A_{gI} block table
+// that the coordinate ring streams.
 __global__ void bh_tc_table_kernel(const double* __restrict__ grid, int64_t n_g, int64_t n_k,
                                    const __grid_constant__ isdf_jastrow J,
                                    const __grid_constant__ BhTc K, float* __restrict__ rowslots,
@@ -1475,6 +1480,13 @@ __global__ void bh_tc_table_kernel(const double* __restrict__ grid, int64_t n_g,
     fy += p00 * dc * vy;
     fz += p00 * dc * vz;
     ajtab[(g >> 5) * J.n_nuc * 32 + I * 32 + (g & 31)] = (float)A;
+  }
+  if (chi_on(J)) {  // the one-body term of Eq. tau-def joins the inner-point-free part
+    double h[3];
+    chi_grad_pair(J, x, y, z, h);
+    fx += h[0];
+    fy += h[1];
+    fz += h[2];
   }
   fvec[g] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
 }
@@ -1534,7 +1546,7 @@ static TcLayout tc_layout(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end,
   return L;
 }
 
-static bool tc_radial(const isdf_jastrow& J) { return J.n_terms == 0 && J.cusp; }
+static bool tc_radial(const isdf_jastrow& J) { return J.n_terms == 0 && J.cusp && !chi_on(J); }
 
 // Multi-centre tables: nuclei x float4 slots per point (0 for the radial
 // correlator; the largest accepted layout when J is unknown).
@@ -1647,6 +1659,7 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
   p.d = (float)J.d;
   p.calG = calG;
   p.err = err;
+  p.wait_ns = wait_limit_ns();
   p.debug = opt.debug_flags;
   p.n_nuc = radial ? 0 : J.n_nuc;
   p.cbytes = S1C<2, false>::C_BASE + 4u * S1C<2, false>::BK * (uint32_t)p.n_nuc;

@@ -41,13 +41,34 @@ def test_binding_covers_header(lib):
     assert set(declared_functions()) == set(_capi.SIGNATURES)
 
 
-def test_struct_layout_matches_header():
-    """Field offsets of the ctypes mirrors follow the C layout rules."""
+def test_struct_layout_matches_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal the C compiler's for
+    the header's structs (a C program built against include/isdftc.h prints them)."""
+    import subprocess
     from paper_2607_17314_b300 import _capi as C
-    assert ctypes.sizeof(C.IsdfOptions) == 32 and C.IsdfOptions.stage_ms.offset == 24
-    assert C.IsdfJastrow.d.offset == 16
-    assert C.IsdfJastrow.nuc_xyz.offset == 24
-    assert ctypes.sizeof(C.IsdfBasis) == 8 + 4 * 8
+    mirrors = {"isdf_options": C.IsdfOptions, "isdf_jastrow": C.IsdfJastrow,
+               "isdf_basis": C.IsdfBasis}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "isdftc.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            cname, field, val = line.split()
+            got[(cname, field)] = int(val)
+    for cname, cls in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
 
 
 def test_workspace_queries(lib):
@@ -182,7 +203,7 @@ def test_undersized_workspace_rejected_before_launch(lib):
     basis = C.IsdfBasis(4, 3, f, f, f, f)
     J = C.IsdfJastrow()
     J.n_types, J.d, J.cusp, J.b[0] = 1, 1.0, 1, 1.0
-    opt64 = C.IsdfOptions(C.ISDF_PREC_FP64, 0, 0, 1, 0, None)
+    opt64 = C.IsdfOptions(C.ISDF_PREC_FP64, 0, 0, 1, 0, None, 0.0, 0.0, 0, 0)
     calls = {
         "isdf_eval_orbitals": lambda: lib.isdf_eval_orbitals(ctypes.byref(basis), f, 4, f, 64, f,
                                                              f, f, 16, None),
@@ -190,7 +211,7 @@ def test_undersized_workspace_rejected_before_launch(lib):
                                                None),
         "isdf_points_fixed_rank": lambda: lib.isdf_points_fixed_rank(
             f, f, f, 64, 4, 4, 4, f, ctypes.byref(n), f, 16, None),
-        "isdf_fit": lambda: lib.isdf_fit(f, f, 64, 4, f, 8, f, f, None, f, 16, None),
+        "isdf_fit": lambda: lib.isdf_fit(f, f, 64, 4, f, 8, f, f, None, None, f, 16, None),
         "tc_kernel_build": lambda: lib.tc_kernel_build(f, f, f, f, 64, 8, 0, 64, ctypes.byref(J),
                                                        None, f, f, f, 16, None),
         "tc_kernel_build (fp64)": lambda: lib.tc_kernel_build(

@@ -51,6 +51,21 @@ def test_adjoint_matches_oracle(api):
     assert err32 < 1e-4
 
 
+def test_adjoint_with_one_body_term_matches_oracle(api):
+    """With the one-body term of Eq. tau-def (parameter-free, in K_c of the
+    M^sq factor), FP64 at 1e-10 and FP32 at 1e-4 against the oracle."""
+    w, xi, xit, Wbar = _case(n_mu=16, seed=5)
+    jas = wl.with_chi(w.jastrow, [1.0], 2 * w.n_occ, beta=0.9)
+    ref = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, jas, Wbar)
+    ref0 = adjoint.grad(w.grid_xyz, w.grid_w, xi, xit, w.jastrow, Wbar)
+    assert np.linalg.norm(ref - ref0) > 1e-3 * np.linalg.norm(ref)
+    args = (_cu(w.grid_xyz), _cu(w.grid_w), _cu(xi), _cu(xit), api.jastrow_from(jas), _cu(Wbar))
+    g64 = api.tc_kernel_adjoint(*args, precision="fp64").cpu().numpy()
+    g32 = api.tc_kernel_adjoint(*args, precision="fp32").cpu().numpy()
+    assert np.linalg.norm(g64 - ref) < 1e-10 * np.linalg.norm(ref)
+    assert np.linalg.norm(g32 - ref) < 1e-4 * np.linalg.norm(ref)
+
+
 def test_adjoint_matches_fd_of_gpu_forward(api):
     """Central differences (h = 1e-4) of L(theta) evaluated with the FP64 GPU
     forward build, for every parameter."""

@@ -44,6 +44,27 @@ def test_producer_stall_times_out_and_context_survives(api, prec):
     assert err < 1e-4, err
 
 
+def test_wait_limit_option(api):
+    """isdf_options.wait_limit_ms bounds the device waits: the stalled build
+    returns ISDF_E_TIMEOUT well before the default 2 s limit would expire."""
+    import time
+    from paper_2607_17314_b300 import _capi as C
+    w, g, wt, xi, xig = _inputs()
+    J = api.jastrow_from(w.jastrow)
+    bad = api.KernelBuilder(g, wt, xi, xig, J, "bf16x3", debug_flags=1, wait_limit_ms=50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = bad(allow_timeout=True)
+    dt = time.perf_counter() - t0
+    assert st == C.ISDF_E_TIMEOUT
+    assert dt < 1.0, dt
+    W, _ = api.tc_kernel_build(g, wt, xi, xig, J, "bf16x3")
+    assert bool(torch.isfinite(W).all())
+    with pytest.raises(C.IsdfError) as e:
+        api.KernelBuilder(g, wt, xi, xig, J, "bf16x3", wait_limit_ms=-1)()
+    assert e.value.status == C.ISDF_E_ARG
+
+
 def test_bad_arguments_rejected_before_launch(api):
     from paper_2607_17314_b300 import _capi as C
     w, g, wt, xi, xig = _inputs()

@@ -15,7 +15,8 @@ their values).  The oracle runs in a process pool started with spawn.
 Tolerances, per element against the normwise bound: W within 1e-5; calG
 within 5e-5, the size of the two-limb split error (each product misses
 lo*lo and the limbs' own rounding, up to ~3 x 2^-18 of |a b|) and, for the
-multi-centre correlator, of its FP32 generation for pairs of far points;
+multi-centre correlator, of its FP32 generation for pairs of far points
+(also with the one-body cusp term of Eq. tau-def, case benzene_chi);
 the measured maxima are 2.6e-5 and 3.3e-5.  Per channel the calG relative
 Frobenius error stays within 1e-5.  With random xi, W carries heavy
 cancellation, so its relative Frobenius error is not the test here (it is
@@ -44,7 +45,10 @@ def _geometry(name):
         return grid, w, wl.radial_jastrow(xyz)
     atoms, xyz = wl.benzene()
     grid, w = wl.becke_grid(xyz, 14, 50)
-    return grid, w, wl.bh_jastrow(atoms, xyz, wl.BH_TERMS_C3, np.random.default_rng(3001))
+    jas = wl.bh_jastrow(atoms, xyz, wl.BH_TERMS_C3, np.random.default_rng(3001))
+    if name == "benzene_chi":  # with the one-body cusp term (C: Z = 6, H: Z = 1; 42 electrons)
+        jas = wl.with_chi(jas, [6.0, 1.0], 42, beta=1.0)
+    return grid, w, jas
 
 
 def _oracle(name, n_mu=300):
@@ -80,7 +84,7 @@ def api():
 
 @pytest.mark.parametrize("prec,debug", [("bf16x3", 0), ("bf16x6", 0), ("bf16x3", 2),
                                         ("tf32x3", 0)])
-@pytest.mark.parametrize("name", ["radial", "benzene"])
+@pytest.mark.parametrize("name", ["radial", "benzene", "benzene_chi"])
 def test_stage1_and_w_every_element(api, name, prec, debug):
     if (debug or prec == "tf32x3") and name != "radial":
         pytest.skip("the multi-centre correlator has one kernel (BF16 limbs)")

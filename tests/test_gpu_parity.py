@@ -136,6 +136,34 @@ def test_fit(P, h6):
         assert fwd < max(1e-10, 8.0 * kappa * np.finfo(float).eps), (c, fwd, kappa)
 
 
+def test_fit_jitter_policy(P, h6):
+    """The jitter policy of isdf_options (Sec. IV.B's adaptive Tikhonov shift):
+    396 pivots on 24 orbitals (300 distinct pair products) make the scalar Gram
+    singular, so the unshifted factorisation fails; with no retries allowed the
+    fit returns ISDF_E_NOT_PD, and with jitter_init 1e-8 the shift used is
+    1e-8 10^k times the Gram's largest diagonal, for which the solve keeps a
+    backward error of 1e-10."""
+    from paper_2607_17314_b300 import _capi as C
+    w, o = h6
+    rng = np.random.default_rng(7)
+    rest = np.setdiff1d(np.arange(w.n_g), o["res"].pivots)
+    piv = np.concatenate([o["res"].pivots, rng.choice(rest, 300, replace=False)]).astype(np.int32)
+    phi, dphi, pv = cu(o["phi"]), cu(o["dphi"]), cu(piv, torch.int32)
+    with pytest.raises(C.IsdfError) as e:
+        P.isdf_fit(phi, dphi, pv, max_jitter_tries=-1)
+    assert e.value.status == C.ISDF_E_NOT_PD
+    xi, _, jit = P.isdf_fit(phi, dphi, pv, jitter_init=1e-8)
+    Gm = fit.grams(o["phi"], o["dphi"], piv)
+    maxd = float(np.max(np.diag(Gm[0])))
+    k = np.log10(jit[0] / (1e-8 * maxd))
+    assert jit[0] > 0 and abs(k - round(k)) < 1e-9 and 0 <= round(k) <= 8, (jit[0], maxd)
+    G = Gm[0] + jit[0] * np.eye(len(piv))
+    X = host(xi)
+    B = fit.rhs(o["phi"], o["dphi"], piv)[0]
+    back = np.linalg.norm(G @ X - B) / (np.linalg.norm(G) * np.linalg.norm(X))
+    assert back < 1e-10, back
+
+
 def _jas(P, w):
     return P.jastrow_from(w.jastrow)
 
@@ -161,6 +189,26 @@ def test_w_tensor_core(P, h6, prec):
     # short by folding every 512 inner points into an FP32 running sum;
     # both limb counts meet the 1e-5 bar
     assert max(errs) < 1e-5, errs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_w_one_body_term(P, h6, prec):
+    """The radial correlator plus the one-body cusp term of Eq. tau-def (H: Z = 1,
+    N = 2 n_occ electrons): FP64 at 1e-10 and the tensor cores (multi-centre
+    generator, the term in its inner-point-free part) at 1e-5 per channel,
+    against the oracle's W on the same fitted factors."""
+    w, o = h6
+    jas = wl.with_chi(wl.radial_jastrow(w.xyz), [1.0], 2 * w.n_occ, beta=1.2)
+    Wo, calGo = wbuild.build(w.grid_xyz, w.grid_w, o["xi"], o["xit"], jas)
+    W, calG = P.tc_kernel_build(cu(w.grid_xyz), cu(w.grid_w), cu(o["xi"]), cu(o["xit"]),
+                                P.jastrow_from(jas), prec)
+    errs = [rel(host(W[c]), Wo[c]) for c in range(4)]
+    gerrs = [rel(host(calG[c]), calGo[c]) for c in range(4)]
+    print(prec, "one-body term: W rel", errs, "calG rel", gerrs)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert max(errs) < tol and max(gerrs) < tol, (errs, gerrs)
+    # the term changes W: it is not silently dropped
+    assert min(rel(Wo[c], o["W"][c]) for c in range(4)) > 1e-3
 
 
 def test_w_tensor_core_single_cta(P, h6):
