@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--kappa", type=str, default="3,6",
                     help="candidate budgets (multiples of N_mu), comma separated")
+    ap.add_argument("--kchunk", type=int, default=0,
+                    help="stage-1 fold interval in inner points (0: the library default)")
     ap.add_argument("--w-nrad", type=int, default=16)
     ap.add_argument("--w-nmu", type=int, default=1024)
     ap.add_argument("--w-nang", type=int, default=50)
@@ -176,7 +178,8 @@ class ClockSampler:
 
 def make_workload(name):
     from synth import workloads as wl
-    fn = {"h50_chain": wl.h50_chain, "h6_chain": wl.h6_chain}[name]
+    fn = {"h50_chain": wl.h50_chain, "h6_chain": wl.h6_chain,
+          "benzene_c6h6": wl.benzene_c6h6}[name]
     return fn()
 
 
@@ -321,7 +324,7 @@ def run_w_only(args):
     xig = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
     g1 = n_g if args.w_slice <= 0 else min(n_g, args.w_slice)
     kb = api.KernelBuilder(g, wt, xi, xig, api.jastrow_from(jas), args.precision, g_end=g1,
-                           time_stages=True)
+                           kchunk=args.kchunk, time_stages=True)
     for _ in range(max(args.warmup, 1)):
         kb()
     s1, s2 = [], []
@@ -406,12 +409,42 @@ def run_adjoint(args):
                       "dtheta_finite": bool(torch.isfinite(d32).all())}), flush=True)
 
 
-def run_validate(args):
-    """Full-size accuracy of the tensor-core path against the FP64 GPU path (the
-    FP64 GPU path is checked against the FP64 oracle at 1e-10 on the smaller
-    configurations): one pass of the path at the requested precision, then W,
-    D, X and the energies rebuilt in FP64 on the GPU from the same orbitals,
-    pivots and fit."""
+def fit_backward_errors(out, cols_n=128, seed=2):
+    """Backward error of the fit's normal equations on sampled grid columns,
+    ||A X - B|| / (||A|| ||X||) per channel, from the GPU's orbitals at the
+    pivots and at the columns (host FP64 GEMMs; A includes the jitter used)."""
+    phi, dphi, piv = out["phi"], out["dphi"], out["pivots"]
+    n_g = phi.shape[1]
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.choice(n_g, cols_n, replace=False))
+    P = piv.cpu().numpy().astype(np.int64)
+    import torch
+    it = torch.as_tensor(cols, device=phi.device)
+    pc = phi[:, it].cpu().numpy()
+    dc = dphi[:, :, it].cpu().numpy()
+    phiP = out["phiP"].cpu().numpy()             # [n_mu][n_orb]
+    dphiP = out["dphiP"].cpu().numpy()           # [3][n_mu][n_orb]
+    GPP = phiP @ phiP.T
+    G = phiP @ pc
+    X = [out["xi"][:, it].cpu().numpy()] + [out["xig"][c][:, it].cpu().numpy() for c in range(3)]
+    res = []
+    for c in range(4):
+        if c == 0:
+            A, B = GPP * GPP, G * G
+        else:
+            A, B = (dphiP[c - 1] @ dphiP[c - 1].T) * GPP, (dphiP[c - 1] @ dc[c - 1]) * G
+        A = A + out["jitter"][c] * np.eye(A.shape[0])
+        res.append(float(np.linalg.norm(A @ X[c] - B) / (np.linalg.norm(A) * np.linalg.norm(X[c]))))
+        del A, B
+    return res, int(len(P))
+
+
+def run_validate_sampled(args):
+    """The benzene workload end to end at full size (271,800 points, 1200
+    orbitals, N_mu = 8000, two-type correlator): one pass of the path with CUDA
+    event stage times, the fit's backward error on sampled grid columns, and
+    the energies' error against the FP64 GPU path from outer-grid slices (a
+    full FP64 W build with this correlator would take hours)."""
     import torch
     from paper_2607_17314_b300 import api, build, pipeline
     build.build()
@@ -420,7 +453,45 @@ def run_validate(args):
     J = api.jastrow_from(wlw.jastrow)
     inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
                           wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
-    out = pipeline.run(inp, precision=args.precision)
+    events = {}
+    stage_ms = []
+    out = pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms,
+                       kchunk=args.kchunk)
+    torch.cuda.synchronize()
+    st = {k: float(v[0].elapsed_time(v[1])) for k, v in events.items()}
+    back, n_piv = fit_backward_errors(out)
+    n_g, n_mu = inp.n_g, inp.n_mu
+    s1 = stage_ms[0][0] if stage_ms else float("nan")
+    err = sampled_energy_error(api, inp, out, J, args.precision)
+    keys = ("E_K", "E_dU", "E0")
+    print(json.dumps({
+        "mode": "validate_sampled", "workload": args.workload, "precision": args.precision,
+        "n_g": n_g, "n_mu": n_mu, "n_orb": int(out["phi"].shape[0]), "n_occ": inp.n_occ,
+        "pivots": n_piv, "jitter": list(map(float, out["jitter"])), "stages_ms": st,
+        "s1_ms": s1, "s1_alg_tflops": 8.0 * n_mu * n_g * n_g / (s1 * 1e-3) / 1e12,
+        "fit_backward_error_sampled_cols": back,
+        "energies_ha": dict(zip(keys, out["E"])),
+        "energies_err_ha_vs_fp64_gpu": err,
+    }), flush=True)
+
+
+def run_validate(args):
+    """Full-size accuracy of the tensor-core path against the FP64 GPU path (the
+    FP64 GPU path is checked against the FP64 oracle at 1e-10 on the smaller
+    configurations): one pass of the path at the requested precision, then W,
+    D, X and the energies rebuilt in FP64 on the GPU from the same orbitals,
+    pivots and fit."""
+    import torch
+    from paper_2607_17314_b300 import api, build, pipeline
+    if args.workload == "benzene_c6h6":
+        return run_validate_sampled(args)
+    build.build()
+    wlw = make_workload(args.workload)
+    b = wlw.basis
+    J = api.jastrow_from(wlw.jastrow)
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
+                          wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
+    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     W64, calG64 = api.tc_kernel_build(inp.grid, inp.w, out["xi"], out["xig"], J, "fp64")
@@ -465,7 +536,7 @@ def run_assembly(args):
     J = api.jastrow_from(wlw.jastrow)
     inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
                           wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
-    out = pipeline.run(inp, precision=args.precision)
+    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk)
     n_orb, n_mu, n_g, n_occ = wlw.n_orb, wlw.n_mu, inp.n_g, wlw.n_occ
 
     def timed(fn, reps=2):
@@ -614,7 +685,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(events=None, stage_ms=None):
-        return pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms)
+        return pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms,
+                            kchunk=args.kchunk)
 
     for _ in range(max(args.warmup, 0)):
         out = step()

@@ -114,7 +114,7 @@ typedef struct {
                          its FP32 chunk sum before the epilogue folds that sum into
                          the IEEE-rounded FP32 running sum (also in tensor memory;
                          the tile is written to FP64 once); rounded up to a multiple
-                         of 32; 0 = default (1024) */
+                         of 32; 0 = default (512) */
   int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (expired bounded waits, CUDA errors) */
@@ -254,9 +254,13 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
  * The one-body term (isdf_jastrow chi) has no parameter in theta; it enters
  * through K_c in the M^sq factor.
  * One nucleus type and at most 30 free terms (else ISDF_E_UNSUPPORTED);
- * precision ISDF_PREC_FP64 or ISDF_PREC_FP32 (pair arithmetic; the
- * reduction is FP64).  dtheta: device [2 + n_terms] FP64 (overwritten).
- * Asynchronous. */
+ * precision ISDF_PREC_FP64 (M tiles and pair arithmetic in FP64 on CUDA
+ * cores; asynchronous) or ISDF_PREC_FP32: the M tiles of each outer slice of
+ * up to 2048 points as one split-BF16 tcgen05 GEMM (three limbs, FP32
+ * accumulation folded every 256 mu, FP64 output slab [4][slice][n_g] in the
+ * workspace), the pair arithmetic in FP32; it synchronises `stream` at the end
+ * and returns ISDF_E_TIMEOUT if a bounded wait of the GEMM expired.  The
+ * reduction is FP64.  dtheta: device [2 + n_terms] FP64 (overwritten). */
 size_t tc_kernel_adjoint_workspace(int64_t n_g, int n_mu, int n_nuc, int precision);
 int tc_kernel_adjoint(const double* grid_xyz, const double* w, const double* xi,
                       const double* xi_grad, int64_t n_g, int n_mu, const isdf_jastrow* jas,
@@ -356,7 +360,9 @@ int isdf_fit_error(const double* phi, const double* w, int64_t n_g, int n_orb,
  * precision: ISDF_PREC_FP64 (CUDA-core FP64 GEMMs) or ISDF_PREC_BF16X3 /
  * ISDF_PREC_BF16X6 (the D4 and D1 contractions and the two GEMM families of
  * X as split-BF16 tcgen05 GEMMs with FP32 accumulation folded every 256 inner
- * points, X always with three limbs; the element-wise parts in FP64).
+ * points, X always with three limbs; the element-wise parts in FP64);
+ * ISDF_PREC_TF32X3 is accepted and runs as ISDF_PREC_BF16X3 (these GEMMs have
+ * no TF32 form).
  * Asynchronous for FP64.  The tensor-core precisions synchronise `stream`
  * after the D and X contractions to read the pipeline's wait-status word and
  * return ISDF_E_TIMEOUT if a bounded wait expired, or ISDF_E_NONFINITE if D

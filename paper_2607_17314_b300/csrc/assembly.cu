@@ -231,7 +231,7 @@ __global__ void du_left_kernel(const double* __restrict__ Xp, const double* __re
 
 size_t xtc_one_body_ws(int n_mu, int n_orb) {
   Carve c(nullptr, 0);
-  c.take<double>(3 * (size_t)n_mu * n_mu);            // P, T, HQ
+  for (int i = 0; i < 3; ++i) c.take<double>((size_t)n_mu * n_mu);  // P, T, HQ
   c.take<double>(3 * (size_t)n_mu * n_orb);           // Z (3 planes)
   c.take<double>((size_t)n_orb * n_mu);               // Y
   c.take<double>(8 * (size_t)n_mu);                   // G, Xo, v1 (3), vab, v3s, tmp

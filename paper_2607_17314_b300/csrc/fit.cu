@@ -88,14 +88,28 @@ int gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,
   return gather_pivots_err(phi, dphi, n_g, n_orb, piv, n_mu, phiP, dphiP, nullptr, s);
 }
 
+// Workspace of the fit, carved in this order by both the size query and the call.
+struct FitWs {
+  int* err;
+  double *phiP, *dphiP, *GPP, *Gram, *Save, *scal;
+  int* info;
+  void carve(Carve& cv, int n_orb, int n_mu) {
+    err = cv.take<int>(64);
+    phiP = cv.take<double>((size_t)n_mu * n_orb);
+    dphiP = cv.take<double>((size_t)3 * n_mu * n_orb);
+    GPP = cv.take<double>((size_t)n_mu * n_mu);
+    Gram = cv.take<double>((size_t)n_mu * n_mu);
+    Save = cv.take<double>((size_t)n_mu * n_mu);
+    scal = cv.take<double>(2);
+    info = cv.take<int>(1);
+  }
+};
+
 size_t fit_ws(int64_t n_g, int n_orb, int n_mu) {
   (void)n_g;
   Carve c(nullptr, 0);
-  c.take<int>(64);
-  c.take<double>((size_t)4 * n_mu * n_orb);
-  c.take<double>((size_t)3 * n_mu * n_mu);
-  c.take<double>(2);
-  c.take<int>(1);
+  FitWs f;
+  f.carve(c, n_orb, n_mu);
   return c.off;
 }
 
@@ -105,14 +119,12 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
   ISDF_ARG(phi && dphi && piv && xi && xig, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
   Carve cv(ws, ws_bytes);
-  int* err = cv.take<int>(64);
-  double* phiP = cv.take<double>((size_t)n_mu * n_orb);
-  double* dphiP = cv.take<double>((size_t)3 * n_mu * n_orb);
-  double* GPP = cv.take<double>((size_t)n_mu * n_mu);
-  double* Gram = cv.take<double>((size_t)n_mu * n_mu);
-  double* Save = cv.take<double>((size_t)n_mu * n_mu);
-  double* scal = cv.take<double>(2);
-  int* info = cv.take<int>(1);
+  FitWs f;
+  f.carve(cv, n_orb, n_mu);
+  int* err = f.err;
+  double *phiP = f.phiP, *dphiP = f.dphiP, *GPP = f.GPP, *Gram = f.Gram, *Save = f.Save;
+  double* scal = f.scal;
+  int* info = f.info;
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
 
   ISDF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));

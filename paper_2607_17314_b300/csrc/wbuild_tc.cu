@@ -801,7 +801,11 @@ struct S1P {
   static constexpr int GW = 8;              // warps of one generator group
   static constexpr int NGW = GW * NGRP;     // generator warps 2 .. 1 + NGW; group k takes
                                             // the k-steps it with it % NGRP == k
-  static constexpr int NEW = 4;             // epilogue warps
+  // epilogue warps: with one generator group, two per tensor-memory lane
+  // quarter (each folds half of the accumulator columns, halving the fold's
+  // load latency while the MMAs wait for the chunk accumulator)
+  static constexpr int NEW = NGRP == 1 ? 8 : 4;
+  static constexpr int EPH = NEW / 4;       // column parts of one lane quarter
   static constexpr int CW = 2 + NGW + NEW;  // coordinate producer warp
   static constexpr int THREADS = 32 * (CW + 1);
   static constexpr int PTS = BNH * BK / (32 * GW);    // inner points per generator thread
@@ -1060,8 +1064,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
       }
     }
   } else {
-    // epilogue: this CTA's 128 accumulator rows
+    // epilogue: this CTA's 128 accumulator rows (lane quarter warp % 4, column
+    // part (warp - first epilogue warp) / 4 of EPH)
     const int quad = warp & 3;
+    const int part = (warp - 2 - C::NGW) >> 2;
+    constexpr int NBLK = (int)C::ACC_COLS / C::FOLD / C::EPH;  // fold blocks per part
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
     const int64_t n_gs = p.g_end - p.g_begin;
     uint32_t u = 0;
@@ -1075,7 +1082,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         const bool first = (ch == 0), last = (ch + 1 == n_chunks);
         constexpr int FW = C::FOLD;
 #pragma unroll 1
-        for (int blk = 0; blk < (int)C::ACC_COLS / FW; ++blk) {
+        for (int blk = part * NBLK; blk < (part + 1) * NBLK; ++blk) {
           uint32_t r[FW];
           __syncwarp();
           tc::tmem_fold_block_n<FW>(tmem + lane_base + blk * FW,
@@ -1301,7 +1308,7 @@ inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
 
 // Inner points per stage-1 tensor-core accumulation run before each fold into
 // the running sum (stage 2 folds every 256), and grid points per stage-2 CTA.
-constexpr int64_t kDefaultChunk = 1024;
+constexpr int64_t kDefaultChunk = 512;
 constexpr int64_t kS2Range = 8192;
 
 }  // namespace

@@ -219,6 +219,7 @@ __global__ void split_t_kernel(const double* __restrict__ src, int64_t src_rs, i
 
 size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x, int precision) {
   (void)n_orb;
+  if (precision == ISDF_PREC_TF32X3) precision = ISDF_PREC_BF16X3;
   Carve c(nullptr, 0);
   c.take<double>(n_mu);
   c.take<double>(n_g);
@@ -251,9 +252,11 @@ size_t xtc_ws(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x, int prec
 int xtc(const double* phiP, int n_orb, int n_occ, const double* xi, const double* w,
         const double* calG, int64_t n_g, int n_mu, double* D, double* Xp, int n_orb_x,
         int precision, void* ws, size_t ws_bytes, cudaStream_t s) {
+  // the split GEMMs of this contraction have BF16 limbs only: TF32X3 runs as BF16X3
+  if (precision == ISDF_PREC_TF32X3) precision = ISDF_PREC_BF16X3;
   ISDF_ARG(precision == ISDF_PREC_FP64 || precision == ISDF_PREC_BF16X3 ||
                precision == ISDF_PREC_BF16X6,
-           "xtc precision must be FP64, BF16X3 or BF16X6");
+           "xtc precision must be FP64, BF16X3, BF16X6 or TF32X3");
   ISDF_ARG(phiP && xi && w && calG && D, "null pointer argument");
   ISDF_ARG(n_occ >= 1 && n_occ <= n_orb && n_mu > 0 && n_g > 0,
            "bad sizes (n_occ must be in [1, n_orb], n_mu and n_g positive)");
