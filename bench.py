@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--w-only", action="store_true",
                     help="profiling mode: time only the W build on an H50-chain grid with "
                          "--w-nrad radial shells and seeded random xi (N_mu = --w-nmu)")
+    ap.add_argument("--streamed", action="store_true",
+                    help="the W build with xi in pinned host memory, streamed in grid batches")
+    ap.add_argument("--bra", type=int, default=25000)
+    ap.add_argument("--ket", type=int, default=25024)
     ap.add_argument("--adjoint", action="store_true",
                     help="adjoint dW/dtheta on the H20 chain (FP32 and FP64) instead of the main line")
     ap.add_argument("--proposer", action="store_true",
@@ -357,6 +361,58 @@ def run_w_only(args):
                            "w_rel_err_tc_vs_fp64": err}
         out["speedup_tc_over_fp64"] = out["s1_alg_tflops"] / out["fp64_gpu"]["tflops"]
     print(json.dumps(out), flush=True)
+
+
+def run_streamed(args):
+    """The W build with xi and xi~ in pinned host memory (Sec. II.D grid-batched
+    streaming, depth-one prefetch) against the resident build, H50-chain
+    geometry (--w-nrad/--w-nmu), radial correlator, seeded random xi."""
+    import torch
+    from synth import workloads as wl
+    from paper_2607_17314_b300 import api, build
+    build.build()
+    _, xyz = wl.h_chain(50, 1.8)
+    grid, w = wl.becke_grid(xyz, args.w_nrad, args.w_nang)
+    jas = api.jastrow_from(wl.radial_jastrow(xyz))
+    n_g, n_mu = grid.shape[0], args.w_nmu
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234)
+    g = torch.tensor(grid, device="cuda")
+    wt = torch.tensor(w, device="cuda")
+    xi = torch.randn((n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    xig = torch.randn((3, n_mu, n_g), dtype=torch.float64, device="cuda", generator=gen) * 1e-3
+    xi_h = xi.cpu().pin_memory()
+    xig_h = xig.cpu().pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            out = fn()
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, ts
+
+    kb = api.KernelBuilder(g, wt, xi, xig, jas, args.precision, kchunk=args.kchunk)
+    _, tr = timed(lambda: kb())
+    Ws, tsd = timed(lambda: api.tc_kernel_build_streamed(g, wt, xi_h, xig_h, jas, args.precision,
+                                                        bra=args.bra, ket=args.ket,
+                                                        kchunk=args.kchunk))
+    n_bra = -(-n_g // args.bra)
+    h2d = 8 * n_mu * n_g * (n_bra + 4)
+    fl = 8.0 * n_mu * n_g * n_g + 8.0 * n_mu * n_mu * n_g
+    rel = [float(torch.linalg.norm(Ws[c] - kb.W[c]) / torch.linalg.norm(kb.W[c])) for c in range(4)]
+    print(json.dumps({"mode": "streamed", "n_g": n_g, "n_mu": n_mu, "precision": args.precision,
+                      "bra": args.bra, "ket": args.ket, "resident_ms": tr, "streamed_ms": tsd,
+                      "resident_tflops": fl / (min(tr) * 1e-3) / 1e12,
+                      "streamed_tflops": fl / (min(tsd) * 1e-3) / 1e12,
+                      "h2d_bytes": h2d, "h2d_gbs_needed": h2d / (min(tsd) * 1e-3) / 1e9,
+                      "w_rel_diff_streamed_vs_resident": rel}), flush=True)
 
 
 def run_adjoint(args):
@@ -659,6 +715,8 @@ def main():
         return run_reference(args, rank, world)
     if args.w_only:
         return run_w_only(args)
+    if args.streamed:
+        return run_streamed(args)
     if args.adjoint:
         return run_adjoint(args)
     if args.proposer:

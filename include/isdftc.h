@@ -244,6 +244,32 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
                     isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * tc_kernel_build with xi and xi_grad in HOST memory (Sec. II.D grid-batched
+ * streaming with depth-one prefetch; the doubly-blocked bra/ket grid loops of
+ * Sec. IV.C): W over the whole grid as
+ *   W[c] = sum_{bra batches b} (w xi~^c)_b [ sum_{ket batches k} calG^c_{b,k} ]^T,
+ *   calG^c_{b,k}[nu][g] = sum_{g' in k} w_g' xi_nu(g') K_c(g, g'),
+ * with batches of `bra` outer and `ket` inner points (ket a multiple of 32).
+ * Each ket batch of xi is copied to the device (cudaMemcpy2DAsync on a stream
+ * of the call) while stage 1 runs on the previous one, and each bra batch of
+ * xi~ and xi while the bra batch's stage 1 runs; xi_host [n_mu][n_g] and
+ * xi_grad_host [3][n_mu][n_g] should be pinned (page-locked) for the copies to
+ * overlap.  Device memory: the grid, w and the per-point coordinate and
+ * nucleus tables, two ket batches and one bra batch of FP64 xi, the bra
+ * batch's calG and the limb operands (the workspace query gives the bytes);
+ * none of it grows with n_g beyond the per-point tables.  The ket loop re-reads
+ * xi from the host once per bra batch.  Tensor-core precisions only
+ * (ISDF_E_ARG for FP64); otherwise as tc_kernel_build (same correlators,
+ * options, error codes); synchronises `stream`.  W [4][n_mu][n_mu] device FP64
+ * (overwritten). */
+size_t tc_kernel_build_streamed_workspace(int64_t n_g, int n_mu, int64_t bra, int64_t ket,
+                                          int precision, const isdf_jastrow* jas);
+int tc_kernel_build_streamed(const double* grid_xyz, const double* w, const double* xi_host,
+                             const double* xi_grad_host, int64_t n_g, int n_mu, int64_t bra,
+                             int64_t ket, const isdf_jastrow* jas, const isdf_options* options,
+                             double* W, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint of the Jastrow kernels with respect to the correlator parameters
  * (not in the paper).  For the seed Wbar [4][n_mu][n_mu] and
  *   L(theta) = sum_c <Wbar^c, W^c(theta)>      (W of tc_kernel_build, full grid)

@@ -8,4 +8,5 @@ whole path (``pipeline``).
 from . import _capi  # noqa: F401
 from .api import (KernelBuilder, isdf_eval_orbitals, isdf_fit, isdf_gather_pivots,  # noqa: F401
                   isdf_points, isdf_points_fixed_rank, jastrow_from, jastrow_struct,
-                  tc_energies, tc_kernel_build, xtc_density_contract)
+                  tc_energies, tc_kernel_build, tc_kernel_build_streamed,
+                  xtc_density_contract)

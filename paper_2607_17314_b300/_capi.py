@@ -73,6 +73,8 @@ SIGNATURES = {
                                      P]),
     "isdf_fit_workspace": (SZ, [I64, INT, INT]),
     "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, P, SZ, P]),
+    "tc_kernel_build_streamed_workspace": (SZ, [I64, INT, I64, I64, INT, P]),
+    "tc_kernel_build_streamed": (INT, [P, P, P, P, I64, INT, I64, I64, P, P, P, P, SZ, P]),
     "isdf_gather_pivots": (INT, [P, P, I64, INT, P, INT, P, P, P]),
     "tc_kernel_build_workspace": (SZ, [I64, INT, I64, I64, INT, ctypes.POINTER(IsdfJastrow)]),
     "tc_kernel_build": (INT, [P, P, P, P, I64, INT, I64, I64, ctypes.POINTER(IsdfJastrow),

@@ -232,6 +232,30 @@ def tc_kernel_build(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, precision="bf1
     return kb.W, kb.calG
 
 
+def tc_kernel_build_streamed(grid_xyz, w, xi_host, xig_host, jastrow: C.IsdfJastrow,
+                             precision="bf16x3", bra: int = 16384, ket: int = 16384,
+                             kchunk: int = 0):
+    """W [4][n_mu][n_mu] on the device from xi [n_mu][n_g] and xi~ [3][n_mu][n_g]
+    held in (pinned) host memory, streamed in bra/ket grid batches with a
+    depth-one prefetch (Sec. II.D); grid_xyz and w on the device."""
+    lib = C.load()
+    _req(grid_xyz, f64, "grid_xyz"); _req(w, f64, "w")
+    for t, n in ((xi_host, "xi_host"), (xig_host, "xig_host")):
+        if t.device.type != "cpu" or t.dtype != f64 or not t.is_contiguous():
+            raise ValueError(f"{n} must be a contiguous FP64 host tensor")
+    n_mu, n_g = xi_host.shape
+    dev = grid_xyz.device
+    opt = options(precision, kchunk)
+    W = torch.empty((4, n_mu, n_mu), dtype=f64, device=dev)
+    ws = _ws(lib.tc_kernel_build_streamed_workspace(n_g, n_mu, bra, ket, opt.precision,
+                                                    ctypes.byref(jastrow)), dev)
+    C.check("tc_kernel_build_streamed", lib.tc_kernel_build_streamed(
+        _ptr(grid_xyz), _ptr(w), ctypes.c_void_p(xi_host.data_ptr()),
+        ctypes.c_void_p(xig_host.data_ptr()), n_g, n_mu, bra, ket, ctypes.byref(jastrow),
+        ctypes.byref(opt), _ptr(W), _ptr(ws), ws.numel(), _stream()))
+    return W
+
+
 def grid_shard(n_g: int, rank: int, world: int) -> Tuple[int, int]:
     """The outer-grid slice [g_begin, g_end) of rank ``rank`` of ``world`` for a
     sharded W build (Sec. IV.C): contiguous, covering [0, n_g) once, sizes

@@ -337,12 +337,12 @@ __global__ void adj_split_t_kernel(const double* __restrict__ src, int64_t src_r
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int64_t r = rb + i, c = cb + threadIdx.x;
     if (r >= rows_pad || c >= cols_pad) continue;
-    double v = tl[threadIdx.x][i];
+    float v = (float)tl[threadIdx.x][i];  // limbs of the FP32 rounding
 #pragma unroll
     for (int l = 0; l < kAdjLimbs; ++l) {
-      const __nv_bfloat16 hb = __double2bfloat16(v);
+      const __nv_bfloat16 hb = __float2bfloat16_rn(v);
       dst[l * plane + r * cols_pad + c] = hb;
-      v -= (double)__bfloat162float(hb);
+      v -= __bfloat162float(hb);
     }
   }
 }

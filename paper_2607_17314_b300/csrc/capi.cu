@@ -44,6 +44,10 @@ size_t wbuild_tc_ws(int64_t, int, int64_t, int64_t, int, const isdf_jastrow*);
 int wbuild_tc(const double*, const double*, const double*, const double*, int64_t, int, int64_t,
               int64_t, const isdf_jastrow&, const isdf_options&, double*, double*, void*, size_t,
               cudaStream_t);
+size_t wbuild_streamed_ws(int64_t, int, int64_t, int64_t, int, const isdf_jastrow*);
+int wbuild_streamed(const double*, const double*, const double*, const double*, int64_t, int,
+                    int64_t, int64_t, const isdf_jastrow&, const isdf_options&, double*, void*,
+                    size_t, cudaStream_t);
 size_t xtc_ws(int64_t, int, int, int, int, int);
 int xtc(const double*, int, int, const double*, const double*, const double*, int64_t, int,
         double*, double*, int, int, void*, size_t, cudaStream_t);
@@ -201,6 +205,31 @@ int tc_kernel_build(const double* grid_xyz, const double* w, const double* xi,
   }
   return wbuild_tc(grid_xyz, w, xi, xi_grad, n_g, n_mu, g_begin, g_end, *jas, opt, W, calG, ws,
                    ws_bytes, s);
+}
+
+size_t tc_kernel_build_streamed_workspace(int64_t n_g, int n_mu, int64_t bra, int64_t ket,
+                                          int precision, const isdf_jastrow* jas) {
+  if (precision == ISDF_PREC_FP64 || bra <= 0 || ket <= 0) return 0;
+  return wbuild_streamed_ws(n_g, n_mu, bra, ket, precision, jas);
+}
+
+int tc_kernel_build_streamed(const double* grid_xyz, const double* w, const double* xi_host,
+                             const double* xi_grad_host, int64_t n_g, int n_mu, int64_t bra,
+                             int64_t ket, const isdf_jastrow* jas, const isdf_options* options,
+                             double* W, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  ISDF_TRY(check_jastrow(jas));
+  ISDF_ARG(grid_xyz && w && xi_host && xi_grad_host && W, "null pointer argument");
+  ISDF_ARG(n_g > 0 && n_mu > 0, "empty sizes");
+  ISDF_ARG(n_g < (1ll << 31) - 64, "n_g too large");
+  isdf_options opt = {ISDF_PREC_BF16X3, 0, 0, 1, 0, nullptr, 0.0, 0.0, 0, 0};
+  if (options) opt = *options;
+  ISDF_ARG(opt.precision == ISDF_PREC_BF16X3 || opt.precision == ISDF_PREC_BF16X6 ||
+               opt.precision == ISDF_PREC_TF32X3,
+           "the streamed build takes the tensor-core precisions");
+  ISDF_ARG(opt.wait_limit_ms >= 0, "negative wait limit");
+  const WaitLimitScope wait_scope(opt.wait_limit_ms);
+  return wbuild_streamed(grid_xyz, w, xi_host, xi_grad_host, n_g, n_mu, bra, ket, *jas, opt, W, ws,
+                         ws_bytes, (cudaStream_t)stream);
 }
 
 size_t xtc_density_contract_workspace(int64_t n_g, int n_mu, int n_orb, int n_occ, int n_orb_x,

@@ -24,6 +24,12 @@ void set_error(const char* fmt, ...);
     }                                                                          \
   } while (0)
 
+inline int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return ISDF_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return ISDF_E_CUDA;
+}
+
 #define ISDF_ARG(cond, ...)                                                    \
   do {                                                                         \
     if (!(cond)) {                                                             \

@@ -116,11 +116,12 @@ __global__ void split_tf32_kernel(const double* __restrict__ src, int64_t src_rs
     v = src[r * src_rs + c0 + c];
     if (colw) v *= colw[c0 + c];
   }
+  float f = (float)v;  // limbs of the FP32 rounding; each remainder is exact in FP32
   for (int l = 0; l < limbs; ++l) {
     uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"((float)v));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
     dst[l * plane + e] = h;
-    v -= (double)__uint_as_float(h);
+    f -= __uint_as_float(h);
   }
 }
 
@@ -139,10 +140,11 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int
     v = src[r * src_rs + c0 + c];
     if (colw) v *= colw[c0 + c];
   }
+  float f = (float)v;  // limbs of the FP32 rounding; each remainder is exact in FP32
   for (int l = 0; l < limbs; ++l) {
-    __nv_bfloat16 h = __double2bfloat16(v);
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
     dst[l * plane + e] = h;
-    v -= (double)__bfloat162float(h);
+    f -= __bfloat162float(h);
   }
 }
 
@@ -155,7 +157,10 @@ __global__ void split_rows_kernel(const double* __restrict__ src, int64_t src_rs
   const int64_t r = blockIdx.y;
   const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (c >= cols_pad) return;
-  double v[4];
+  // the limbs split the FP32 rounding of the value, so that the only FP64
+  // arithmetic per element is the weight product and one conversion (B300's
+  // FP64 pipe is narrow); each remainder is exact in FP32
+  float v[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int64_t cc = c + q;
@@ -164,16 +169,16 @@ __global__ void split_rows_kernel(const double* __restrict__ src, int64_t src_rs
       x = src[r * src_rs + c0 + cc];
       if (colw) x *= colw[c0 + cc];
     }
-    v[q] = x;
+    v[q] = (float)x;
   }
   __nv_bfloat16* out = dst + r * cols_pad + c;
   for (int l = 0; l < limbs; ++l) {
     uint32_t bits[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat16 h = __double2bfloat16(v[q]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(v[q]);
       bits[q] = (uint32_t)__bfloat16_as_ushort(h);
-      v[q] -= (double)__bfloat162float(h);
+      v[q] -= __bfloat162float(h);
     }
     *reinterpret_cast<uint2*>(out + l * plane) =
         make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
@@ -251,6 +256,10 @@ struct S1Params {
   double* calG;          // [4][n_mu][g_end - g_begin]
   int* err;
   uint64_t wait_ns;      // bound of every mbarrier wait
+  int64_t k_begin;       // first inner point of this launch (multiple of 32): the inner
+                         // coordinates and A_{g'I} blocks are read from k_begin on, the
+                         // (w xi) operand map covers the n_k inner points from there
+  int accumulate;        // 1: add the tile into calG instead of writing it
   int debug;
   // multi-centre correlator (BH kernels only)
   int n_nuc;
@@ -374,10 +383,10 @@ __device__ __forceinline__ void s1_load_coords(const S1Params& p, const S1Smem& 
       if (!tc::mbar_wait(&sm.cempty[cs], ph ^ 1, sm.abort_flag, p.err, p.wait_ns)) return;
       uint8_t* dst = sm.ring + cs * p.cbytes;
       tc::mbar_arrive_expect_tx(&sm.cfull[cs], p.cbytes);
-      bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &sm.cfull[cs]);
-      bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + k0, C::BK * 16, &sm.cfull[cs]);
+      bulk_copy_g2s(dst, p.xyz_hi + p.k_begin + k0, C::BK * 16, &sm.cfull[cs]);
+      bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + p.k_begin + k0, C::BK * 16, &sm.cfull[cs]);
       if (BH && p.n_nuc > 0)
-        bulk_copy_g2s(dst + C::C_BASE, p.ajtab + (k0 / C::BK) * p.n_nuc * C::BK,
+        bulk_copy_g2s(dst + C::C_BASE, p.ajtab + ((p.k_begin + k0) / C::BK) * p.n_nuc * C::BK,
                       (uint32_t)p.n_nuc * C::BK * 4, &sm.cfull[cs]);
     }
   }
@@ -524,7 +533,7 @@ __device__ __forceinline__ void s1_gen_bh(const S1Params& p, const S1Smem& sm, i
     const float4 gh = gvalid ? p.xyz_hi[g] : zero;
     const float4 glo = gvalid ? p.xyz_lo[g] : zero;
     const float4 fg = gvalid ? p.fvec[g] : zero;
-    const int64_t gself = gvalid ? g : -1;
+    const int64_t gself = gvalid ? g - p.k_begin : -1;  // in this launch's inner range
     // this warp's rows of the nucleus table (the previous tile's reads are done)
     __syncwarp();
     for (int idx = lane & 3; idx < n_nuc * NS4; idx += 4)
@@ -668,7 +677,10 @@ __device__ __forceinline__ void s1_epilogue(const S1Params& p, const S1Smem& sm,
           const int64_t gbase = g_tile * C::BN + (blk % (C::BN / 32)) * 32;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
+            if (gbase + j < n_gs) {
+              const double v = (double)__uint_as_float(r[j]);
+              dst[gbase + j] = p.accumulate ? dst[gbase + j] + v : v;
+            }
         }
       }
       __syncwarp();
@@ -936,8 +948,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
           if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err, p.wait_ns)) goto done;
           uint8_t* dst = ring + cs * C::C_BYTES;
           tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
-          bulk_copy_g2s(dst, p.xyz_hi + k0, C::BK * 16, &cfull[cs]);
-          bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + k0, C::BK * 16, &cfull[cs]);
+          bulk_copy_g2s(dst, p.xyz_hi + p.k_begin + k0, C::BK * 16, &cfull[cs]);
+          bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + p.k_begin + k0, C::BK * 16, &cfull[cs]);
         }
       }
     }
@@ -1098,7 +1110,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
             const int64_t gbase = g_tile * C::BN + (col >> 7) * C::BNH + (col & 31);
 #pragma unroll
             for (int j = 0; j < FW; ++j)
-              if (gbase + j < n_gs) dst[gbase + j] = (double)__uint_as_float(r[j]);
+              if (gbase + j < n_gs) {
+                const double v = (double)__uint_as_float(r[j]);
+                dst[gbase + j] = p.accumulate ? dst[gbase + j] + v : v;
+              }
           }
         }
         __syncwarp();
@@ -1571,6 +1586,187 @@ static void bh_tc_dims(const isdf_jastrow* J, int& nn, int& ns4) {
   ns4 = bh_tc_form(*J, K) == ISDF_OK ? K.ns4 : 6;
 }
 
+// Per-call state of stage 1 shared by the resident and the streamed builds:
+// the correlator's form, the full-grid coordinate and nucleus tables (outer
+// points are read at their grid index, inner points from k_begin on).
+struct S1Setup {
+  bool radial, tf32, pair;
+  BhTc K;
+  int limbs1, eb1;
+  int64_t n_k;        // full-grid padded extent of the tables
+  int64_t kchunk;
+  float4 *hi, *lo, *rowslots, *fvec;
+  float* ajtab;
+};
+
+static void s1_tables_carve(Carve& cv, const S1Setup& S, int n_nuc, float4*& hi, float4*& lo,
+                            float4*& rowslots, float4*& fvec, float*& ajtab) {
+  hi = cv.take<float4>(S.n_k);
+  lo = cv.take<float4>(S.n_k);
+  rowslots = nullptr;
+  fvec = nullptr;
+  ajtab = nullptr;
+  if (!S.radial && n_nuc > 0) {
+    rowslots = cv.take<float4>((size_t)S.n_k * n_nuc * S.K.ns4);
+    fvec = cv.take<float4>(S.n_k);
+    ajtab = cv.take<float>((size_t)S.n_k * n_nuc);
+  } else if (!S.radial) {
+    fvec = cv.take<float4>(S.n_k);
+  }
+}
+
+static int s1_setup(const isdf_jastrow& J, const isdf_options& opt, int64_t n_g, S1Setup& S) {
+  S.radial = tc_radial(J);
+  S.tf32 = opt.precision == ISDF_PREC_TF32X3;
+  ISDF_ARG(!S.tf32 || S.radial, "the TF32 stage 1 takes the radial correlator only");
+  memset(&S.K, 0, sizeof(S.K));
+  if (!S.radial) ISDF_TRY(bh_tc_form(J, S.K));
+  S.limbs1 = opt.precision == ISDF_PREC_BF16X6 ? 3 : 2;
+  S.eb1 = S.tf32 ? 4 : 2;
+  // The radial correlator runs on CTA pairs (256-row tiles).  Debug bit 1 asks
+  // for the single-CTA kernel with two limbs; its three-limb form gave
+  // run-to-run wrong elements on multi-tile grids and is not offered.  The
+  // multi-centre generator is single-CTA.
+  S.pair = S.radial && ((opt.debug_flags & 2) == 0 || S.limbs1 == 3 || S.tf32);
+  S.n_k = round_up(n_g, 32);
+  S.kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : kDefaultChunk;
+  return ISDF_OK;
+}
+
+// Coordinates (FP32 hi/lo) and, for the multi-centre correlator, the per-point
+// nucleus tables over the whole grid.
+static int s1_tables(const double* grid, int64_t n_g, const isdf_jastrow& J, const S1Setup& S,
+                     cudaStream_t s) {
+  coords_kernel<<<nb256(S.n_k), 256, 0, s>>>(grid, n_g, S.n_k, S.hi, S.lo);
+  ISDF_LAUNCH_CHECK();
+  if (!S.radial) {
+    if (J.n_nuc > 0) {
+      bh_tc_table_kernel<<<nb256(S.n_k), 256, 0, s>>>(grid, n_g, S.n_k, J, S.K, (float*)S.rowslots,
+                                                       S.fvec, S.ajtab);
+      ISDF_LAUNCH_CHECK();
+    } else {
+      ISDF_CUDA(cudaMemsetAsync(S.fvec, 0, sizeof(float4) * S.n_k, s));
+    }
+  }
+  return ISDF_OK;
+}
+
+// Stage-1 operand: limbs of (w xi)[:, k0 .. k0 + n_in) into A1
+// [limbs1][mu_pad1][n_kb] (zero padding), from a source with row stride src_rs
+// whose column k0 - c0 holds inner point k0.
+static int s1_operand(const S1Setup& S, const double* src, int64_t src_rs, int64_t c0,
+                      const double* w_in, int n_mu, int64_t n_in, int64_t mu_pad1, int64_t n_kb,
+                      uint8_t* A1, CUtensorMap* mA, cudaStream_t s) {
+  memset(mA, 0, 3 * sizeof(CUtensorMap));
+  const size_t plane = (size_t)S.eb1 * mu_pad1 * n_kb;
+  if (S.tf32) {
+    split_tf32_kernel<<<nb256(mu_pad1 * n_kb), 256, 0, s>>>(src, src_rs, c0, w_in, n_mu, n_in,
+                                                           mu_pad1, n_kb, S.limbs1, (uint32_t*)A1);
+    ISDF_LAUNCH_CHECK();
+    for (int l = 0; l < S.limbs1; ++l)
+      ISDF_TRY(make_map_f32(&mA[l], A1 + l * plane, mu_pad1, n_kb, 128));
+  } else {
+    ISDF_TRY(split_operand(src, src_rs, c0, w_in, n_mu, n_in, mu_pad1, n_kb, S.limbs1, A1, s));
+    for (int l = 0; l < S.limbs1; ++l)
+      ISDF_TRY(make_map(&mA[l], A1 + l * plane, mu_pad1, n_kb, 128));
+  }
+  return ISDF_OK;
+}
+
+// One stage-1 launch: calG[c][nu][g - g_begin] (=, or += with accumulate) of
+// the inner points k_begin .. k_begin + n_kb (padded) for the outer slice.
+static int s1_launch(const S1Setup& S, const isdf_jastrow& J, const CUtensorMap* mA, int n_mu,
+                     int64_t n_g, int64_t mu_pad, int64_t mu_pad1, int64_t k_begin, int64_t n_kb,
+                     int64_t g_begin, int64_t g_end, double* calG, int accumulate, int debug,
+                     int* err, cudaStream_t s) {
+  S1Params p;
+  p.xyz_hi = S.hi; p.xyz_lo = S.lo;
+  p.n_g = n_g; p.n_k = n_kb; p.n_mu = n_mu;
+  p.n_mu_tiles = S.pair ? (int)(mu_pad1 / 256) : (int)(mu_pad / 128);
+  p.g_begin = g_begin; p.g_end = g_end;
+  p.n_g_tiles = ceil_div(g_end - g_begin, 64);
+  p.kchunk = S.kchunk;
+  p.d = (float)J.d;
+  p.calG = calG;
+  p.err = err;
+  p.wait_ns = wait_limit_ns();
+  p.k_begin = k_begin;
+  p.accumulate = accumulate;
+  p.debug = debug;
+  p.n_nuc = S.radial ? 0 : J.n_nuc;
+  p.cbytes = S1C<2, false>::C_BASE + 4u * S1C<2, false>::BK * (uint32_t)p.n_nuc;
+  p.tab_bytes = S.radial ? 0u : (uint32_t)(p.n_nuc * S.K.ns4 * S1C<2, false>::BN * 16);
+  p.oexp[0] = S.radial ? 1 : S.K.oexp[0];
+  p.oexp[1] = S.radial ? 1 : S.K.oexp[1];
+  for (int e = 0; e < 4; ++e) p.rho[e] = S.radial ? 0.f : (float)S.K.rho[e];
+  p.rowslots = S.rowslots;
+  p.fvec = S.fvec;
+  p.ajtab = S.ajtab;
+  int dev = 0, nsm = 148;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
+  unsigned grid1 = (unsigned)(n_tiles < nsm ? n_tiles : nsm);
+  if (S.pair) grid1 = 2u * (unsigned)(n_tiles < nsm / 2 ? n_tiles : nsm / 2);
+  const BhTc& K = S.K;
+  if (S.tf32) return launch_s1_pair<2, true>(grid1, mA, p, s);
+  if (S.pair)
+    return S.limbs1 == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
+  if (S.radial) return launch_s1<2, -1, 0>(grid1, mA, p, s);
+  if (K.ng == 1 && K.deg == 2)
+    return S.limbs1 == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
+  if (K.ng == 1)
+    return S.limbs1 == 2 ? launch_s1<2, 1, 3>(grid1, mA, p, s) : launch_s1<3, 1, 3>(grid1, mA, p, s);
+  return S.limbs1 == 2 ? launch_s1<2, 2, 3>(grid1, mA, p, s) : launch_s1<3, 2, 3>(grid1, mA, p, s);
+}
+
+// Stage 2 over an outer slice of gs points: W[c] += (w xi~^c)_slice calG[c]^T
+// (c < 3) and W[3] += (w xi)_slice calG[3]^T, in split-BF16 limbs.  src_xi /
+// src_xig hold the slice's columns at column offset c0 with row stride src_rs.
+static int s2_accumulate(const double* src_xi, const double* src_xig, int64_t src_rs,
+                         int64_t xig_plane, int64_t c0, const double* w_slice, const double* calG,
+                         int n_mu, int64_t gs, int limbs, int64_t mu_pad, int64_t gs_pad,
+                         int64_t kchunk2, uint16_t* A2, uint16_t* B2, double* W, int* err,
+                         cudaStream_t s) {
+  const size_t plane = (size_t)limbs * mu_pad * gs_pad;
+  const void* Ap[4];
+  const void* Bp[4];
+  for (int c = 0; c < 4; ++c) {
+    const double* src = c < 3 ? src_xig + (int64_t)c * xig_plane : src_xi;
+    ISDF_TRY(split_operand(src, src_rs, c0, w_slice, n_mu, gs, mu_pad, gs_pad, limbs,
+                           A2 + c * plane, s));
+    ISDF_TRY(split_operand(calG + (int64_t)c * n_mu * gs, gs, 0, nullptr, n_mu, gs, mu_pad,
+                           gs_pad, limbs, B2 + c * plane, s));
+    Ap[c] = A2 + c * plane;
+    Bp[c] = B2 + c * plane;
+  }
+  return splitgemm(limbs, 4, Ap, Bp, n_mu, n_mu, gs_pad, kS2Range, kchunk2, W, n_mu,
+                   (int64_t)n_mu * n_mu, 1.0, err, s);
+}
+
+static int s2_limbs(int precision) {
+  // TF32X3: stage 1 in two TF32 limbs, stage 2 in three BF16 limbs
+  return (precision == ISDF_PREC_BF16X6 || precision == ISDF_PREC_TF32X3) ? 3 : 2;
+}
+
+static int finish_checks(const isdf_options& opt, double* W, int n_mu, int* err, cudaStream_t s) {
+  // every input value reaches W: a NaN or Inf there leaves a non-finite W
+  ISDF_TRY(scan_nonfinite(W, (int64_t)4 * n_mu * n_mu, err, s));
+  int h_err = 0;
+  ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ISDF_CUDA(cudaStreamSynchronize(s));
+  (void)opt;
+  if (h_err & DEV_ERR_TIMEOUT) {
+    set_error("tensor-core pipeline wait expired (device error word 0x%x)", h_err);
+    return ISDF_E_TIMEOUT;
+  }
+  if (h_err & DEV_ERR_NONFINITE) {
+    set_error("W is not finite (NaN or Inf in the grid, weights or xi)");
+    return ISDF_E_NONFINITE;
+  }
+  return ISDF_OK;
+}
+
 size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int precision,
                     const isdf_jastrow* J) {
   TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, precision);
@@ -1578,16 +1774,18 @@ size_t wbuild_tc_ws(int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, int p
   c.take<int>(64);
   c.take<float4>(L.n_k);
   c.take<float4>(L.n_k);
-  c.take<uint8_t>((size_t)L.limbs1 * L.eb1 * L.mu_pad1 * L.n_k);  // S1 A
-  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
-  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
   int nn, ns4;
   bh_tc_dims(J, nn, ns4);
   if (nn > 0) {
     c.take<float4>((size_t)L.n_k * nn * ns4);
     c.take<float4>(L.n_k);
     c.take<float>((size_t)L.n_k * nn);
+  } else if (J && !tc_radial(*J)) {
+    c.take<float4>(L.n_k);
   }
+  c.take<uint8_t>((size_t)L.limbs1 * L.eb1 * L.mu_pad1 * L.n_k);  // S1 A
+  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 A (4 channels)
+  c.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);     // S2 B (calG limbs)
   return c.off;
 }
 
@@ -1595,155 +1793,209 @@ int wbuild_tc(const double* grid, const double* w, const double* xi, const doubl
               int64_t n_g, int n_mu, int64_t g_begin, int64_t g_end, const isdf_jastrow& J,
               const isdf_options& opt, double* W, double* calG, void* ws, size_t ws_bytes,
               cudaStream_t s) {
-  const bool radial = tc_radial(J);
-  const bool tf32 = opt.precision == ISDF_PREC_TF32X3;
-  ISDF_ARG(!tf32 || radial, "the TF32 stage 1 takes the radial correlator only");
-  BhTc K;
-  if (!radial) ISDF_TRY(bh_tc_form(J, K));
+  S1Setup S;
+  ISDF_TRY(s1_setup(J, opt, n_g, S));
   const TcLayout L = tc_layout(n_g, n_mu, g_begin, g_end, opt.precision);
   Carve cv(ws, ws_bytes);
   int* err = cv.take<int>(64);
-  float4* hi = cv.take<float4>(L.n_k);
-  float4* lo = cv.take<float4>(L.n_k);
+  s1_tables_carve(cv, S, J.n_nuc, S.hi, S.lo, S.rowslots, S.fvec, S.ajtab);
   uint8_t* A1 = cv.take<uint8_t>((size_t)L.limbs1 * L.eb1 * L.mu_pad1 * L.n_k);
   uint16_t* A2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
   uint16_t* B2 = cv.take<uint16_t>((size_t)4 * L.limbs * L.mu_pad * L.gs_pad);
-  float4* rowslots = nullptr;
-  float4* fvec = nullptr;
-  float* ajtab = nullptr;
-  if (!radial && J.n_nuc > 0) {
-    rowslots = cv.take<float4>((size_t)L.n_k * J.n_nuc * K.ns4);
-    fvec = cv.take<float4>(L.n_k);
-    ajtab = cv.take<float>((size_t)L.n_k * J.n_nuc);
-  } else if (!radial) {
-    fvec = cv.take<float4>(L.n_k);
-  }
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   ISDF_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
+  const int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 256;
 
-  int64_t kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : kDefaultChunk;
-  int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 256;
-
-  // operands of stage 1
-  coords_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, hi, lo);
-  ISDF_LAUNCH_CHECK();
-  if (!radial) {
-    if (J.n_nuc > 0) {
-      bh_tc_table_kernel<<<nb256(L.n_k), 256, 0, s>>>(grid, n_g, L.n_k, J, K, (float*)rowslots,
-                                                       fvec, ajtab);
-      ISDF_LAUNCH_CHECK();
-    } else {
-      ISDF_CUDA(cudaMemsetAsync(fvec, 0, sizeof(float4) * L.n_k, s));
-    }
-  }
+  ISDF_TRY(s1_tables(grid, n_g, J, S, s));
   CUtensorMap mA[3];
-  memset(mA, 0, sizeof(mA));
-  const size_t a1_plane = (size_t)L.eb1 * L.mu_pad1 * L.n_k;
-  if (tf32) {
-    split_tf32_kernel<<<nb256(L.mu_pad1 * L.n_k), 256, 0, s>>>(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1,
-                                                              L.n_k, L.limbs1, (uint32_t*)A1);
-    ISDF_LAUNCH_CHECK();
-    for (int l = 0; l < L.limbs1; ++l)
-      ISDF_TRY(make_map_f32(&mA[l], A1 + l * a1_plane, L.mu_pad1, L.n_k, 128));
-  } else {
-    ISDF_TRY(split_operand(xi, n_g, 0, w, n_mu, n_g, L.mu_pad1, L.n_k, L.limbs1, A1, s));
-    for (int l = 0; l < L.limbs1; ++l)
-      ISDF_TRY(make_map(&mA[l], A1 + l * a1_plane, L.mu_pad1, L.n_k, 128));
-  }
-  // The radial correlator runs on CTA pairs (256-row tiles).  Debug bit 1 asks
-  // for the single-CTA kernel with two limbs; its three-limb form gave
-  // run-to-run wrong elements on multi-tile grids and is not offered.  The
-  // multi-centre generator is single-CTA.
-  const bool pair = radial && ((opt.debug_flags & 2) == 0 || L.limbs1 == 3 || tf32);
-
-  S1Params p;
-  p.xyz_hi = hi; p.xyz_lo = lo;
-  p.n_g = n_g; p.n_k = L.n_k; p.n_mu = n_mu;
-  p.n_mu_tiles = pair ? (int)(L.mu_pad1 / 256) : (int)(L.mu_pad / 128);
-  p.g_begin = g_begin; p.g_end = g_end;
-  p.n_g_tiles = ceil_div(L.gs, L.bn);
-  p.kchunk = kchunk;
-  p.d = (float)J.d;
-  p.calG = calG;
-  p.err = err;
-  p.wait_ns = wait_limit_ns();
-  p.debug = opt.debug_flags;
-  p.n_nuc = radial ? 0 : J.n_nuc;
-  p.cbytes = S1C<2, false>::C_BASE + 4u * S1C<2, false>::BK * (uint32_t)p.n_nuc;
-  p.tab_bytes = radial ? 0u : (uint32_t)(p.n_nuc * K.ns4 * S1C<2, false>::BN * 16);
-  p.oexp[0] = radial ? 1 : K.oexp[0];
-  p.oexp[1] = radial ? 1 : K.oexp[1];
-  for (int e = 0; e < 4; ++e) p.rho[e] = radial ? 0.f : (float)K.rho[e];
-  p.rowslots = rowslots;
-  p.fvec = fvec;
-  p.ajtab = ajtab;
-  int dev = 0, nsm = 148;
-  ISDF_CUDA(cudaGetDevice(&dev));
-  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t n_tiles = (int64_t)p.n_mu_tiles * p.n_g_tiles;
-  unsigned grid1 = (unsigned)(n_tiles < nsm ? n_tiles : nsm);
-  if (pair) grid1 = 2u * (unsigned)(n_tiles < nsm / 2 ? n_tiles : nsm / 2);
+  ISDF_TRY(s1_operand(S, xi, n_g, 0, w, n_mu, n_g, L.mu_pad1, L.n_k, A1, mA, s));
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   const bool timed = opt.stage_ms != nullptr && opt.sync_check;
   if (timed) {
     for (int i = 0; i < 4; ++i) ISDF_CUDA(cudaEventCreate(&ev[i]));
     ISDF_CUDA(cudaEventRecord(ev[0], s));
   }
-  int rc;
-  if (tf32)
-    rc = launch_s1_pair<2, true>(grid1, mA, p, s);
-  else if (pair)
-    rc = L.limbs1 == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
-  else if (radial)
-    rc = launch_s1<2, -1, 0>(grid1, mA, p, s);
-  else if (K.ng == 1 && K.deg == 2)
-    rc = L.limbs1 == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);
-  else if (K.ng == 1)
-    rc = L.limbs1 == 2 ? launch_s1<2, 1, 3>(grid1, mA, p, s) : launch_s1<3, 1, 3>(grid1, mA, p, s);
-  else
-    rc = L.limbs1 == 2 ? launch_s1<2, 2, 3>(grid1, mA, p, s) : launch_s1<3, 2, 3>(grid1, mA, p, s);
-  if (rc != ISDF_OK) return rc;
+  ISDF_TRY(s1_launch(S, J, mA, n_mu, n_g, L.mu_pad, L.mu_pad1, 0, L.n_k, g_begin, g_end, calG, 0,
+                     opt.debug_flags, err, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[1], s));
-
-  // operands of stage 2: (w xi~^c) and (w xi) over the slice; calG limbs
-  const size_t plane = (size_t)L.limbs * L.mu_pad * L.gs_pad;
-  const void* Ap[4];
-  const void* Bp[4];
-  for (int c = 0; c < 4; ++c) {
-    const double* src = c < 3 ? xig + (int64_t)c * n_mu * n_g : xi;
-    ISDF_TRY(split_operand(src, n_g, g_begin, w, n_mu, L.gs, L.mu_pad, L.gs_pad, L.limbs,
-                           A2 + c * plane, s));
-    ISDF_TRY(split_operand(calG + (int64_t)c * n_mu * L.gs, L.gs, 0, nullptr, n_mu, L.gs,
-                           L.mu_pad, L.gs_pad, L.limbs, B2 + c * plane, s));
-    Ap[c] = A2 + c * plane;
-    Bp[c] = B2 + c * plane;
-  }
   ISDF_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 4 * (size_t)n_mu * n_mu, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[2], s));
-  ISDF_TRY(splitgemm(L.limbs, 4, Ap, Bp, n_mu, n_mu, L.gs_pad, kS2Range, kchunk2, W, n_mu,
-                     (int64_t)n_mu * n_mu, 1.0, err, s));
+  // stage 2: (w xi~^c) and (w xi) over the slice, calG in limbs
+  ISDF_TRY(s2_accumulate(xi, xig, n_g, (int64_t)n_mu * n_g, g_begin, w, calG, n_mu, L.gs, L.limbs,
+                         L.mu_pad, L.gs_pad, kchunk2, A2, B2, W, err, s));
   if (timed) ISDF_CUDA(cudaEventRecord(ev[3], s));
   if (opt.sync_check) {
-    // every input value reaches W: a NaN or Inf there leaves a non-finite W
-    ISDF_TRY(scan_nonfinite(W, (int64_t)4 * n_mu * n_mu, err, s));
-    int h_err = 0;
-    ISDF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ISDF_CUDA(cudaStreamSynchronize(s));
+    const int rc = finish_checks(opt, W, n_mu, err, s);
     if (timed) {
       ISDF_CUDA(cudaEventElapsedTime(&opt.stage_ms[0], ev[0], ev[1]));
       ISDF_CUDA(cudaEventElapsedTime(&opt.stage_ms[1], ev[2], ev[3]));
       for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     }
-    if (h_err & DEV_ERR_TIMEOUT) {
-      set_error("tensor-core pipeline wait expired (device error word 0x%x)", h_err);
-      return ISDF_E_TIMEOUT;
-    }
-    if (h_err & DEV_ERR_NONFINITE) {
-      set_error("W is not finite (NaN or Inf in the grid, weights or xi)");
-      return ISDF_E_NONFINITE;
-    }
+    return rc;
   }
   return ISDF_OK;
+}
+
+// ------------------------------------------------------------------ streamed build
+
+// Layout of the streamed build (Sec. II.D grid-batched streaming, Sec. IV.C
+// doubly-blocked grid loops): the device holds the full-grid coordinate and
+// nucleus tables, two inner (ket) batches of xi in FP64 (the copy of the next
+// one overlaps the current one's stage 1), one outer (bra) batch of xi and
+// xi~ in FP64, the bra batch's calG, and the limb operands.
+struct StreamWs {
+  int* err;
+  double* ket[2];     // [n_mu][ket]
+  double* bra;        // [4][n_mu][bra]: xi~ (3 planes), then xi
+  double* calG;       // [4][n_mu][bra]
+  uint8_t* A1;        // [limbs1][mu_pad1][round_up(ket, 32)] (element bytes eb1)
+  uint16_t *A2, *B2;  // [4][limbs][mu_pad][round_up(bra, 32)]
+  void carve(Carve& cv, S1Setup& S, int n_mu, int n_nuc, int64_t bra_n, int64_t ket_n,
+             int limbs) {
+    err = cv.take<int>(64);
+    s1_tables_carve(cv, S, n_nuc, S.hi, S.lo, S.rowslots, S.fvec, S.ajtab);
+    for (int i = 0; i < 2; ++i) ket[i] = cv.take<double>((size_t)n_mu * ket_n);
+    bra = cv.take<double>((size_t)4 * n_mu * bra_n);
+    calG = cv.take<double>((size_t)4 * n_mu * bra_n);
+    const int64_t mu_pad1 = round_up(n_mu, 256), mu_pad = round_up(n_mu, 128);
+    A1 = cv.take<uint8_t>((size_t)S.limbs1 * S.eb1 * mu_pad1 * round_up(ket_n, 32));
+    A2 = cv.take<uint16_t>((size_t)4 * limbs * mu_pad * round_up(bra_n, 32));
+    B2 = cv.take<uint16_t>((size_t)4 * limbs * mu_pad * round_up(bra_n, 32));
+  }
+};
+
+size_t wbuild_streamed_ws(int64_t n_g, int n_mu, int64_t bra_n, int64_t ket_n, int precision,
+                          const isdf_jastrow* J) {
+  isdf_jastrow Jr;
+  memset(&Jr, 0, sizeof(Jr));
+  isdf_options opt = {precision, 0, 0, 1, 0, nullptr, 0.0, 0.0, 0, 0};
+  S1Setup S;
+  memset(&S, 0, sizeof(S));
+  if (J) {
+    if (s1_setup(*J, opt, n_g, S) != ISDF_OK) return 0;
+  } else {
+    // the largest accepted layout: a multi-centre correlator with 32 nuclei
+    S.radial = false;
+    S.K.ns4 = 6;
+    S.limbs1 = precision == ISDF_PREC_BF16X6 ? 3 : 2;
+    S.eb1 = precision == ISDF_PREC_TF32X3 ? 4 : 2;
+    S.n_k = round_up(n_g, 32);
+  }
+  Carve c(nullptr, 0);
+  StreamWs b;
+  b.carve(c, S, n_mu, J ? J->n_nuc : 32, bra_n, ket_n, s2_limbs(precision));
+  return c.off;
+}
+
+int wbuild_streamed(const double* grid, const double* w, const double* xi_h, const double* xig_h,
+                    int64_t n_g, int n_mu, int64_t bra_n, int64_t ket_n, const isdf_jastrow& J,
+                    const isdf_options& opt, double* W, void* ws, size_t ws_bytes,
+                    cudaStream_t s) {
+  ISDF_ARG(xi_h && xig_h && W && grid && w, "null pointer argument");
+  ISDF_ARG(bra_n > 0 && ket_n > 0 && ket_n % 32 == 0, "batch sizes: bra > 0, ket a positive "
+           "multiple of 32");
+  S1Setup S;
+  ISDF_TRY(s1_setup(J, opt, n_g, S));
+  const int limbs = s2_limbs(opt.precision);
+  const int64_t mu_pad1 = round_up(n_mu, 256), mu_pad = round_up(n_mu, 128);
+  Carve cv(ws, ws_bytes);
+  StreamWs b;
+  b.carve(cv, S, n_mu, J.n_nuc, bra_n, ket_n, limbs);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  const int64_t kchunk2 = opt.s2_kchunk > 0 ? round_up(opt.s2_kchunk, 32) : 256;
+
+  // a copy stream for the host-to-device batches and events between the two
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  cudaEvent_t bra_copied = nullptr, bra_freed = nullptr;
+  int rc = ISDF_OK;
+  auto cleanup = [&]() {
+    for (int i = 0; i < 2; ++i) {
+      if (copied[i]) cudaEventDestroy(copied[i]);
+      if (freed[i]) cudaEventDestroy(freed[i]);
+    }
+    if (bra_copied) cudaEventDestroy(bra_copied);
+    if (bra_freed) cudaEventDestroy(bra_freed);
+    if (cs) cudaStreamDestroy(cs);
+  };
+#define STREAM_TRY(x)                 \
+  do {                                \
+    rc = (x);                         \
+    if (rc != ISDF_OK) {              \
+      cleanup();                      \
+      return rc;                      \
+    }                                 \
+  } while (0)
+#define STREAM_CUDA(x) STREAM_TRY(cuda_status((x), #x))
+  STREAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    STREAM_CUDA(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
+    STREAM_CUDA(cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming));
+  }
+  STREAM_CUDA(cudaEventCreateWithFlags(&bra_copied, cudaEventDisableTiming));
+  STREAM_CUDA(cudaEventCreateWithFlags(&bra_freed, cudaEventDisableTiming));
+  STREAM_CUDA(cudaMemsetAsync(b.err, 0, 64 * sizeof(int), s));
+  STREAM_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 4 * (size_t)n_mu * n_mu, s));
+  STREAM_TRY(s1_tables(grid, n_g, J, S, s));
+  // the copy stream starts after the tables and buffers are set up on s
+  STREAM_CUDA(cudaEventRecord(freed[0], s));
+  STREAM_CUDA(cudaEventRecord(freed[1], s));
+  STREAM_CUDA(cudaEventRecord(bra_freed, s));
+
+  const int64_t n_ket = ceil_div(n_g, ket_n), n_bra = ceil_div(n_g, bra_n);
+  const int64_t total = n_ket * n_bra;
+  // copy of ket batch `it` (bra-major order) into slot it % 2
+  auto copy_ket = [&](int64_t it) -> int {
+    const int64_t k = it % n_ket;
+    const int64_t h0 = k * ket_n, hn = n_g - h0 < ket_n ? n_g - h0 : ket_n;
+    const int slot = (int)(it & 1);
+    ISDF_CUDA(cudaStreamWaitEvent(cs, freed[slot], 0));
+    ISDF_CUDA(cudaMemcpy2DAsync(b.ket[slot], (size_t)hn * 8, xi_h + h0, (size_t)n_g * 8,
+                                (size_t)hn * 8, (size_t)n_mu, cudaMemcpyHostToDevice, cs));
+    ISDF_CUDA(cudaEventRecord(copied[slot], cs));
+    return ISDF_OK;
+  };
+  auto copy_bra = [&](int64_t bi) -> int {
+    const int64_t g0 = bi * bra_n, gn = n_g - g0 < bra_n ? n_g - g0 : bra_n;
+    ISDF_CUDA(cudaStreamWaitEvent(cs, bra_freed, 0));
+    for (int c = 0; c < 4; ++c) {
+      const double* src = c < 3 ? xig_h + (int64_t)c * n_mu * n_g : xi_h;
+      ISDF_CUDA(cudaMemcpy2DAsync(b.bra + (size_t)c * n_mu * gn, (size_t)gn * 8, src + g0,
+                                  (size_t)n_g * 8, (size_t)gn * 8, (size_t)n_mu,
+                                  cudaMemcpyHostToDevice, cs));
+    }
+    ISDF_CUDA(cudaEventRecord(bra_copied, cs));
+    return ISDF_OK;
+  };
+  STREAM_TRY(copy_ket(0));
+  for (int64_t bi = 0; bi < n_bra; ++bi) {
+    const int64_t g0 = bi * bra_n, gn = n_g - g0 < bra_n ? n_g - g0 : bra_n;
+    STREAM_TRY(copy_bra(bi));
+    for (int64_t k = 0; k < n_ket; ++k) {
+      const int64_t it = bi * n_ket + k;
+      const int slot = (int)(it & 1);
+      if (it + 1 < total) STREAM_TRY(copy_ket(it + 1));  // depth-one prefetch
+      const int64_t h0 = k * ket_n, hn = n_g - h0 < ket_n ? n_g - h0 : ket_n;
+      const int64_t nkb = round_up(hn, 32);
+      STREAM_CUDA(cudaStreamWaitEvent(s, copied[slot], 0));
+      CUtensorMap mA[3];
+      STREAM_TRY(s1_operand(S, b.ket[slot], hn, 0, w + h0, n_mu, hn, mu_pad1, nkb, b.A1, mA, s));
+      STREAM_CUDA(cudaEventRecord(freed[slot], s));
+      STREAM_TRY(s1_launch(S, J, mA, n_mu, n_g, mu_pad, mu_pad1, h0, nkb, g0, g0 + gn, b.calG,
+                           k > 0 ? 1 : 0, opt.debug_flags, b.err, s));
+    }
+    STREAM_CUDA(cudaStreamWaitEvent(s, bra_copied, 0));
+    STREAM_TRY(s2_accumulate(b.bra + (size_t)3 * n_mu * gn, b.bra, gn, (int64_t)n_mu * gn, 0,
+                             w + g0, b.calG, n_mu, gn, limbs, mu_pad, round_up(gn, 32), kchunk2,
+                             b.A2, b.B2, W, b.err, s));
+    STREAM_CUDA(cudaEventRecord(bra_freed, s));
+  }
+  rc = opt.sync_check ? finish_checks(opt, W, n_mu, b.err, s) : ISDF_OK;
+  if (!opt.sync_check) cudaStreamSynchronize(s);  // the events and copy stream end with the call
+  cleanup();
+  return rc;
+#undef STREAM_CUDA
+#undef STREAM_TRY
 }
 
 }  // namespace isdf

@@ -216,6 +216,8 @@ def test_undersized_workspace_rejected_before_launch(lib):
                                                        None, f, f, f, 16, None),
         "tc_kernel_build (fp64)": lambda: lib.tc_kernel_build(
             f, f, f, f, 64, 8, 0, 64, ctypes.byref(J), ctypes.byref(opt64), f, f, f, 16, None),
+        "tc_kernel_build_streamed": lambda: lib.tc_kernel_build_streamed(
+            f, f, f, f, 64, 8, 64, 64, ctypes.byref(J), None, f, f, 16, None),
         "tc_kernel_adjoint": lambda: lib.tc_kernel_adjoint(f, f, f, f, 64, 8, ctypes.byref(J), f,
                                                            C.PRECISIONS["fp64"], f, f, 16, None),
         "xtc_density_contract": lambda: lib.xtc_density_contract(f, 4, 2, f, f, f, 64, 8, f, f, 4,
@@ -230,3 +232,24 @@ def test_undersized_workspace_rejected_before_launch(lib):
         st = call()
         assert st == C.ISDF_E_ARG, (name, st, lib.isdf_last_error())
         assert b"workspace too small" in lib.isdf_last_error(), (name, lib.isdf_last_error())
+
+
+def test_streamed_build_argument_checks(lib):
+    """The streamed W build rejects the FP64 precision and ket batches that are
+    not multiples of 32 before any device work, and its workspace query is 0
+    for them."""
+    from paper_2607_17314_b300 import _capi as C
+    f = ctypes.c_void_p(256)
+    J = C.IsdfJastrow()
+    J.n_types, J.d, J.cusp, J.b[0] = 1, 1.0, 1, 1.0
+    opt64 = C.IsdfOptions(C.ISDF_PREC_FP64, 0, 0, 1, 0, None, 0.0, 0.0, 0, 0)
+    st = lib.tc_kernel_build_streamed(f, f, f, f, 4096, 64, 1024, 1024, ctypes.byref(J),
+                                      ctypes.byref(opt64), f, f, 1 << 30, None)
+    assert st == C.ISDF_E_ARG and b"tensor-core precisions" in lib.isdf_last_error()
+    st = lib.tc_kernel_build_streamed(f, f, f, f, 4096, 64, 1024, 1000, ctypes.byref(J), None, f,
+                                      f, 1 << 30, None)
+    assert st == C.ISDF_E_ARG and b"multiple of 32" in lib.isdf_last_error()
+    assert lib.tc_kernel_build_streamed_workspace(4096, 64, 1024, 1024, C.ISDF_PREC_FP64, None) == 0
+    small = lib.tc_kernel_build_streamed_workspace(100000, 2000, 8192, 8192, 1, ctypes.byref(J))
+    big = lib.tc_kernel_build_workspace(100000, 2000, 0, 100000, 1, ctypes.byref(J))
+    assert 0 < small < big

@@ -211,6 +211,49 @@ def test_w_one_body_term(P, h6, prec):
     assert min(rel(Wo[c], o["W"][c]) for c in range(4)) > 1e-3
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_w_streamed_from_host(P, h6, prec):
+    """The streamed build (xi and xi~ in pinned host memory, bra batches of 1000
+    outer points, ket batches of 1024 inner points: ragged tiles and a ragged
+    last batch) against the oracle's W at 1e-5 per channel, and against the
+    resident build at 5e-6."""
+    w, o = h6
+    J = _jas(P, w)
+    xi_h = torch.as_tensor(o["xi"]).contiguous().pin_memory()
+    xig_h = torch.as_tensor(o["xit"]).contiguous().pin_memory()
+    g, wt = cu(w.grid_xyz), cu(w.grid_w)
+    Ws = P.tc_kernel_build_streamed(g, wt, xi_h, xig_h, J, prec, bra=1000, ket=1024)
+    Wr, _ = P.tc_kernel_build(g, wt, cu(o["xi"]), cu(o["xit"]), J, prec)
+    errs = [rel(host(Ws[c]), o["W"][c]) for c in range(4)]
+    diffs = [rel(host(Ws[c]), host(Wr[c])) for c in range(4)]
+    print(prec, "streamed W rel vs oracle", errs, "vs resident", diffs)
+    assert max(errs) < 1e-5, errs
+    assert max(diffs) < 5e-6, diffs
+
+
+def test_w_streamed_multi_centre(P):
+    """The streamed build with the two-type multi-centre correlator and the
+    one-body term on a small benzene grid (random xi, so W carries heavy
+    cancellation): against the resident build at 5e-6 and the oracle at 1e-4."""
+    atoms, xyz = wl.benzene()
+    grid, wgt = wl.becke_grid(xyz, 6, 26)
+    jas = wl.with_chi(wl.bh_jastrow(atoms, xyz, wl.BH_TERMS_C3, np.random.default_rng(11)),
+                      [6.0, 1.0], 42)
+    n_mu = 40
+    xi = wl.seeded_matrix((n_mu, grid.shape[0]), 31, 1e-2)
+    xit = wl.seeded_matrix((3, n_mu, grid.shape[0]), 32, 1e-2)
+    Wo, _ = wbuild.build(grid, wgt, xi, xit, jas)
+    Ws = P.tc_kernel_build_streamed(cu(grid), cu(wgt), torch.as_tensor(xi).pin_memory(),
+                                    torch.as_tensor(xit).pin_memory(), P.jastrow_from(jas),
+                                    "bf16x3", bra=300, ket=320)
+    Wr, _ = P.tc_kernel_build(cu(grid), cu(wgt), cu(xi), cu(xit), P.jastrow_from(jas), "bf16x3")
+    errs = [rel(host(Ws[c]), Wo[c]) for c in range(4)]
+    diffs = [rel(host(Ws[c]), host(Wr[c])) for c in range(4)]
+    print("streamed multi-centre W rel vs oracle", errs, "vs resident", diffs)
+    assert max(diffs) < 5e-6, diffs
+    assert max(errs) < 1e-4, errs
+
+
 def test_w_tensor_core_single_cta(P, h6):
     """The single-CTA stage-1 kernel (128-row tiles), kept for the multi-centre
     correlator, on the radial correlator with two limbs (debug bit 1 selects it)."""
