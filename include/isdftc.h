@@ -114,7 +114,7 @@ typedef struct {
                          its FP32 chunk sum before the epilogue folds that sum into
                          the IEEE-rounded FP32 running sum (also in tensor memory;
                          the tile is written to FP64 once); rounded up to a multiple
-                         of 32; 0 = default (512) */
+                         of 32; 0 = default (384; 128 for ISDF_PREC_TF32X3) */
   int32_t s2_kchunk;  /* fold interval of stage 2; 0 = default (256) */
   int32_t sync_check; /* 1 (default): synchronise the stream on return and report
                          device-side errors (expired bounded waits, CUDA errors) */

@@ -162,7 +162,10 @@ __device__ __forceinline__ float softplusf(float t) {
 }
 
 // Gradient of the mean weighted BCE over n_total points (this call covers
-// n_pts of them), accumulated into grad; the loss sum into *loss.
+// n_pts of them), accumulated into grad; the loss sum into *loss.  Each block
+// loops over point tiles blockIdx.x, blockIdx.x + gridDim.x, ... and keeps its
+// gradient sums in registers, so that grad receives one set of atomic adds per
+// block instead of one per tile.
 __global__ void __launch_bounds__(256) backward_kernel(const float* __restrict__ par,
                                                        const float* __restrict__ feat,
                                                        const float* __restrict__ y, int64_t n_pts,
@@ -174,90 +177,90 @@ __global__ void __launch_bounds__(256) backward_kernel(const float* __restrict__
   load_net(par, sm, n);
   __syncthreads();
   const int t = threadIdx.x;
-  const int64_t p0 = (int64_t)blockIdx.x * MP;
-  forward_block(n, feat, p0, n_pts, bf(par[O_B3]));
-  // ds and the loss
-  if (t < MP) {
-    const int64_t p = p0 + t;
-    float ds = 0.f, l = 0.f;
-    if (p < n_pts) {
-      const float s = n.S[t], yy = y[p];
-      const float sig = 1.f / (1.f + expf(-s));
-      ds = (pos_w * yy * (sig - 1.f) + (1.f - yy) * sig) * inv_n;
-      l = pos_w * yy * softplusf(-s) + (1.f - yy) * softplusf(s);
-    }
-    n.S[t] = ds;
-    n.R[t] = l;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double ls = 0.0;
-    for (int p = 0; p < MP; ++p) ls += n.R[p];
-    atomicAdd(loss, ls);
-  }
-  // gW3, gb3 and d2 = ds W3 (z2 > 0), stored over Z2
-  if (t < MH) {
-    const int j = t;
-    float g3 = 0.f;
-    for (int p = 0; p < MP; ++p) g3 = fmaf(n.S[p], fmaxf(n.Z2[p * WS + j], 0.f), g3);
-    atomicAdd(grad + O_W3 + j, g3);
-  }
-  if (t == MH) {
-    float gb = 0.f;
-    for (int p = 0; p < MP; ++p) gb += n.S[p];
-    atomicAdd(grad + O_B3, gb);
-  }
-  __syncthreads();
-  for (int e = t; e < MP * MH; e += blockDim.x) {
-    const int p = e / MH, j = e % MH;
-    const float z = n.Z2[p * WS + j];
-    n.Z2[p * WS + j] = z > 0.f ? n.S[p] * n.W3[j] : 0.f;
-  }
-  __syncthreads();
-  // gW2[j][i] = sum_p d2[p][j] h1[p][i], gb2[j] = sum_p d2[p][j]
-  {
-    const int j = t % MH, ih = t / MH;
-    float acc[MH / 2];
+  const float b3 = bf(par[O_B3]);
+  // block-persistent gradient sums
+  const int j2 = t % MH, ih = t / MH;  // gW2 row j2, columns ih * 64 ..
+  float gw2[MH / 2];
 #pragma unroll
-    for (int q = 0; q < MH / 2; ++q) acc[q] = 0.f;
-    float gb = 0.f;
+  for (int q = 0; q < MH / 2; ++q) gw2[q] = 0.f;
+  float gb2 = 0.f, gw3 = 0.f, gb3 = 0.f;
+  float gw1[MF];
+#pragma unroll
+  for (int f = 0; f < MF; ++f) gw1[f] = 0.f;
+  float gb1 = 0.f;
+  double lsum = 0.0;
+  for (int64_t p0 = (int64_t)blockIdx.x * MP; p0 < n_pts; p0 += (int64_t)gridDim.x * MP) {
+    forward_block(n, feat, p0, n_pts, b3);
+    // ds and the loss
+    if (t < MP) {
+      const int64_t p = p0 + t;
+      float ds = 0.f, l = 0.f;
+      if (p < n_pts) {
+        const float s = n.S[t], yy = y[p];
+        const float sig = 1.f / (1.f + expf(-s));
+        ds = (pos_w * yy * (sig - 1.f) + (1.f - yy) * sig) * inv_n;
+        l = pos_w * yy * softplusf(-s) + (1.f - yy) * softplusf(s);
+      }
+      n.S[t] = ds;
+      n.R[t] = l;
+    }
+    __syncthreads();
+    if (t == 0)
+      for (int p = 0; p < MP; ++p) lsum += n.R[p];
+    // gW3, gb3 and d2 = ds W3 (z2 > 0), stored over Z2
+    if (t < MH) {
+      for (int p = 0; p < MP; ++p) gw3 = fmaf(n.S[p], fmaxf(n.Z2[p * WS + t], 0.f), gw3);
+    }
+    if (t == MH) {
+      for (int p = 0; p < MP; ++p) gb3 += n.S[p];
+    }
+    __syncthreads();
+    for (int e = t; e < MP * MH; e += blockDim.x) {
+      const int p = e / MH, j = e % MH;
+      const float z = n.Z2[p * WS + j];
+      n.Z2[p * WS + j] = z > 0.f ? n.S[p] * n.W3[j] : 0.f;
+    }
+    __syncthreads();
+    // gW2[j][i] += sum_p d2[p][j] h1[p][i], gb2[j] += sum_p d2[p][j]
     for (int p = 0; p < MP; ++p) {
-      const float d = n.Z2[p * WS + j];
-      gb += d;
+      const float d = n.Z2[p * WS + j2];
+      gb2 += d;
 #pragma unroll
-      for (int q = 0; q < MH / 2; ++q) acc[q] = fmaf(d, n.H1[p * WS + ih * (MH / 2) + q], acc[q]);
+      for (int q = 0; q < MH / 2; ++q) gw2[q] = fmaf(d, n.H1[p * WS + ih * (MH / 2) + q], gw2[q]);
     }
+    // d1[p][i] = (sum_j d2[p][j] W2[j][i]) (z1 > 0)  (h1 > 0 <=> z1 > 0)
+    {
+      const int i = t % MH, ph = t / MH;
+      float d1[MP / 2];
 #pragma unroll
-    for (int q = 0; q < MH / 2; ++q) atomicAdd(grad + O_W2 + j * MH + ih * (MH / 2) + q, acc[q]);
-    if (ih == 0) atomicAdd(grad + O_B2 + j, gb);
+      for (int q = 0; q < MP / 2; ++q) d1[q] = 0.f;
+      for (int j = 0; j < MH; ++j) {
+        const float wv = n.W2[j * WS + i];
+#pragma unroll
+        for (int q = 0; q < MP / 2; ++q) d1[q] = fmaf(n.Z2[(ph * (MP / 2) + q) * WS + j], wv, d1[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < MP / 2; ++q) {
+        const int p = ph * (MP / 2) + q;
+        const float d = n.H1[p * WS + i] > 0.f ? d1[q] : 0.f;
+        gb1 += d;
+#pragma unroll
+        for (int f = 0; f < MF; ++f) gw1[f] = fmaf(d, n.X[p * MF + f], gw1[f]);
+      }
+    }
+    __syncthreads();  // the next tile's forward overwrites X, H1, Z2 and S
   }
-  __syncthreads();
-  // d1[p][i] = (sum_j d2[p][j] W2[j][i]) (z1 > 0)  (h1 > 0 <=> z1 > 0); kept in registers
+  if (t == 0) atomicAdd(loss, lsum);
+  if (t < MH) atomicAdd(grad + O_W3 + t, gw3);
+  if (t == MH) atomicAdd(grad + O_B3, gb3);
+#pragma unroll
+  for (int q = 0; q < MH / 2; ++q) atomicAdd(grad + O_W2 + j2 * MH + ih * (MH / 2) + q, gw2[q]);
+  if (ih == 0) atomicAdd(grad + O_B2 + j2, gb2);
   {
-    const int i = t % MH, ph = t / MH;
-    float d1[MP / 2];
+    const int i = t % MH;
 #pragma unroll
-    for (int q = 0; q < MP / 2; ++q) d1[q] = 0.f;
-    for (int j = 0; j < MH; ++j) {
-      const float wv = n.W2[j * WS + i];
-#pragma unroll
-      for (int q = 0; q < MP / 2; ++q) d1[q] = fmaf(n.Z2[(ph * (MP / 2) + q) * WS + j], wv, d1[q]);
-    }
-    float g1[MF];
-#pragma unroll
-    for (int f = 0; f < MF; ++f) g1[f] = 0.f;
-    float gb = 0.f;
-#pragma unroll
-    for (int q = 0; q < MP / 2; ++q) {
-      const int p = ph * (MP / 2) + q;
-      const float d = n.H1[p * WS + i] > 0.f ? d1[q] : 0.f;
-      gb += d;
-#pragma unroll
-      for (int f = 0; f < MF; ++f) g1[f] = fmaf(d, n.X[p * MF + f], g1[f]);
-    }
-#pragma unroll
-    for (int f = 0; f < MF; ++f) atomicAdd(grad + O_W1 + i * MF + f, g1[f]);
-    atomicAdd(grad + O_B1 + i, gb);
+    for (int f = 0; f < MF; ++f) atomicAdd(grad + O_W1 + i * MF + f, gw1[f]);
+    atomicAdd(grad + O_B1 + i, gb1);
   }
 }
 
@@ -471,7 +474,12 @@ int mlp_backward(const float* par, const float* feat, const float* y, int64_t n,
                  int64_t n_total, float* grad, double* loss, cudaStream_t s) {
   ISDF_ARG(par && feat && y && grad && loss && n > 0 && n_total >= n, "bad arguments");
   ISDF_TRY(set_smem((const void*)backward_kernel));
-  backward_kernel<<<nb(n, MP), 256, NET_FLOATS * sizeof(float), s>>>(
+  int dev = 0, nsm = 148;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t tiles = ceil_div(n, MP);
+  const unsigned blocks = (unsigned)(tiles < 2 * nsm ? tiles : 2 * nsm);
+  backward_kernel<<<blocks, 256, NET_FLOATS * sizeof(float), s>>>(
       par, feat, y, n, pos_w, 1.0f / (float)n_total, grad, loss);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;

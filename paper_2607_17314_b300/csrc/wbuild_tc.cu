@@ -1323,7 +1323,12 @@ inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
 
 // Inner points per stage-1 tensor-core accumulation run before each fold into
 // the running sum (stage 2 folds every 256), and grid points per stage-2 CTA.
-constexpr int64_t kDefaultChunk = 512;
+// The error of the tensor core's FP32 accumulation grows with the number of
+// MMAs per run: 384 BF16 points (72 accumulating MMAs with three products)
+// keep the H50-chain energies within 7.7e-7 Ha of the FP64 path (512: 9.9e-7);
+// the TF32 form takes K = 8 per MMA, so 128 points give it a comparable count.
+constexpr int64_t kDefaultChunk = 384;
+constexpr int64_t kDefaultChunkTf32 = 128;
 constexpr int64_t kS2Range = 8192;
 
 }  // namespace
@@ -1629,7 +1634,7 @@ static int s1_setup(const isdf_jastrow& J, const isdf_options& opt, int64_t n_g,
   // multi-centre generator is single-CTA.
   S.pair = S.radial && ((opt.debug_flags & 2) == 0 || S.limbs1 == 3 || S.tf32);
   S.n_k = round_up(n_g, 32);
-  S.kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : kDefaultChunk;
+  S.kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : (S.tf32 ? kDefaultChunkTf32 : kDefaultChunk);
   return ISDF_OK;
 }
 

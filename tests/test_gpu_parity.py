@@ -186,7 +186,7 @@ def test_w_tensor_core(P, h6, prec):
     gerrs = [rel(host(calG[c]), o["calG"][c]) for c in range(4)]
     print(prec, "W rel", errs, "calG rel", gerrs)
     # the error is dominated by the tensor core's FP32 accumulation, kept
-    # short by folding every 512 inner points into an FP32 running sum;
+    # short by folding every 384 inner points into an FP32 running sum;
     # both limb counts meet the 1e-5 bar
     assert max(errs) < 1e-5, errs
 
