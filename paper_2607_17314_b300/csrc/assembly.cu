@@ -163,11 +163,10 @@ __global__ void right_operand_kernel(const double* __restrict__ phiP,
       v = Xp[pair_row(q, s) * n_mu + mu];
     }
   }
-  float f = (float)v;  // limbs of the FP32 rounding; each remainder is exact in FP32
-  for (int l = 0; l < limbs; ++l) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+  for (int l = 0; l < limbs; ++l) {  // three limbs: split in FP64
+    const __nv_bfloat16 h = __double2bfloat16(v);
     out[l * plane + e] = h;
-    f -= __bfloat162float(h);
+    v -= (double)__bfloat162float(h);
   }
 }
 

@@ -477,8 +477,9 @@ int mlp_backward(const float* par, const float* feat, const float* y, int64_t n,
   int dev = 0, nsm = 148;
   ISDF_CUDA(cudaGetDevice(&dev));
   ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // one block per SM (the network image takes ~141 KB of shared memory)
   const int64_t tiles = ceil_div(n, MP);
-  const unsigned blocks = (unsigned)(tiles < 2 * nsm ? tiles : 2 * nsm);
+  const unsigned blocks = (unsigned)(tiles < nsm ? tiles : nsm);
   backward_kernel<<<blocks, 256, NET_FLOATS * sizeof(float), s>>>(
       par, feat, y, n, pos_w, 1.0f / (float)n_total, grad, loss);
   ISDF_LAUNCH_CHECK();

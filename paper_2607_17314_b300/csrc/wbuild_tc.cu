@@ -140,6 +140,14 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t src_rs, int
     v = src[r * src_rs + c0 + c];
     if (colw) v *= colw[c0 + c];
   }
+  if (limbs == 3) {  // three limbs reach below the FP32 rounding: split in FP64
+    for (int l = 0; l < 3; ++l) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      dst[l * plane + e] = h;
+      v -= (double)__bfloat162float(h);
+    }
+    return;
+  }
   float f = (float)v;  // limbs of the FP32 rounding; each remainder is exact in FP32
   for (int l = 0; l < limbs; ++l) {
     const __nv_bfloat16 h = __float2bfloat16_rn(f);
@@ -157,21 +165,38 @@ __global__ void split_rows_kernel(const double* __restrict__ src, int64_t src_rs
   const int64_t r = blockIdx.y;
   const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (c >= cols_pad) return;
-  // the limbs split the FP32 rounding of the value, so that the only FP64
-  // arithmetic per element is the weight product and one conversion (B300's
-  // FP64 pipe is narrow); each remainder is exact in FP32
-  float v[4];
+  // with two limbs (16 significant bits) the limbs split the FP32 rounding of
+  // the value, so that the only FP64 arithmetic per element is the weight
+  // product and one conversion (B300's FP64 pipe is narrow; each remainder is
+  // exact in FP32); three limbs reach below it and split in FP64
+  double x[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int64_t cc = c + q;
-    double x = 0.0;
+    x[q] = 0.0;
     if (r < rows && cc < cols) {
-      x = src[r * src_rs + c0 + cc];
-      if (colw) x *= colw[c0 + cc];
+      x[q] = src[r * src_rs + c0 + cc];
+      if (colw) x[q] *= colw[c0 + cc];
     }
-    v[q] = (float)x;
   }
   __nv_bfloat16* out = dst + r * cols_pad + c;
+  if (limbs == 3) {
+    for (int l = 0; l < 3; ++l) {
+      uint32_t bits[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 h = __double2bfloat16(x[q]);
+        bits[q] = (uint32_t)__bfloat16_as_ushort(h);
+        x[q] -= (double)__bfloat162float(h);
+      }
+      *reinterpret_cast<uint2*>(out + l * plane) =
+          make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
+    }
+    return;
+  }
+  float v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = (float)x[q];
   for (int l = 0; l < limbs; ++l) {
     uint32_t bits[4];
 #pragma unroll

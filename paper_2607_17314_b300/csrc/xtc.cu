@@ -206,11 +206,20 @@ __global__ void split_t_kernel(const double* __restrict__ src, int64_t src_rs, i
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int64_t r = r0 + i, c = cb + threadIdx.x;
     if (r >= rows_pad || c >= cols_pad) continue;
-    float v = (float)t[threadIdx.x][i];  // limbs of the FP32 rounding
+    double v = t[threadIdx.x][i];
+    if (limbs == 3) {  // three limbs reach below the FP32 rounding: split in FP64
+      for (int l = 0; l < 3; ++l) {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        dst[l * plane + r * cols_pad + c] = h;
+        v -= (double)__bfloat162float(h);
+      }
+      continue;
+    }
+    float f = (float)v;  // limbs of the FP32 rounding
     for (int l = 0; l < limbs; ++l) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
       dst[l * plane + r * cols_pad + c] = h;
-      v -= __bfloat162float(h);
+      f -= __bfloat162float(h);
     }
   }
 }
