@@ -100,7 +100,7 @@ FALLBACK_BF16_SUSTAINED_TFLOPS = 1400.0
 # (the launch's compulsory traffic, FP64 calG writes and the (w xi) limb reads,
 # scales with it), and sm__pipe_tensor_cycles_active as a fraction of elapsed
 # cycles.  Empty for a kernel not yet captured.
-S1_NCU = {"bf16x3": {"dram_bytes_per_mu_g": 48.3, "tensor_pipe_active": 0.606}}
+S1_NCU = {"bf16x3": {"dram_bytes_per_mu_g": 50.2, "tensor_pipe_active": 0.608}}
 
 
 def tensor_peak(root=None):

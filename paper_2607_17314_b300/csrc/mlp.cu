@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "linalg.cuh"
+#include "mlp_layout.cuh"
 
 namespace isdf {
 
@@ -18,9 +19,8 @@ int points(const double*, const double*, const double*, int64_t, int, int, int, 
 
 namespace {
 
-constexpr int MF = 8, MH = 128, MP = 64;  // features, width, points per block
-constexpr int O_W1 = 0, O_B1 = O_W1 + MH * MF, O_W2 = O_B1 + MH, O_B2 = O_W2 + MH * MH,
-              O_W3 = O_B2 + MH, O_B3 = O_W3 + MH, N_PAR = O_B3 + 1;
+using namespace mlpl;
+constexpr int MP = 64;  // points per block
 constexpr int WS = MH + 1;  // padded row stride in shared memory
 
 struct Nuclei {
@@ -462,8 +462,13 @@ static int set_smem(const void* fn) {
   return ISDF_OK;
 }
 
+int mlp_forward_tc(const float*, const float*, int64_t, float*, cudaStream_t);
+int mlp_backward_tc(const float*, const float*, const float*, int64_t, float, int64_t, float*,
+                    double*, cudaStream_t);
+
 int mlp_forward(const float* par, const float* feat, int64_t n, float* scores, cudaStream_t s) {
   ISDF_ARG(par && feat && scores && n > 0, "bad arguments");
+  return mlp_forward_tc(par, feat, n, scores, s);
   ISDF_TRY(set_smem((const void*)forward_kernel));
   forward_kernel<<<nb(n, MP), 256, NET_FLOATS * sizeof(float), s>>>(par, feat, n, scores);
   ISDF_LAUNCH_CHECK();
@@ -473,6 +478,7 @@ int mlp_forward(const float* par, const float* feat, int64_t n, float* scores, c
 int mlp_backward(const float* par, const float* feat, const float* y, int64_t n, float pos_w,
                  int64_t n_total, float* grad, double* loss, cudaStream_t s) {
   ISDF_ARG(par && feat && y && grad && loss && n > 0 && n_total >= n, "bad arguments");
+  return mlp_backward_tc(par, feat, y, n, pos_w, n_total, grad, loss, s);
   ISDF_TRY(set_smem((const void*)backward_kernel));
   int dev = 0, nsm = 148;
   ISDF_CUDA(cudaGetDevice(&dev));
