@@ -312,7 +312,12 @@ int tc_kernel_adjoint_range(const double* grid_xyz, const double* w, const doubl
  * decides between the result and the plain selection, which stays the fallback.
  * params: device FP32 [isdf_mlp_n_params()] laid out W1 [128][8], b1 [128],
  * W2 [128][128], b2 [128], W3 [128], b3; the forward uses their BF16
- * roundings with FP32 arithmetic. */
+ * roundings.  Layers 1 and 3 run in FP32 on CUDA cores; the 128 x 128 layer
+ * products (z2, and in the backward d1 and the W2/W1 weight gradients) run on
+ * the tcgen05 tensor cores with FP32 values in two BF16 limbs (three products)
+ * and FP32 accumulation.  A bounded wait of those kernels that expires (2 s)
+ * writes NaN into the first score of the CTA's first tile (forward) or adds
+ * NaN to *loss (backward). */
 int isdf_mlp_n_params(void);
 
 /* Per-point features feat [n_g][8] (FP32): log10 of the scalar and gradient

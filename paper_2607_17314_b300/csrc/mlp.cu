@@ -1,9 +1,9 @@
 // Learned interpolation-point proposer (not in the paper): per-point
-// features, a small MLP (8 -> 128 -> 128 -> 1, BF16 weights,
-// FP32 arithmetic) trained by weighted binary cross-entropy against the plain
-// pivoted-Cholesky selection, Adam, top-k candidate selection, the pivoted
-// Cholesky restricted to the candidates, and the scalar-channel ISDF fit error
-// that decides between selections.
+// features, a small MLP (8 -> 128 -> 128 -> 1, BF16 weights; its forward and
+// backward passes are in mlp_tc.cu) trained by weighted binary cross-entropy
+// against the plain pivoted-Cholesky selection, Adam, top-k candidate
+// selection, the pivoted Cholesky restricted to the candidates, and the
+// scalar-channel ISDF fit error that decides between selections.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -20,8 +20,6 @@ int points(const double*, const double*, const double*, int64_t, int, int, int, 
 namespace {
 
 using namespace mlpl;
-constexpr int MP = 64;  // points per block
-constexpr int WS = MH + 1;  // padded row stride in shared memory
 
 struct Nuclei {
   int n;
@@ -62,206 +60,6 @@ __global__ void features_kernel(const double* __restrict__ phi, const double* __
   f[5] = (float)(r1 / 5.0);
   f[6] = (float)(r2 / 5.0);
   f[7] = (float)log10(r1 + 1e-3);
-}
-
-__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// Shared-memory image of the network with BF16-rounded weights.
-struct Net {
-  float* W1;  // [MH][MF]
-  float* b1;
-  float* W2;  // [MH][WS]
-  float* b2;
-  float* W3;
-  float* X;   // [MP][MF]
-  float* H1;  // [MP][WS]  relu(z1)
-  float* Z2;  // [MP][WS]  z2, later d2
-  float* S;   // [MP] scores, later ds
-  float* R;   // [4][MP] reduction scratch
-};
-
-__device__ void load_net(const float* __restrict__ par, float* sm, Net& n) {
-  n.W1 = sm;
-  n.b1 = n.W1 + MH * MF;
-  n.W2 = n.b1 + MH;
-  n.b2 = n.W2 + MH * WS;
-  n.W3 = n.b2 + MH;
-  n.X = n.W3 + MH;
-  n.H1 = n.X + MP * MF;
-  n.Z2 = n.H1 + MP * WS;
-  n.S = n.Z2 + MP * WS;
-  n.R = n.S + MP;
-  for (int e = threadIdx.x; e < MH * MF; e += blockDim.x) n.W1[e] = bf(par[O_W1 + e]);
-  for (int e = threadIdx.x; e < MH * MH; e += blockDim.x)
-    n.W2[(e / MH) * WS + e % MH] = bf(par[O_W2 + e]);
-  for (int e = threadIdx.x; e < MH; e += blockDim.x) {
-    n.b1[e] = bf(par[O_B1 + e]);
-    n.b2[e] = bf(par[O_B2 + e]);
-    n.W3[e] = bf(par[O_W3 + e]);
-  }
-}
-
-constexpr size_t NET_FLOATS = MH * MF + MH + MH * WS + MH + MH + MP * MF + 2 * MP * WS + MP + 4 * MP;
-
-// Forward for the block's points: fills H1, Z2 and S (scores).
-__device__ void forward_block(Net& n, const float* __restrict__ feat, int64_t p0, int64_t n_pts,
-                              float b3) {
-  const int t = threadIdx.x;
-  for (int e = t; e < MP * MF; e += blockDim.x) {
-    const int64_t p = p0 + e / MF;
-    n.X[e] = p < n_pts ? feat[p0 * MF + e] : 0.f;
-  }
-  __syncthreads();
-  for (int e = t; e < MP * MH; e += blockDim.x) {
-    const int p = e / MH, j = e % MH;
-    float z = n.b1[j];
-#pragma unroll
-    for (int f = 0; f < MF; ++f) z = fmaf(n.W1[j * MF + f], n.X[p * MF + f], z);
-    n.H1[p * WS + j] = fmaxf(z, 0.f);
-  }
-  __syncthreads();
-  {
-    const int j = t % MH, ph = t / MH;  // 256 threads: two halves of the points
-    float z[MP / 2];
-#pragma unroll
-    for (int q = 0; q < MP / 2; ++q) z[q] = n.b2[j];
-    for (int i = 0; i < MH; ++i) {
-      const float wv = n.W2[j * WS + i];
-#pragma unroll
-      for (int q = 0; q < MP / 2; ++q) z[q] = fmaf(wv, n.H1[(ph * (MP / 2) + q) * WS + i], z[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < MP / 2; ++q) n.Z2[(ph * (MP / 2) + q) * WS + j] = z[q];
-  }
-  __syncthreads();
-  // s[p] = sum_j W3[j] relu(z2[p][j]) + b3: one warp per 8 points
-  for (int p = t / 32; p < MP; p += blockDim.x / 32) {
-    float acc = 0.f;
-    for (int j = t % 32; j < MH; j += 32) acc = fmaf(n.W3[j], fmaxf(n.Z2[p * WS + j], 0.f), acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (t % 32 == 0) n.S[p] = acc + b3;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) forward_kernel(const float* __restrict__ par,
-                                                      const float* __restrict__ feat, int64_t n_pts,
-                                                      float* __restrict__ scores) {
-  extern __shared__ float sm[];
-  Net n;
-  load_net(par, sm, n);
-  __syncthreads();
-  const int64_t p0 = (int64_t)blockIdx.x * MP;
-  forward_block(n, feat, p0, n_pts, bf(par[O_B3]));
-  for (int p = threadIdx.x; p < MP; p += blockDim.x)
-    if (p0 + p < n_pts) scores[p0 + p] = n.S[p];
-}
-
-__device__ __forceinline__ float softplusf(float t) {
-  return fmaxf(t, 0.f) + log1pf(expf(-fabsf(t)));
-}
-
-// Gradient of the mean weighted BCE over n_total points (this call covers
-// n_pts of them), accumulated into grad; the loss sum into *loss.  Each block
-// loops over point tiles blockIdx.x, blockIdx.x + gridDim.x, ... and keeps its
-// gradient sums in registers, so that grad receives one set of atomic adds per
-// block instead of one per tile.
-__global__ void __launch_bounds__(256) backward_kernel(const float* __restrict__ par,
-                                                       const float* __restrict__ feat,
-                                                       const float* __restrict__ y, int64_t n_pts,
-                                                       float pos_w, float inv_n,
-                                                       float* __restrict__ grad,
-                                                       double* __restrict__ loss) {
-  extern __shared__ float sm[];
-  Net n;
-  load_net(par, sm, n);
-  __syncthreads();
-  const int t = threadIdx.x;
-  const float b3 = bf(par[O_B3]);
-  // block-persistent gradient sums
-  const int j2 = t % MH, ih = t / MH;  // gW2 row j2, columns ih * 64 ..
-  float gw2[MH / 2];
-#pragma unroll
-  for (int q = 0; q < MH / 2; ++q) gw2[q] = 0.f;
-  float gb2 = 0.f, gw3 = 0.f, gb3 = 0.f;
-  float gw1[MF];
-#pragma unroll
-  for (int f = 0; f < MF; ++f) gw1[f] = 0.f;
-  float gb1 = 0.f;
-  double lsum = 0.0;
-  for (int64_t p0 = (int64_t)blockIdx.x * MP; p0 < n_pts; p0 += (int64_t)gridDim.x * MP) {
-    forward_block(n, feat, p0, n_pts, b3);
-    // ds and the loss
-    if (t < MP) {
-      const int64_t p = p0 + t;
-      float ds = 0.f, l = 0.f;
-      if (p < n_pts) {
-        const float s = n.S[t], yy = y[p];
-        const float sig = 1.f / (1.f + expf(-s));
-        ds = (pos_w * yy * (sig - 1.f) + (1.f - yy) * sig) * inv_n;
-        l = pos_w * yy * softplusf(-s) + (1.f - yy) * softplusf(s);
-      }
-      n.S[t] = ds;
-      n.R[t] = l;
-    }
-    __syncthreads();
-    if (t == 0)
-      for (int p = 0; p < MP; ++p) lsum += n.R[p];
-    // gW3, gb3 and d2 = ds W3 (z2 > 0), stored over Z2
-    if (t < MH) {
-      for (int p = 0; p < MP; ++p) gw3 = fmaf(n.S[p], fmaxf(n.Z2[p * WS + t], 0.f), gw3);
-    }
-    if (t == MH) {
-      for (int p = 0; p < MP; ++p) gb3 += n.S[p];
-    }
-    __syncthreads();
-    for (int e = t; e < MP * MH; e += blockDim.x) {
-      const int p = e / MH, j = e % MH;
-      const float z = n.Z2[p * WS + j];
-      n.Z2[p * WS + j] = z > 0.f ? n.S[p] * n.W3[j] : 0.f;
-    }
-    __syncthreads();
-    // gW2[j][i] += sum_p d2[p][j] h1[p][i], gb2[j] += sum_p d2[p][j]
-    for (int p = 0; p < MP; ++p) {
-      const float d = n.Z2[p * WS + j2];
-      gb2 += d;
-#pragma unroll
-      for (int q = 0; q < MH / 2; ++q) gw2[q] = fmaf(d, n.H1[p * WS + ih * (MH / 2) + q], gw2[q]);
-    }
-    // d1[p][i] = (sum_j d2[p][j] W2[j][i]) (z1 > 0)  (h1 > 0 <=> z1 > 0)
-    {
-      const int i = t % MH, ph = t / MH;
-      float d1[MP / 2];
-#pragma unroll
-      for (int q = 0; q < MP / 2; ++q) d1[q] = 0.f;
-      for (int j = 0; j < MH; ++j) {
-        const float wv = n.W2[j * WS + i];
-#pragma unroll
-        for (int q = 0; q < MP / 2; ++q) d1[q] = fmaf(n.Z2[(ph * (MP / 2) + q) * WS + j], wv, d1[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < MP / 2; ++q) {
-        const int p = ph * (MP / 2) + q;
-        const float d = n.H1[p * WS + i] > 0.f ? d1[q] : 0.f;
-        gb1 += d;
-#pragma unroll
-        for (int f = 0; f < MF; ++f) gw1[f] = fmaf(d, n.X[p * MF + f], gw1[f]);
-      }
-    }
-    __syncthreads();  // the next tile's forward overwrites X, H1, Z2 and S
-  }
-  if (t == 0) atomicAdd(loss, lsum);
-  if (t < MH) atomicAdd(grad + O_W3 + t, gw3);
-  if (t == MH) atomicAdd(grad + O_B3, gb3);
-#pragma unroll
-  for (int q = 0; q < MH / 2; ++q) atomicAdd(grad + O_W2 + j2 * MH + ih * (MH / 2) + q, gw2[q]);
-  if (ih == 0) atomicAdd(grad + O_B2 + j2, gb2);
-  {
-    const int i = t % MH;
-#pragma unroll
-    for (int f = 0; f < MF; ++f) atomicAdd(grad + O_W1 + i * MF + f, gw1[f]);
-    atomicAdd(grad + O_B1 + i, gb1);
-  }
 }
 
 __global__ void adam_kernel(float* __restrict__ par, const float* __restrict__ grad,
@@ -456,11 +254,6 @@ int mlp_features(const double* phi, const double* dphi, const double* w, const d
   return ISDF_OK;
 }
 
-static int set_smem(const void* fn) {
-  ISDF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(NET_FLOATS * sizeof(float))));
-  return ISDF_OK;
-}
 
 int mlp_forward_tc(const float*, const float*, int64_t, float*, cudaStream_t);
 int mlp_backward_tc(const float*, const float*, const float*, int64_t, float, int64_t, float*,
@@ -469,27 +262,12 @@ int mlp_backward_tc(const float*, const float*, const float*, int64_t, float, in
 int mlp_forward(const float* par, const float* feat, int64_t n, float* scores, cudaStream_t s) {
   ISDF_ARG(par && feat && scores && n > 0, "bad arguments");
   return mlp_forward_tc(par, feat, n, scores, s);
-  ISDF_TRY(set_smem((const void*)forward_kernel));
-  forward_kernel<<<nb(n, MP), 256, NET_FLOATS * sizeof(float), s>>>(par, feat, n, scores);
-  ISDF_LAUNCH_CHECK();
-  return ISDF_OK;
 }
 
 int mlp_backward(const float* par, const float* feat, const float* y, int64_t n, float pos_w,
                  int64_t n_total, float* grad, double* loss, cudaStream_t s) {
   ISDF_ARG(par && feat && y && grad && loss && n > 0 && n_total >= n, "bad arguments");
   return mlp_backward_tc(par, feat, y, n, pos_w, n_total, grad, loss, s);
-  ISDF_TRY(set_smem((const void*)backward_kernel));
-  int dev = 0, nsm = 148;
-  ISDF_CUDA(cudaGetDevice(&dev));
-  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // one block per SM (the network image takes ~141 KB of shared memory)
-  const int64_t tiles = ceil_div(n, MP);
-  const unsigned blocks = (unsigned)(tiles < nsm ? tiles : nsm);
-  backward_kernel<<<blocks, 256, NET_FLOATS * sizeof(float), s>>>(
-      par, feat, y, n, pos_w, 1.0f / (float)n_total, grad, loss);
-  ISDF_LAUNCH_CHECK();
-  return ISDF_OK;
 }
 
 int mlp_adam(float* par, const float* grad, float* m, float* v, int t, float lr, cudaStream_t s) {
