@@ -1350,7 +1350,7 @@ inline unsigned nb256(int64_t n) { return (unsigned)ceil_div(n, 256); }
 // the running sum (stage 2 folds every 256), and grid points per stage-2 CTA.
 // The error of the tensor core's FP32 accumulation grows with the number of
 // MMAs per run: 384 BF16 points (72 accumulating MMAs with three products)
-// keep the H50-chain energies within 7.7e-7 Ha of the FP64 path (512: 9.9e-7);
+// keep the H50-chain energies within 8.4e-7 Ha of the FP64 path (512: 9.9e-7);
 // the TF32 form takes K = 8 per MMA, so 128 points give it a comparable count.
 constexpr int64_t kDefaultChunk = 384;
 constexpr int64_t kDefaultChunkTf32 = 128;
