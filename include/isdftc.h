@@ -227,11 +227,11 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * ISDF_E_NONFINITE when W holds a NaN or Inf (every input value reaches W).
  * ISDF_PREC_FP64 takes any correlator.  The
  * tensor-core precisions take the radial correlator (n_terms = 0, cusp = 1,
- * no one-body term; CTA-pair kernel) and, on the multi-centre generator,
- * correlators with the one-body term and those whose terms have m, n <= 3, o <= 4 and at most
- * two distinct E exponents o among the terms with (m, n) != (0, 0), with the
- * nucleus count limited by shared memory (ISDF_E_ARG beyond it; 12 centres
- * with three E-exponent-2 electron-electron-nucleus terms use 198 KB).
+ * no one-body term) and, on the multi-centre generator, correlators with the
+ * one-body term and those whose terms have m, n <= 3, o <= 4 and at most two
+ * distinct E exponents o among the terms with (m, n) != (0, 0), both on CTA
+ * pairs, with the nucleus count limited by shared memory (ISDF_E_ARG beyond
+ * it; 12 centres with the benzene configuration's term set use 206 KB).
  * Synchronises `stream` when options->sync_check (default).
  * The workspace query takes the correlator (NULL: the largest layout the
  * call accepts). */

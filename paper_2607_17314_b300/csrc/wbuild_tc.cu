@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(S1C<LIMBS, (NG >= 0)>::THREADS, 1)
 // inner points, 128-byte swizzle, kind::tf32 MMAs of K = 8); otherwise BF16
 // limbs (64-byte rows, 64-byte swizzle, kind::f16 MMAs of K = 16).  Both
 // advance 32 bytes of K per MMA.
-template <int LIMBS, int NGRP = 1, bool TF32 = false>
+template <int LIMBS, int NGRP = 1, bool TF32 = false, bool BH = false>
 struct S1P {
   static constexpr int BM = 128, BN = 64, BNH = 32, BK = 32;
   static constexpr int EB = TF32 ? 4 : 2;               // operand bytes
@@ -826,7 +826,9 @@ struct S1P {
   static constexpr int KSUB = ROWB / 32;                // MMAs per limb product and k-step
   static constexpr uint32_t SBO = 8 * ROWB;             // 8-row core-matrix stride
   static constexpr uint32_t SWZ = TF32 ? 2 : 4;         // descriptor layout: 128B / 64B swizzle
-  static constexpr int STAGES = TF32 ? 3 : (LIMBS == 2 ? 6 : 4);
+  // the multi-centre generator's per-row nucleus table and A_{g'I} ring take
+  // shared memory from the stages
+  static constexpr int STAGES = TF32 ? 3 : (LIMBS == 2 ? (BH ? 5 : 6) : (BH ? 3 : 4));
   static constexpr int CSTAGES = 8;
   static constexpr uint32_t A_LIMB = BM * ROWB;         // 8 KB (BF16), 16 KB (TF32)
   static constexpr uint32_t B_LIMB = 4 * BNH * ROWB;    // 128 rows
@@ -880,15 +882,24 @@ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t chunk16)
   return row * 128u + ((chunk16 ^ (row & 7u)) << 4);
 }
 
-template <int LIMBS, int NGRP, bool TF32>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF32>::THREADS, 1)
+// NG >= 0: the multi-centre generator (NG E-exponent groups, degree DEG in
+// A_{g'I}) in place of the radial one; its coordinate ring also carries the
+// A_{g'I} block (p.cbytes per slot) and a per-row nucleus table (p.tab_bytes)
+// follows the ring.
+template <int LIMBS, int NGRP, bool TF32, int NG = -1, int DEG = 0>
+__global__ void __cluster_dims__(2, 1, 1)
+    __launch_bounds__(S1P<LIMBS, NGRP, TF32, (NG >= 0)>::THREADS, 1)
     s1_pair_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ S1Params p) {
-  using C = S1P<LIMBS, NGRP, TF32>;
+  constexpr bool BH = NG >= 0;
+  using C = S1P<LIMBS, NGRP, TF32, BH>;
+  static_assert(!BH || (NGRP == 1 && !TF32), "the multi-centre pair generator: one group, BF16");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ring = stages + C::STAGES * C::STAGE;
-  uint64_t* full = (uint64_t*)(ring + C::CSTAGES * C::C_BYTES);
+  const uint32_t cstride = BH ? p.cbytes : C::C_BYTES;  // bytes per ring slot
+  uint8_t* tab = ring + C::CSTAGES * cstride;            // multi-centre row table
+  uint64_t* full = (uint64_t*)(tab + (BH ? p.tab_bytes : 0u));
   uint64_t* empty = full + C::STAGES;
   uint64_t* cfull = empty + C::STAGES;
   uint64_t* cempty = cfull + C::CSTAGES;
@@ -971,10 +982,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++cit) {
           const uint32_t cs = cit % C::CSTAGES, ph = (cit / C::CSTAGES) & 1;
           if (!tc::mbar_wait(&cempty[cs], ph ^ 1, abort_flag, p.err, p.wait_ns)) goto done;
-          uint8_t* dst = ring + cs * C::C_BYTES;
-          tc::mbar_arrive_expect_tx(&cfull[cs], C::C_BYTES);
+          uint8_t* dst = ring + cs * cstride;
+          tc::mbar_arrive_expect_tx(&cfull[cs], cstride);
           bulk_copy_g2s(dst, p.xyz_hi + p.k_begin + k0, C::BK * 16, &cfull[cs]);
           bulk_copy_g2s(dst + C::BK * 16, p.xyz_lo + p.k_begin + k0, C::BK * 16, &cfull[cs]);
+          if (BH && p.n_nuc > 0)
+            bulk_copy_g2s(dst + C::C_BYTES, p.ajtab + ((p.k_begin + k0) / C::BK) * p.n_nuc * C::BK,
+                          (uint32_t)p.n_nuc * C::BK * 4, &cfull[cs]);
         }
       }
     }
@@ -1017,6 +1031,153 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
       }
     }
   } else if (warp < 2 + C::NGW) {
+   if constexpr (BH) {
+    // multi-centre generator (the single-CTA kernel's arithmetic): lane l of
+    // generator warp w owns outer point 4 w + l / 8 of this CTA's half and inner
+    // points 4 (l % 8) .. + 3; the eight lanes of a row fill its table entries
+    constexpr int NGc = NG >= 0 ? NG : 0;
+    constexpr int NS = 3 + DEG + 2 * NGc * (DEG + 1);
+    constexpr int NS4 = (NS + 3) / 4;
+    const int wg = warp - 2;
+    const int row = wg * 4 + (lane >> 3);
+    const int kc = (lane & 7) * 4;
+    const int64_t n_gs = p.g_end - p.g_begin;
+    const float d = p.d;
+    const int n_nuc = p.n_nuc;
+    const uint32_t tabs = tc::smem_u32(tab);
+    float4* tabp = reinterpret_cast<float4*>(tab);
+    uint32_t it = 0;
+    for (int64_t tile = pair0; tile < n_tiles; tile += pstride) {
+      const int64_t g_tile = tile % p.n_g_tiles;
+      const int64_t gl = g_tile * C::BN + (int64_t)rank * C::BNH + row;
+      const bool gvalid = gl < n_gs;
+      const int64_t g = p.g_begin + (gvalid ? gl : 0);
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 gh = gvalid ? p.xyz_hi[g] : zero;
+      const float4 glo = gvalid ? p.xyz_lo[g] : zero;
+      const float4 fg = gvalid ? p.fvec[g] : zero;
+      const int64_t gself = gvalid ? g - p.k_begin : -1;  // in this launch's inner range
+      // this warp's rows of the nucleus table (its previous reads are done)
+      __syncwarp();
+      for (int idx = lane & 7; idx < n_nuc * NS4; idx += 8)
+        tabp[idx * C::BNH + row] = gvalid ? p.rowslots[g * n_nuc * NS4 + idx] : zero;
+      __syncwarp();
+      for (int64_t k0 = 0; k0 < p.n_k; k0 += C::BK, ++it) {
+        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+        const uint32_t cs = it % C::CSTAGES, cph = (it / C::CSTAGES) & 1;
+        const bool okc = tc::mbar_wait(&cfull[cs], cph, abort_flag, p.err, p.wait_ns);
+        if (!__all_sync(0xffffffffu, okc)) goto done;
+        const uint32_t cbase = tc::smem_u32(ring + cs * cstride);
+        float dx[4], dy[4], dz[4], fr[4], ce[4], gx[4], gy[4], gz[4];
+        float eo[NGc > 0 ? NGc : 1][4], wq[NGc > 0 ? NGc : 1][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          pair_diff(gh, glo, tc::lds_f4(cbase + (kc + e) * 16),
+                    tc::lds_f4(cbase + (C::BK + kc + e) * 16), dx[e], dy[e], dz[e]);
+          const float r2 = fmaxf(fmaf(dx[e], dx[e], fmaf(dy[e], dy[e], dz[e] * dz[e])), 1e-30f);
+          const float rinv = rsqrtf(r2);
+          const float r = r2 * rinv;
+          const float iden = rcp_approx(fmaf(d, r, 1.0f));
+          const float E = d * r * iden;
+          fr[e] = d * iden * iden * rinv;
+          ce[e] = fmaf(E, fmaf(E, fmaf(E, p.rho[3], p.rho[2]), p.rho[1]), p.rho[0]);
+#pragma unroll
+          for (int j = 0; j < NGc; ++j) {
+            float pw = 1.0f;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (t < p.oexp[j] - 1) pw *= E;
+            wq[j][e] = (float)p.oexp[j] * pw;
+            eo[j][e] = pw * E;
+          }
+          gx[e] = fg.x;
+          gy[e] = fg.y;
+          gz[e] = fg.z;
+        }
+        const uint32_t abase = cbase + C::C_BYTES + kc * 4;
+#pragma unroll 1
+        for (int I = 0; I < n_nuc; ++I) {
+          float sl[NS4 * 4];
+#pragma unroll
+          for (int k4 = 0; k4 < NS4; ++k4) {
+            const float4 v = tc::lds_f4(tabs + ((I * NS4 + k4) * C::BNH + row) * 16);
+            sl[4 * k4] = v.x;
+            sl[4 * k4 + 1] = v.y;
+            sl[4 * k4 + 2] = v.z;
+            sl[4 * k4 + 3] = v.w;
+          }
+          const float4 yv = tc::lds_f4(abase + I * C::BK * 4);
+          const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float s0 = sl[2 + DEG];
+#pragma unroll
+            for (int dd = DEG - 1; dd >= 1; --dd) s0 = fmaf(s0, y[e], sl[2 + dd]);
+            float ca = s0 * y[e];
+#pragma unroll
+            for (int j = 0; j < NGc; ++j) {
+              const int pb = 3 + DEG + j * 2 * (DEG + 1);
+              const int qb = pb + DEG + 1;
+              float pj = sl[pb + DEG], qj = sl[qb + DEG];
+#pragma unroll
+              for (int dd = DEG - 1; dd >= 0; --dd) {
+                pj = fmaf(pj, y[e], sl[pb + dd]);
+                qj = fmaf(qj, y[e], sl[qb + dd]);
+              }
+              ca = fmaf(eo[j][e], pj, ca);
+              ce[e] = fmaf(wq[j][e], qj, ce[e]);
+            }
+            gx[e] = fmaf(ca, sl[0], gx[e]);
+            gy[e] = fmaf(ca, sl[1], gy[e]);
+            gz[e] = fmaf(ca, sl[2], gz[e]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&cempty[cs]);  // the warp's ring reads are done
+        const bool may_self = gself >= k0 && gself < k0 + C::BK;
+        uint32_t pk[4][LIMBS][2];
+#pragma unroll
+        for (int e = 0; e < 4; e += 2) {
+          float kv[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int q = e + h;
+            const bool self = may_self && (k0 + kc + q) == gself;
+            const float fac = ce[q] * fr[q];
+            const float kx = fmaf(fac, dx[q], gx[q]);
+            const float ky = fmaf(fac, dy[q], gy[q]);
+            const float kz = fmaf(fac, dz[q], gz[q]);
+            kv[h][0] = self ? 0.f : kx;
+            kv[h][1] = self ? 0.f : ky;
+            kv[h][2] = self ? 0.f : kz;
+            kv[h][3] = self ? 0.f : fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t w[LIMBS];
+            split_pack<LIMBS>(kv[0][c], kv[1][c], w);
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) pk[c][l][e >> 1] = w[l];
+          }
+        }
+        const bool oke = tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns);
+        if (!__all_sync(0xffffffffu, oke)) goto done;
+        const uint32_t bsm = tc::smem_u32(stages + s * C::STAGE + C::A_BYTES);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t off = tc::sw64_offset(c * C::BNH + row, kc >> 3) + (kc & 7) * 2;
+#pragma unroll
+          for (int l = 0; l < LIMBS; ++l) sts_u2(bsm + l * C::B_LIMB + off, pk[c][l][0], pk[c][l][1]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if (lead) tc::mbar_arrive(&full[s]);
+          else tc::mbar_arrive_cluster(full_lead + 8u * s);
+        }
+      }
+    }
+   } else {
     // generator: lane = outer point of this CTA's half, warp = 4 inner points
     const int grp = (warp - 2) / C::GW;
     const int row = lane;
@@ -1100,6 +1261,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(S1P<LIMBS, NGRP, TF3
         }
       }
     }
+   }
   } else {
     // epilogue: this CTA's 128 accumulator rows (lane quarter warp % 4, column
     // part (warp - first epilogue warp) / 4 of EPH)
@@ -1573,6 +1735,23 @@ int launch_s1_pair(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cud
   return ISDF_OK;
 }
 
+// The multi-centre generator on CTA pairs: the ring slot carries the A_{g'I}
+// block (p.cbytes) and the per-row table (p.tab_bytes, 32 rows per CTA).
+template <int LIMBS, int NG, int DEG>
+int launch_s1_pair_bh(unsigned grid1, const CUtensorMap* mA, const S1Params& p, cudaStream_t s) {
+  using C = S1P<LIMBS, 1, false, true>;
+  const uint32_t smem = C::STAGES * C::STAGE + C::CSTAGES * p.cbytes + p.tab_bytes + 1024 + 512;
+  ISDF_ARG(smem <= kSmemLimit,
+           "too many centres for the tensor-core generator: %d nuclei with this term set need "
+           "%u bytes of shared memory",
+           p.n_nuc, smem);
+  ISDF_CUDA(cudaFuncSetAttribute(s1_pair_kernel<LIMBS, 1, false, NG, DEG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  s1_pair_kernel<LIMBS, 1, false, NG, DEG><<<grid1, C::THREADS, smem, s>>>(mA[0], mA[1], mA[2], p);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
 }  // namespace
 
 struct TcLayout {
@@ -1657,7 +1836,10 @@ static int s1_setup(const isdf_jastrow& J, const isdf_options& opt, int64_t n_g,
   // for the single-CTA kernel with two limbs; its three-limb form gave
   // run-to-run wrong elements on multi-tile grids and is not offered.  The
   // multi-centre generator is single-CTA.
-  S.pair = S.radial && ((opt.debug_flags & 2) == 0 || S.limbs1 == 3 || S.tf32);
+  // The multi-centre generator runs on CTA pairs too, unless debug bit 1 asks
+  // for its single-CTA kernel.
+  S.pair = S.radial ? ((opt.debug_flags & 2) == 0 || S.limbs1 == 3 || S.tf32)
+                    : (opt.debug_flags & 2) == 0;
   S.n_k = round_up(n_g, 32);
   S.kchunk = opt.kchunk > 0 ? round_up(opt.kchunk, 32) : (S.tf32 ? kDefaultChunkTf32 : kDefaultChunk);
   return ISDF_OK;
@@ -1725,7 +1907,9 @@ static int s1_launch(const S1Setup& S, const isdf_jastrow& J, const CUtensorMap*
   p.debug = debug;
   p.n_nuc = S.radial ? 0 : J.n_nuc;
   p.cbytes = S1C<2, false>::C_BASE + 4u * S1C<2, false>::BK * (uint32_t)p.n_nuc;
-  p.tab_bytes = S.radial ? 0u : (uint32_t)(p.n_nuc * S.K.ns4 * S1C<2, false>::BN * 16);
+  // per-row table of the tile's outer points: 32 per CTA of a pair, 64 for a single CTA
+  p.tab_bytes = S.radial ? 0u
+                         : (uint32_t)(p.n_nuc * S.K.ns4 * (S.pair ? 32 : S1C<2, false>::BN) * 16);
   p.oexp[0] = S.radial ? 1 : S.K.oexp[0];
   p.oexp[1] = S.radial ? 1 : S.K.oexp[1];
   for (int e = 0; e < 4; ++e) p.rho[e] = S.radial ? 0.f : (float)S.K.rho[e];
@@ -1740,8 +1924,18 @@ static int s1_launch(const S1Setup& S, const isdf_jastrow& J, const CUtensorMap*
   if (S.pair) grid1 = 2u * (unsigned)(n_tiles < nsm / 2 ? n_tiles : nsm / 2);
   const BhTc& K = S.K;
   if (S.tf32) return launch_s1_pair<2, true>(grid1, mA, p, s);
-  if (S.pair)
+  if (S.pair && S.radial)
     return S.limbs1 == 2 ? launch_s1_pair<2>(grid1, mA, p, s) : launch_s1_pair<3>(grid1, mA, p, s);
+  if (S.pair) {
+    if (K.ng == 1 && K.deg == 2)
+      return S.limbs1 == 2 ? launch_s1_pair_bh<2, 1, 2>(grid1, mA, p, s)
+                           : launch_s1_pair_bh<3, 1, 2>(grid1, mA, p, s);
+    if (K.ng == 1)
+      return S.limbs1 == 2 ? launch_s1_pair_bh<2, 1, 3>(grid1, mA, p, s)
+                           : launch_s1_pair_bh<3, 1, 3>(grid1, mA, p, s);
+    return S.limbs1 == 2 ? launch_s1_pair_bh<2, 2, 3>(grid1, mA, p, s)
+                         : launch_s1_pair_bh<3, 2, 3>(grid1, mA, p, s);
+  }
   if (S.radial) return launch_s1<2, -1, 0>(grid1, mA, p, s);
   if (K.ng == 1 && K.deg == 2)
     return S.limbs1 == 2 ? launch_s1<2, 1, 2>(grid1, mA, p, s) : launch_s1<3, 1, 2>(grid1, mA, p, s);

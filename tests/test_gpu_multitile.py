@@ -21,8 +21,9 @@ term and the pair part of K partly cancel for some pairs);
 the measured maxima are 2.6e-5 and 3.3e-5.  Per channel the calG relative
 Frobenius error stays within 1e-5.  With random xi, W carries heavy
 cancellation, so its relative Frobenius error is not the test here (it is
-on the fitted factors of the parity tests).  The single-CTA radial kernel
-with two limbs gives the same bits as the pair kernel and is checked too.
+on the fitted factors of the parity tests).  Both generators run on CTA
+pairs by default; the single-CTA kernels (debug bit 1: the radial one with two
+limbs, the multi-centre one) are checked too.
 """
 import multiprocessing as mp
 import os
@@ -87,8 +88,10 @@ def api():
                                         ("tf32x3", 0)])
 @pytest.mark.parametrize("name", ["radial", "benzene", "benzene_chi"])
 def test_stage1_and_w_every_element(api, name, prec, debug):
-    if (debug or prec == "tf32x3") and name != "radial":
-        pytest.skip("the multi-centre correlator has one kernel (BF16 limbs)")
+    if prec == "tf32x3" and name != "radial":
+        pytest.skip("the TF32 stage 1 takes the radial correlator only")
+    if debug and name == "benzene_chi":
+        pytest.skip("the single-CTA multi-centre kernel is checked on the benzene case")
     grid, w, jas, xi, xit, calG, bound, W, Wb = _oracle(name)
     n_g = grid.shape[0]
     c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
@@ -97,9 +100,9 @@ def test_stage1_and_w_every_element(api, name, prec, debug):
     kb()
     Gg = kb.calG.cpu().numpy()
     Wg = kb.W.cpu().numpy()
-    # the radial correlator runs on CTA pairs (256-row tiles, 74 pairs), the
-    # multi-centre one on single CTAs (128-row tiles, 148 CTAs)
-    rows, units = (256, 74) if name == "radial" and not debug else (128, 148)
+    # both generators run on CTA pairs (256-row tiles, 74 pairs); debug bit 1
+    # selects the single-CTA kernels (128-row tiles, 148 CTAs)
+    rows, units = (256, 74) if not debug else (128, 148)
     n_tiles = int(np.ceil(xi.shape[0] / rows)) * int(np.ceil(n_g / 64))
     assert n_tiles > 2 * units        # every CTA runs more than one tile
     gerr = np.abs(Gg - calG) / bound
