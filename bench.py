@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--proposer", action="store_true",
                     help="learned proposer on perturbed H30 chains (60,000 points, 240 orbitals, "
                          "N_mu = 1200): train on --n-train, report on --n-test held-out chains")
+    ap.add_argument("--vmc", action="store_true",
+                    help="VMC optimisation of the correlator (Sec. II.C) on an H20 chain: "
+                         "Metropolis sweeps, then Gauss-Newton iterations on the fixed sample")
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--sweeps", type=int, default=40)
     ap.add_argument("--n-train", type=int, default=24)
     ap.add_argument("--n-test", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=40)
@@ -707,6 +712,97 @@ def run_proposer(args):
     print(json.dumps(line), flush=True)
 
 
+def run_vmc(args):
+    """Reference-variance VMC optimisation of the correlator (Sec. II.C) on an
+    H20 chain (s/p basis, 80 functions, 10 doubly occupied orbitals, the
+    28-term one-type BH correlator: 30 parameters).  --walkers walkers start
+    around the nuclei, take --sweeps Metropolis sweeps of |Phi_0|^2 (random
+    numbers drawn on the device and passed in), then each timed step is one
+    Gauss-Newton iteration on that fixed sample: local energies with their
+    parameter Jacobian, then the step of Eq. gn applied to theta.  The
+    oracle's local energy and Jacobian are timed on a few walkers."""
+    import numpy as np
+    import torch
+    from synth import workloads as wl
+    from paper_2607_17314_b300 import api, build
+    build.build()
+    atoms, xyz, basis, C, n_occ, jas = wl.vmc_chain(20, terms=wl.bh_terms_c4(), jscale=0.05)
+    N, Nw = 2 * n_occ, args.walkers
+    Z = np.ones(len(atoms))
+    B = tuple(torch.as_tensor(np.ascontiguousarray(a)).cuda()
+              for a in (basis.center, basis.powers.astype(np.int32), basis.exps, basis.coefs))
+    Cg = torch.as_tensor(np.ascontiguousarray(C)).cuda()
+    R = torch.as_tensor(wl.vmc_walkers(xyz, Nw, N, seed=61)).cuda()
+    J = api.jastrow_from(jas)
+    theta0 = np.concatenate([[jas.d], np.asarray(jas.b, float), np.asarray(jas.coef, float).ravel()])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(62)
+    normals = torch.randn((args.sweeps, N, Nw, 3), dtype=torch.float64, device="cuda", generator=gen)
+    uniforms = torch.rand((args.sweeps, N, Nw), dtype=torch.float64, device="cuda", generator=gen)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    acc = api.isdf_vmc_sample(B, Cg, n_occ, R, normals, uniforms, 0.5)
+    e1.record()
+    torch.cuda.synchronize()
+    sample_ms = e0.elapsed_time(e1)
+    theta = torch.as_tensor(theta0.copy()).cuda()
+    opt = api.VmcOptimizer(B, Cg, n_occ, R, J, Z, theta)
+    var = [opt.var]
+    lams = []
+    for _ in range(max(args.warmup, 3)):
+        v, lam, _ = opt.step()
+        var.append(v)
+        lams.append(lam)
+    ts = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0.record()
+        v, lam, _ = opt.step()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        var.append(v)
+        lams.append(lam)
+    # one local energy + Jacobian pass alone
+    torch.cuda.synchronize()
+    e0.record()
+    api.isdf_vmc_local_energy(B, Cg, n_occ, R, J, Z, theta=theta)
+    e1.record()
+    torch.cuda.synchronize()
+    jac_ms = e0.elapsed_time(e1)
+    # energies alone (no Jacobian)
+    torch.cuda.synchronize()
+    e0.record()
+    api.isdf_vmc_local_energy(B, Cg, n_occ, R, J, Z, theta=theta, grad=False)
+    e1.record()
+    torch.cuda.synchronize()
+    eloc_ms = e0.elapsed_time(e1)
+    # parity on seeded walkers (oracle inputs from the generator, not the GPU)
+    from oracle import vmc as ovmc
+    Rs = wl.vmc_walkers(xyz, 4, N, seed=63)
+    t0 = time.time()
+    refE = ovmc.local_energies(Rs, basis, C[:, :n_occ], jas, xyz, Z)
+    refJ = ovmc.energy_jacobian_fd(Rs, basis, C[:, :n_occ], jas, xyz, Z)
+    oracle_s = time.time() - t0
+    Eg, dEg = api.isdf_vmc_local_energy(B, Cg, n_occ, torch.as_tensor(Rs).cuda(), J, Z)
+    line = {"mode": "vmc", "workload": "H20 chain, s/p basis (80 functions), 20 electrons, "
+                                       "28-term BH correlator (30 parameters)",
+            "walkers": Nw, "sweeps": args.sweeps, "sample_ms": sample_ms,
+            "moves_per_s": args.sweeps * N * Nw / (sample_ms * 1e-3),
+            "acceptance": acc / float(args.sweeps * N * Nw),
+            "gn_iteration_ms": ts, "walker_iterations_per_s": Nw / (min(ts) * 1e-3),
+            "local_energy_only_ms": eloc_ms, "local_energy_and_jacobian_ms": jac_ms,
+            "variance_per_iteration": var, "lambda_per_iteration": lams,
+            "oracle": {"walkers": 4, "energy_and_jacobian_s": oracle_s,
+                       "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))},
+            "oracle_ratio_per_walker": (oracle_s / 4) / (jac_ms * 1e-3 / Nw),
+            "parity": {"E_max_abs": float(np.max(np.abs(Eg.cpu().numpy() - refE))),
+                       "dE_max_abs": float(np.max(np.abs(dEg.cpu().numpy() - refJ))),
+                       "dE_scale": float(np.max(np.abs(refJ)))}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -721,6 +817,8 @@ def main():
         return run_adjoint(args)
     if args.proposer:
         return run_proposer(args)
+    if args.vmc:
+        return run_vmc(args)
     if args.validate:
         return run_validate(args)
     if args.assembly:

@@ -495,6 +495,72 @@ int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n
                        const int32_t* pivots, int n_mu, double* phi_piv, double* dphi_piv,
                        isdf_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Reference-variance VMC optimisation of the correlator (Sec. II.C, Eqs. Eloc,
+ * var-loss and gn).  Trial function Psi_T = exp(tau) Phi_0: Phi_0 the
+ * closed-shell determinant of the first n_occ orbitals (columns of mo_coef),
+ * electrons 0 .. n_occ-1 spin up and n_occ .. 2 n_occ-1 spin down; tau =
+ * sum_{i<j} u(r_i, r_j) with u of isdf_jastrow (cusp, free terms, one-body
+ * term).  The nuclei of the Hamiltonian are the correlator's (jas->nuc_xyz)
+ * with charges[I] (host [n_nuc]).  walkers: device [n_walkers][2 n_occ][3]
+ * bohr.  theta = (d, b_0 .. b_{T-1}, coef[t][k] row-major), P = 1 + T + T K
+ * (isdf_vmc_n_params).  Limits: 1 <= n_occ <= 64, and the per-walker tables
+ * must fit one CTA's shared memory (ISDF_E_ARG otherwise).  FP64 throughout.
+ *
+ * isdf_vmc_local_energy: E[w] = E_loc of Eq. Eloc,
+ *   E_loc = -1/2 sum_i [lap_i Phi_0/Phi_0 + 2 grad_i tau . grad_i Phi_0/Phi_0
+ *                       + lap_i tau + |grad_i tau|^2] + V,
+ *   V = sum_{i<j} 1/r_ij - sum_{i,I} Z_I/r_iI + sum_{I<J} Z_I Z_J/R_IJ,
+ * with the correlator's parameters from theta (device [P]) or, when theta is
+ * NULL, from jas.  dE (device [P][n_walkers] or NULL): dE_loc/dtheta; the d and
+ * b_t rows by central differences of step fd_step, the coefficient rows exact
+ * (E_loc is quadratic in them).  b_t rows are 0 when the correlator has no
+ * free terms.  A singular determinant gives NaN energies.  Asynchronous. */
+int isdf_vmc_n_params(const isdf_jastrow* jas);
+size_t isdf_vmc_local_energy_workspace(int n_bf, int n_occ, int64_t n_walkers,
+                                       const isdf_jastrow* jas);
+int isdf_vmc_local_energy(const isdf_basis* basis, const double* mo_coef, int n_orb, int n_occ,
+                          const double* walkers, int64_t n_walkers, const isdf_jastrow* jas,
+                          const double* charges, const double* theta, double fd_step, double* E,
+                          double* dE, void* ws, size_t ws_bytes, isdf_stream_t stream);
+
+/* n_steps Metropolis sweeps on |Phi_0|^2 (the sample does not depend on the
+ * correlator).  Sweep s moves electrons i = 0 .. 2 n_occ-1 in turn:
+ *   r' = r_i + sigma normals[s][i][w][0..2],
+ *   accepted when uniforms[s][i][w] < (Phi_0(R')/Phi_0(R))^2,
+ * the ratio taken against the walker's inverse determinant, which an accepted
+ * move updates by Sherman-Morrison (each call starts from a fresh inversion).
+ * normals device [n_steps][2 n_occ][n_walkers][3], uniforms device
+ * [n_steps][2 n_occ][n_walkers] (the random numbers are inputs); walkers are
+ * updated in place; *accepted (device int64) = accepted moves of this call.
+ * Asynchronous. */
+int isdf_vmc_sample(const isdf_basis* basis, const double* mo_coef, int n_orb, int n_occ,
+                    double* walkers, int64_t n_walkers, const double* normals,
+                    const double* uniforms, int n_steps, double sigma, int64_t* accepted,
+                    isdf_stream_t stream);
+
+/* One Gauss-Newton step of Eq. gn on the clipped objective of Eq. var-loss:
+ *   m, dev = mean and mean absolute deviation of E; E~ = clip(E, m - 5 dev, m + 5 dev);
+ *   r_k = E~_k - mean(E~); var = sum r_k^2 / (n - 1);
+ *   dr = d r / d theta with clipped energies following their bound
+ *        (d(m +- 5 dev), d dev = mean(sign(E - m) (dE - dm)));
+ *   C = dr dr^T / n + lambda I;  step = -eta C^-1 (2/(n-1) dr r).
+ * E device [n_walkers], dE device [n_par][n_walkers]; step device [n_par];
+ * stats device [4] = (mean(E~), var, m, dev); theta device [n_par] or NULL:
+ * theta += step when the factorisation succeeds.  Synchronises `stream`;
+ * ISDF_E_NOT_PD when C is not positive definite (lambda = 0 with a rank-
+ * deficient Jacobian).  The paper adapts lambda without stating the rule; the
+ * Python front end's vmc_optimize takes a step only when the clipped variance
+ * at the new theta is lower (then lambda /= 3), else keeps theta and sets
+ * lambda *= 10. */
+size_t isdf_vmc_gn_step_workspace(int64_t n_walkers, int n_par);
+/* The objective of Eq. var-loss alone: stats device [4] as isdf_vmc_gn_step.
+ * Asynchronous. */
+int isdf_vmc_objective(const double* E, int64_t n_walkers, double* stats, isdf_stream_t stream);
+int isdf_vmc_gn_step(const double* E, const double* dE, int64_t n_walkers, int n_par,
+                     double lambda, double eta, double* theta, double* step, double* stats,
+                     void* ws, size_t ws_bytes, isdf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

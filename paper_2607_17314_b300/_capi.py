@@ -105,6 +105,17 @@ SIGNATURES = {
     "tc_xtc_one_body_workspace": (SZ, [INT, INT]),
     "tc_xtc_one_body": (INT, [P, P, P, P, P, INT, INT, INT, P, P,
                               ctypes.POINTER(ctypes.c_double), P, SZ, P]),
+    "isdf_vmc_n_params": (INT, [ctypes.POINTER(IsdfJastrow)]),
+    "isdf_vmc_local_energy_workspace": (SZ, [INT, INT, I64, ctypes.POINTER(IsdfJastrow)]),
+    "isdf_vmc_local_energy": (INT, [ctypes.POINTER(IsdfBasis), P, INT, INT, P, I64,
+                                    ctypes.POINTER(IsdfJastrow), P, P, ctypes.c_double, P, P,
+                                    P, SZ, P]),
+    "isdf_vmc_sample": (INT, [ctypes.POINTER(IsdfBasis), P, INT, INT, P, I64, P, P, INT,
+                              ctypes.c_double, P, P]),
+    "isdf_vmc_gn_step_workspace": (SZ, [I64, INT]),
+    "isdf_vmc_objective": (INT, [P, I64, P, P]),
+    "isdf_vmc_gn_step": (INT, [P, P, I64, INT, ctypes.c_double, ctypes.c_double, P, P, P, P, SZ,
+                               P]),
 }
 
 _lib = None

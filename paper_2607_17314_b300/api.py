@@ -395,3 +395,121 @@ class TCKernel(torch.autograd.Function):
         grid_xyz, w, xi, xig = ctx.saved_tensors
         g = tc_kernel_adjoint(grid_xyz, w, xi, xig, ctx.J, Wbar.contiguous(), ctx.prec)
         return g.to(ctx.theta_device), None, None, None, None, None, None
+
+
+def _basis(center, powers, exps, coefs) -> C.IsdfBasis:
+    for t, n, dt in ((center, "center", f64), (exps, "exps", f64), (coefs, "coefs", f64),
+                     (powers, "powers", torch.int32)):
+        _req(t, dt, n)
+    n_bf, n_prim = exps.shape
+    return C.IsdfBasis(n_bf, n_prim, _ptr(center), _ptr(powers), _ptr(exps), _ptr(coefs))
+
+
+def isdf_vmc_local_energy(basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges,
+                          theta=None, fd_step: float = 1e-5, grad: bool = True):
+    """E_loc [n_walkers] of Eq. Eloc and, with grad, dE_loc/dtheta [P][n_walkers]
+    (theta = (d, b_t, coef row-major); None = the struct's values).
+    basis = (center, powers, exps, coefs) device tensors; charges host [n_nuc]."""
+    lib = C.load()
+    B = _basis(*basis)
+    _req(mo_coef, f64, "mo_coef"); _req(walkers, f64, "walkers")
+    dev = walkers.device
+    n_walk = walkers.shape[0]
+    P = lib.isdf_vmc_n_params(ctypes.byref(jastrow))
+    if theta is not None:
+        _req(theta, f64, "theta")
+        if theta.numel() != P:
+            raise ValueError(f"theta needs {P} values")
+    Z = (ctypes.c_double * max(1, jastrow.n_nuc))(*[float(z) for z in charges])
+    E = torch.empty(n_walk, dtype=f64, device=dev)
+    dE = torch.empty((P, n_walk), dtype=f64, device=dev) if grad else None
+    ws = _ws(lib.isdf_vmc_local_energy_workspace(B.n_bf, n_occ, n_walk, ctypes.byref(jastrow)), dev)
+    C.check("isdf_vmc_local_energy", lib.isdf_vmc_local_energy(
+        ctypes.byref(B), _ptr(mo_coef), mo_coef.shape[1], n_occ, _ptr(walkers), n_walk,
+        ctypes.byref(jastrow), ctypes.cast(Z, ctypes.c_void_p), _ptr(theta), float(fd_step),
+        _ptr(E), _ptr(dE), _ptr(ws), ws.numel(), _stream()))
+    return (E, dE) if grad else E
+
+
+def isdf_vmc_sample(basis, mo_coef, n_occ: int, walkers, normals, uniforms, sigma: float) -> int:
+    """Metropolis sweeps on |Phi_0|^2, walkers moved in place; returns the
+    number of accepted moves (synchronises)."""
+    lib = C.load()
+    B = _basis(*basis)
+    for t, n in ((mo_coef, "mo_coef"), (walkers, "walkers"), (normals, "normals"),
+                 (uniforms, "uniforms")):
+        _req(t, f64, n)
+    n_steps = uniforms.shape[0]
+    acc = torch.zeros(1, dtype=torch.int64, device=walkers.device)
+    C.check("isdf_vmc_sample", lib.isdf_vmc_sample(
+        ctypes.byref(B), _ptr(mo_coef), mo_coef.shape[1], n_occ, _ptr(walkers), walkers.shape[0],
+        _ptr(normals), _ptr(uniforms), n_steps, float(sigma), _ptr(acc), _stream()))
+    return int(acc.item())
+
+
+def isdf_vmc_gn_step(E, dE, lam: float, eta: float, theta=None):
+    """Gauss-Newton step of Eq. gn: returns (step [P], stats [4] = clipped
+    mean, variance, raw mean, mean absolute deviation); theta += step in place
+    when given."""
+    lib = C.load()
+    _req(E, f64, "E"); _req(dE, f64, "dE")
+    P, n_w = dE.shape
+    step = torch.empty(P, dtype=f64, device=E.device)
+    stats = torch.empty(4, dtype=f64, device=E.device)
+    if theta is not None:
+        _req(theta, f64, "theta")
+    ws = _ws(lib.isdf_vmc_gn_step_workspace(n_w, P), E.device)
+    C.check("isdf_vmc_gn_step", lib.isdf_vmc_gn_step(
+        _ptr(E), _ptr(dE), n_w, P, float(lam), float(eta), _ptr(theta), _ptr(step), _ptr(stats),
+        _ptr(ws), ws.numel(), _stream()))
+    return step, stats
+
+
+def isdf_vmc_objective(E):
+    """stats [4] = (clipped mean, clipped variance, raw mean, mean absolute
+    deviation) of Eq. var-loss."""
+    lib = C.load()
+    _req(E, f64, "E")
+    stats = torch.empty(4, dtype=f64, device=E.device)
+    C.check("isdf_vmc_objective", lib.isdf_vmc_objective(_ptr(E), E.numel(), _ptr(stats), _stream()))
+    return stats
+
+
+class VmcOptimizer:
+    """Gauss-Newton iterations of Eq. gn on a fixed sample (reference-variance
+    protocol) with an adaptive Tikhonov shift: a step is kept only when the
+    clipped variance at the new theta is lower (then lam /= 3), otherwise
+    theta stays and lam *= 10.  theta (device [P]) is updated in place."""
+
+    def __init__(self, basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges,
+                 theta, lam: float = 1e-3, eta: float = 0.5, fd_step: float = 1e-5,
+                 lam_min: float = 1e-8, lam_max: float = 1e6):
+        self.args = (basis, mo_coef, n_occ, walkers, jastrow, charges)
+        self.theta, self.lam, self.eta, self.h = theta, lam, eta, fd_step
+        self.lam_min, self.lam_max = lam_min, lam_max
+        E = isdf_vmc_local_energy(*self.args, theta, fd_step, grad=False)
+        self.var = float(isdf_vmc_objective(E)[1])
+
+    def step(self):
+        """One iteration; returns (variance, lam, accepted)."""
+        E, dE = isdf_vmc_local_energy(*self.args, self.theta, self.h)
+        trial = self.theta.clone()
+        isdf_vmc_gn_step(E, dE, self.lam, self.eta, theta=trial)
+        Et = isdf_vmc_local_energy(*self.args, trial, self.h, grad=False)
+        vt = float(isdf_vmc_objective(Et)[1])
+        ok = vt < self.var
+        if ok:
+            self.theta.copy_(trial)
+            self.var = vt
+            self.lam = max(self.lam / 3.0, self.lam_min)
+        else:
+            self.lam = min(self.lam * 10.0, self.lam_max)
+        return self.var, self.lam, ok
+
+
+def vmc_optimize(basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges, theta,
+                 n_iter: int, **kw):
+    """n_iter iterations of VmcOptimizer; returns their (variance, lam,
+    accepted) history."""
+    opt = VmcOptimizer(basis, mo_coef, n_occ, walkers, jastrow, charges, theta, **kw)
+    return [opt.step() for _ in range(n_iter)]

@@ -80,6 +80,18 @@ size_t xtc_panel_ws(int, int, int64_t, int);
 int xtc_panel(const double*, const double*, const double*, const double*, const double*, int, int,
               int64_t, int64_t, int, double*, double*, void*, size_t, cudaStream_t);
 
+int vmc_n_params(const isdf_jastrow&);
+size_t vmc_local_energy_ws(int, int, int64_t, const isdf_jastrow&);
+int vmc_local_energy(const isdf_basis*, const double*, int, int, const double*, int64_t,
+                     const isdf_jastrow&, const double*, const double*, double, double*, double*,
+                     void*, size_t, cudaStream_t);
+int vmc_sample(const isdf_basis*, const double*, int, int, double*, int64_t, const double*,
+               const double*, int, double, int64_t*, cudaStream_t);
+size_t vmc_gn_step_ws(int64_t, int);
+int vmc_objective(const double*, int64_t, double*, cudaStream_t);
+int vmc_gn_step(const double*, const double*, int64_t, int, double, double, double*, double*,
+                double*, void*, size_t, cudaStream_t);
+
 static int check_jastrow(const isdf_jastrow* J) {
   ISDF_ARG(J, "null Jastrow");
   ISDF_ARG(J->n_nuc >= 0 && J->n_nuc <= ISDF_MAX_NUC, "n_nuc out of range");
@@ -360,4 +372,43 @@ int tc_two_body_panel(const double* W, const double* D, const double* X_packed,
                    K_panel, dU_panel, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+
+int isdf_vmc_n_params(const isdf_jastrow* jas) { return jas ? vmc_n_params(*jas) : 0; }
+
+size_t isdf_vmc_local_energy_workspace(int n_bf, int n_occ, int64_t n_walkers,
+                                       const isdf_jastrow* jas) {
+  return jas ? vmc_local_energy_ws(n_bf, n_occ, n_walkers, *jas) : 0;
+}
+
+int isdf_vmc_local_energy(const isdf_basis* basis, const double* mo_coef, int n_orb, int n_occ,
+                          const double* walkers, int64_t n_walkers, const isdf_jastrow* jas,
+                          const double* charges, const double* theta, double fd_step, double* E,
+                          double* dE, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  ISDF_TRY(check_jastrow(jas));
+  return vmc_local_energy(basis, mo_coef, n_orb, n_occ, walkers, n_walkers, *jas, charges, theta,
+                          fd_step, E, dE, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int isdf_vmc_sample(const isdf_basis* basis, const double* mo_coef, int n_orb, int n_occ,
+                    double* walkers, int64_t n_walkers, const double* normals,
+                    const double* uniforms, int n_steps, double sigma, int64_t* accepted,
+                    isdf_stream_t stream) {
+  return vmc_sample(basis, mo_coef, n_orb, n_occ, walkers, n_walkers, normals, uniforms, n_steps,
+                    sigma, accepted, (cudaStream_t)stream);
+}
+
+int isdf_vmc_objective(const double* E, int64_t n_walkers, double* stats, isdf_stream_t stream) {
+  return vmc_objective(E, n_walkers, stats, (cudaStream_t)stream);
+}
+
+size_t isdf_vmc_gn_step_workspace(int64_t n_walkers, int n_par) {
+  return vmc_gn_step_ws(n_walkers, n_par);
+}
+
+int isdf_vmc_gn_step(const double* E, const double* dE, int64_t n_walkers, int n_par,
+                     double lambda, double eta, double* theta, double* step, double* stats,
+                     void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  return vmc_gn_step(E, dE, n_walkers, n_par, lambda, eta, theta, step, stats, ws, ws_bytes,
+                     (cudaStream_t)stream);
+}
 }  // extern "C"

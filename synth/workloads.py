@@ -552,3 +552,37 @@ CONFIGS = {
 def seeded_matrix(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """Standard-normal test matrix (e.g. an adjoint seed Wbar)."""
     return scale * np.random.default_rng(seed).standard_normal(shape)
+
+
+# --------------------------------------------------------------------------
+# VMC inputs (Sec. II.C): walker configurations and the sampler's random numbers
+# --------------------------------------------------------------------------
+
+def vmc_walkers(xyz: np.ndarray, n_walk: int, n_elec: int, seed: int,
+                spread: float = 1.0) -> np.ndarray:
+    """[n_walk][n_elec][3]: each electron on a uniformly drawn nucleus plus a
+    standard-normal offset of scale `spread` bohr."""
+    rng = np.random.default_rng(seed)
+    at = rng.integers(0, xyz.shape[0], size=(n_walk, n_elec))
+    return xyz[at] + spread * rng.standard_normal((n_walk, n_elec, 3))
+
+
+def vmc_random(n_steps: int, n_elec: int, n_walk: int, seed: int):
+    """Metropolis random numbers in the sampler's order: normals
+    [n_steps][n_elec][n_walk][3] and uniforms [n_steps][n_elec][n_walk] in [0, 1)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((n_steps, n_elec, n_walk, 3)),
+            rng.random((n_steps, n_elec, n_walk)))
+
+
+def vmc_chain(n_atom: int = 20, spacing: float = 1.8, seed: int = 6001,
+              terms=None, jscale: float = 0.05):
+    """Atoms, positions, s/p basis (4 functions per H), orthonormalised MO
+    coefficients (n_occ = n_atom / 2 occupied) and BH correlator of an H chain,
+    for the VMC optimisation of the correlator."""
+    atoms, xyz = h_chain(n_atom, spacing)
+    rng = np.random.default_rng(seed)
+    basis = make_basis(atoms, xyz, {"H": [0, 1]}, rng)
+    C = make_mo_coef(basis, basis.n_bf, rng)
+    jas = bh_jastrow(atoms, xyz, bh_terms_c4() if terms is None else terms, rng, scale=jscale)
+    return atoms, xyz, basis, C, max(1, n_atom // 2), jas

@@ -253,3 +253,46 @@ def test_streamed_build_argument_checks(lib):
     small = lib.tc_kernel_build_streamed_workspace(100000, 2000, 8192, 8192, 1, ctypes.byref(J))
     big = lib.tc_kernel_build_workspace(100000, 2000, 0, 100000, 1, ctypes.byref(J))
     assert 0 < small < big
+
+
+def test_vmc_argument_checks(lib):
+    """The VMC entry points (Sec. II.C) reject bad sizes, steps and undersized
+    workspaces before any device work."""
+    from paper_2607_17314_b300 import _capi as C
+    fake = ctypes.c_void_p(256)
+    B = C.IsdfBasis(8, 3, fake, fake, fake, fake)
+    J = C.IsdfJastrow()
+    J.n_nuc, J.n_types, J.n_terms, J.d, J.cusp = 2, 1, 1, 1.0, 1
+    J.b[0], J.coef[0][0] = 1.0, 0.1
+    J.mno[0][0] = 1
+    assert lib.isdf_vmc_n_params(ctypes.byref(J)) == 3
+    Z = (ctypes.c_double * 2)(1.0, 1.0)
+    zp = ctypes.cast(Z, ctypes.c_void_p)
+    need = lib.isdf_vmc_local_energy_workspace(8, 2, 16, ctypes.byref(J))
+    assert need >= 8 * (5 * 8 * 64 + 5 * 2 * 64)
+
+    def eloc(n_occ, ws_bytes, h=1e-5, dE=fake):
+        return lib.isdf_vmc_local_energy(ctypes.byref(B), fake, 8, n_occ, fake, 16,
+                                         ctypes.byref(J), zp, None, h, fake, dE, fake, ws_bytes,
+                                         None)
+    for n_occ in (0, 9, 65):
+        assert eloc(n_occ, need) == C.ISDF_E_ARG
+    assert eloc(2, need - 1) == C.ISDF_E_ARG
+    assert b"workspace too small" in lib.isdf_last_error()
+    assert eloc(2, need, h=0.0) == C.ISDF_E_ARG
+    assert b"fd_step" in lib.isdf_last_error()
+    acc = ctypes.c_void_p(512)
+    for sigma, n_occ in ((0.0, 2), (float("nan"), 2), (0.5, 0)):
+        st = lib.isdf_vmc_sample(ctypes.byref(B), fake, 8, n_occ, fake, 16, fake, fake, 2, sigma,
+                                 acc, None)
+        assert st == C.ISDF_E_ARG
+    st = lib.isdf_vmc_sample(ctypes.byref(B), fake, 8, 2, fake, 16, None, None, 2, 0.5, acc, None)
+    assert st == C.ISDF_E_ARG and b"random inputs" in lib.isdf_last_error()
+    gw = lib.isdf_vmc_gn_step_workspace(100, 3)
+    assert gw >= 8 * (3 * 100 + 100 + 3 + 9)
+    assert lib.isdf_vmc_gn_step(fake, fake, 1, 3, 0.0, 1.0, None, fake, fake, fake, gw,
+                                None) == C.ISDF_E_ARG
+    assert lib.isdf_vmc_gn_step(fake, fake, 100, 3, -1.0, 1.0, None, fake, fake, fake, gw,
+                                None) == C.ISDF_E_ARG
+    assert lib.isdf_vmc_gn_step(fake, fake, 100, 3, 0.0, 1.0, None, fake, fake, fake, gw - 1,
+                                None) == C.ISDF_E_ARG

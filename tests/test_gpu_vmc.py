@@ -1,0 +1,172 @@
+"""GPU VMC optimisation of the correlator (Sec. II.C: Eqs. Eloc, var-loss, gn)
+against the FP64 oracle: local energies, their parameter Jacobian, the
+Metropolis sampler and the Gauss-Newton step."""
+import numpy as np
+import pytest
+import torch
+
+from synth import workloads as wl
+from oracle import vmc, adjoint
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_17314_b300 import build
+    build.build()
+    from paper_2607_17314_b300 import api
+    return api
+
+
+def _cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def _basis(b):
+    return (_cu(b.center), _cu(b.powers.astype(np.int32)), _cu(b.exps), _cu(b.coefs))
+
+
+def _system(n_atom=4, n_occ=2, seed=11, n_terms=6, scale=0.3, chi=False):
+    atoms, xyz, basis, C, _, jas = wl.vmc_chain(n_atom, seed=seed, terms=wl.bh_terms_c4()[:n_terms],
+                                                jscale=scale)
+    jas.b = np.array([1.15])
+    jas.d = 0.9
+    if chi:
+        jas = wl.with_chi(jas, [-0.4], 2 * n_occ, beta=1.3)
+    return xyz, basis, C, n_occ, jas, np.ones(n_atom)
+
+
+def _scale(x):
+    return max(1.0, float(np.max(np.abs(x))))
+
+
+@pytest.mark.parametrize("n_atom,n_occ,n_terms,chi", [(4, 2, 6, False), (4, 3, 6, True),
+                                                      (3, 1, 0, False), (10, 9, 10, True)])
+def test_local_energy_matches_oracle(api, n_atom, n_occ, n_terms, chi):
+    xyz, basis, C, n_occ, jas, Z = _system(n_atom, n_occ, n_terms=n_terms, chi=chi)
+    if n_terms == 0:
+        jas = wl.radial_jastrow(xyz, d=0.8)
+    R = wl.vmc_walkers(xyz, 13, 2 * n_occ, seed=5)
+    ref = vmc.local_energies(R, basis, C[:, :n_occ], jas, xyz, Z)
+    E = api.isdf_vmc_local_energy(_basis(basis), _cu(C), n_occ, _cu(R), api.jastrow_from(jas), Z,
+                                  grad=False).cpu().numpy()
+    err = np.max(np.abs(E - ref))
+    print("E_loc max err", err, "scale", _scale(ref))
+    assert err < 1e-10 * _scale(ref), (E, ref)
+
+
+def test_local_energy_many_electrons_per_spin(api):
+    """33 electrons per spin: the pivot search spans two rows per lane."""
+    xyz, basis, C, _, jas, Z = _system(n_atom=12, n_occ=33, n_terms=3)
+    R = wl.vmc_walkers(xyz, 3, 66, seed=8, spread=1.5)
+    ref = vmc.local_energies(R, basis, C[:, :33], jas, xyz, Z)
+    E = api.isdf_vmc_local_energy(_basis(basis), _cu(C), 33, _cu(R), api.jastrow_from(jas), Z,
+                                  grad=False).cpu().numpy()
+    assert np.max(np.abs(E - ref)) < 1e-8 * _scale(ref), (E, ref)
+
+
+@pytest.mark.parametrize("chi", [False, True])
+def test_jacobian_matches_oracle(api, chi):
+    """d and b rows: central differences of the same step on both sides; the
+    coefficient rows exact on the GPU against the oracle's central differences
+    (exact for a quadratic up to rounding)."""
+    xyz, basis, C, n_occ, jas, Z = _system(chi=chi)
+    R = wl.vmc_walkers(xyz, 5, 2 * n_occ, seed=21)
+    h = 1e-5
+    refE = vmc.local_energies(R, basis, C[:, :n_occ], jas, xyz, Z)
+    refJ = vmc.energy_jacobian_fd(R, basis, C[:, :n_occ], jas, xyz, Z, h=h)
+    E, dE = api.isdf_vmc_local_energy(_basis(basis), _cu(C), n_occ, _cu(R), api.jastrow_from(jas),
+                                      Z, fd_step=h)
+    E, dE = E.cpu().numpy(), dE.cpu().numpy()
+    assert dE.shape == refJ.shape
+    assert np.max(np.abs(E - refE)) < 1e-9 * _scale(refE)
+    err = np.max(np.abs(dE - refJ), axis=1)
+    print("Jacobian row errors", err)
+    # central differences of step h carry rounding ~ eps |E| / h on either side
+    tol = 50 * np.finfo(float).eps * _scale(refE) / h
+    assert np.all(err < tol), (dE, refJ, tol)
+
+
+def test_theta_from_device_overrides_struct(api):
+    xyz, basis, C, n_occ, jas, Z = _system()
+    th = adjoint.get_theta(jas)
+    th2 = th * (1.0 + 0.1 * np.sin(np.arange(len(th))))
+    jas2 = adjoint.set_theta(jas, th2)
+    R = wl.vmc_walkers(xyz, 7, 2 * n_occ, seed=3)
+    ref = vmc.local_energies(R, basis, C[:, :n_occ], jas2, xyz, Z)
+    E = api.isdf_vmc_local_energy(_basis(basis), _cu(C), n_occ, _cu(R), api.jastrow_from(jas), Z,
+                                  theta=_cu(th2), grad=False).cpu().numpy()
+    assert np.max(np.abs(E - ref)) < 1e-9 * _scale(ref)
+
+
+@pytest.mark.parametrize("n_occ,n_steps", [(2, 4), (3, 3)])
+def test_sampler_matches_oracle(api, n_occ, n_steps):
+    """Same random numbers -> the same accepted moves (exact count) and final
+    positions; the GPU takes the ratio against an updated inverse, the oracle
+    from two determinants."""
+    xyz, basis, C, _, jas, Z = _system(n_atom=4, n_occ=n_occ)
+    N, Nw = 2 * n_occ, 6
+    R = wl.vmc_walkers(xyz, Nw, N, seed=31)
+    normals, uniforms = wl.vmc_random(n_steps, N, Nw, seed=32)
+    refR, ref_acc = vmc.metropolis(R, basis, C[:, :n_occ], normals, uniforms, 0.6)
+    Rg = _cu(R)
+    acc = api.isdf_vmc_sample(_basis(basis), _cu(C), n_occ, Rg, _cu(normals), _cu(uniforms), 0.6)
+    assert acc == ref_acc
+    assert 0 < acc < n_steps * N * Nw
+    assert np.max(np.abs(Rg.cpu().numpy() - refR)) < 1e-12
+
+
+def test_gn_step_matches_oracle(api):
+    rng = np.random.default_rng(41)
+    Nw, P = 400, 9
+    E = -2.0 + 0.3 * rng.standard_normal(Nw)
+    E[:4] = [8.0, -12.0, 6.5, -9.0]           # beyond m +- 5 dev: both clip branches
+    dE = rng.standard_normal((P, Nw))
+    dE[2] *= 0.01
+    lam, eta = 1e-3, 0.7
+    ref = vmc.gauss_newton_step(E, dE, lam, eta)
+    _, mean, var = vmc.clipped_objective(E)
+    theta = _cu(np.arange(P, dtype=float))
+    step, stats = api.isdf_vmc_gn_step(_cu(E), _cu(dE), lam, eta, theta=theta)
+    step, stats = step.cpu().numpy(), stats.cpu().numpy()
+    assert np.max(np.abs(step - ref)) < 1e-10 * np.max(np.abs(ref)), (step, ref)
+    assert abs(stats[0] - mean) < 1e-12 and abs(stats[1] - var) < 1e-12 * var
+    assert np.max(np.abs(theta.cpu().numpy() - (np.arange(P) + step))) == 0.0
+
+
+def test_objective_matches_oracle(api):
+    rng = np.random.default_rng(44)
+    E = -1.0 + 0.5 * rng.standard_normal(300)
+    E[7], E[9] = 15.0, -20.0
+    _, mean, var = vmc.clipped_objective(E)
+    m = np.mean(E)
+    dev = np.mean(np.abs(E - m))
+    st = api.isdf_vmc_objective(_cu(E)).cpu().numpy()
+    assert np.allclose(st, [mean, var, m, dev], rtol=1e-13, atol=1e-14), (st, mean, var, m, dev)
+
+
+def test_optimisation_lowers_the_sampled_variance(api):
+    """Sample |Phi_0|^2, then Gauss-Newton iterations on that fixed sample
+    (the reference-variance protocol) with the adaptive shift: the clipped
+    variance never rises and ends well below its start."""
+    xyz, basis, C, n_occ, jas, Z = _system(n_atom=6, n_occ=3, n_terms=10, scale=0.2)
+    N, Nw = 2 * n_occ, 512
+    Rg = _cu(wl.vmc_walkers(xyz, Nw, N, seed=51))
+    normals, uniforms = wl.vmc_random(20, N, Nw, seed=52)
+    B = _basis(basis)
+    api.isdf_vmc_sample(B, _cu(C), n_occ, Rg, _cu(normals), _cu(uniforms), 0.5)
+    J = api.jastrow_from(jas)
+    theta = _cu(adjoint.get_theta(jas))
+    opt = api.VmcOptimizer(B, _cu(C), n_occ, Rg, J, Z, theta)
+    v0 = opt.var
+    hist = [opt.step() for _ in range(8)]
+    var = [v0] + [h[0] for h in hist]
+    print("variance per iteration", var, "lambda", [h[1] for h in hist])
+    assert np.all(np.isfinite(var)) and np.all(np.diff(var) <= 0.0)
+    assert var[-1] < 0.8 * var[0]
+    # the final theta reproduces the final variance
+    E = api.isdf_vmc_local_energy(B, _cu(C), n_occ, Rg, J, Z, theta=theta, grad=False)
+    assert float(api.isdf_vmc_objective(E)[1]) == var[-1]
