@@ -27,6 +27,8 @@
 // determinants in shared memory and moves one electron at a time: the
 // acceptance ratio is the row-expansion of the new orbital row against the
 // inverse, and an accepted move updates the inverse by Sherman-Morrison.
+#include <algorithm>
+
 #include "jastrow.cuh"
 #include "linalg.cuh"
 
@@ -250,8 +252,8 @@ __global__ void __launch_bounds__(kVmcThreads) slater_kernel(const double* __res
 
 // Shared-memory layout of eloc_kernel (in doubles).
 struct ElocLayout {
-  int pos, drift, gt, coef, nt, acc, red, total;
-  __host__ __device__ ElocLayout(int N, int n_nuc, int n_pc, bool terms) {
+  int pos, drift, gt, coef, nt, acc, red, pair, total;
+  __host__ __device__ ElocLayout(int N, int n_nuc, int n_pc, bool terms, bool table) {
     pos = 0;
     drift = pos + 3 * N;
     gt = drift + 4 * N;
@@ -259,13 +261,16 @@ struct ElocLayout {
     nt = coef + (n_pc > 0 ? n_pc : 1);
     acc = nt + (terms ? 6 * N * n_nuc : 0);
     red = acc + 4 * N * (n_pc + 1);
-    total = red + 40;
+    pair = red + 40;
+    total = pair + (terms && table ? 5 * N * N : 0);
   }
 };
 
-// Local energy of walker blockIdx.x for parameter set blockIdx.y:
+// Local energy of walker blockIdx.x for parameter set blockIdx.y (MAXA: the
+// largest exponent m, n of the free terms is at most MAXA):
 //   set 0 = theta, 1/2 = d +- h, 3+2t / 4+2t = b_t +- h.
 // E_set [n_sets][n_walk]; dEc [n_pc][n_walk] (set 0 only, may be null).
+template <int MAXA, bool TABLE>
 __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
     isdf_jastrow J, const double* __restrict__ theta, double h, int64_t n_walk, int N,
     const double* __restrict__ walkers, const double* __restrict__ drift_g,
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
   const int T = J.n_types, K = J.n_terms, n_nuc = J.n_nuc;
   const int n_pc = T * K;
   const bool terms = K > 0 && n_nuc > 0;
-  const ElocLayout L(N, n_nuc, n_pc, terms);
+  const ElocLayout L(N, n_nuc, n_pc, terms, TABLE);
   double* pos = sm + L.pos;
   double* drift = sm + L.drift;
   double* gt = sm + L.gt;
@@ -282,6 +287,7 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
   double* nt = sm + L.nt;
   double* acc = sm + L.acc;
   double* red = sm + L.red;
+  double* pair = sm + L.pair;  // TABLE: [N][N][5] = F0, F1 (dx, dy, dz), F2 of one o
   const int64_t w = blockIdx.x;
   const int set = blockIdx.y;
   // parameters of this set
@@ -321,57 +327,27 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
   __syncthreads();
   const bool chi = chi_on(J);
   const double chi_scale = chi ? (double)(N - 1) / (double)(J.n_elec - 1) : 0.0;
-  // (electron i, slot p): p = 0 the coefficient-free part, p = 1 + t K + k term (t, k)
-  for (int item = threadIdx.x; item < N * (n_pc + 1); item += blockDim.x) {
-    const int i = item % N, p = item / N;
+  // Coefficient-free part (cusp and one-body terms), one thread per electron.
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
     double gx = 0.0, gy = 0.0, gz = 0.0, l = 0.0;
-    const int t = p > 0 ? (p - 1) / K : 0, k = p > 0 ? (p - 1) - t * K : 0;
-    const int m = p > 0 ? J.mno[k][0] : 0, nn = p > 0 ? J.mno[k][1] : 0,
-              o = p > 0 ? J.mno[k][2] : 0;
-    if (p > 0 || J.cusp)
+    if (J.cusp) {
+      const double s = 0.5 / d;
       for (int j = 0; j < N; ++j) {
         if (j == i) continue;
         const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
                      dz = pos[3 * i + 2] - pos[3 * j + 2];
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
         const double rinv = r > 0.0 ? 1.0 / r : 0.0;
-        const double ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;
         const double den = 1.0 + d * r;
-        const double E = d * r / den;
         const double E1 = d / (den * den);
-        const double lapE = -2.0 * d * d / (den * den * den) + 2.0 * E1 * rinv;
-        if (p == 0) {
-          const double s = 0.5 / d;
-          gx += s * E1 * ex;
-          gy += s * E1 * ey;
-          gz += s * E1 * ez;
-          l += s * lapE;
-          continue;
-        }
-        const double Eo = ipow(E, o);
-        const double Eo1 = o > 0 ? o * ipow(E, o - 1) : 0.0;
-        const double Eo2 = o > 1 ? o * (o - 1) * ipow(E, o - 2) : 0.0;
-        for (int I = 0; I < n_nuc; ++I) {
-          if (J.nuc_type[I] != t) continue;
-          const double* ni = nt + 6 * (i * n_nuc + I);
-          const double Ai = ni[0], A1 = ni[1], lapA = ni[2];
-          const double Aj = nt[6 * (j * n_nuc + I)];
-          const double S = ipow(Ai, m) * ipow(Aj, nn) + ipow(Aj, m) * ipow(Ai, nn);
-          const double S1 = (m > 0 ? m * ipow(Ai, m - 1) * ipow(Aj, nn) : 0.0) +
-                            (nn > 0 ? nn * ipow(Aj, m) * ipow(Ai, nn - 1) : 0.0);
-          const double S2 = (m > 1 ? m * (m - 1) * ipow(Ai, m - 2) * ipow(Aj, nn) : 0.0) +
-                            (nn > 1 ? nn * (nn - 1) * ipow(Aj, m) * ipow(Ai, nn - 2) : 0.0);
-          const double cos = ni[3] * ex + ni[4] * ey + ni[5] * ez;
-          const double ga = S1 * Eo * A1, ge = S * Eo1 * E1;
-          gx += ga * ni[3] + ge * ex;
-          gy += ga * ni[4] + ge * ey;
-          gz += ga * ni[5] + ge * ez;
-          l += S2 * Eo * A1 * A1 + S1 * Eo * lapA + 2.0 * S1 * Eo1 * A1 * E1 * cos +
-               S * (Eo2 * E1 * E1 + Eo1 * lapE);
-        }
+        gx += s * E1 * dx * rinv;
+        gy += s * E1 * dy * rinv;
+        gz += s * E1 * dz * rinv;
+        l += s * (-2.0 * d * d / (den * den * den) + 2.0 * E1 * rinv);
       }
-    if (p == 0 && chi) {
-      // one-body term: (N - 1) partners each add grad chi(r_i) / (n_elec - 1)
+    }
+    if (chi) {
+      // (N - 1) partners each add grad chi(r_i) / (n_elec - 1) and its Laplacian
       double cg[3];
       chi_grad_pair(J, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], cg);
       double lc = 0.0;
@@ -389,11 +365,161 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
       gz += (double)(N - 1) * cg[2];
       l += chi_scale * lc;
     }
-    double* a = acc + 4 * (p * N + i);
-    a[0] = gx;
-    a[1] = gy;
-    a[2] = gz;
-    a[3] = l;
+    acc[4 * i] = gx;
+    acc[4 * i + 1] = gy;
+    acc[4 * i + 2] = gz;
+    acc[4 * i + 3] = l;
+  }
+  for (int q = threadIdx.x; q < 4 * N * n_pc; q += blockDim.x) acc[4 * N + q] = 0.0;
+  __syncthreads();
+  // Free terms.  For electron i, nucleus I and the exponent o of E_ij, the
+  // partner sums are moments of A_jI:
+  //   T0[a] = sum_j A_jI^a E^o,  T1[a] = sum_j A_jI^a (E^o)' e_ij,
+  //   T2[a] = sum_j A_jI^a [(E^o)'' + (E^o)' 2/r_ij]   (lap of E^o = this bracket),
+  // and term (m, n, o) with S = A_i^m A_j^n + A_j^m A_i^n sums to
+  //   grad = A'(m A_i^(m-1) T0[n] + n A_i^(n-1) T0[m]) e_iI + A_i^m T1[n] + A_i^n T1[m]
+  //   lap  = A'^2 (m(m-1) A_i^(m-2) T0[n] + n(n-1) A_i^(n-2) T0[m])
+  //          + lap A (m A_i^(m-1) T0[n] + n A_i^(n-1) T0[m])
+  //          + 2 A' (m A_i^(m-1) e_iI.T1[n] + n A_i^(n-1) e_iI.T1[m])
+  //          + A_i^m T2[n] + A_i^n T2[m].
+  // One warp per electron; lane = (nucleus, slice of partners); the terms are
+  // linear in the moments, so each lane's partial moments give partial terms
+  // and one warp reduction per (term, type) sums nuclei and slices.
+  if (terms) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const int nl = n_nuc < 32 ? n_nuc : 32;
+    const int nsl = 32 / nl;
+    const int Il = lane % nl, js = lane / nl;
+    const int n_chunks = (n_nuc + nl - 1) / nl;
+    unsigned omask = 0;
+    for (int k = 0; k < K; ++k) omask |= 1u << J.mno[k][2];
+    for (int o = 0; o <= 8; ++o) {
+      if (!((omask >> o) & 1u)) continue;
+      if (TABLE) {
+        // pair factors of this o, once per pair instead of once per lane
+        __syncthreads();
+        for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
+          const int i = q / N, j = q - i * N;
+          const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                       dz = pos[3 * i + 2] - pos[3 * j + 2];
+          const double r = sqrt(dx * dx + dy * dy + dz * dz);
+          const double rinv = r > 0.0 ? 1.0 / r : 0.0;
+          const double den = 1.0 + d * r;
+          const double E = d * r / den;
+          const double E1 = d / (den * den);
+          const double lapE = -2.0 * d * d / (den * den * den) + 2.0 * E1 * rinv;
+          const double Eo1 = o > 0 ? o * ipow(E, o - 1) : 0.0;
+          const double F1 = Eo1 * E1 * rinv;
+          double* f = pair + 5 * q;
+          f[0] = ipow(E, o);
+          f[1] = F1 * dx;
+          f[2] = F1 * dy;
+          f[3] = F1 * dz;
+          f[4] = (o > 1 ? o * (o - 1) * ipow(E, o - 2) * E1 * E1 : 0.0) + Eo1 * lapE;
+        }
+        __syncthreads();
+      }
+      for (int i = warp; i < N; i += n_warps)
+        for (int ch = 0; ch < n_chunks; ++ch) {
+          const int I = ch * nl + Il;
+          const bool on = js < nsl && I < n_nuc;
+          double T0[MAXA + 1], T1x[MAXA + 1], T1y[MAXA + 1], T1z[MAXA + 1], T2[MAXA + 1];
+#pragma unroll
+          for (int a = 0; a <= MAXA; ++a) T0[a] = T1x[a] = T1y[a] = T1z[a] = T2[a] = 0.0;
+          if (on && TABLE)
+            for (int j = js; j < N; j += nsl) {
+              if (j == i) continue;
+              const double* f = pair + 5 * (i * N + j);
+              const double F0 = f[0], F1x = f[1], F1y = f[2], F1z = f[3], F2 = f[4];
+              const double Aj = nt[6 * (j * n_nuc + I)];
+              double pw = 1.0;
+#pragma unroll
+              for (int a = 0; a <= MAXA; ++a) {
+                T0[a] += F0 * pw;
+                T1x[a] += F1x * pw;
+                T1y[a] += F1y * pw;
+                T1z[a] += F1z * pw;
+                T2[a] += F2 * pw;
+                pw *= Aj;
+              }
+            }
+          if (on && !TABLE)
+            for (int j = js; j < N; j += nsl) {
+              if (j == i) continue;
+              const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                           dz = pos[3 * i + 2] - pos[3 * j + 2];
+              const double r = sqrt(dx * dx + dy * dy + dz * dz);
+              const double rinv = r > 0.0 ? 1.0 / r : 0.0;
+              const double den = 1.0 + d * r;
+              const double E = d * r / den;
+              const double E1 = d / (den * den);
+              const double lapE = -2.0 * d * d / (den * den * den) + 2.0 * E1 * rinv;
+              const double F0 = ipow(E, o);
+              const double Eo1 = o > 0 ? o * ipow(E, o - 1) : 0.0;
+              const double F1 = Eo1 * E1 * rinv;  // times (dx, dy, dz) = times r e_ij
+              const double F2 = (o > 1 ? o * (o - 1) * ipow(E, o - 2) * E1 * E1 : 0.0) + Eo1 * lapE;
+              const double Aj = nt[6 * (j * n_nuc + I)];
+              double pw = 1.0;
+#pragma unroll
+              for (int a = 0; a <= MAXA; ++a) {
+                T0[a] += F0 * pw;
+                const double f1 = F1 * pw;
+                T1x[a] += f1 * dx;
+                T1y[a] += f1 * dy;
+                T1z[a] += f1 * dz;
+                T2[a] += F2 * pw;
+                pw *= Aj;
+              }
+            }
+          const double* ni = nt + 6 * (i * n_nuc + (on ? I : 0));
+          const double Ai = on ? ni[0] : 0.0, A1 = on ? ni[1] : 0.0, lapA = on ? ni[2] : 0.0;
+          const double ex = on ? ni[3] : 0.0, ey = on ? ni[4] : 0.0, ez = on ? ni[5] : 0.0;
+          const int ti = on ? J.nuc_type[I] : -1;
+          for (int k = 0; k < K; ++k) {
+            if (J.mno[k][2] != o) continue;
+            const int m = J.mno[k][0], n = J.mno[k][1];
+            double t0m = 0, t0n = 0, t1mx = 0, t1my = 0, t1mz = 0, t1nx = 0, t1ny = 0, t1nz = 0,
+                   t2m = 0, t2n = 0;
+#pragma unroll
+            for (int a = 0; a <= MAXA; ++a) {
+              if (a == m) {
+                t0m = T0[a]; t1mx = T1x[a]; t1my = T1y[a]; t1mz = T1z[a]; t2m = T2[a];
+              }
+              if (a == n) {
+                t0n = T0[a]; t1nx = T1x[a]; t1ny = T1y[a]; t1nz = T1z[a]; t2n = T2[a];
+              }
+            }
+            const double am = ipow(Ai, m), an = ipow(Ai, n);
+            const double dm = m > 0 ? m * ipow(Ai, m - 1) : 0.0;
+            const double dn = n > 0 ? n * ipow(Ai, n - 1) : 0.0;
+            const double sm2 = m > 1 ? m * (m - 1) * ipow(Ai, m - 2) : 0.0;
+            const double sn2 = n > 1 ? n * (n - 1) * ipow(Ai, n - 2) : 0.0;
+            const double s1 = dm * t0n + dn * t0m;
+            const double ga = s1 * A1;
+            double v[4];
+            v[0] = ga * ex + am * t1nx + an * t1mx;
+            v[1] = ga * ey + am * t1ny + an * t1my;
+            v[2] = ga * ez + am * t1nz + an * t1mz;
+            const double ct = dm * (ex * t1nx + ey * t1ny + ez * t1nz) +
+                              dn * (ex * t1mx + ey * t1my + ez * t1mz);
+            v[3] = A1 * A1 * (sm2 * t0n + sn2 * t0m) + lapA * s1 + 2.0 * A1 * ct + am * t2n +
+                   an * t2m;
+            for (int t = 0; t < T; ++t) {
+              double u[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                u[c] = ti == t ? v[c] : 0.0;
+                for (int off = 16; off; off >>= 1) u[c] += __shfl_down_sync(0xffffffffu, u[c], off);
+              }
+              if (lane == 0) {
+                double* a = acc + 4 * ((1 + t * K + k) * N + i);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a[c] += u[c];
+              }
+            }
+          }
+        }
+      }
   }
   __syncthreads();
   // E_loc = -1/2 sum_i [lap Phi/Phi + 2 grad tau . grad Phi/Phi + lap tau + |grad tau|^2] + V
@@ -675,8 +801,8 @@ int n_sets_of(const isdf_jastrow& J, bool want_grad) {
   return 3 + ((J.n_terms > 0 && J.n_nuc > 0) ? 2 * J.n_types : 0);
 }
 
-size_t eloc_smem(const isdf_jastrow& J, int N) {
-  const ElocLayout L(N, J.n_nuc, J.n_types * J.n_terms, J.n_terms > 0 && J.n_nuc > 0);
+size_t eloc_smem(const isdf_jastrow& J, int N, bool table) {
+  const ElocLayout L(N, J.n_nuc, J.n_types * J.n_terms, J.n_terms > 0 && J.n_nuc > 0, table);
   return (size_t)L.total * sizeof(double);
 }
 
@@ -697,7 +823,7 @@ int vmc_local_energy(const isdf_basis* basis, const double* C, int n_orb, int n_
   ISDF_ARG(n_walk >= 1 && basis->n_bf > 0 && basis->n_prim > 0, "empty sizes");
   ISDF_ARG(!dE || (h > 0.0 && std::isfinite(h)), "fd_step must be positive");
   const int N = 2 * n_occ;
-  const size_t smem = eloc_smem(J, N);
+  const size_t smem = eloc_smem(J, N, false);
   ISDF_ARG(smem <= kVmcSmemMax, "electrons x nuclei x coefficients exceed shared memory (%zu B)",
            smem);
   const int n_sets = n_sets_of(J, dE != nullptr);
@@ -727,11 +853,18 @@ int vmc_local_energy(const isdf_basis* basis, const double* C, int n_orb, int n_
   slater_kernel<<<(unsigned)n_walk, kVmcThreads, smem_sl, s>>>(W.orb, n_occ, n_walk, walkers, nuc,
                                                                W.drift, W.V);
   ISDF_LAUNCH_CHECK();
-  ISDF_CUDA(cudaFuncSetAttribute(eloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
   const int T = J.n_types;
   double* dEc = dE ? dE + (int64_t)(1 + T) * n_walk : nullptr;
-  eloc_kernel<<<dim3((unsigned)n_walk, (unsigned)n_sets), kVmcThreads, smem, s>>>(
+  int max_a = 0;
+  for (int k = 0; k < J.n_terms; ++k)
+    max_a = std::max(max_a, std::max(J.mno[k][0], J.mno[k][1]));
+  const bool table = eloc_smem(J, N, true) <= kVmcSmemMax;
+  auto kern = max_a <= 3 ? (table ? eloc_kernel<3, true> : eloc_kernel<3, false>)
+                         : (table ? eloc_kernel<8, true> : eloc_kernel<8, false>);
+  const size_t smem_run = eloc_smem(J, N, table);
+  ISDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_run));
+  kern<<<dim3((unsigned)n_walk, (unsigned)n_sets), kVmcThreads, smem_run, s>>>(
       J, theta, h, n_walk, N, walkers, W.drift, W.V, W.E_set, J.n_terms > 0 ? dEc : nullptr);
   ISDF_LAUNCH_CHECK();
   eloc_finish_kernel<<<(unsigned)ceil_div(n_walk, 256), 256, 0, s>>>(W.E_set, n_walk, T,

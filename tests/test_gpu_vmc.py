@@ -58,6 +58,35 @@ def test_local_energy_matches_oracle(api, n_atom, n_occ, n_terms, chi):
     assert err < 1e-10 * _scale(ref), (E, ref)
 
 
+@pytest.mark.parametrize("case", ["two_types", "high_exponents", "forty_nuclei"])
+def test_local_energy_and_jacobian_layouts(api, case):
+    """Two nucleus types (benzene geometry), exponents above 3 (the general
+    moment table), and more nuclei than lanes (several passes per warp)."""
+    if case == "two_types":
+        w = wl.benzene_small(n_rad=2, n_ang=6, n_mu=8)
+        xyz, basis, C, n_occ, jas = w.xyz, w.basis, w.mo_coef, 5, w.jastrow
+        jas.coef = jas.coef * 6.0
+        Z = np.array([6.0 if a == "C" else 1.0 for a in w.atoms])
+    elif case == "high_exponents":
+        xyz, basis, C, n_occ, jas, Z = _system(n_atom=5, n_occ=3, n_terms=0)
+        terms = [(4, 1, 2), (0, 5, 0), (2, 6, 3), (1, 1, 1), (8, 0, 0), (3, 3, 4)]
+        jas = wl.bh_jastrow(["H"] * 5, xyz, terms, np.random.default_rng(4), scale=0.4)
+        jas.b = np.array([1.3])
+    else:
+        xyz, basis, C, n_occ, jas, Z = _system(n_atom=40, n_occ=3, n_terms=5)
+    R = wl.vmc_walkers(xyz, 3, 2 * n_occ, seed=12, spread=1.3)
+    h = 1e-5
+    refE = vmc.local_energies(R, basis, C[:, :n_occ], jas, xyz, Z)
+    refJ = vmc.energy_jacobian_fd(R, basis, C[:, :n_occ], jas, xyz, Z, h=h)
+    E, dE = api.isdf_vmc_local_energy(_basis(basis), _cu(C), n_occ, _cu(R), api.jastrow_from(jas),
+                                      Z, fd_step=h)
+    E, dE = E.cpu().numpy(), dE.cpu().numpy()
+    print(case, "E err", np.max(np.abs(E - refE)), "J err", np.max(np.abs(dE - refJ)))
+    assert np.max(np.abs(E - refE)) < 1e-10 * _scale(refE), (E, refE)
+    tol = 50 * np.finfo(float).eps * _scale(refE) / h
+    assert np.max(np.abs(dE - refJ)) < tol, (dE, refJ, tol)
+
+
 def test_local_energy_many_electrons_per_spin(api):
     """33 electrons per spin: the pivot search spans two rows per lane."""
     xyz, basis, C, _, jas, Z = _system(n_atom=12, n_occ=33, n_terms=3)
@@ -66,6 +95,25 @@ def test_local_energy_many_electrons_per_spin(api):
     E = api.isdf_vmc_local_energy(_basis(basis), _cu(C), 33, _cu(R), api.jastrow_from(jas), Z,
                                   grad=False).cpu().numpy()
     assert np.max(np.abs(E - ref)) < 1e-8 * _scale(ref), (E, ref)
+
+
+def test_local_energy_largest_walker(api):
+    """64 electrons per spin (the limit) on 30 nuclei: the pair-factor table no
+    longer fits shared memory and the kernel recomputes the pair factors per
+    lane.  The seeded configuration keeps both determinants well conditioned
+    (condition numbers below 1e4), so FP64 rounding stays near 1e-12."""
+    xyz, basis, C, _, jas, Z = _system(n_atom=30, n_occ=64, n_terms=3)
+    R = wl.vmc_walkers(xyz, 2, 128, seed=12, spread=0.8)
+    h = 1e-5
+    refE = vmc.local_energies(R, basis, C[:, :64], jas, xyz, Z)
+    refJ = vmc.energy_jacobian_fd(R, basis, C[:, :64], jas, xyz, Z, h=h)
+    E, dE = api.isdf_vmc_local_energy(_basis(basis), _cu(C), 64, _cu(R), api.jastrow_from(jas), Z,
+                                      fd_step=h)
+    E, dE = E.cpu().numpy(), dE.cpu().numpy()
+    print("N=128 E err", np.max(np.abs(E - refE)), "J err", np.max(np.abs(dE - refJ)),
+          "scales", _scale(refE), _scale(refJ))
+    assert np.max(np.abs(E - refE)) < 1e-9 * _scale(refE), (E, refE)
+    assert np.max(np.abs(dE - refJ)) < 50 * np.finfo(float).eps * _scale(refE) / h
 
 
 @pytest.mark.parametrize("chi", [False, True])
