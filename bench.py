@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--vmc", action="store_true",
                     help="VMC optimisation of the correlator (Sec. II.C) on an H20 chain: "
                          "Metropolis sweeps, then Gauss-Newton iterations on the fixed sample")
+    ap.add_argument("--fit-mode", type=int, default=1, choices=[0, 1],
+                    help="the fit's FP64 products: 0 on CUDA cores, 1 emulated on the tensor cores")
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--sweeps", type=int, default=40)
     ap.add_argument("--n-train", type=int, default=24)
@@ -273,6 +275,8 @@ def run_config(args, wlw, world):
             "precision": args.precision,
             "l2": f"inputs larger than L2 (w xi limbs {limbs * 2 * n_mu * n_g / 1e9:.2f} GB)",
             "parallelism": f"replicas{world}",
+            "fit": ("FP64 products emulated on the tensor cores" if getattr(args, "fit_mode", 0)
+                    else "FP64 on CUDA cores"),
             "value_basis": "W build (stage 1 + stage 2 + operand prep) inside each full-path step"}
 
 
@@ -517,7 +521,7 @@ def run_validate_sampled(args):
     events = {}
     stage_ms = []
     out = pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms,
-                       kchunk=args.kchunk)
+                       kchunk=args.kchunk, fit_mode=args.fit_mode)
     torch.cuda.synchronize()
     st = {k: float(v[0].elapsed_time(v[1])) for k, v in events.items()}
     back, n_piv = fit_backward_errors(out)
@@ -552,7 +556,7 @@ def run_validate(args):
     J = api.jastrow_from(wlw.jastrow)
     inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
                           wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
-    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk)
+    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk, fit_mode=args.fit_mode)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     W64, calG64 = api.tc_kernel_build(inp.grid, inp.w, out["xi"], out["xig"], J, "fp64")
@@ -597,7 +601,7 @@ def run_assembly(args):
     J = api.jastrow_from(wlw.jastrow)
     inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
                           wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
-    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk)
+    out = pipeline.run(inp, precision=args.precision, kchunk=args.kchunk, fit_mode=args.fit_mode)
     n_orb, n_mu, n_g, n_occ = wlw.n_orb, wlw.n_mu, inp.n_g, wlw.n_occ
 
     def timed(fn, reps=2):
@@ -846,7 +850,7 @@ def main():
 
     def step(events=None, stage_ms=None):
         return pipeline.run(inp, precision=args.precision, events=events, stage_ms=stage_ms,
-                            kchunk=args.kchunk)
+                            kchunk=args.kchunk, fit_mode=args.fit_mode)
 
     for _ in range(max(args.warmup, 0)):
         out = step()
@@ -961,7 +965,8 @@ def main():
             dev = [t.to("cuda", non_blocking=True) for t in pinned]
             inp2 = pipeline.Inputs(dev[0], dev[1].to(torch.int32), dev[2], dev[3], dev[4], dev[5],
                                    dev[6], n_mu, wlw.n_occ, J)
-            o2 = pipeline.run(inp2, precision=args.precision)
+            o2 = pipeline.run(inp2, precision=args.precision, kchunk=args.kchunk,
+                              fit_mode=args.fit_mode)
             W_host.copy_(o2["W"], non_blocking=True)
         e1.record(stream)
         barrier()

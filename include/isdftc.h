@@ -136,6 +136,11 @@ typedef struct {
   int32_t wait_limit_ms;  /* tc_kernel_build: bound of every device-side wait of
                              its tensor-core kernels, in ms; 0 = default 2000;
                              larger values are clamped to 60000 */
+  int32_t fit_mode;       /* isdf_fit: 0 = FP64 on CUDA cores (default); 1 = the
+                             right-hand-side GEMMs and the triangular solves as
+                             FP64 products emulated on the tensor cores
+                             (isdf_dgemm_emulated; workspace from
+                             isdf_fit_workspace_mode) */
 } isdf_options;
 
 const char* isdf_last_error(void);
@@ -205,12 +210,37 @@ int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* 
  * Errors: ISDF_E_ARG when a pivot index lies outside [0, n_g) (checked on the
  * device before any solve; such an index is never dereferenced);
  * ISDF_E_NONFINITE when phi or dphi hold a NaN or Inf, or the solutions
- * overflow; ISDF_E_NOT_PD if a system stays indefinite. */
+ * overflow; ISDF_E_NOT_PD if a system stays indefinite.
+ * With options->fit_mode = 1 the right-hand sides G, dG^c and the two
+ * triangular solves (by blocks of 128 with inverted diagonal blocks) run as
+ * the emulated FP64 products of isdf_dgemm_emulated; the Grams and their
+ * Cholesky factors stay FP64 on CUDA cores. */
 size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu);
+/* Workspace for fit_mode 0 (= isdf_fit_workspace) or 1 (adds the emulated
+ * products' digit planes: 16 (n_g + 64) max(n_orb, 128) bytes and less); 0 for
+ * another mode. */
+size_t isdf_fit_workspace_mode(int64_t n_g, int n_orb, int n_mu, int fit_mode);
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
              const int32_t* pivots, int n_mu, double* xi, double* xi_grad,
              double* jitter_used, const isdf_options* options, void* ws, size_t ws_bytes,
              isdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * FP64 matrix product emulated on the BF16 tensor cores (not in the paper; the
+ * fit's FP64 solves otherwise set the step time on B300, whose FP64 rate is
+ * ~1 TFLOP/s):  C = alpha A B + beta C, beta 0 or 1, A [M][K] (row stride lda),
+ * B [K][N] (ldb), C [M][N] (ldc), all FP64 row-major on the device.
+ * Each row of A and column of B is scaled by a power of two and cut into eight
+ * signed 7-bit digits held exactly in BF16; the 36 digit products of weight
+ * >= 2^-63 are summed exactly in FP32 per weight (at most 128 inner terms per
+ * tensor-core run; longer K is split over CTAs whose results are added with
+ * FP64 atomics) and combined exactly in 64-bit integers before one rounding to
+ * FP64.  Error within (K + 4) 2^-52 max_k|A_mk| max_k|B_kn| per element.
+ * A NaN or Inf in A or B gives undefined values in C.  Asynchronous. */
+size_t isdf_dgemm_emulated_workspace(int64_t M, int64_t N, int64_t K);
+int isdf_dgemm_emulated(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                        const double* B, int64_t ldb, double alpha, double beta, double* C,
+                        int64_t ldc, void* ws, size_t ws_bytes, isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Jastrow kernels of the ISDF K integrals (Eqs. K1-isdf and K3-isdf):

@@ -56,7 +56,7 @@ class IsdfOptions(ctypes.Structure):
     _fields_ = [("precision", I32), ("kchunk", I32), ("s2_kchunk", I32), ("sync_check", I32),
                 ("debug_flags", I32), ("stage_ms", ctypes.POINTER(ctypes.c_float)),
                 ("jitter_init", ctypes.c_double), ("jitter_growth", ctypes.c_double),
-                ("max_jitter_tries", I32), ("wait_limit_ms", I32)]
+                ("max_jitter_tries", I32), ("wait_limit_ms", I32), ("fit_mode", I32)]
 
 
 # name -> (restype, argtypes)
@@ -72,6 +72,10 @@ SIGNATURES = {
     "isdf_points_fixed_rank": (INT, [P, P, P, I64, INT, INT, INT, P, ctypes.POINTER(INT), P, SZ,
                                      P]),
     "isdf_fit_workspace": (SZ, [I64, INT, INT]),
+    "isdf_fit_workspace_mode": (SZ, [I64, INT, INT, INT]),
+    "isdf_dgemm_emulated_workspace": (SZ, [I64, I64, I64]),
+    "isdf_dgemm_emulated": (INT, [I64, I64, I64, P, I64, P, I64, ctypes.c_double, ctypes.c_double,
+                                  P, I64, P, SZ, P]),
     "isdf_fit": (INT, [P, P, I64, INT, P, INT, P, P, P, P, P, SZ, P]),
     "tc_kernel_build_streamed_workspace": (SZ, [I64, INT, I64, I64, INT, P]),
     "tc_kernel_build_streamed": (INT, [P, P, P, P, I64, INT, I64, I64, P, P, P, P, SZ, P]),

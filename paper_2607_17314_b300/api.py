@@ -134,10 +134,12 @@ def isdf_points_fixed_rank(phi, dphi, w, n_ch_phi: int, n_ch_grad: int,
 
 
 def isdf_fit(phi, dphi, pivots, jitter_init: float = 0.0, jitter_growth: float = 0.0,
-             max_jitter_tries: int = 0):
+             max_jitter_tries: int = 0, fit_mode: int = 0):
     """xi [n_mu][n_g], xi~ [3][n_mu][n_g] and the jitter per system.  The
     jitter policy (Sec. IV.B): 0 selects the library defaults (1e-14 of the
-    largest diagonal, x10 per retry, 8 retries); max_jitter_tries < 0 allows none."""
+    largest diagonal, x10 per retry, 8 retries); max_jitter_tries < 0 allows none.
+    fit_mode 1 runs the right-hand sides and the solves as FP64 products
+    emulated on the tensor cores."""
     lib = C.load()
     dev = phi.device
     _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(pivots, torch.int32, "pivots")
@@ -146,13 +148,35 @@ def isdf_fit(phi, dphi, pivots, jitter_init: float = 0.0, jitter_growth: float =
     xi = torch.empty((n_mu, n_g), dtype=f64, device=dev)
     xig = torch.empty((3, n_mu, n_g), dtype=f64, device=dev)
     jit = (ctypes.c_double * 4)()
-    ws = _ws(lib.isdf_fit_workspace(n_g, n_orb, n_mu), dev)
+    ws = _ws(lib.isdf_fit_workspace_mode(n_g, n_orb, n_mu, int(fit_mode)), dev)
     opt = options(jitter_init=jitter_init, jitter_growth=jitter_growth,
-                  max_jitter_tries=max_jitter_tries)
+                  max_jitter_tries=max_jitter_tries, fit_mode=fit_mode)
     C.check("isdf_fit", lib.isdf_fit(_ptr(phi), _ptr(dphi), n_g, n_orb, _ptr(pivots), n_mu,
                                      _ptr(xi), _ptr(xig), jit, ctypes.byref(opt), _ptr(ws),
                                      ws.numel(), _stream()))
     return xi, xig, list(jit)
+
+
+def isdf_dgemm_emulated(A, B, alpha: float = 1.0, out=None):
+    """alpha A B, added in place to `out` when given, with the FP64 products
+    emulated on the tensor cores; A [M][K], B [K][N] FP64."""
+    lib = C.load()
+    _req(A, f64, "A"); _req(B, f64, "B")
+    M, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    N = B.shape[1]
+    beta = 0.0
+    if out is None:
+        out = torch.empty((M, N), dtype=f64, device=A.device)
+    else:
+        _req(out, f64, "out")
+        beta = 1.0
+    ws = _ws(lib.isdf_dgemm_emulated_workspace(M, N, K), A.device)
+    C.check("isdf_dgemm_emulated", lib.isdf_dgemm_emulated(
+        M, N, K, _ptr(A), K, _ptr(B), N, float(alpha), beta, _ptr(out), N, _ptr(ws), ws.numel(),
+        _stream()))
+    return out
 
 
 def isdf_gather_pivots(phi, dphi, pivots):
@@ -171,12 +195,12 @@ def isdf_gather_pivots(phi, dphi, pivots):
 def options(precision="bf16x3", kchunk: int = 0, s2_kchunk: int = 0, sync_check: bool = True,
             debug_flags: int = 0, stage_ms=None, jitter_init: float = 0.0,
             jitter_growth: float = 0.0, max_jitter_tries: int = 0,
-            wait_limit_ms: int = 0) -> C.IsdfOptions:
+            wait_limit_ms: int = 0, fit_mode: int = 0) -> C.IsdfOptions:
     """isdf_options for the W build and the fit; 0 selects the library defaults."""
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return C.IsdfOptions(prec, kchunk, s2_kchunk, int(sync_check), debug_flags, stage_ms,
                          float(jitter_init), float(jitter_growth), int(max_jitter_tries),
-                         int(wait_limit_ms))
+                         int(wait_limit_ms), int(fit_mode))
 
 
 class KernelBuilder:

@@ -32,9 +32,12 @@ int points(const double*, const double*, const double*, int64_t, int, int, int, 
 size_t points_ranks_ws(int64_t n_g, int n_phi, int n_grad);
 int points_ranks(const double*, const double*, const double*, int64_t, int, int, int, int32_t*,
                  int*, void*, size_t, cudaStream_t);
-size_t fit_ws(int64_t, int, int);
+size_t fit_ws(int64_t, int, int, int);
 int fit(const double*, const double*, int64_t, int, const int32_t*, int, double*, double*,
-        double*, double, double, int, void*, size_t, cudaStream_t);
+        double*, double, double, int, int, void*, size_t, cudaStream_t);
+size_t em_dgemm_ws(int64_t, int64_t, int64_t);
+int em_dgemm(int64_t, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t,
+             int64_t, double, bool, double*, int64_t, void*, size_t, cudaStream_t);
 int gather_pivots(const double*, const double*, int64_t, int, const int32_t*, int, double*,
                   double*, cudaStream_t);
 size_t wbuild_fp64_ws(int64_t n_g, const isdf_jastrow* J);
@@ -161,22 +164,47 @@ int isdf_points_fixed_rank(const double* phi, const double* dphi, const double* 
                       ws_bytes, (cudaStream_t)stream);
 }
 
-size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu) { return fit_ws(n_g, n_orb, n_mu); }
+size_t isdf_fit_workspace(int64_t n_g, int n_orb, int n_mu) {
+  return fit_ws(n_g, n_orb, n_mu, 0);
+}
+
+size_t isdf_fit_workspace_mode(int64_t n_g, int n_orb, int n_mu, int fit_mode) {
+  return (fit_mode == 0 || fit_mode == 1) ? fit_ws(n_g, n_orb, n_mu, fit_mode) : 0;
+}
+
+size_t isdf_dgemm_emulated_workspace(int64_t M, int64_t N, int64_t K) {
+  return em_dgemm_ws(M > 0 ? M : 1, N > 0 ? N : 1, K > 0 ? K : 1);
+}
+
+int isdf_dgemm_emulated(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                        const double* B, int64_t ldb, double alpha, double beta, double* C,
+                        int64_t ldc, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  ISDF_ARG(M >= 0 && N >= 0 && K >= 0, "negative sizes");
+  ISDF_ARG(beta == 0.0 || beta == 1.0, "beta must be 0 or 1");
+  ISDF_ARG(std::isfinite(alpha), "alpha must be finite");
+  if (M == 0 || N == 0) return ISDF_OK;
+  ISDF_ARG(C && (K == 0 || (A && B)), "null pointer argument");
+  ISDF_ARG(lda >= K && ldb >= N && ldc >= N, "leading dimensions too small");
+  return em_dgemm(M, N, K, A, lda, 1, B, ldb, 1, alpha, beta == 0.0, C, ldc, ws, ws_bytes,
+                  (cudaStream_t)stream);
+}
 
 int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* pivots,
              int n_mu, double* xi, double* xi_grad, double* jitter_used,
              const isdf_options* options, void* ws, size_t ws_bytes, isdf_stream_t stream) {
   double j0 = 1e-14, growth = 10.0;
-  int tries = 8;
+  int tries = 8, mode = 0;
   if (options) {
     ISDF_ARG(options->jitter_init >= 0.0 && options->jitter_growth >= 0.0,
              "negative jitter policy");
     if (options->jitter_init > 0.0) j0 = options->jitter_init;
     if (options->jitter_growth > 0.0) growth = options->jitter_growth;
     if (options->max_jitter_tries != 0) tries = options->max_jitter_tries < 0 ? 0 : options->max_jitter_tries;
+    ISDF_ARG(options->fit_mode == 0 || options->fit_mode == 1, "fit_mode must be 0 or 1");
+    mode = options->fit_mode;
   }
   return fit(phi, dphi, n_g, n_orb, pivots, n_mu, xi, xi_grad, jitter_used, j0, growth, tries,
-             ws, ws_bytes, (cudaStream_t)stream);
+             mode, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int isdf_gather_pivots(const double* phi, const double* dphi, int64_t n_g, int n_orb,

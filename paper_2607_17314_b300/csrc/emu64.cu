@@ -1,0 +1,524 @@
+// FP64 matrix products on the BF16 tensor cores by exact integer slices, and
+// the blocked triangular solves of the ISDF fit (Sec. IV.B) built on them.
+//
+// A row of A (a column of B) is scaled by 2^-e, e the smallest integer with
+// |x| < 2^e over the row, so each scaled element lies in (-1, 1).  Its
+// magnitude, truncated to 56 fraction bits, is cut into S = 8 base-2^7 digits
+// d_1 .. d_8 that carry the element's sign; each digit is an integer of at most
+// 7 bits, which BF16 holds exactly.  Then
+//   (A B)_mn ~= 2^(e_m + e_n) sum_{p + q <= 9} 2^(-7 (p + q)) sum_k d_p(A_mk) d_q(B_kn).
+// Each inner sum over k of one level L = p + q is a sum of integers: with at
+// most 8 digit pairs per level and at most 128 terms, its magnitude stays below
+// 8 * 127^2 * 128 < 2^24, so the tensor core's FP32 accumulation of a level is
+// exact.  The epilogue combines the 8 levels exactly in a 64-bit integer scaled
+// by 2^52 (the two lowest levels keep their bits down to 2^-52 of the scale) and
+// converts once to FP64.  The dropped pairs (p + q > 9: at most ~2^-53.2 of
+// 2^(e_m + e_n) per term), the truncation below 2^-56 and the two lowest
+// levels' rounding (2 units of 2^-52) bound the error by (K + 4) 2^-52 of
+// 2^(e_m + e_n), the size of FP64 rounding over K terms of that magnitude.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "linalg.cuh"
+#include "tc_ptx.cuh"
+
+namespace isdf {
+
+int tma_map_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows);
+
+namespace {
+
+constexpr int kS = 8;              // digits per value
+constexpr int kBits = 7;           // bits per digit
+constexpr int kFrac = kS * kBits;  // 56 fraction bits
+constexpr int kZeroExp = -4000;    // exponent of an all-zero row or column
+constexpr int kBadExp = 4000;      // a NaN or Inf in the row or column
+
+constexpr int EM_BM = 128, EM_BN = 64, EM_BK = 32, EM_STAGES = 2, EM_THREADS = 192;
+constexpr int EM_KCHUNK = 128;  // exact FP32 accumulation bound per level
+constexpr uint32_t EM_AT = EM_BM * EM_BK * 2;
+constexpr uint32_t EM_BT = EM_BN * EM_BK * 2;
+constexpr uint32_t EM_STAGE = kS * (EM_AT + EM_BT);
+constexpr uint32_t EM_SMEM = EM_STAGES * EM_STAGE + 1024 + 256;
+constexpr uint32_t EM_TMEM = kS * EM_BN;  // 8 levels x 64 columns
+static_assert(EM_TMEM == 512, "tensor memory holds the eight level accumulators");
+
+constexpr int TRSM_TB = 128;  // block size of the triangular solves (= EM_KCHUNK)
+
+// Smallest e with |x| < 2^e (integer arithmetic on the bits).
+__device__ __forceinline__ int exp_of(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return kZeroExp;
+  const int be = (int)(b >> 52);
+  if (be == 0x7FF) return kBadExp;
+  if (be) return be - 1022;
+  return (64 - __clzll((long long)b)) - 1074;
+}
+
+// The 8 signed digits of x 2^-e (|x| < 2^e), truncated below 2^-56.
+__device__ __forceinline__ void digits_of(double x, int e, int (&d)[kS]) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const uint64_t b = bits & 0x7FFFFFFFFFFFFFFFull;
+  uint64_t M = 0;
+  const int be = (int)(b >> 52);
+  if (b != 0 && be != 0x7FF && e != kBadExp) {
+    const uint64_t mant = be ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : b;
+    const int sh = (be ? be - 1075 : -1074) + kFrac - e;  // M = mant 2^sh < 2^56
+    if (sh >= 0) M = mant << sh;
+    else if (sh > -64) M = mant >> (-sh);
+  }
+  const bool neg = (bits >> 63) != 0;
+#pragma unroll
+  for (int p = 0; p < kS; ++p) {
+    const int v = (int)((M >> (kFrac - kBits * (p + 1))) & 127u);
+    d[p] = neg ? -v : v;
+  }
+}
+
+// e[m] over the row m of A (A(m, k) = src[m rs + k cs]), one warp per row.
+__global__ void em_row_exp_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                  int64_t rows, int64_t cols, int* __restrict__ e,
+                                  int* __restrict__ err) {
+  const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= rows) return;
+  int mx = kZeroExp;
+  for (int64_t k = lane; k < cols; k += 32) mx = max(mx, exp_of(src[m * rs + k * cs]));
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    e[m] = mx;
+    if (mx == kBadExp && err) atomicOr(err, DEV_ERR_NONFINITE);
+  }
+}
+
+// e[n] over the column n of B (B(k, n) = src[k rs + n cs]), one thread per column.
+__global__ void em_col_exp_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                  int64_t K, int64_t N, int* __restrict__ e,
+                                  int* __restrict__ err) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  int mx = kZeroExp;
+  for (int64_t k = 0; k < K; ++k) mx = max(mx, exp_of(src[k * rs + n * cs]));
+  e[n] = mx;
+  if (mx == kBadExp && err) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
+// Digits of A into out [kS][rows_pad][k_pad] (k contiguous); padding is zero.
+// One thread per (row, 8 consecutive k).
+__global__ void em_split_rows_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                     int64_t rows, int64_t cols, const int* __restrict__ e,
+                                     int64_t rows_pad, int64_t k_pad,
+                                     __nv_bfloat16* __restrict__ out) {
+  const int64_t groups = k_pad / 8;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows_pad * groups) return;
+  const int64_t m = t / groups, k0 = (t - m * groups) * 8;
+  const int em = m < rows ? e[m] : kZeroExp;
+  __align__(16) __nv_bfloat16 v[kS][8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t k = k0 + j;
+    const double x = (m < rows && k < cols) ? src[m * rs + k * cs] : 0.0;
+    int d[kS];
+    digits_of(x, em, d);
+#pragma unroll
+    for (int p = 0; p < kS; ++p) v[p][j] = __int2bfloat16_rn(d[p]);
+  }
+  const int64_t plane = rows_pad * k_pad;
+#pragma unroll
+  for (int p = 0; p < kS; ++p)
+    *reinterpret_cast<uint4*>(out + p * plane + m * k_pad + k0) =
+        *reinterpret_cast<const uint4*>(v[p]);
+}
+
+// Digits of B (K x N) into out [kS][n_pad][k_pad] (k contiguous, i.e. B^T).
+// One thread per (column, 8 consecutive k); consecutive threads take
+// consecutive columns so that the reads along a row of B coalesce.
+__global__ void em_split_cols_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                     int64_t K, int64_t N, const int* __restrict__ e,
+                                     int64_t n_pad, int64_t k_pad,
+                                     __nv_bfloat16* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pad * (k_pad / 8)) return;
+  const int64_t n = t % n_pad, k0 = (t / n_pad) * 8;
+  const int en = n < N ? e[n] : kZeroExp;
+  __align__(16) __nv_bfloat16 v[kS][8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t k = k0 + j;
+    const double x = (n < N && k < K) ? src[k * rs + n * cs] : 0.0;
+    int d[kS];
+    digits_of(x, en, d);
+#pragma unroll
+    for (int p = 0; p < kS; ++p) v[p][j] = __int2bfloat16_rn(d[p]);
+  }
+  const int64_t plane = n_pad * k_pad;
+#pragma unroll
+  for (int p = 0; p < kS; ++p)
+    *reinterpret_cast<uint4*>(out + p * plane + n * k_pad + k0) =
+        *reinterpret_cast<const uint4*>(v[p]);
+}
+
+struct EmMaps {
+  CUtensorMap a[kS];
+  CUtensorMap b[kS];
+};
+
+struct EmParams {
+  int64_t M, N, k_tiles;
+  int m_tiles, n_tiles, kchunks;
+  const int* ea;
+  const int* eb;
+  double* C;
+  int64_t ldc;
+  double alpha;
+  int mode;  // 0: C = alpha A B; 1: C += alpha A B; 2: the same with atomics (K split)
+  int* err;
+  uint64_t wait_ns;
+};
+
+// x 2^E for a finite x (exponent arithmetic on the bits when the result stays
+// normal; ldexp otherwise).
+__device__ __forceinline__ double scale2(double x, int E) {
+  if (x == 0.0) return 0.0;
+  const long long b = __double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7FF);
+  const int nb = be + E;
+  if (be > 0 && nb > 0 && nb < 0x7FF) return __longlong_as_double(b + ((long long)E << 52));
+  return ldexp(x, E);
+}
+
+// One CTA per (64-column tile, 128-row tile, K chunk of <= 128): warp 0 loads
+// the 8 digit planes of both operands by TMA (two stages of 32 k), warp 1
+// issues the 36 products of each 16-k step into the 8 level accumulators in
+// tensor memory (level p + q - 2 at columns 64 (p + q - 2)), warps 2..5 combine
+// the levels of their 32 rows.
+__global__ void __launch_bounds__(EM_THREADS, 1)
+    emgemm_kernel(const __grid_constant__ EmMaps maps, const EmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + EM_STAGES * EM_STAGE);
+  uint64_t* empty = full + EM_STAGES;
+  uint64_t* acc_full = empty + EM_STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  int64_t unit = blockIdx.x;
+  const int nt = (int)(unit % p.n_tiles);
+  unit /= p.n_tiles;
+  const int mt = (int)(unit % p.m_tiles);
+  unit /= p.m_tiles;
+  const int kc = (int)unit;
+  constexpr int64_t KT = EM_KCHUNK / EM_BK;
+  const int64_t kt0 = (int64_t)kc * KT;
+  const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < EM_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, EM_TMEM);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int m0 = mt * EM_BM, n0 = nt * EM_BN;
+
+  if (kt1 > kt0) {
+    if (warp == 0) {
+      if (lane == 0) {
+        uint32_t it = 0;
+        for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
+          const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) break;
+          tc::mbar_arrive_expect_tx(&full[s], EM_STAGE);
+          uint8_t* base = smem + s * EM_STAGE;
+          const int32_t x = (int32_t)(kt * EM_BK);
+#pragma unroll
+          for (int q = 0; q < kS; ++q) {
+            tc::tma_load_2d(base + q * EM_AT, &maps.a[q], &full[s], x, m0);
+            tc::tma_load_2d(base + kS * EM_AT + q * EM_BT, &maps.b[q], &full[s], x, n0);
+          }
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_f16(EM_BM, EM_BN, 1);
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
+          const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
+          if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err, p.wait_ns)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t base = tc::smem_u32(smem + s * EM_STAGE);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+            for (int pa = 0; pa < kS; ++pa) {
+              const uint64_t ad = tc::smem_desc(base + pa * EM_AT + kk * 32, 16, 512, 4);
+#pragma unroll
+              for (int qb = 0; qb < kS - pa; ++qb) {
+                const uint64_t bd =
+                    tc::smem_desc(base + kS * EM_AT + qb * EM_BT + kk * 32, 16, 512, 4);
+                // the first product of every level zeroes it (pa = 0 reaches all levels)
+                const uint32_t acc = (kt == kt0 && kk == 0 && pa == 0) ? 0u : 1u;
+                tc::umma_f16(tmem + (uint32_t)((pa + qb) * EM_BN), ad, bd, idesc, acc);
+              }
+            }
+          tc::umma_commit(&empty[s]);
+        }
+        if (ok) tc::umma_commit(acc_full);
+      }
+    } else {
+      const int quad = warp & 3;
+      const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+      const int64_t m = m0 + 32 * quad + lane;
+      const bool ok = tc::mbar_wait(acc_full, 0, abort_flag, p.err, p.wait_ns);
+      if (__all_sync(0xffffffffu, ok)) {
+        tc::tc_fence_after();
+        const int ea = m < p.M ? p.ea[m] : kZeroExp;
+#pragma unroll 1
+        for (int cb = 0; cb < EM_BN / 8; ++cb) {
+          uint32_t r[kS][8];
+#pragma unroll
+          for (int l = 0; l < kS; ++l)
+            tc::tmem_ld_32x32b_x8(tmem + lane_base + (uint32_t)(l * EM_BN + cb * 8), r[l]);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t n = n0 + cb * 8 + j;
+            // V = 2^52 sum_L acc_L 2^(-7 L), L = l + 2
+            long long V = 0;
+#pragma unroll
+            for (int l = 0; l < kS; ++l) {
+              const long long a = (long long)__float2int_rn(__uint_as_float(r[l][j]));
+              const int sh = 52 - kBits * (l + 2);
+              V += sh >= 0 ? a * (1ll << sh) : (a >> (-sh));
+            }
+            if (m < p.M && n < p.N) {
+              const int eb = p.eb[n];
+              double val = 0.0;
+              if (ea != kZeroExp && eb != kZeroExp)
+                val = p.alpha * scale2((double)V, ea + eb - 52);
+              double* c = p.C + m * p.ldc + n;
+              if (p.mode == 0) *c = val;
+              else if (p.mode == 1) *c += val;
+              else atomicAdd(c, val);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    // a bounded wait expired: give issued copies and products time to land
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) {
+    }
+  }
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, EM_TMEM);
+  }
+}
+
+// Inverse of every diagonal block of the lower-triangular L [n][n]:
+// out[j] (TB x TB, zero above the diagonal and beyond the block's size) by
+// forward substitution, thread c producing column c.
+__global__ void __launch_bounds__(TRSM_TB) trtri_blocks_kernel(const double* __restrict__ L, int n,
+                                                               double* __restrict__ out) {
+  extern __shared__ double Ls[];  // [TB][TB]
+  const int j0 = blockIdx.x * TRSM_TB;
+  const int jb = n - j0 < TRSM_TB ? n - j0 : TRSM_TB;
+  double* X = out + (int64_t)blockIdx.x * TRSM_TB * TRSM_TB;
+  for (int q = threadIdx.x; q < TRSM_TB * TRSM_TB; q += blockDim.x) {
+    const int i = q / TRSM_TB, k = q - i * TRSM_TB;
+    Ls[q] = (i < jb && k <= i) ? L[(int64_t)(j0 + i) * n + j0 + k] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  for (int i = 0; i < TRSM_TB; ++i) {
+    double v = 0.0;
+    if (i < jb && c < jb && i >= c) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) s -= Ls[i * TRSM_TB + k] * X[k * TRSM_TB + c];
+      v = s / Ls[i * TRSM_TB + i];
+    }
+    X[i * TRSM_TB + c] = v;
+  }
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)ceil_div(n, b); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+// Workspace of one emulated product with at most Mmax rows, Nmax columns and
+// Kmax inner terms: the digit planes of both operands, the exponents and an
+// error word.
+struct EmWs {
+  __nv_bfloat16 *a, *b;
+  int *ea, *eb, *err;
+  int64_t m_cap, n_cap, k_cap;
+  void carve(Carve& cv, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
+    m_cap = round_up(Mmax, EM_BM);
+    n_cap = round_up(Nmax, EM_BN);
+    k_cap = round_up(Kmax, EM_BK);
+    a = cv.take<__nv_bfloat16>((size_t)kS * m_cap * k_cap);
+    b = cv.take<__nv_bfloat16>((size_t)kS * n_cap * k_cap);
+    ea = cv.take<int>((size_t)m_cap);
+    eb = cv.take<int>((size_t)n_cap);
+    err = cv.take<int>(64);
+  }
+};
+
+size_t em_dgemm_ws(int64_t Mmax, int64_t Nmax, int64_t Kmax) {
+  Carve c(nullptr, 0);
+  EmWs w;
+  w.carve(c, Mmax, Nmax, Kmax);
+  return c.off;
+}
+
+// C (M x N, row stride ldc) = alpha A B (overwrite) or C += alpha A B, with
+// A(m, k) = A[m a_rs + k a_cs] and B(k, n) = B[k b_rs + n b_cs] in FP64; the
+// products on the tensor cores as described at the top of this file.  C may
+// alias B's storage (the digits are taken before C is written).
+int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int64_t a_cs,
+             const double* B, int64_t b_rs, int64_t b_cs, double alpha, bool overwrite,
+             double* C, int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return ISDF_OK;
+  Carve cv(ws, ws_bytes);
+  EmWs w;
+  w.carve(cv, M, N, K > 0 ? K : 1);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  if (K <= 0) {
+    if (overwrite)
+      ISDF_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, s));
+    return ISDF_OK;
+  }
+  const int64_t Mp = round_up(M, EM_BM), Np = round_up(N, EM_BN), Kp = round_up(K, EM_BK);
+  em_row_exp_kernel<<<nblk(M, 8), 256, 0, s>>>(A, a_rs, a_cs, M, K, w.ea, w.err);
+  ISDF_LAUNCH_CHECK();
+  em_col_exp_kernel<<<nblk(N, 256), 256, 0, s>>>(B, b_rs, b_cs, K, N, w.eb, w.err);
+  ISDF_LAUNCH_CHECK();
+  em_split_rows_kernel<<<nblk(Mp * (Kp / 8), 256), 256, 0, s>>>(A, a_rs, a_cs, M, K, w.ea, Mp,
+                                                                 Kp, w.a);
+  ISDF_LAUNCH_CHECK();
+  em_split_cols_kernel<<<nblk(Np * (Kp / 8), 256), 256, 0, s>>>(B, b_rs, b_cs, K, N, w.eb, Np,
+                                                                 Kp, w.b);
+  ISDF_LAUNCH_CHECK();
+  EmMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  for (int q = 0; q < kS; ++q) {
+    ISDF_TRY(tma_map_bf16(&maps.a[q], w.a + (size_t)q * Mp * Kp, Mp, Kp, EM_BM));
+    ISDF_TRY(tma_map_bf16(&maps.b[q], w.b + (size_t)q * Np * Kp, Np, Kp, EM_BN));
+  }
+  EmParams p;
+  p.M = M;
+  p.N = N;
+  p.k_tiles = Kp / EM_BK;
+  p.m_tiles = (int)(Mp / EM_BM);
+  p.n_tiles = (int)(Np / EM_BN);
+  p.kchunks = (int)ceil_div(Kp, EM_KCHUNK);
+  p.ea = w.ea;
+  p.eb = w.eb;
+  p.C = C;
+  p.ldc = ldc;
+  p.alpha = alpha;
+  p.err = w.err;
+  p.wait_ns = wait_limit_ns();
+  if (p.kchunks == 1) {
+    p.mode = overwrite ? 0 : 1;
+  } else {
+    if (overwrite)
+      ISDF_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, s));
+    p.mode = 2;
+  }
+  const int64_t units = (int64_t)p.m_tiles * p.n_tiles * p.kchunks;
+  ISDF_ARG(units < (1ll << 31), "too many GEMM work units");
+  ISDF_CUDA(cudaFuncSetAttribute(emgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)EM_SMEM));
+  emgemm_kernel<<<(unsigned)units, EM_THREADS, EM_SMEM, s>>>(maps, p);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+// The error word of the last em_dgemm on this workspace (device int).
+int* em_err_word(void* ws, int64_t Mmax, int64_t Nmax, int64_t Kmax) {
+  Carve cv(ws, ~size_t(0));
+  EmWs w;
+  w.carve(cv, Mmax, Nmax, Kmax);
+  return w.err;
+}
+
+// Workspace of em_potrs_lower: the inverted diagonal blocks and one product's
+// digit planes (at most n rows, nrhs columns, 128 inner terms).
+size_t em_potrs_ws(int n, int64_t nrhs) {
+  Carve c(nullptr, 0);
+  c.take<double>((size_t)ceil_div(n, TRSM_TB) * TRSM_TB * TRSM_TB);
+  EmWs w;
+  w.carve(c, n, nrhs, TRSM_TB);
+  return c.off;
+}
+
+// Solve (L L^T) X = B in place (B [n][nrhs], row stride ldb; L lower triangular
+// [n][n]) by blocks of 128: each diagonal block is inverted once in FP64, and
+// every block step is two emulated products,
+//   forward   X_j = inv(L_jj) B_j,      B_r -= L_rj X_j     (r > j),
+//   backward  X_j = inv(L_jj)^T Y_j,    Y_r -= L_jr^T X_j   (r < j).
+int em_potrs_lower(const double* L, int n, double* B, int64_t nrhs, int64_t ldb, void* ws,
+                   size_t ws_bytes, cudaStream_t s) {
+  ISDF_ARG(L && B && n > 0 && nrhs > 0, "em_potrs_lower: empty arguments");
+  Carve cv(ws, ws_bytes);
+  const int nb = (int)ceil_div(n, TRSM_TB);
+  double* Linv = cv.take<double>((size_t)nb * TRSM_TB * TRSM_TB);
+  void* gws = (char*)ws + cv.off;
+  const size_t gbytes = ws_bytes > cv.off ? ws_bytes - cv.off : 0;
+  EmWs w;
+  w.carve(cv, n, nrhs, TRSM_TB);
+  ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
+  const size_t smem = (size_t)TRSM_TB * TRSM_TB * sizeof(double);
+  ISDF_CUDA(cudaFuncSetAttribute(trtri_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  trtri_blocks_kernel<<<nb, TRSM_TB, smem, s>>>(L, n, Linv);
+  ISDF_LAUNCH_CHECK();
+  for (int j = 0; j < nb; ++j) {
+    const int j0 = j * TRSM_TB, jb = n - j0 < TRSM_TB ? n - j0 : TRSM_TB;
+    const double* Li = Linv + (size_t)j * TRSM_TB * TRSM_TB;
+    double* Bj = B + (int64_t)j0 * ldb;
+    ISDF_TRY(em_dgemm(jb, nrhs, jb, Li, TRSM_TB, 1, Bj, ldb, 1, 1.0, true, Bj, ldb, gws, gbytes,
+                      s));
+    const int rest = n - j0 - jb;
+    if (rest > 0)
+      ISDF_TRY(em_dgemm(rest, nrhs, jb, L + (int64_t)(j0 + jb) * n + j0, n, 1, Bj, ldb, 1, -1.0,
+                        false, B + (int64_t)(j0 + jb) * ldb, ldb, gws, gbytes, s));
+  }
+  for (int j = nb - 1; j >= 0; --j) {
+    const int j0 = j * TRSM_TB, jb = n - j0 < TRSM_TB ? n - j0 : TRSM_TB;
+    const double* Li = Linv + (size_t)j * TRSM_TB * TRSM_TB;
+    double* Bj = B + (int64_t)j0 * ldb;
+    ISDF_TRY(em_dgemm(jb, nrhs, jb, Li, 1, TRSM_TB, Bj, ldb, 1, 1.0, true, Bj, ldb, gws, gbytes,
+                      s));
+    if (j0 > 0)
+      ISDF_TRY(em_dgemm(j0, nrhs, jb, L + (int64_t)j0 * n, 1, n, Bj, ldb, 1, -1.0, false, B, ldb,
+                        gws, gbytes, s));
+  }
+  return ISDF_OK;
+}
+
+}  // namespace isdf

@@ -6,9 +6,21 @@
 //   gradient c: Gram = dG^c_PP o G_PP,     RHS = dG^c o G
 //   Cholesky of each Gram with the adaptive Tikhonov retry of Sec. IV.B,
 //   then two blocked triangular solves over all grid columns in place.
+// fit_mode 1 takes the right-hand-side GEMMs and the triangular solves (98 %
+// of the flops) as FP64 products emulated exactly on the tensor cores
+// (emu64.cu); the Grams and their Cholesky factors stay FP64 on CUDA cores.
 #include "linalg.cuh"
 
 namespace isdf {
+
+size_t em_dgemm_ws(int64_t Mmax, int64_t Nmax, int64_t Kmax);
+int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int64_t a_cs,
+             const double* B, int64_t b_rs, int64_t b_cs, double alpha, bool overwrite,
+             double* C, int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t em_potrs_ws(int n, int64_t nrhs);
+int em_potrs_lower(const double* L, int n, double* B, int64_t nrhs, int64_t ldb, void* ws,
+                   size_t ws_bytes, cudaStream_t s);
+
 namespace {
 
 __global__ void gather_pivots_kernel(const double* __restrict__ src, int64_t n_g, int n_orb,
@@ -93,7 +105,9 @@ struct FitWs {
   int* err;
   double *phiP, *dphiP, *GPP, *Gram, *Save, *scal;
   int* info;
-  void carve(Carve& cv, int n_orb, int n_mu) {
+  void* em = nullptr;  // emulated products (fit_mode 1)
+  size_t em_bytes = 0;
+  void carve(Carve& cv, int64_t n_g, int n_orb, int n_mu, int mode) {
     err = cv.take<int>(64);
     phiP = cv.take<double>((size_t)n_mu * n_orb);
     dphiP = cv.take<double>((size_t)3 * n_mu * n_orb);
@@ -102,25 +116,31 @@ struct FitWs {
     Save = cv.take<double>((size_t)n_mu * n_mu);
     scal = cv.take<double>(2);
     info = cv.take<int>(1);
+    if (mode == 1) {
+      const size_t a = em_dgemm_ws(n_mu, n_g, n_orb), b = em_potrs_ws(n_mu, n_g);
+      em_bytes = a > b ? a : b;
+      em = cv.take<char>(em_bytes);
+    }
   }
 };
 
-size_t fit_ws(int64_t n_g, int n_orb, int n_mu) {
-  (void)n_g;
+size_t fit_ws(int64_t n_g, int n_orb, int n_mu, int mode) {
   Carve c(nullptr, 0);
   FitWs f;
-  f.carve(c, n_orb, n_mu);
+  f.carve(c, n_g, n_orb, n_mu, mode);
   return c.off;
 }
 
 int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int32_t* piv,
         int n_mu, double* xi, double* xig, double* jitter_used, double jitter_init,
-        double jitter_growth, int max_tries, void* ws, size_t ws_bytes, cudaStream_t s) {
+        double jitter_growth, int max_tries, int mode, void* ws, size_t ws_bytes,
+        cudaStream_t s) {
   ISDF_ARG(phi && dphi && piv && xi && xig, "null pointer argument");
   ISDF_ARG(n_g > 0 && n_orb > 0 && n_mu > 0, "empty sizes");
+  ISDF_ARG(mode == 0 || mode == 1, "fit_mode must be 0 or 1");
   Carve cv(ws, ws_bytes);
   FitWs f;
-  f.carve(cv, n_orb, n_mu);
+  f.carve(cv, n_g, n_orb, n_mu, mode);
   int* err = f.err;
   double *phiP = f.phiP, *dphiP = f.dphiP, *GPP = f.GPP, *Gram = f.Gram, *Save = f.Save;
   double* scal = f.scal;
@@ -153,16 +173,25 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
   ISDF_TRY(dgemm(g, s));
 
   // right-hand sides: G into xi, dG^c into xig, then the Hadamard products
-  Dgemm r;
-  r.M = n_mu; r.N = n_g; r.K = n_orb;
-  r.A = phiP; r.a_rs = n_orb; r.a_cs = 1; r.a_bs = 0;
-  r.B = phi; r.b_rs = n_g; r.b_cs = 1; r.b_bs = 0;
-  r.C = xi; r.ldc = n_g; r.c_bs = 0;
-  ISDF_TRY(dgemm(r, s));
-  r.A = dphiP; r.a_bs = (int64_t)n_mu * n_orb;
-  r.B = dphi; r.b_bs = (int64_t)n_orb * n_g;
-  r.C = xig; r.c_bs = ng; r.batch = 3;
-  ISDF_TRY(dgemm(r, s));
+  if (mode == 1) {
+    ISDF_TRY(em_dgemm(n_mu, n_g, n_orb, phiP, n_orb, 1, phi, n_g, 1, 1.0, true, xi, n_g, f.em,
+                      f.em_bytes, s));
+    for (int c = 0; c < 3; ++c)
+      ISDF_TRY(em_dgemm(n_mu, n_g, n_orb, dphiP + (int64_t)c * n_mu * n_orb, n_orb, 1,
+                        dphi + (int64_t)c * n_orb * n_g, n_g, 1, 1.0, true, xig + c * ng, n_g,
+                        f.em, f.em_bytes, s));
+  } else {
+    Dgemm r;
+    r.M = n_mu; r.N = n_g; r.K = n_orb;
+    r.A = phiP; r.a_rs = n_orb; r.a_cs = 1; r.a_bs = 0;
+    r.B = phi; r.b_rs = n_g; r.b_cs = 1; r.b_bs = 0;
+    r.C = xi; r.ldc = n_g; r.c_bs = 0;
+    ISDF_TRY(dgemm(r, s));
+    r.A = dphiP; r.a_bs = (int64_t)n_mu * n_orb;
+    r.B = dphi; r.b_bs = (int64_t)n_orb * n_g;
+    r.C = xig; r.c_bs = ng; r.batch = 3;
+    ISDF_TRY(dgemm(r, s));
+  }
   rhs_finish_kernel<<<nblocks(ng), 256, 0, s>>>(xi, xig, ng);
   ISDF_LAUNCH_CHECK();
 
@@ -206,7 +235,10 @@ int fit(const double* phi, const double* dphi, int64_t n_g, int n_orb, const int
     }
     if (jitter_used) jitter_used[ch] = lam;
     double* rhs = ch == 0 ? xi : xig + (int64_t)(ch - 1) * ng;
-    ISDF_TRY(dpotrs_lower(Gram, n_mu, rhs, n_g, n_g, s));
+    if (mode == 1)
+      ISDF_TRY(em_potrs_lower(Gram, n_mu, rhs, n_g, n_g, f.em, f.em_bytes, s));
+    else
+      ISDF_TRY(dpotrs_lower(Gram, n_mu, rhs, n_g, n_g, s));
   }
   // overflow in the solves
   ISDF_TRY(scan_nonfinite(xi, ng, err, s));

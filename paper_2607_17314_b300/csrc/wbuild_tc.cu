@@ -73,6 +73,11 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols
   return ISDF_OK;
 }
 
+// The same map for other translation units (BF16 [rows][cols], 64-byte swizzle).
+int tma_map_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  return make_map(m, base, rows, cols, box_rows);
+}
+
 // Tensor map over an FP32 (TF32 limbs) matrix [rows][cols] with a box of 32
 // columns x box_rows rows and the 128-byte swizzle.
 static int make_map_f32(CUtensorMap* m, const void* base, int64_t rows, int64_t cols,

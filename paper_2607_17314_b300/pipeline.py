@@ -52,10 +52,11 @@ def upload(center, powers, exps, coefs, mo_coef, grid, w, n_mu, n_occ, jastrow,
 
 def run(inp: Inputs, precision: str = "bf16x3", n_orb_x: Optional[int] = None,
         events: Optional[Dict[str, list]] = None, kchunk: int = 0,
-        stage_ms: Optional[list] = None) -> Dict[str, object]:
+        stage_ms: Optional[list] = None, fit_mode: int = 0) -> Dict[str, object]:
     """One pass of the path.  ``events`` (name -> list) collects CUDA event
     pairs around each step; ``stage_ms`` collects the device times of the two
-    W-build stages (tensor-core precisions)."""
+    W-build stages (tensor-core precisions); ``fit_mode`` 1 runs the fit's
+    FP64 products emulated on the tensor cores."""
     def mark(name):
         if events is None:
             return None
@@ -73,7 +74,7 @@ def run(inp: Inputs, precision: str = "bf16x3", n_orb_x: Optional[int] = None,
     piv = api.isdf_points(phi, dphi, inp.w, inp.n_mu)
     mark("a2")
     mark("a3")
-    xi, xig, jit = api.isdf_fit(phi, dphi, piv)
+    xi, xig, jit = api.isdf_fit(phi, dphi, piv, fit_mode=fit_mode)
     mark("a3")
     mark("a4")
     W, calG = api.tc_kernel_build(inp.grid, inp.w, xi, xig, inp.jastrow, precision, kchunk=kchunk,

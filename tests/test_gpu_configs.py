@@ -67,9 +67,10 @@ def test_h50_chain_orbitals_pivots_fit(api):
     phi_h, dphi_h = phi.cpu().numpy(), dphi.cpu().numpy()
     ref = pivots.select(phi_h, dphi_h, w.grid_w, n_cut, keep_L=False)
     assert np.array_equal(piv, ref.pivots)
-    # fit at the full N_mu on the GPU's own selection
+    # fit at the full N_mu on the GPU's own selection, FP64 on CUDA cores (mode 0)
+    # and with the FP64 products emulated on the tensor cores (mode 1: 16 blocks
+    # of 128 in each triangular solve)
     piv_full = api.isdf_points(phi, dphi, wt, w.n_mu)
-    xi, xig, jit = api.isdf_fit(phi, dphi, piv_full)
     P = piv_full.cpu().numpy()
     rng = np.random.default_rng(2)
     cols = np.sort(rng.choice(w.n_g, 256, replace=False))
@@ -78,17 +79,20 @@ def test_h50_chain_orbitals_pivots_fit(api):
     G = phiP @ phi_h[:, cols]
     B = [G * G] + [(dphi_h[c][:, P].T @ dphi_h[c][:, cols]) * G for c in range(3)]
     it = torch.as_tensor(cols).cuda()
-    X = [xi[:, it].cpu().numpy()] + [xig[c][:, it].cpu().numpy() for c in range(3)]
-    for c in range(4):
-        A = Gm[c] + jit[c] * np.eye(len(P))
-        back = np.linalg.norm(A @ X[c] - B[c]) / (np.linalg.norm(A) * np.linalg.norm(X[c]))
-        Xo = sla.cho_solve(sla.cho_factor(A, lower=True), B[c])
-        kappa = np.linalg.cond(A)
-        fwd = np.linalg.norm(X[c] - Xo) / np.linalg.norm(Xo)
-        print("H50 fit channel %d: backward %.2e, forward %.2e, cond %.2e, jitter %.1e"
-              % (c, back, fwd, kappa, jit[c]))
-        assert back < 1e-10, (c, back)
-        assert fwd < max(1e-10, 8.0 * kappa * np.finfo(float).eps), (c, fwd, kappa)
+    for mode, fwd_factor in ((0, 8.0), (1, 64.0)):
+        xi, xig, jit = api.isdf_fit(phi, dphi, piv_full, fit_mode=mode)
+        X = [xi[:, it].cpu().numpy()] + [xig[c][:, it].cpu().numpy() for c in range(3)]
+        del xi, xig
+        for c in range(4):
+            A = Gm[c] + jit[c] * np.eye(len(P))
+            back = np.linalg.norm(A @ X[c] - B[c]) / (np.linalg.norm(A) * np.linalg.norm(X[c]))
+            Xo = sla.cho_solve(sla.cho_factor(A, lower=True), B[c])
+            kappa = np.linalg.cond(A)
+            fwd = np.linalg.norm(X[c] - Xo) / np.linalg.norm(Xo)
+            print("H50 fit mode %d channel %d: backward %.2e, forward %.2e, cond %.2e, jitter %.1e"
+                  % (mode, c, back, fwd, kappa, jit[c]))
+            assert back < 1e-10, (mode, c, back)
+            assert fwd < max(1e-10, fwd_factor * kappa * np.finfo(float).eps), (mode, c, fwd, kappa)
 
 
 def test_benzene_orbitals_and_pivots(api):

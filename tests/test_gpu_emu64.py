@@ -1,0 +1,137 @@
+"""FP64 products emulated on the tensor cores (isdf_dgemm_emulated) and the
+fit that uses them (isdf_fit with fit_mode 1), against extended-precision
+products, exact integer products and the FP64 oracle of the fit (Sec. II.D's
+normal equations, Sec. IV.B's solves)."""
+import numpy as np
+import pytest
+import torch
+
+from synth import workloads as wl
+from oracle import orbitals, pivots, fit
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_17314_b300 import build
+    build.build()
+    from paper_2607_17314_b300 import api
+    return api
+
+
+def cu(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dt).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def exact_product(A, B):
+    """A B in extended precision (64-bit significand), then rounded to FP64."""
+    return (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+
+
+def scale_bound(A, B):
+    """(K + 4) 2^-52 max_k|A_mk| max_k|B_kn|, the emulation's per-element error
+    bound: the dropped digit pairs give at most ~2^-53.2 of the scale per
+    term, the truncated digits 2^-55, and the two lowest levels' rounding
+    in the 64-bit combination at most 2 units of 2^-52."""
+    K = A.shape[1]
+    return (K + 4) * 2.0 ** -52 * np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
+
+
+@pytest.mark.parametrize("M,N,K,spread", [(300, 130, 128, 0.0), (129, 65, 37, 3.0),
+                                          (200, 257, 300, 6.0), (7, 3, 1, 0.0)])
+def test_emulated_product_within_bound(api, M, N, K, spread):
+    """Ragged M, N (not multiples of the 128 x 64 tiles), K within one
+    tensor-core run and K split over three runs (atomics), rows and columns of
+    wide dynamic range, a zero row, a zero column and mixed signs."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * 10.0 ** rng.uniform(-spread, spread, (M, K))
+    B = rng.standard_normal((K, N)) * 10.0 ** rng.uniform(-spread, spread, (K, N))
+    A[min(2, M - 1)] = 0.0
+    B[:, min(1, N - 1)] = 0.0
+    C = host(api.isdf_dgemm_emulated(cu(A), cu(B)))
+    ref = exact_product(A, B)
+    err = np.abs(C - ref)
+    bound = scale_bound(A, B)
+    ratio = float(np.max(err / np.where(bound > 0, bound, 1.0)))
+    fp64 = float(np.max(np.abs(A @ B - ref) / np.where(bound > 0, bound, 1.0)))
+    print(f"M={M} N={N} K={K}: error / bound {ratio:.3e} (FP64 GEMM {fp64:.3e})")
+    assert np.all(err <= bound), ratio
+    assert np.all(C[min(2, M - 1)] == 0.0) and np.all(C[:, min(1, N - 1)] == 0.0)
+
+
+def test_emulated_product_of_integers_is_exact(api):
+    """Integer matrices whose FP64 product is exact: every digit product and
+    level sum is an integer, so the emulated result is bit-identical."""
+    rng = np.random.default_rng(3)
+    A = rng.integers(-120, 121, (150, 300)).astype(float)
+    B = rng.integers(-120, 121, (300, 70)).astype(float)
+    C = host(api.isdf_dgemm_emulated(cu(A), cu(B)))
+    assert np.array_equal(C, A @ B)
+
+
+def test_emulated_product_accumulates(api):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((70, 90))
+    B = rng.standard_normal((90, 40))
+    C0 = rng.standard_normal((70, 40))
+    out = cu(C0)
+    api.isdf_dgemm_emulated(cu(A), cu(B), alpha=-1.5, out=out)
+    ref = (C0.astype(np.longdouble) - 1.5 * (A.astype(np.longdouble) @ B.astype(np.longdouble))
+           ).astype(np.float64)
+    bound = 1.5 * scale_bound(A, B) + EPS * np.abs(C0)
+    assert np.all(np.abs(host(out) - ref) <= bound)
+
+
+def _fit_case(n_mu):
+    w = wl.h6_chain()
+    phi, dphi = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    res = pivots.select(phi, dphi, w.grid_w, n_mu)
+    return w, phi, dphi, res.pivots
+
+
+@pytest.mark.parametrize("n_mu", [96, 200])
+def test_emulated_fit_against_oracle(api, n_mu):
+    """Sec. II.D's normal equations solved with the emulated products (one
+    block of 128 at N_mu = 96; two blocks, with trailing updates both ways,
+    at N_mu = 200, where the scalar Gram's condition number is ~1e12): backward error at 1e-10 against the oracle's Grams and
+    right-hand sides, forward agreement with the oracle within the Grams'
+    condition number times 64 FP64 unit roundoffs (the emulated products carry
+    about K 2^-52 of their scale, some 10x FP64's typical rounding)."""
+    w, phi, dphi, piv = _fit_case(n_mu)
+    xi, xig, jit = api.isdf_fit(cu(phi), cu(dphi), cu(piv, torch.int32), fit_mode=1)
+    xo, xto, lams = fit.fit(phi, dphi, piv)
+    assert np.allclose(jit, lams)
+    Gm = fit.grams(phi, dphi, piv)
+    Bm = fit.rhs(phi, dphi, piv)
+    X = np.concatenate([host(xi)[None], host(xig)])
+    Xo = np.concatenate([xo[None], xto])
+    for c in range(4):
+        G = Gm[c] + lams[c] * np.eye(Gm.shape[1])
+        back = np.linalg.norm(G @ X[c] - Bm[c]) / (np.linalg.norm(G) * np.linalg.norm(X[c]))
+        kappa = np.linalg.cond(G)
+        fwd = np.linalg.norm(X[c] - Xo[c]) / np.linalg.norm(Xo[c])
+        print(f"n_mu={n_mu} channel {c}: backward {back:.2e} cond {kappa:.2e} forward {fwd:.2e}")
+        assert back < 1e-10, (c, back)
+        assert fwd < max(1e-10, 64.0 * kappa * EPS), (c, fwd, kappa)
+
+
+def test_emulated_fit_matches_fp64_fit_on_gpu(api):
+    """fit_mode 1 against fit_mode 0 on the same GPU inputs (N_mu = 200)."""
+    w, phi, dphi, piv = _fit_case(200)
+    args = (cu(phi), cu(dphi), cu(piv, torch.int32))
+    x1, g1, _ = api.isdf_fit(*args, fit_mode=1)
+    x0, g0, _ = api.isdf_fit(*args, fit_mode=0)
+    Gm = fit.grams(phi, dphi, piv)
+    for c, (a, b) in enumerate([(x1, x0)] + [(g1[i], g0[i]) for i in range(3)]):
+        kappa = np.linalg.cond(Gm[c])
+        d = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        assert d < max(1e-10, 64.0 * kappa * EPS), (c, d, kappa)
