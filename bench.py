@@ -74,6 +74,10 @@ def parse():
                          "Metropolis sweeps, then Gauss-Newton iterations on the fixed sample")
     ap.add_argument("--fit-mode", type=int, default=1, choices=[0, 1],
                     help="the fit's FP64 products: 0 on CUDA cores, 1 emulated on the tensor cores")
+    ap.add_argument("--emu64", action="store_true",
+                    help="the fit on the H50 chain with FP64 on CUDA cores and with the FP64 "
+                         "products emulated on the tensor cores, and one emulated GEMM")
+    ap.add_argument("--emu-n", type=int, default=100000)
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--sweeps", type=int, default=40)
     ap.add_argument("--n-train", type=int, default=24)
@@ -811,6 +815,58 @@ def run_vmc(args):
     print(json.dumps(line), flush=True)
 
 
+def run_emu64(args):
+    """The ISDF fit of the H50 chain (100,000 points, 400 orbitals, N_mu = 2000)
+    with fit_mode 0 (FP64 on CUDA cores) and 1 (FP64 products emulated on the
+    tensor cores), and one emulated GEMM of the solves' update shape (2000 x
+    --emu-n x 128) against torch's FP64 matmul; CUDA events."""
+    import torch
+    from paper_2607_17314_b300 import api, build, pipeline
+    build.build()
+    wlw = make_workload("h50_chain")
+    b = wlw.basis
+    J = api.jastrow_from(wlw.jastrow)
+    inp = pipeline.upload(b.center, b.powers, b.exps, b.coefs, wlw.mo_coef, wlw.grid_xyz,
+                          wlw.grid_w, wlw.n_mu, wlw.n_occ, J)
+    phi, dphi = api.isdf_eval_orbitals(inp.center, inp.powers, inp.exps, inp.coefs, inp.mo_coef,
+                                       inp.grid)
+    piv = api.isdf_points(phi, dphi, inp.w, inp.n_mu)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        ts, out = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, ts
+    (x0, g0, _), t0 = timed(lambda: api.isdf_fit(phi, dphi, piv, fit_mode=0), 1)
+    (x1, g1, _), t1 = timed(lambda: api.isdf_fit(phi, dphi, piv, fit_mode=1),
+                            max(args.steps, 1) + 1)
+    diff = [float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))] + \
+        [float(torch.linalg.norm(g1[c] - g0[c]) / torch.linalg.norm(g0[c])) for c in range(3)]
+    del x0, g0, x1, g1
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    A = torch.randn((2000, 128), dtype=torch.float64, device="cuda", generator=gen)
+    B = torch.randn((128, args.emu_n), dtype=torch.float64, device="cuda", generator=gen)
+    C, tg = timed(lambda: api.isdf_dgemm_emulated(A, B), max(args.warmup, 1) + max(args.steps, 1))
+    C0, tr = timed(lambda: A @ B, 3)
+    flops = 2.0 * 2000 * args.emu_n * 128
+    print(json.dumps({"mode": "emu64", "workload": "h50_chain fit (N_mu = 2000, 400 orbitals, "
+                                                   "100,000 points)",
+                      "fit_fp64_ms": t0, "fit_emulated_ms": t1[1:],
+                      "fit_rel_diff": diff,
+                      "gemm": {"shape": [2000, args.emu_n, 128], "emulated_ms": tg[-1],
+                               "emulated_tflops_fp64_equiv": flops / (min(tg[1:]) * 1e-3) / 1e12,
+                               "torch_fp64_ms": min(tr[1:]),
+                               "rel_diff": float(torch.linalg.norm(C - C0) / torch.linalg.norm(C0))}}),
+          flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -827,6 +883,8 @@ def main():
         return run_proposer(args)
     if args.vmc:
         return run_vmc(args)
+    if args.emu64:
+        return run_emu64(args)
     if args.validate:
         return run_validate(args)
     if args.assembly:

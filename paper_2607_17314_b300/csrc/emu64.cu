@@ -34,7 +34,10 @@ constexpr int kFrac = kS * kBits;  // 56 fraction bits
 constexpr int kZeroExp = -4000;    // exponent of an all-zero row or column
 constexpr int kBadExp = 4000;      // a NaN or Inf in the row or column
 
-constexpr int EM_BM = 128, EM_BN = 64, EM_BK = 32, EM_STAGES = 2, EM_THREADS = 192;
+constexpr int EM_BM = 128, EM_BN = 64, EM_BK = 32, EM_STAGES = 2;
+constexpr int EM_EPI_WARPS = 16;  // four per tensor-memory lane quarter, 16 columns each
+constexpr int EM_EPI_COLS = EM_BN * 4 / EM_EPI_WARPS;
+constexpr int EM_THREADS = 64 + 32 * EM_EPI_WARPS;
 constexpr int EM_KCHUNK = 128;  // exact FP32 accumulation bound per level
 constexpr uint32_t EM_AT = EM_BM * EM_BK * 2;
 constexpr uint32_t EM_BT = EM_BN * EM_BK * 2;
@@ -173,26 +176,135 @@ struct EmParams {
   int64_t ldc;
   double alpha;
   int mode;  // 0: C = alpha A B; 1: C += alpha A B; 2: the same with atomics (K split)
+  int vec;   // C rows 16-byte aligned: 16-byte stores
   int* err;
   uint64_t wait_ns;
 };
 
-// x 2^E for a finite x (exponent arithmetic on the bits when the result stays
-// normal; ldexp otherwise).
-__device__ __forceinline__ double scale2(double x, int E) {
-  if (x == 0.0) return 0.0;
-  const long long b = __double_as_longlong(x);
-  const int be = (int)((b >> 52) & 0x7FF);
-  const int nb = be + E;
-  if (be > 0 && nb > 0 && nb < 0x7FF) return __longlong_as_double(b + ((long long)E << 52));
-  return ldexp(x, E);
+// sign * V * 2^E rounded to the nearest FP64 (ties to even), by integer
+// arithmetic on the bits; ldexp covers results outside the normal range.
+__device__ __forceinline__ double i64_scaled(long long V, int E, bool negate) {
+  if (V == 0) return 0.0;
+  uint64_t sign = V < 0 ? 1ull : 0ull;
+  uint64_t u = V < 0 ? (uint64_t)(-V) : (uint64_t)V;
+  if (negate) sign ^= 1ull;
+  const int lz = __clzll((long long)u);
+  u <<= lz;                           // bit 63 set: value = u 2^(E - lz)
+  uint64_t mant = u >> 11;            // 53 bits
+  const uint64_t rem = u & 0x7FFull;  // 11 rounding bits
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  int ex = 63 - lz + E;               // value = mant 2^(ex - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const int be = ex + 1023;
+  if (be > 0 && be < 0x7FF)
+    return __longlong_as_double((long long)((sign << 63) | ((uint64_t)be << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
+  const double v = ldexp((double)mant, ex - 52);
+  return sign ? -v : v;
 }
 
-// One CTA per (64-column tile, 128-row tile, K chunk of <= 128): warp 0 loads
-// the 8 digit planes of both operands by TMA (two stages of 32 k), warp 1
-// issues the 36 products of each 16-k step into the 8 level accumulators in
-// tensor memory (level p + q - 2 at columns 64 (p + q - 2)), warps 2..5 combine
-// the levels of their 32 rows.
+// One tile's level accumulators -> FP64 outputs: a warp takes 32 rows and the
+// EM_EPI_COLS columns [c0, c0 + EM_EPI_COLS) of the tile.  Per output
+//   V = 2^52 sum_L acc_L 2^(-7 L),  L = 2 .. 9,
+// formed from the level pairs P = acc_L 2^7 + acc_(L+1), exact in 32 bits
+// (|acc_L| <= (L - 1) 127^2 128, so |P| < 2^31), then four 64-bit terms
+// (the lowest pair keeps its bits down to 2^-52); then the scale
+// 2^(e_m + e_n - 52) and alpha.  The level pairs are taken out of tensor
+// memory first and acc_empty is signalled, so that the next tile's products
+// run while this tile's outputs are formed and stored.  mode 0 stores, 1 adds,
+// 2 adds atomically; each thread writes 8 consecutive columns of its row
+// (64 bytes) per block.
+__device__ __forceinline__ void em_epilogue(const EmParams& p, uint32_t taddr, int64_t m,
+                                            int64_t n0, int c0, uint64_t* acc_empty) {
+  constexpr int NB = EM_EPI_COLS / 8;
+  int P[NB][8][kS / 2];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint32_t r[kS][8];
+#pragma unroll
+    for (int l = 0; l < kS; ++l)
+      tc::tmem_ld_32x32b_x8(taddr + (uint32_t)(l * EM_BN + c0 + b * 8), r[l]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int h = 0; h < kS / 2; ++h)
+        P[b][j][h] = __float2int_rn(__uint_as_float(r[2 * h][j])) * (1 << kBits) +
+                     __float2int_rn(__uint_as_float(r[2 * h + 1][j]));
+  }
+  // the accumulators are free for the next tile
+  __syncwarp();
+  tc::tc_fence_before();
+  tc::mbar_arrive(acc_empty);
+
+  const int ea = m < p.M ? p.ea[m] : kZeroExp;
+  const bool unit_alpha = p.alpha == 1.0 || p.alpha == -1.0;
+  const bool neg = p.alpha < 0.0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int64_t nb = n0 + c0 + b * 8;
+    if (m >= p.M || nb >= p.N) continue;
+    int ebv[8];
+    if (nb + 8 <= p.N) {
+      const int4 e0 = __ldg(reinterpret_cast<const int4*>(p.eb + nb));
+      const int4 e1 = __ldg(reinterpret_cast<const int4*>(p.eb + nb) + 1);
+      ebv[0] = e0.x; ebv[1] = e0.y; ebv[2] = e0.z; ebv[3] = e0.w;
+      ebv[4] = e1.x; ebv[5] = e1.y; ebv[6] = e1.z; ebv[7] = e1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ebv[j] = nb + j < p.N ? p.eb[nb + j] : kZeroExp;
+    }
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // pair h holds levels 2h + 2, 2h + 3: weight 2^(52 - 7 (2h + 3))
+      const long long V = (long long)P[b][j][0] * (1ll << 31) +
+                          (long long)P[b][j][1] * (1ll << 17) +
+                          (long long)P[b][j][2] * (1ll << 3) + (long long)(P[b][j][3] >> 11);
+      double x = 0.0;
+      if (ea != kZeroExp && ebv[j] != kZeroExp) {
+        x = i64_scaled(V, ea + ebv[j] - 52, unit_alpha && neg);
+        if (!unit_alpha) x *= p.alpha;
+      }
+      v[j] = x;
+    }
+    double* c = p.C + m * p.ldc + nb;
+    if (p.vec && nb + 8 <= p.N && p.mode != 2) {
+      double2* c2 = reinterpret_cast<double2*>(c);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double2 o = make_double2(v[2 * j], v[2 * j + 1]);
+        if (p.mode == 1) {
+          const double2 q = c2[j];
+          o.x += q.x;
+          o.y += q.y;
+        }
+        c2[j] = o;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (nb + j >= p.N) break;
+        if (p.mode == 0) c[j] = v[j];
+        else if (p.mode == 1) c[j] += v[j];
+        else atomicAdd(c + j, v[j]);
+      }
+    }
+  }
+}
+
+// Persistent: CTA b takes the work units b, b + gridDim.x, ... (unit = K chunk
+// fastest, then the 128-row tile, then the 64-column tile, so that the CTAs
+// running together share B tiles and the K chunks of one output tile run
+// side by side).  Warp 0 loads the 8 digit planes of both operands by TMA
+// into a two-stage ring that runs ahead across tiles; warp 1 issues the 36
+// products of each 16-k step into the 8 level accumulators in tensor memory
+// (level p + q - 2 at columns 64 (p + q - 2)) once the epilogue has drained
+// the previous tile; warps 2 .. 17 combine the levels (warp w: the rows of
+// lane quarter w % 4, columns 16 ((w - 2) / 4) ..).
 __global__ void __launch_bounds__(EM_THREADS, 1)
     emgemm_kernel(const __grid_constant__ EmMaps maps, const EmParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -200,19 +312,12 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   uint64_t* full = (uint64_t*)(smem + EM_STAGES * EM_STAGE);
   uint64_t* empty = full + EM_STAGES;
   uint64_t* acc_full = empty + EM_STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
-  int64_t unit = blockIdx.x;
-  const int nt = (int)(unit % p.n_tiles);
-  unit /= p.n_tiles;
-  const int mt = (int)(unit % p.m_tiles);
-  unit /= p.m_tiles;
-  const int kc = (int)unit;
   constexpr int64_t KT = EM_KCHUNK / EM_BK;
-  const int64_t kt0 = (int64_t)kc * KT;
-  const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
-
+  const int64_t units = (int64_t)p.kchunks * p.m_tiles * p.n_tiles;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < EM_STAGES; ++s) {
@@ -220,6 +325,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, EM_EPI_WARPS * 32);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -231,30 +337,45 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int m0 = mt * EM_BM, n0 = nt * EM_BN;
 
-  if (kt1 > kt0) {
-    if (warp == 0) {
-      if (lane == 0) {
-        uint32_t it = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int kc = (int)(u % p.kchunks);
+        const int mt = (int)((u / p.kchunks) % p.m_tiles);
+        const int nt = (int)(u / ((int64_t)p.kchunks * p.m_tiles));
+        const int64_t kt0 = (int64_t)kc * KT;
+        const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
           const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) break;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) {
+            ok = false;
+            break;
+          }
           tc::mbar_arrive_expect_tx(&full[s], EM_STAGE);
           uint8_t* base = smem + s * EM_STAGE;
           const int32_t x = (int32_t)(kt * EM_BK);
 #pragma unroll
           for (int q = 0; q < kS; ++q) {
-            tc::tma_load_2d(base + q * EM_AT, &maps.a[q], &full[s], x, m0);
-            tc::tma_load_2d(base + kS * EM_AT + q * EM_BT, &maps.b[q], &full[s], x, n0);
+            tc::tma_load_2d(base + q * EM_AT, &maps.a[q], &full[s], x, mt * EM_BM);
+            tc::tma_load_2d(base + kS * EM_AT + q * EM_BT, &maps.b[q], &full[s], x, nt * EM_BN);
           }
         }
       }
-    } else if (warp == 1) {
-      if (lane == 0) {
-        constexpr uint32_t idesc = tc::idesc_f16(EM_BM, EM_BN, 1);
-        uint32_t it = 0;
-        bool ok = true;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(EM_BM, EM_BN, 1);
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++lt) {
+        const int kc = (int)(u % p.kchunks);
+        const int64_t kt0 = (int64_t)kc * KT;
+        const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
+        if (!tc::mbar_wait(acc_empty, (lt & 1) ^ 1, abort_flag, p.err, p.wait_ns)) break;
+        tc::tc_fence_after();
         for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
           const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
           if (!tc::mbar_wait(&full[s], ph, abort_flag, p.err, p.wait_ns)) {
@@ -281,45 +402,20 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
         if (ok) tc::umma_commit(acc_full);
       }
-    } else {
-      const int quad = warp & 3;
-      const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-      const int64_t m = m0 + 32 * quad + lane;
-      const bool ok = tc::mbar_wait(acc_full, 0, abort_flag, p.err, p.wait_ns);
-      if (__all_sync(0xffffffffu, ok)) {
-        tc::tc_fence_after();
-        const int ea = m < p.M ? p.ea[m] : kZeroExp;
-#pragma unroll 1
-        for (int cb = 0; cb < EM_BN / 8; ++cb) {
-          uint32_t r[kS][8];
-#pragma unroll
-          for (int l = 0; l < kS; ++l)
-            tc::tmem_ld_32x32b_x8(tmem + lane_base + (uint32_t)(l * EM_BN + cb * 8), r[l]);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int64_t n = n0 + cb * 8 + j;
-            // V = 2^52 sum_L acc_L 2^(-7 L), L = l + 2
-            long long V = 0;
-#pragma unroll
-            for (int l = 0; l < kS; ++l) {
-              const long long a = (long long)__float2int_rn(__uint_as_float(r[l][j]));
-              const int sh = 52 - kBits * (l + 2);
-              V += sh >= 0 ? a * (1ll << sh) : (a >> (-sh));
-            }
-            if (m < p.M && n < p.N) {
-              const int eb = p.eb[n];
-              double val = 0.0;
-              if (ea != kZeroExp && eb != kZeroExp)
-                val = p.alpha * scale2((double)V, ea + eb - 52);
-              double* c = p.C + m * p.ldc + n;
-              if (p.mode == 0) *c = val;
-              else if (p.mode == 1) *c += val;
-              else atomicAdd(c, val);
-            }
-          }
-        }
-      }
+    }
+  } else {
+    const int quad = warp & 3;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    uint32_t lt = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++lt) {
+      const int mt = (int)((u / p.kchunks) % p.m_tiles);
+      const int nt = (int)(u / ((int64_t)p.kchunks * p.m_tiles));
+      // warp-collective tensor-memory loads: reconverge after the spin-wait
+      const bool ok = tc::mbar_wait(acc_full, lt & 1, abort_flag, p.err, p.wait_ns);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc::tc_fence_after();
+      em_epilogue(p, tmem + lane_base, (int64_t)mt * EM_BM + 32 * quad + lane,
+                  (int64_t)nt * EM_BN, EM_EPI_COLS * ((warp - 2) / 4), acc_empty);
     }
   }
   tc::tc_fence_before();
@@ -449,11 +545,15 @@ int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int
       ISDF_CUDA(cudaMemset2DAsync(C, ldc * sizeof(double), 0, N * sizeof(double), M, s));
     p.mode = 2;
   }
+  p.vec = ((uintptr_t)C % 16 == 0 && ldc % 2 == 0) ? 1 : 0;
   const int64_t units = (int64_t)p.m_tiles * p.n_tiles * p.kchunks;
-  ISDF_ARG(units < (1ll << 31), "too many GEMM work units");
+  int dev = 0, nsm = 148;
+  ISDF_CUDA(cudaGetDevice(&dev));
+  ISDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)(units < nsm ? units : nsm);
   ISDF_CUDA(cudaFuncSetAttribute(emgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)EM_SMEM));
-  emgemm_kernel<<<(unsigned)units, EM_THREADS, EM_SMEM, s>>>(maps, p);
+  emgemm_kernel<<<grid, EM_THREADS, EM_SMEM, s>>>(maps, p);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }
