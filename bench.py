@@ -73,7 +73,8 @@ def parse():
                     help="VMC optimisation of the correlator (Sec. II.C) on an H20 chain: "
                          "Metropolis sweeps, then Gauss-Newton iterations on the fixed sample")
     ap.add_argument("--fit-mode", type=int, default=1, choices=[0, 1],
-                    help="the fit's FP64 products: 0 on CUDA cores, 1 emulated on the tensor cores")
+                    help="the FP64 products of the orbitals and the fit: 0 on CUDA cores, "
+                         "1 emulated on the tensor cores")
     ap.add_argument("--emu64", action="store_true",
                     help="the fit on the H50 chain with FP64 on CUDA cores and with the FP64 "
                          "products emulated on the tensor cores, and one emulated GEMM")
@@ -279,8 +280,8 @@ def run_config(args, wlw, world):
             "precision": args.precision,
             "l2": f"inputs larger than L2 (w xi limbs {limbs * 2 * n_mu * n_g / 1e9:.2f} GB)",
             "parallelism": f"replicas{world}",
-            "fit": ("FP64 products emulated on the tensor cores" if getattr(args, "fit_mode", 0)
-                    else "FP64 on CUDA cores"),
+            "fp64_products": ("orbitals and fit: emulated on the tensor cores"
+                              if getattr(args, "fit_mode", 0) else "FP64 on CUDA cores"),
             "value_basis": "W build (stage 1 + stage 2 + operand prep) inside each full-path step"}
 
 

@@ -159,6 +159,14 @@ size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g);
 int isdf_eval_orbitals(const isdf_basis* basis, const double* mo_coef, int n_orb,
                        const double* grid_xyz, int64_t n_g, double* phi, double* dphi,
                        void* ws, size_t ws_bytes, isdf_stream_t stream);
+/* The same with mode 0 (= isdf_eval_orbitals: FP64 GEMMs on CUDA cores) or
+ * mode 1: the four contractions C^T chi as the emulated FP64 products of
+ * isdf_dgemm_emulated (error within (n_bf + 4) 2^-52 2^(e_p + e_g) per value,
+ * 2^e the powers of two above max_f|C_fp| and max_f|chi_f(g)|).  The workspace query takes n_orb for mode 1. */
+size_t isdf_eval_orbitals_workspace_mode(int n_bf, int64_t n_g, int n_orb, int mode);
+int isdf_eval_orbitals_mode(const isdf_basis* basis, const double* mo_coef, int n_orb,
+                            const double* grid_xyz, int64_t n_g, double* phi, double* dphi,
+                            int mode, void* ws, size_t ws_bytes, isdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Interpolation points by weighted pivoted Cholesky (Alg. 1; gradient branch
@@ -235,7 +243,8 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * >= 2^-63 are summed exactly in FP32 per weight (at most 128 inner terms per
  * tensor-core run; longer K is split over CTAs whose results are added with
  * FP64 atomics) and combined exactly in 64-bit integers before one rounding to
- * FP64.  Error within (K + 4) 2^-52 max_k|A_mk| max_k|B_kn| per element.
+ * FP64.  Error within (K + 4) 2^-52 2^(e_m + e_n) per element, 2^e_m the power
+ * of two above max_k|A_mk| and 2^e_n that above max_k|B_kn|.
  * A NaN or Inf in A or B gives undefined values in C.  Asynchronous. */
 size_t isdf_dgemm_emulated_workspace(int64_t M, int64_t N, int64_t K);
 int isdf_dgemm_emulated(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,

@@ -66,6 +66,9 @@ SIGNATURES = {
     "isdf_kernel_launches": (ctypes.c_uint64, []),
     "isdf_eval_orbitals_workspace": (SZ, [INT, I64]),
     "isdf_eval_orbitals": (INT, [ctypes.POINTER(IsdfBasis), P, INT, P, I64, P, P, P, SZ, P]),
+    "isdf_eval_orbitals_workspace_mode": (SZ, [INT, I64, INT, INT]),
+    "isdf_eval_orbitals_mode": (INT, [ctypes.POINTER(IsdfBasis), P, INT, P, I64, P, P, INT, P, SZ,
+                                      P]),
     "isdf_points_workspace": (SZ, [I64, INT]),
     "isdf_points": (INT, [P, P, P, I64, INT, INT, INT, P, ctypes.POINTER(INT), P, SZ, P]),
     "isdf_points_fixed_rank_workspace": (SZ, [I64, INT, INT]),

@@ -79,8 +79,10 @@ def jastrow_from(obj) -> C.IsdfJastrow:
                           getattr(obj, "n_elec", 0))
 
 
-def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz) -> Tuple[torch.Tensor, torch.Tensor]:
-    """phi [n_orb][n_g], dphi [3][n_orb][n_g] (Alg. 2 step 2)."""
+def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz,
+                       mode: int = 0) -> Tuple[torch.Tensor, torch.Tensor]:
+    """phi [n_orb][n_g], dphi [3][n_orb][n_g] (Alg. 2 step 2); mode 1 takes
+    the contractions as FP64 products emulated on the tensor cores."""
     lib = C.load()
     dev = grid_xyz.device
     for t, n, dt in ((center, "center", f64), (exps, "exps", f64), (coefs, "coefs", f64),
@@ -93,10 +95,16 @@ def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz) -> Tuple[
     basis = C.IsdfBasis(n_bf, n_prim, _ptr(center), _ptr(powers), _ptr(exps), _ptr(coefs))
     phi = torch.empty((n_orb, n_g), dtype=f64, device=dev)
     dphi = torch.empty((3, n_orb, n_g), dtype=f64, device=dev)
-    ws = _ws(lib.isdf_eval_orbitals_workspace(n_bf, n_g), dev)
-    C.check("isdf_eval_orbitals", lib.isdf_eval_orbitals(
-        ctypes.byref(basis), _ptr(mo_coef), n_orb, _ptr(grid_xyz), n_g, _ptr(phi), _ptr(dphi),
-        _ptr(ws), ws.numel(), _stream()))
+    if mode == 0:
+        ws = _ws(lib.isdf_eval_orbitals_workspace(n_bf, n_g), dev)
+        C.check("isdf_eval_orbitals", lib.isdf_eval_orbitals(
+            ctypes.byref(basis), _ptr(mo_coef), n_orb, _ptr(grid_xyz), n_g, _ptr(phi),
+            _ptr(dphi), _ptr(ws), ws.numel(), _stream()))
+    else:
+        ws = _ws(lib.isdf_eval_orbitals_workspace_mode(n_bf, n_g, n_orb, int(mode)), dev)
+        C.check("isdf_eval_orbitals_mode", lib.isdf_eval_orbitals_mode(
+            ctypes.byref(basis), _ptr(mo_coef), n_orb, _ptr(grid_xyz), n_g, _ptr(phi),
+            _ptr(dphi), int(mode), _ptr(ws), ws.numel(), _stream()))
     return phi, dphi
 
 

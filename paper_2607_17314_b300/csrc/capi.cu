@@ -23,9 +23,9 @@ void set_error(const char* fmt, ...) {
 }
 
 // implemented in the kernel translation units
-size_t eval_orbitals_ws(int n_bf, int64_t n_g);
+size_t eval_orbitals_ws(int n_bf, int64_t n_g, int mode, int n_orb_max);
 int eval_orbitals(const isdf_basis*, const double*, int, const double*, int64_t, double*, double*,
-                  void*, size_t, cudaStream_t);
+                  int, void*, size_t, cudaStream_t);
 size_t points_ws(int64_t n_g, int n_mu);
 int points(const double*, const double*, const double*, int64_t, int, int, int, int32_t*, int*,
            void*, size_t, cudaStream_t);
@@ -135,12 +135,26 @@ const char* isdf_last_error(void) { return g_err; }
 int isdf_abi_version(void) { return 2; }
 uint64_t isdf_kernel_launches(void) { return g_launches.load(); }
 
-size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g) { return eval_orbitals_ws(n_bf, n_g); }
+size_t isdf_eval_orbitals_workspace(int n_bf, int64_t n_g) {
+  return eval_orbitals_ws(n_bf, n_g, 0, 1);
+}
+
+size_t isdf_eval_orbitals_workspace_mode(int n_bf, int64_t n_g, int n_orb, int mode) {
+  if (mode != 0 && mode != 1) return 0;
+  return eval_orbitals_ws(n_bf, n_g, mode, n_orb > 0 ? n_orb : 1);
+}
+
+int isdf_eval_orbitals_mode(const isdf_basis* basis, const double* mo_coef, int n_orb,
+                            const double* grid_xyz, int64_t n_g, double* phi, double* dphi,
+                            int mode, void* ws, size_t ws_bytes, isdf_stream_t stream) {
+  return eval_orbitals(basis, mo_coef, n_orb, grid_xyz, n_g, phi, dphi, mode, ws, ws_bytes,
+                       (cudaStream_t)stream);
+}
 
 int isdf_eval_orbitals(const isdf_basis* basis, const double* mo_coef, int n_orb,
                        const double* grid_xyz, int64_t n_g, double* phi, double* dphi, void* ws,
                        size_t ws_bytes, isdf_stream_t stream) {
-  return eval_orbitals(basis, mo_coef, n_orb, grid_xyz, n_g, phi, dphi, ws, ws_bytes,
+  return eval_orbitals(basis, mo_coef, n_orb, grid_xyz, n_g, phi, dphi, 0, ws, ws_bytes,
                        (cudaStream_t)stream);
 }
 

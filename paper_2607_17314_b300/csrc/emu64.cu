@@ -11,10 +11,10 @@
 // most 8 digit pairs per level and at most 128 terms, its magnitude stays below
 // 8 * 127^2 * 128 < 2^24, so the tensor core's FP32 accumulation of a level is
 // exact.  The epilogue combines the 8 levels exactly in a 64-bit integer scaled
-// by 2^52 (the two lowest levels keep their bits down to 2^-52 of the scale) and
+// by 2^52 (the lowest level pair keeps its bits down to 2^-52 of the scale) and
 // converts once to FP64.  The dropped pairs (p + q > 9: at most ~2^-53.2 of
-// 2^(e_m + e_n) per term), the truncation below 2^-56 and the two lowest
-// levels' rounding (2 units of 2^-52) bound the error by (K + 4) 2^-52 of
+// 2^(e_m + e_n) per term), the truncation below 2^-56 and the lowest level
+// pair's rounding (1 unit of 2^-52) bound the error by (K + 4) 2^-52 of
 // 2^(e_m + e_n), the size of FP64 rounding over K terms of that magnitude.
 #include <cuda.h>
 #include <cuda_bf16.h>

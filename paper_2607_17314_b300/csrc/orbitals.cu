@@ -51,23 +51,41 @@ __global__ void __launch_bounds__(128) ao_eval_kernel(isdf_basis b, const double
 
 }  // namespace
 
-size_t eval_orbitals_ws(int n_bf, int64_t n_g) {
+size_t em_dgemm_ws(int64_t Mmax, int64_t Nmax, int64_t Kmax);
+int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int64_t a_cs,
+             const double* B, int64_t b_rs, int64_t b_cs, double alpha, bool overwrite,
+             double* C, int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t s);
+
+// mode 1 adds the workspace of the emulated products (n_orb <= the bound given).
+size_t eval_orbitals_ws(int n_bf, int64_t n_g, int mode, int n_orb_max) {
   Carve c(nullptr, 0);
   c.take<double>((size_t)4 * n_bf * n_g);
+  if (mode == 1) c.take<char>(em_dgemm_ws(n_orb_max, n_g, n_bf));
   return c.off;
 }
 
 int eval_orbitals(const isdf_basis* basis, const double* C, int n_orb, const double* grid,
-                  int64_t n_g, double* phi, double* dphi, void* ws, size_t ws_bytes,
+                  int64_t n_g, double* phi, double* dphi, int mode, void* ws, size_t ws_bytes,
                   cudaStream_t s) {
   ISDF_ARG(basis && C && grid && phi && dphi, "null pointer argument");
   ISDF_ARG(n_orb > 0 && n_g > 0 && basis->n_bf > 0 && basis->n_prim > 0, "empty sizes");
+  ISDF_ARG(mode == 0 || mode == 1, "mode must be 0 or 1");
   Carve cv(ws, ws_bytes);
   double* chi = cv.take<double>((size_t)4 * basis->n_bf * n_g);
+  const size_t em_bytes = mode == 1 ? em_dgemm_ws(n_orb, n_g, basis->n_bf) : 0;
+  char* em = mode == 1 ? cv.take<char>(em_bytes) : nullptr;
   ISDF_ARG(ws && cv.ok(), "workspace too small: need %zu bytes", cv.off);
   ao_eval_kernel<<<(unsigned)ceil_div(n_g, 128), 128, 0, s>>>(*basis, grid, n_g, chi);
   ISDF_LAUNCH_CHECK();
   const int64_t nbf = basis->n_bf;
+  if (mode == 1) {
+    // phi^c = C^T chi^c: A(m, k) = C[k][m]
+    for (int c = 0; c < 4; ++c)
+      ISDF_TRY(em_dgemm(n_orb, n_g, nbf, C, 1, n_orb, chi + c * nbf * n_g, n_g, 1, 1.0, true,
+                        c == 0 ? phi : dphi + (int64_t)(c - 1) * n_orb * n_g, n_g, em, em_bytes,
+                        s));
+    return ISDF_OK;
+  }
   Dgemm g;
   g.M = n_orb; g.N = n_g; g.K = nbf;
   g.A = C; g.a_rs = 1; g.a_cs = n_orb; g.a_bs = 0;

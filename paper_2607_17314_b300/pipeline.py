@@ -55,8 +55,8 @@ def run(inp: Inputs, precision: str = "bf16x3", n_orb_x: Optional[int] = None,
         stage_ms: Optional[list] = None, fit_mode: int = 0) -> Dict[str, object]:
     """One pass of the path.  ``events`` (name -> list) collects CUDA event
     pairs around each step; ``stage_ms`` collects the device times of the two
-    W-build stages (tensor-core precisions); ``fit_mode`` 1 runs the fit's
-    FP64 products emulated on the tensor cores."""
+    W-build stages (tensor-core precisions); ``fit_mode`` 1 runs the FP64
+    products of the orbitals and of the fit emulated on the tensor cores."""
     def mark(name):
         if events is None:
             return None
@@ -68,7 +68,7 @@ def run(inp: Inputs, precision: str = "bf16x3", n_orb_x: Optional[int] = None,
     out: Dict[str, object] = {}
     mark("a1")
     phi, dphi = api.isdf_eval_orbitals(inp.center, inp.powers, inp.exps, inp.coefs, inp.mo_coef,
-                                       inp.grid)
+                                       inp.grid, mode=fit_mode)
     mark("a1")
     mark("a2")
     piv = api.isdf_points(phi, dphi, inp.w, inp.n_mu)

@@ -37,10 +37,10 @@ def _cu(a, dt=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(dt).cuda()
 
 
-def _orbitals(api, w):
+def _orbitals(api, w, mode=0):
     b = w.basis
     return api.isdf_eval_orbitals(_cu(b.center), _cu(b.powers, torch.int32), _cu(b.exps),
-                                  _cu(b.coefs), _cu(w.mo_coef), _cu(w.grid_xyz))
+                                  _cu(b.coefs), _cu(w.mo_coef), _cu(w.grid_xyz), mode=mode)
 
 
 def _check_orbitals_sampled(w, phi, dphi, n=4096, seed=1):
@@ -57,6 +57,12 @@ def _check_orbitals_sampled(w, phi, dphi, n=4096, seed=1):
 
 def test_h50_chain_orbitals_pivots_fit(api):
     w = wl.h50_chain()
+    # orbitals with the contractions emulated on the tensor cores (mode 1)
+    phi, dphi = _orbitals(api, w, mode=1)
+    ep, ed = _check_orbitals_sampled(w, phi, dphi)
+    print("H50 orbitals mode 1: relative errors %.2e %.2e" % (ep, ed))
+    assert ep < 1e-12 and ed < 1e-12, (ep, ed)
+    del phi, dphi
     phi, dphi = _orbitals(api, w)
     ep, ed = _check_orbitals_sampled(w, phi, dphi)
     assert ep < 1e-12 and ed < 1e-12, (ep, ed)

@@ -37,13 +37,24 @@ def exact_product(A, B):
     return (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
 
 
+def pow2_above(x):
+    """2^e with e the smallest integer such that x < 2^e (0 where x = 0): the
+    power-of-two scale the emulation takes for a row or column maximum."""
+    x = np.asarray(x, dtype=float)
+    out = np.zeros_like(x)
+    nz = x > 0
+    out[nz] = 2.0 ** (np.floor(np.log2(x[nz])) + 1.0)
+    return out
+
+
 def scale_bound(A, B):
-    """(K + 4) 2^-52 max_k|A_mk| max_k|B_kn|, the emulation's per-element error
-    bound: the dropped digit pairs give at most ~2^-53.2 of the scale per
-    term, the truncated digits 2^-55, and the two lowest levels' rounding
-    in the 64-bit combination at most 2 units of 2^-52."""
+    """(K + 4) 2^-52 2^(e_m + e_n), the emulation's per-element error bound
+    (2^e_m > max_k|A_mk|, 2^e_n > max_k|B_kn|): the dropped digit pairs give at
+    most ~2^-53.2 of the scale per term, the truncated digits 2^-55, and the
+    lowest level pair's rounding in the 64-bit combination 1 unit of 2^-52."""
     K = A.shape[1]
-    return (K + 4) * 2.0 ** -52 * np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
+    return (K + 4) * 2.0 ** -52 * pow2_above(np.abs(A).max(1))[:, None] * \
+        pow2_above(np.abs(B).max(0))[None, :]
 
 
 @pytest.mark.parametrize("M,N,K,spread", [(300, 130, 128, 0.0), (129, 65, 37, 3.0),
@@ -135,3 +146,27 @@ def test_emulated_fit_matches_fp64_fit_on_gpu(api):
         kappa = np.linalg.cond(Gm[c])
         d = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
         assert d < max(1e-10, 64.0 * kappa * EPS), (c, d, kappa)
+
+
+def test_emulated_orbitals_within_bound(api):
+    """Alg. 2 step 2 with the contractions C^T chi emulated (mode 1) on the H6
+    grid: every value within (n_bf + 4) 2^-52 2^(e_p + e_g) of the oracle
+    (2^e_p > max_f|C_fp|, 2^e_g > max_f|chi_f(g)|), plus both sides' FP64
+    rounding of the basis values."""
+    w = wl.h6_chain()
+    b = w.basis
+    phi, dphi = api.isdf_eval_orbitals(cu(b.center), cu(b.powers, torch.int32), cu(b.exps),
+                                       cu(b.coefs), cu(w.mo_coef), cu(w.grid_xyz), mode=1)
+    p_ref, d_ref = orbitals.eval_orbitals(w.basis, w.mo_coef, w.grid_xyz)
+    v, g = orbitals.eval_ao(w.basis, w.grid_xyz)
+    cmax = pow2_above(np.abs(w.mo_coef).max(0))[:, None]
+    nbf = w.mo_coef.shape[0]
+    csum = np.abs(w.mo_coef).T @ np.ones(nbf)
+    for got, ref, ao in [(host(phi), p_ref, v)] + [(host(dphi)[c], d_ref[c], g[c]) for c in range(3)]:
+        amax = np.abs(ao).max(0)[None, :]
+        bound = ((nbf + 4) * 2.0 ** -52 * cmax * pow2_above(amax)
+                 + (nbf + 8) * EPS * csum[:, None] * amax + 4 * EPS * np.abs(ref))
+        err = np.abs(got - ref)
+        ratio = np.where(bound > 0, err / np.where(bound > 0, bound, 1.0), np.where(err > 0, np.inf, 0.0))
+        print("orbital error / bound", float(ratio.max()))
+        assert np.all(ratio <= 1.0), float(ratio.max())
