@@ -134,32 +134,47 @@ __global__ void em_split_rows_kernel(const double* __restrict__ src, int64_t rs,
         *reinterpret_cast<const uint4*>(v[p]);
 }
 
-// Digits of B (K x N) into out [kS][n_pad][k_pad] (k contiguous, i.e. B^T).
-// One thread per (column, 8 consecutive k); consecutive threads take
-// consecutive columns so that the reads along a row of B coalesce.
-__global__ void em_split_cols_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
-                                     int64_t K, int64_t N, const int* __restrict__ e,
-                                     int64_t n_pad, int64_t k_pad,
-                                     __nv_bfloat16* __restrict__ out) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_pad * (k_pad / 8)) return;
-  const int64_t n = t % n_pad, k0 = (t / n_pad) * 8;
+// Digits of B (K x N) into out [kS][n_pad][k_pad] (k contiguous, i.e. B^T),
+// through a shared-memory tile of 64 columns x 64 k per block: the reads run
+// along the rows of B (consecutive threads, consecutive columns) and the
+// writes along the k rows of the output (128 contiguous bytes per digit plane
+// and column).
+constexpr int SC_N = 64, SC_K = 64, SC_LD = SC_K + 8;  // row stride in BF16 (16-byte rows)
+constexpr size_t SC_SMEM = (size_t)kS * SC_N * SC_LD * sizeof(__nv_bfloat16);
+
+__global__ void __launch_bounds__(256) em_split_cols_kernel(
+    const double* __restrict__ src, int64_t rs, int64_t cs, int64_t K, int64_t N,
+    const int* __restrict__ e, int64_t n_pad, int64_t k_pad, __nv_bfloat16* __restrict__ out) {
+  extern __shared__ __align__(16) __nv_bfloat16 sc_tile[];  // [kS][SC_N][SC_LD]
+  auto tile = reinterpret_cast<__nv_bfloat16(*)[SC_N][SC_LD]>(sc_tile);
+  const int64_t n0 = (int64_t)blockIdx.x * SC_N, k0 = (int64_t)blockIdx.y * SC_K;
+  const int nl = threadIdx.x % SC_N, kq = threadIdx.x / SC_N;  // 4 groups of 16 k
+  const int64_t n = n0 + nl;
   const int en = n < N ? e[n] : kZeroExp;
-  __align__(16) __nv_bfloat16 v[kS][8];
+#pragma unroll 4
+  for (int j = 0; j < SC_K / 4; j += 2) {
+    int d0[kS], d1[kS];
+    const int kl = kq * (SC_K / 4) + j;
+    const int64_t k = k0 + kl;
+    const double x0 = (n < N && k < K) ? src[k * rs + n * cs] : 0.0;
+    const double x1 = (n < N && k + 1 < K) ? src[(k + 1) * rs + n * cs] : 0.0;
+    digits_of(x0, en, d0);
+    digits_of(x1, en, d1);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int64_t k = k0 + j;
-    const double x = (n < N && k < K) ? src[k * rs + n * cs] : 0.0;
-    int d[kS];
-    digits_of(x, en, d);
-#pragma unroll
-    for (int p = 0; p < kS; ++p) v[p][j] = __int2bfloat16_rn(d[p]);
+    for (int p = 0; p < kS; ++p)
+      *reinterpret_cast<__nv_bfloat162*>(&tile[p][nl][kl]) =
+          __halves2bfloat162(__int2bfloat16_rn(d0[p]), __int2bfloat16_rn(d1[p]));
   }
+  __syncthreads();
+  // 8 planes x 64 columns x 8 chunks of 16 bytes
   const int64_t plane = n_pad * k_pad;
-#pragma unroll
-  for (int p = 0; p < kS; ++p)
-    *reinterpret_cast<uint4*>(out + p * plane + n * k_pad + k0) =
-        *reinterpret_cast<const uint4*>(v[p]);
+  for (int q = threadIdx.x; q < kS * SC_N * (SC_K / 8); q += blockDim.x) {
+    const int c = q % (SC_K / 8), row = (q / (SC_K / 8)) % SC_N, p = q / (SC_N * (SC_K / 8));
+    const int64_t nn = n0 + row, kk = k0 + c * 8;
+    if (nn < n_pad && kk < k_pad)
+      *reinterpret_cast<uint4*>(out + p * plane + nn * k_pad + kk) =
+          *reinterpret_cast<const uint4*>(&tile[p][row][c * 8]);
+  }
 }
 
 struct EmMaps {
@@ -515,8 +530,10 @@ int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int
   em_split_rows_kernel<<<nblk(Mp * (Kp / 8), 256), 256, 0, s>>>(A, a_rs, a_cs, M, K, w.ea, Mp,
                                                                  Kp, w.a);
   ISDF_LAUNCH_CHECK();
-  em_split_cols_kernel<<<nblk(Np * (Kp / 8), 256), 256, 0, s>>>(B, b_rs, b_cs, K, N, w.eb, Np,
-                                                                 Kp, w.b);
+  ISDF_CUDA(cudaFuncSetAttribute(em_split_cols_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+  em_split_cols_kernel<<<dim3((unsigned)ceil_div(Np, SC_N), (unsigned)ceil_div(Kp, SC_K)), 256,
+                         SC_SMEM, s>>>(B, b_rs, b_cs, K, N, w.eb, Np, Kp, w.b);
   ISDF_LAUNCH_CHECK();
   EmMaps maps;
   memset(&maps, 0, sizeof(maps));
