@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kVmcThreads) slater_kernel(const double* __res
 
 // Shared-memory layout of eloc_kernel (in doubles).
 struct ElocLayout {
-  int pos, drift, gt, coef, nt, acc, red, pair, total;
+  int pos, drift, gt, coef, nt, acc, red, snuc, pair, total;
   __host__ __device__ ElocLayout(int N, int n_nuc, int n_pc, bool terms, bool table) {
     pos = 0;
     drift = pos + 3 * N;
@@ -261,7 +261,8 @@ struct ElocLayout {
     nt = coef + (n_pc > 0 ? n_pc : 1);
     acc = nt + (terms ? 6 * N * n_nuc : 0);
     red = acc + 4 * N * (n_pc + 1);
-    pair = red + 40;
+    snuc = red + 40;
+    pair = snuc + (terms ? 9 * n_nuc : 0);
     total = pair + (terms && table ? 5 * N * N : 0);
   }
 };
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
   double* acc = sm + L.acc;
   double* red = sm + L.red;
   double* pair = sm + L.pair;  // TABLE: [N][N][5] = F0, F1 (dx, dy, dz), F2 of one o
+  double* snuc = sm + L.snuc;  // [n_nuc][9]: sum over all electrons j of A_jI^a
   const int64_t w = blockIdx.x;
   const int set = blockIdx.y;
   // parameters of this set
@@ -393,9 +395,30 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
     const int n_chunks = (n_nuc + nl - 1) / nl;
     unsigned omask = 0;
     for (int k = 0; k < K; ++k) omask |= 1u << J.mno[k][2];
+    if (omask & 1u) {
+      // o = 0: E^0 = 1 has no derivative, so T1 = T2 = 0 and T0[a] is the sum
+      // over all electrons of A_jI^a minus electron i's own term
+      for (int I = threadIdx.x; I < n_nuc; I += blockDim.x) {
+        double S[MAXA + 1];
+#pragma unroll
+        for (int a = 0; a <= MAXA; ++a) S[a] = 0.0;
+        for (int j = 0; j < N; ++j) {
+          const double Aj = nt[6 * (j * n_nuc + I)];
+          double pw = 1.0;
+#pragma unroll
+          for (int a = 0; a <= MAXA; ++a) {
+            S[a] += pw;
+            pw *= Aj;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a <= MAXA; ++a) snuc[9 * I + a] = S[a];
+      }
+      __syncthreads();
+    }
     for (int o = 0; o <= 8; ++o) {
       if (!((omask >> o) & 1u)) continue;
-      if (TABLE) {
+      if (TABLE && o > 0) {
         // pair factors of this o, once per pair instead of once per lane
         __syncthreads();
         for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
@@ -426,7 +449,16 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
           double T0[MAXA + 1], T1x[MAXA + 1], T1y[MAXA + 1], T1z[MAXA + 1], T2[MAXA + 1];
 #pragma unroll
           for (int a = 0; a <= MAXA; ++a) T0[a] = T1x[a] = T1y[a] = T1z[a] = T2[a] = 0.0;
-          if (on && TABLE)
+          if (on && o == 0 && js == 0) {
+            const double Ai = nt[6 * (i * n_nuc + I)];
+            double pw = 1.0;
+#pragma unroll
+            for (int a = 0; a <= MAXA; ++a) {
+              T0[a] = snuc[9 * I + a] - pw;
+              pw *= Ai;
+            }
+          }
+          if (on && TABLE && o > 0)
             for (int j = js; j < N; j += nsl) {
               if (j == i) continue;
               const double* f = pair + 5 * (i * N + j);
@@ -443,7 +475,7 @@ __global__ void __launch_bounds__(kVmcThreads) eloc_kernel(
                 pw *= Aj;
               }
             }
-          if (on && !TABLE)
+          if (on && !TABLE && o > 0)
             for (int j = js; j < N; j += nsl) {
               if (j == i) continue;
               const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
