@@ -790,6 +790,25 @@ def run_vmc(args):
     e1.record()
     torch.cuda.synchronize()
     eloc_ms = e0.elapsed_time(e1)
+    # the warm-up / refinement schedule: each step continues the chains for 10
+    # sweeps, then one Gauss-Newton step; Polyak-Ruppert average of the last 4
+    th_s = torch.as_tensor(theta0.copy()).cuda()
+    torch.cuda.synchronize()
+    e0.record()
+    avg, sched = api.vmc_schedule(B, Cg, n_occ, R, J, Z, th_s, n_warm=4, n_refine=8, window=4,
+                                  sweeps=10, sigma=0.5, generator=gen)
+    e1.record()
+    torch.cuda.synchronize()
+    sched_ms = e0.elapsed_time(e1)
+    R2 = torch.as_tensor(wl.vmc_walkers(xyz, Nw, N, seed=64)).cuda()
+    n2 = torch.randn((args.sweeps, N, Nw, 3), dtype=torch.float64, device="cuda", generator=gen)
+    u2 = torch.rand((args.sweeps, N, Nw), dtype=torch.float64, device="cuda", generator=gen)
+    api.isdf_vmc_sample(B, Cg, n_occ, R2, n2, u2, 0.5)
+    th0 = torch.as_tensor(theta0.copy()).cuda()
+    v_start = float(api.isdf_vmc_objective(
+        api.isdf_vmc_local_energy(B, Cg, n_occ, R2, J, Z, theta=th0, grad=False))[1])
+    v_avg = float(api.isdf_vmc_objective(
+        api.isdf_vmc_local_energy(B, Cg, n_occ, R2, J, Z, theta=avg, grad=False))[1])
     # parity on seeded walkers (oracle inputs from the generator, not the GPU)
     from oracle import vmc as ovmc
     Rs = wl.vmc_walkers(xyz, 4, N, seed=63)
@@ -807,6 +826,10 @@ def run_vmc(args):
             "gn_iteration_ms": ts, "walker_iterations_per_s": Nw / (min(ts) * 1e-3),
             "local_energy_only_ms": eloc_ms, "local_energy_and_jacobian_ms": jac_ms,
             "variance_per_iteration": var, "lambda_per_iteration": lams,
+            "schedule": {"warm_up": 4, "refinement": 8, "polyak_window": 4, "sweeps_per_step": 10,
+                         "ms_per_step": sched_ms / 12,
+                         "variance_per_step": [h[0] for h in sched],
+                         "fresh_sample_variance": {"start": v_start, "polyak_average": v_avg}},
             "oracle": {"walkers": 4, "energy_and_jacobian_s": oracle_s,
                        "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))},
             "oracle_ratio_per_walker": (oracle_s / 4) / (jac_ms * 1e-3 / Nw),

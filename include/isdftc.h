@@ -596,6 +596,11 @@ size_t isdf_vmc_gn_step_workspace(int64_t n_walkers, int n_par);
 /* The objective of Eq. var-loss alone: stats device [4] as isdf_vmc_gn_step.
  * Asynchronous. */
 int isdf_vmc_objective(const double* E, int64_t n_walkers, double* stats, isdf_stream_t stream);
+/* Polyak-Ruppert averaging of the parameters (Sec. II.C: the production
+ * correlator averages the stationary tail of the refinement trajectory):
+ * avg[p] += (theta[p] - avg[p]) / k for the k-th averaged iterate (k >= 1; k = 1
+ * copies theta).  theta, avg: device [n_par].  Asynchronous. */
+int isdf_vmc_polyak(const double* theta, double* avg, int n_par, int64_t k, isdf_stream_t stream);
 int isdf_vmc_gn_step(const double* E, const double* dE, int64_t n_walkers, int n_par,
                      double lambda, double eta, double* theta, double* step, double* stats,
                      void* ws, size_t ws_bytes, isdf_stream_t stream);

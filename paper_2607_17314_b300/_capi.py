@@ -121,6 +121,7 @@ SIGNATURES = {
                               ctypes.c_double, P, P]),
     "isdf_vmc_gn_step_workspace": (SZ, [I64, INT]),
     "isdf_vmc_objective": (INT, [P, I64, P, P]),
+    "isdf_vmc_polyak": (INT, [P, P, INT, I64, P]),
     "isdf_vmc_gn_step": (INT, [P, P, I64, INT, ctypes.c_double, ctypes.c_double, P, P, P, P, SZ,
                                P]),
 }

@@ -508,10 +508,12 @@ def isdf_vmc_objective(E):
 
 
 class VmcOptimizer:
-    """Gauss-Newton iterations of Eq. gn on a fixed sample (reference-variance
-    protocol) with an adaptive Tikhonov shift: a step is kept only when the
-    clipped variance at the new theta is lower (then lam /= 3), otherwise
-    theta stays and lam *= 10.  theta (device [P]) is updated in place."""
+    """Gauss-Newton iterations of Eq. gn (reference-variance protocol) with an
+    adaptive Tikhonov shift: a step is kept only when the clipped variance at
+    the new theta, on the same walkers, is lower than at the current theta
+    (then lam /= 3); otherwise theta stays and lam *= 10.  theta (device [P])
+    is updated in place; the walkers may be moved between steps (a fresh
+    sample of |Phi_0|^2 per step)."""
 
     def __init__(self, basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges,
                  theta, lam: float = 1e-3, eta: float = 0.5, fd_step: float = 1e-5,
@@ -523,20 +525,62 @@ class VmcOptimizer:
         self.var = float(isdf_vmc_objective(E)[1])
 
     def step(self):
-        """One iteration; returns (variance, lam, accepted)."""
+        """One iteration on the current walkers; returns (variance, lam, accepted)."""
         E, dE = isdf_vmc_local_energy(*self.args, self.theta, self.h)
         trial = self.theta.clone()
-        isdf_vmc_gn_step(E, dE, self.lam, self.eta, theta=trial)
+        _, stats = isdf_vmc_gn_step(E, dE, self.lam, self.eta, theta=trial)
+        cur = float(stats[1])
         Et = isdf_vmc_local_energy(*self.args, trial, self.h, grad=False)
         vt = float(isdf_vmc_objective(Et)[1])
-        ok = vt < self.var
+        ok = vt < cur
         if ok:
             self.theta.copy_(trial)
             self.var = vt
             self.lam = max(self.lam / 3.0, self.lam_min)
         else:
+            self.var = cur
             self.lam = min(self.lam * 10.0, self.lam_max)
         return self.var, self.lam, ok
+
+
+def isdf_vmc_polyak(theta, avg, k: int):
+    """avg += (theta - avg) / k in place (the k-th Polyak-Ruppert iterate)."""
+    lib = C.load()
+    _req(theta, f64, "theta"); _req(avg, f64, "avg")
+    C.check("isdf_vmc_polyak", lib.isdf_vmc_polyak(_ptr(theta), _ptr(avg), theta.numel(), int(k),
+                                                   _stream()))
+    return avg
+
+
+def vmc_schedule(basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges, theta,
+                 n_warm: int, n_refine: int, window: int, sweeps: int, sigma: float,
+                 generator=None, **kw):
+    """A warm-up / refinement run of the reference-variance optimisation
+    (Sec. II.C): every step continues the walkers' Metropolis chains on
+    |Phi_0|^2 for `sweeps` sweeps (random numbers drawn on the device from
+    `generator`), then takes one VmcOptimizer step on them; the production
+    parameters are the Polyak-Ruppert average of theta over the last `window`
+    refinement steps.  theta is updated in place; returns (theta_avg, history
+    of (variance, lam, accepted, acceptance ratio))."""
+    if not 1 <= window <= n_refine:
+        raise ValueError("need 1 <= window <= n_refine")
+    N = 2 * n_occ
+    n_w = walkers.shape[0]
+    opt = VmcOptimizer(basis, mo_coef, n_occ, walkers, jastrow, charges, theta, **kw)
+    avg = torch.empty_like(theta)
+    hist = []
+    for s in range(n_warm + n_refine):
+        normals = torch.randn((sweeps, N, n_w, 3), dtype=f64, device=walkers.device,
+                              generator=generator)
+        uniforms = torch.rand((sweeps, N, n_w), dtype=f64, device=walkers.device,
+                              generator=generator)
+        acc = isdf_vmc_sample(basis, mo_coef, n_occ, walkers, normals, uniforms, sigma)
+        var, lam, ok = opt.step()
+        hist.append((var, lam, ok, acc / float(sweeps * N * n_w)))
+        k = s - (n_warm + n_refine - window) + 1
+        if k >= 1:
+            isdf_vmc_polyak(theta, avg, k)
+    return avg, hist
 
 
 def vmc_optimize(basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJastrow, charges, theta,

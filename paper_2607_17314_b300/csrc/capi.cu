@@ -92,6 +92,7 @@ int vmc_sample(const isdf_basis*, const double*, int, int, double*, int64_t, con
                const double*, int, double, int64_t*, cudaStream_t);
 size_t vmc_gn_step_ws(int64_t, int);
 int vmc_objective(const double*, int64_t, double*, cudaStream_t);
+int vmc_polyak(const double*, double*, int, int64_t, cudaStream_t);
 int vmc_gn_step(const double*, const double*, int64_t, int, double, double, double*, double*,
                 double*, void*, size_t, cudaStream_t);
 
@@ -441,6 +442,11 @@ int isdf_vmc_sample(const isdf_basis* basis, const double* mo_coef, int n_orb, i
 
 int isdf_vmc_objective(const double* E, int64_t n_walkers, double* stats, isdf_stream_t stream) {
   return vmc_objective(E, n_walkers, stats, (cudaStream_t)stream);
+}
+
+int isdf_vmc_polyak(const double* theta, double* avg, int n_par, int64_t k,
+                    isdf_stream_t stream) {
+  return vmc_polyak(theta, avg, n_par, k, (cudaStream_t)stream);
 }
 
 size_t isdf_vmc_gn_step_workspace(int64_t n_walkers, int n_par) {

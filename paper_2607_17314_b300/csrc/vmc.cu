@@ -798,6 +798,13 @@ __global__ void gn_finish_kernel(const double* __restrict__ x, int P, double eta
   if (theta && *info == 0) theta[p] += st;
 }
 
+// Polyak-Ruppert running mean: avg += (theta - avg) / k (k = 1, 2, ...).
+__global__ void polyak_kernel(const double* __restrict__ theta, double* __restrict__ avg, int P,
+                              double inv_k) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) avg[p] += (theta[p] - avg[p]) * inv_k;
+}
+
 struct ElocWs {
   double *ao, *orb, *drift, *V, *E_set;
   size_t off;
@@ -931,6 +938,14 @@ int vmc_objective(const double* E, int64_t n_w, double* stats, cudaStream_t s) {
   ISDF_ARG(n_w >= 2, "need n_walkers >= 2");
   gn_stats_kernel<<<1, 1024, 0, s>>>(E, nullptr, n_w, 0, 0.0, nullptr, nullptr, nullptr, nullptr,
                                      stats);
+  ISDF_LAUNCH_CHECK();
+  return ISDF_OK;
+}
+
+int vmc_polyak(const double* theta, double* avg, int P, int64_t k, cudaStream_t s) {
+  ISDF_ARG(theta && avg, "null pointer argument");
+  ISDF_ARG(P >= 1 && k >= 1, "need n_par >= 1 and k >= 1");
+  polyak_kernel<<<(unsigned)ceil_div(P, 128), 128, 0, s>>>(theta, avg, P, 1.0 / (double)k);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }

@@ -218,3 +218,48 @@ def test_optimisation_lowers_the_sampled_variance(api):
     # the final theta reproduces the final variance
     E = api.isdf_vmc_local_energy(B, _cu(C), n_occ, Rg, J, Z, theta=theta, grad=False)
     assert float(api.isdf_vmc_objective(E)[1]) == var[-1]
+
+
+def test_polyak_running_mean(api):
+    rng = np.random.default_rng(61)
+    xs = rng.standard_normal((6, 11))
+    avg = _cu(np.zeros(11))
+    for k, x in enumerate(xs, 1):
+        api.isdf_vmc_polyak(_cu(x), avg, k)
+    assert np.allclose(avg.cpu().numpy(), xs.mean(axis=0), rtol=1e-14, atol=1e-15)
+
+
+def test_schedule_with_fresh_samples_and_averaging(api):
+    """Warm-up and refinement steps, each on a continued Metropolis sample of
+    |Phi_0|^2, then the Polyak-Ruppert average of the refinement tail: the
+    averaged correlator has a lower clipped variance than the starting one on
+    a fresh, independent sample."""
+    xyz, basis, C, n_occ, jas, Z = _system(n_atom=6, n_occ=3, n_terms=10, scale=0.2)
+    N, Nw = 2 * n_occ, 512
+    B = _basis(basis)
+    Cg = _cu(C)
+    J = api.jastrow_from(jas)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(71)
+    Rg = _cu(wl.vmc_walkers(xyz, Nw, N, seed=72))
+    nrm = torch.randn((20, N, Nw, 3), dtype=torch.float64, device="cuda", generator=gen)
+    uni = torch.rand((20, N, Nw), dtype=torch.float64, device="cuda", generator=gen)
+    api.isdf_vmc_sample(B, Cg, n_occ, Rg, nrm, uni, 0.5)          # burn-in
+    theta0 = _cu(adjoint.get_theta(jas))
+    theta = theta0.clone()
+    avg, hist = api.vmc_schedule(B, Cg, n_occ, Rg, J, Z, theta, n_warm=4, n_refine=6, window=4,
+                                 sweeps=4, sigma=0.5, generator=gen)
+    print("schedule", [(round(h[0], 4), h[1], h[2], round(h[3], 3)) for h in hist])
+    assert len(hist) == 10 and all(np.isfinite(h[0]) and 0.2 < h[3] < 0.95 for h in hist)
+    assert torch.all(torch.isfinite(avg))
+    # an independent sample
+    R2 = _cu(wl.vmc_walkers(xyz, Nw, N, seed=73))
+    nrm = torch.randn((30, N, Nw, 3), dtype=torch.float64, device="cuda", generator=gen)
+    uni = torch.rand((30, N, Nw), dtype=torch.float64, device="cuda", generator=gen)
+    api.isdf_vmc_sample(B, Cg, n_occ, R2, nrm, uni, 0.5)
+    v0 = float(api.isdf_vmc_objective(api.isdf_vmc_local_energy(B, Cg, n_occ, R2, J, Z, theta=theta0,
+                                                                grad=False))[1])
+    v1 = float(api.isdf_vmc_objective(api.isdf_vmc_local_energy(B, Cg, n_occ, R2, J, Z, theta=avg,
+                                                                grad=False))[1])
+    print("clipped variance on a fresh sample: start", v0, "averaged", v1)
+    assert v1 < v0
