@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(AdjArgs<T> a, const __gri
 
 // Pair terms of the outer rows [a.g_begin, a.g_end) with M read from the slab
 // the tensor-core GEMM wrote: slab[c][g - a.g_begin][h] (FP64, c = x, y, z, sq).
-__global__ void __launch_bounds__(256) adj_pair_slab_kernel(AdjArgs<float> a,
+__global__ void __launch_bounds__(256, 2) adj_pair_slab_kernel(AdjArgs<float> a,
                                                             const double* __restrict__ slab,
                                                             const __grid_constant__ isdf_jastrow J) {
   __shared__ double red[8][2 + NGRP * 5];
