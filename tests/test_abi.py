@@ -296,3 +296,40 @@ def test_vmc_argument_checks(lib):
                                 None) == C.ISDF_E_ARG
     assert lib.isdf_vmc_gn_step(fake, fake, 100, 3, 0.0, 1.0, None, fake, fake, fake, gw - 1,
                                 None) == C.ISDF_E_ARG
+
+
+def test_emulated_products_argument_checks(lib):
+    """isdf_dgemm_emulated, the mode workspaces and isdf_vmc_polyak reject bad
+    arguments before any device work."""
+    from paper_2607_17314_b300 import _capi as C
+    fake = ctypes.c_void_p(256)
+    ws = lib.isdf_dgemm_emulated_workspace(300, 200, 128)
+    # 8 digit planes of both operands (BF16) at the padded sizes
+    assert ws >= 16 * (384 * 128 + 256 * 128)
+    assert lib.isdf_dgemm_emulated(0, 5, 5, None, 5, None, 5, 1.0, 0.0, None, 5, None, 0,
+                                   None) == C.ISDF_OK  # empty product: nothing to do
+    for beta in (0.5, -1.0):
+        assert lib.isdf_dgemm_emulated(4, 4, 4, fake, 4, fake, 4, 1.0, beta, fake, 4, fake, ws,
+                                       None) == C.ISDF_E_ARG
+    assert lib.isdf_dgemm_emulated(4, 4, 4, fake, 4, fake, 4, float("nan"), 0.0, fake, 4, fake,
+                                   ws, None) == C.ISDF_E_ARG
+    assert lib.isdf_dgemm_emulated(4, 4, 8, fake, 4, fake, 4, 1.0, 0.0, fake, 4, fake, ws,
+                                   None) == C.ISDF_E_ARG  # lda < K
+    assert lib.isdf_dgemm_emulated(4, 4, 4, fake, 4, fake, 4, 1.0, 0.0, fake, 4, fake, 16,
+                                   None) == C.ISDF_E_ARG  # workspace too small
+    assert b"workspace too small" in lib.isdf_last_error()
+    assert lib.isdf_fit_workspace_mode(1000, 40, 100, 2) == 0
+    assert lib.isdf_fit_workspace_mode(1000, 40, 100, 1) > lib.isdf_fit_workspace_mode(1000, 40,
+                                                                                        100, 0)
+    assert lib.isdf_fit_workspace_mode(1000, 40, 100, 0) == lib.isdf_fit_workspace(1000, 40, 100)
+    assert lib.isdf_eval_orbitals_workspace_mode(50, 1000, 40, 3) == 0
+    assert lib.isdf_eval_orbitals_workspace_mode(50, 1000, 40, 0) == \
+        lib.isdf_eval_orbitals_workspace(50, 1000)
+    opt = C.IsdfOptions()
+    opt.fit_mode = 2
+    st = lib.isdf_fit(fake, fake, 100, 4, fake, 8, fake, fake, None, ctypes.byref(opt), fake,
+                      1 << 30, None)
+    assert st == C.ISDF_E_ARG and b"fit_mode" in lib.isdf_last_error()
+    assert lib.isdf_vmc_polyak(fake, fake, 0, 1, None) == C.ISDF_E_ARG
+    assert lib.isdf_vmc_polyak(fake, fake, 4, 0, None) == C.ISDF_E_ARG
+    assert lib.isdf_vmc_objective(fake, 1, fake, None) == C.ISDF_E_ARG
