@@ -263,3 +263,22 @@ def test_schedule_with_fresh_samples_and_averaging(api):
                                                                 grad=False))[1])
     print("clipped variance on a fresh sample: start", v0, "averaged", v1)
     assert v1 < v0
+
+
+def test_local_energy_of_a_gaussian_pair_is_closed_form(api):
+    """The GPU kernels against the closed form of E_loc for one doubly
+    occupied s-Gaussian exp(-a r^2) at a Z = 2 nucleus and no correlator:
+    E_loc = -1/2 sum_i (4 a^2 r_i^2 - 6 a) - Z sum_i 1/r_i + 1/r_12."""
+    a, Z = 0.7, 2.0
+    basis = wl.Basis(center=np.zeros((1, 3)), powers=np.zeros((1, 3), np.int32),
+                     exps=np.array([[a]]), coefs=np.array([[1.0]]), atom=np.zeros(1, np.int32))
+    jas = wl.Jastrow(nuc_xyz=np.zeros((1, 3)), nuc_type=np.zeros(1, np.int32),
+                     mno=np.zeros((0, 3), np.int32), coef=np.zeros((1, 0)), b=np.ones(1), d=1.0,
+                     cusp=False)
+    R = np.random.default_rng(23).normal(size=(37, 2, 3)) * 1.3
+    E = api.isdf_vmc_local_energy(_basis(basis), _cu(np.ones((1, 1))), 1, _cu(R),
+                                  api.jastrow_from(jas), [Z], grad=False).cpu().numpy()
+    r = np.linalg.norm(R, axis=2)
+    want = (-0.5 * np.sum(4 * a * a * r * r - 6 * a, axis=1) - Z * np.sum(1.0 / r, axis=1)
+            + 1.0 / np.linalg.norm(R[:, 0] - R[:, 1], axis=1))
+    assert np.max(np.abs(E - want)) < 1e-12 * _scale(want), (E, want)

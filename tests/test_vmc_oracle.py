@@ -145,3 +145,36 @@ def test_gauss_newton_step_is_least_squares_on_a_linear_model():
     Bc = B - B.mean(axis=1)[:, None]
     ref, *_ = np.linalg.lstsq(Bc.T, -(a - a.mean()), rcond=None)
     assert np.allclose(step, ref, rtol=1e-10, atol=1e-12)
+
+
+def gaussian_helium_like(a=0.7, Z=2.0):
+    """One s-Gaussian exp(-a r^2) at the origin, doubly occupied, no
+    correlator (cusp off, no terms): Phi_0 = phi(r_1) phi(r_2)."""
+    basis = wl.Basis(center=np.zeros((1, 3)), powers=np.zeros((1, 3), np.int32),
+                     exps=np.array([[a]]), coefs=np.array([[1.0]]), atom=np.zeros(1, np.int32))
+    jas = wl.Jastrow(nuc_xyz=np.zeros((1, 3)), nuc_type=np.zeros(1, np.int32),
+                     mno=np.zeros((0, 3), np.int32), coef=np.zeros((1, 0)), b=np.ones(1), d=1.0,
+                     cusp=False)
+    return basis, np.ones((1, 1)), jas, np.zeros((1, 3)), np.array([Z])
+
+
+def gaussian_helium_like_eloc(R, a, Z):
+    """Closed form: lap exp(-a r^2) / exp(-a r^2) = 4 a^2 r^2 - 6 a, so
+    E_loc = -1/2 sum_i (4 a^2 r_i^2 - 6 a) - Z sum_i 1/r_i + 1/r_12."""
+    r = np.linalg.norm(R, axis=1)
+    return (-0.5 * np.sum(4 * a * a * r * r - 6 * a) - Z * np.sum(1.0 / r)
+            + 1.0 / np.linalg.norm(R[0] - R[1]))
+
+
+def test_local_energy_of_a_gaussian_pair_is_closed_form():
+    """Eq. Eloc for Psi_T = Phi_0 (tau = 0) with Phi_0 = phi(r_1) phi(r_2),
+    phi a single Gaussian: the orbital Laplacian, the drift and the Coulomb
+    terms against the closed form, for several configurations."""
+    a, Z = 0.7, 2.0
+    basis, C, jas, nuc, charges = gaussian_helium_like(a, Z)
+    rng = np.random.default_rng(17)
+    for _ in range(6):
+        R = rng.normal(size=(2, 3)) * 1.3
+        got = vmc.local_energy(R, basis, C, jas, nuc, charges)
+        want = gaussian_helium_like_eloc(R, a, Z)
+        assert abs(got - want) < 1e-11 * max(1.0, abs(want)), (got, want)
