@@ -178,3 +178,34 @@ def test_local_energy_of_a_gaussian_pair_is_closed_form():
         got = vmc.local_energy(R, basis, C, jas, nuc, charges)
         want = gaussian_helium_like_eloc(R, a, Z)
         assert abs(got - want) < 1e-11 * max(1.0, abs(want)), (got, want)
+
+
+def test_clipped_residual_jacobian_matches_finite_differences():
+    """Eq. var-loss with clipping active on both sides: for E(theta) = a + B^T theta
+    the central differences of the clipped residuals r = E~ - mean(E~) and of the
+    clipped variance equal residual_jacobian and 2/(N_w - 1) dr r.  The bounds
+    m +- 5 dev move with theta, so the clipped entries follow their bound."""
+    rng = np.random.default_rng(8)
+    Nw, P = 300, 3
+    a = rng.normal(size=Nw)
+    a[:5] = [9.0, -11.0, 8.5, -7.9, 12.0]   # beyond m +- 5 dev
+    B = rng.normal(size=(P, Nw)) * 0.3
+    th = rng.normal(size=P) * 0.1
+
+    def resid(t):
+        Ec, mean, var = vmc.clipped_objective(a + B.T @ t)
+        return Ec - mean, var
+
+    E = a + B.T @ th
+    Ec, mean, var = vmc.clipped_objective(E)
+    assert np.sum(Ec != E) >= 4  # clipping is active
+    dr = vmc.residual_jacobian(E, B)
+    h = 1e-6
+    for p in range(P):
+        e = np.zeros(P)
+        e[p] = h
+        rp, vp = resid(th + e)
+        rm, vm = resid(th - e)
+        assert np.max(np.abs((rp - rm) / (2 * h) - dr[p])) < 1e-7
+        grad = 2.0 / (Nw - 1) * dr[p] @ (Ec - mean)
+        assert abs((vp - vm) / (2 * h) - grad) < 1e-7 * max(1.0, abs(grad))
