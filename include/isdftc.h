@@ -241,9 +241,9 @@ int isdf_fit(const double* phi, const double* dphi, int64_t n_g, int n_orb,
  * Each row of A and column of B is scaled by a power of two and cut into eight
  * signed 7-bit digits held exactly in BF16; the 36 digit products of weight
  * >= 2^-63 are summed exactly in FP32 per weight (at most 128 inner terms per
- * tensor-core run; longer K is split over CTAs whose results are added with
- * FP64 atomics) and combined exactly in 64-bit integers before one rounding to
- * FP64.  Error within (K + 4) 2^-52 2^(e_m + e_n) per element, 2^e_m the power
+ * tensor-core run) and combined exactly in 64-bit integers, up to 8 runs of one
+ * output tile in turn, before one rounding to FP64; longer K is split over CTAs
+ * whose results are added with FP64 atomics.  Error within (K + 4) 2^-52 2^(e_m + e_n) per element, 2^e_m the power
  * of two above max_k|A_mk| and 2^e_n that above max_k|B_kn|.
  * A NaN or Inf in A or B gives undefined values in C.  Asynchronous. */
 size_t isdf_dgemm_emulated_workspace(int64_t M, int64_t N, int64_t K);

@@ -190,6 +190,7 @@ struct EmParams {
   double* C;
   int64_t ldc;
   double alpha;
+  int kin;   // K chunks of <= 128 that one work unit takes in turn (V summed in 64 bits)
   int mode;  // 0: C = alpha A B; 1: C += alpha A B; 2: the same with atomics (K split)
   int vec;   // C rows 16-byte aligned: 16-byte stores
   int* err;
@@ -226,40 +227,50 @@ __device__ __forceinline__ double i64_scaled(long long V, int E, bool negate) {
 //   V = 2^52 sum_L acc_L 2^(-7 L),  L = 2 .. 9,
 // formed from the level pairs P = acc_L 2^7 + acc_(L+1), exact in 32 bits
 // (|acc_L| <= (L - 1) 127^2 128, so |P| < 2^31), then four 64-bit terms
-// (the lowest pair keeps its bits down to 2^-52); then the scale
-// 2^(e_m + e_n - 52) and alpha.  The level pairs are taken out of tensor
-// memory first and acc_empty is signalled, so that the next tile's products
-// run while this tile's outputs are formed and stored.  mode 0 stores, 1 adds,
-// 2 adds atomically; each thread writes 8 consecutive columns of its row
-// (64 bytes) per block.
-__device__ __forceinline__ void em_epilogue(const EmParams& p, uint32_t taddr, int64_t m,
-                                            int64_t n0, int c0, uint64_t* acc_empty) {
-  constexpr int NB = EM_EPI_COLS / 8;
-  int P[NB][8][kS / 2];
+// (the lowest pair keeps its bits down to 2^-52).  em_drain adds V of one K
+// chunk to the thread's running sums (every chunk has the same row and column
+// scales, so the sum is exact; |V| < 2^59.1 per chunk keeps up to 8 chunks in
+// 64 bits) and signals acc_empty, so that the next products run while the
+// outputs are formed and stored; em_store applies the scale 2^(e_m + e_n - 52)
+// and alpha.  mode 0 stores, 1 adds, 2 adds atomically; each thread writes 8
+// consecutive columns of its row (64 bytes) per block.
+constexpr int EM_NB = EM_EPI_COLS / 8;
+
+__device__ __forceinline__ void em_drain(uint32_t taddr, int c0, bool first,
+                                         long long (&Vs)[EM_NB][8], uint64_t* acc_empty) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
+  for (int b = 0; b < EM_NB; ++b) {
     uint32_t r[kS][8];
 #pragma unroll
     for (int l = 0; l < kS; ++l)
       tc::tmem_ld_32x32b_x8(taddr + (uint32_t)(l * EM_BN + c0 + b * 8), r[l]);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < 8; ++j) {
+      int P[kS / 2];
 #pragma unroll
       for (int h = 0; h < kS / 2; ++h)
-        P[b][j][h] = __float2int_rn(__uint_as_float(r[2 * h][j])) * (1 << kBits) +
-                     __float2int_rn(__uint_as_float(r[2 * h + 1][j]));
+        P[h] = __float2int_rn(__uint_as_float(r[2 * h][j])) * (1 << kBits) +
+               __float2int_rn(__uint_as_float(r[2 * h + 1][j]));
+      // pair h holds levels 2h + 2, 2h + 3: weight 2^(52 - 7 (2h + 3))
+      const long long V = (long long)P[0] * (1ll << 31) + (long long)P[1] * (1ll << 17) +
+                          (long long)P[2] * (1ll << 3) + (long long)(P[3] >> 11);
+      Vs[b][j] = first ? V : Vs[b][j] + V;
+    }
   }
-  // the accumulators are free for the next tile
+  // the accumulators are free for the next products
   __syncwarp();
   tc::tc_fence_before();
   tc::mbar_arrive(acc_empty);
+}
 
+__device__ __forceinline__ void em_store(const EmParams& p, int64_t m, int64_t n0, int c0,
+                                         const long long (&Vs)[EM_NB][8]) {
   const int ea = m < p.M ? p.ea[m] : kZeroExp;
   const bool unit_alpha = p.alpha == 1.0 || p.alpha == -1.0;
   const bool neg = p.alpha < 0.0;
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
+  for (int b = 0; b < EM_NB; ++b) {
     const int64_t nb = n0 + c0 + b * 8;
     if (m >= p.M || nb >= p.N) continue;
     int ebv[8];
@@ -275,13 +286,9 @@ __device__ __forceinline__ void em_epilogue(const EmParams& p, uint32_t taddr, i
     double v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      // pair h holds levels 2h + 2, 2h + 3: weight 2^(52 - 7 (2h + 3))
-      const long long V = (long long)P[b][j][0] * (1ll << 31) +
-                          (long long)P[b][j][1] * (1ll << 17) +
-                          (long long)P[b][j][2] * (1ll << 3) + (long long)(P[b][j][3] >> 11);
       double x = 0.0;
       if (ea != kZeroExp && ebv[j] != kZeroExp) {
-        x = i64_scaled(V, ea + ebv[j] - 52, unit_alpha && neg);
+        x = i64_scaled(Vs[b][j], ea + ebv[j] - 52, unit_alpha && neg);
         if (!unit_alpha) x *= p.alpha;
       }
       v[j] = x;
@@ -361,8 +368,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const int kc = (int)(u % p.kchunks);
         const int mt = (int)((u / p.kchunks) % p.m_tiles);
         const int nt = (int)(u / ((int64_t)p.kchunks * p.m_tiles));
-        const int64_t kt0 = (int64_t)kc * KT;
-        const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
+        const int64_t kt0 = (int64_t)kc * p.kin * KT;
+        const int64_t kt1 = kt0 + p.kin * KT < p.k_tiles ? kt0 + p.kin * KT : p.k_tiles;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
           const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
           if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, p.err, p.wait_ns)) {
@@ -385,11 +392,16 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       constexpr uint32_t idesc = tc::idesc_f16(EM_BM, EM_BN, 1);
       uint32_t it = 0, lt = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++lt) {
-        const int kc = (int)(u % p.kchunks);
-        const int64_t kt0 = (int64_t)kc * KT;
-        const int64_t kt1 = kt0 + KT < p.k_tiles ? kt0 + KT : p.k_tiles;
-        if (!tc::mbar_wait(acc_empty, (lt & 1) ^ 1, abort_flag, p.err, p.wait_ns)) break;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+       const int kc = (int)(u % p.kchunks);
+       const int64_t ku = (int64_t)kc * p.kin * KT;
+       const int64_t ku1 = ku + p.kin * KT < p.k_tiles ? ku + p.kin * KT : p.k_tiles;
+       for (int64_t kt0 = ku; kt0 < ku1 && ok; kt0 += KT, ++lt) {
+        const int64_t kt1 = kt0 + KT < ku1 ? kt0 + KT : ku1;
+        if (!tc::mbar_wait(acc_empty, (lt & 1) ^ 1, abort_flag, p.err, p.wait_ns)) {
+          ok = false;
+          break;
+        }
         tc::tc_fence_after();
         for (int64_t kt = kt0; kt < kt1; ++kt, ++it) {
           const uint32_t s = it % EM_STAGES, ph = (it / EM_STAGES) & 1;
@@ -416,21 +428,34 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           tc::umma_commit(&empty[s]);
         }
         if (ok) tc::umma_commit(acc_full);
+       }
       }
     }
   } else {
     const int quad = warp & 3;
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    const int c0 = EM_EPI_COLS * ((warp - 2) / 4);
     uint32_t lt = 0;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++lt) {
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const int kc = (int)(u % p.kchunks);
       const int mt = (int)((u / p.kchunks) % p.m_tiles);
       const int nt = (int)(u / ((int64_t)p.kchunks * p.m_tiles));
-      // warp-collective tensor-memory loads: reconverge after the spin-wait
-      const bool ok = tc::mbar_wait(acc_full, lt & 1, abort_flag, p.err, p.wait_ns);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      tc::tc_fence_after();
-      em_epilogue(p, tmem + lane_base, (int64_t)mt * EM_BM + 32 * quad + lane,
-                  (int64_t)nt * EM_BN, EM_EPI_COLS * ((warp - 2) / 4), acc_empty);
+      const int64_t ku = (int64_t)kc * p.kin * KT;
+      const int64_t ku1 = ku + p.kin * KT < p.k_tiles ? ku + p.kin * KT : p.k_tiles;
+      long long Vs[EM_NB][8];
+      for (int64_t kt0 = ku; kt0 < ku1; kt0 += KT, ++lt) {
+        // warp-collective tensor-memory loads: reconverge after the spin-wait
+        const bool got = tc::mbar_wait(acc_full, lt & 1, abort_flag, p.err, p.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        em_drain(tmem + lane_base, c0, kt0 == ku, Vs, acc_empty);
+      }
+      if (!ok) break;
+      em_store(p, (int64_t)mt * EM_BM + 32 * quad + lane, (int64_t)nt * EM_BN, c0, Vs);
     }
   }
   tc::tc_fence_before();
@@ -547,7 +572,11 @@ int em_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t a_rs, int
   p.k_tiles = Kp / EM_BK;
   p.m_tiles = (int)(Mp / EM_BM);
   p.n_tiles = (int)(Np / EM_BN);
-  p.kchunks = (int)ceil_div(Kp, EM_KCHUNK);
+  // K chunks of <= 128 run in turn in one work unit (exact 64-bit sums) up to 8
+  // of them; longer K is split over work units added with FP64 atomics
+  const int kch = (int)ceil_div(Kp, EM_KCHUNK);
+  p.kin = kch <= 8 ? kch : 1;
+  p.kchunks = kch <= 8 ? 1 : kch;
   p.ea = w.ea;
   p.eb = w.eb;
   p.C = C;

@@ -58,11 +58,14 @@ def scale_bound(A, B):
 
 
 @pytest.mark.parametrize("M,N,K,spread", [(300, 130, 128, 0.0), (129, 65, 37, 3.0),
-                                          (200, 257, 300, 6.0), (7, 3, 1, 0.0)])
+                                          (200, 257, 300, 6.0), (7, 3, 1, 0.0),
+                                          (150, 70, 1100, 2.0)])
 def test_emulated_product_within_bound(api, M, N, K, spread):
-    """Ragged M, N (not multiples of the 128 x 64 tiles), K within one
-    tensor-core run and K split over three runs (atomics), rows and columns of
-    wide dynamic range, a zero row, a zero column and mixed signs."""
+    """Ragged M, N (not multiples of the 128 x 64 tiles); K within one
+    tensor-core run, K over three runs summed in 64-bit integers in one work
+    unit, and K = 1100 (nine runs) split over work units added with FP64
+    atomics; rows and columns of wide dynamic range, a zero row, a zero column
+    and mixed signs."""
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K)) * 10.0 ** rng.uniform(-spread, spread, (M, K))
     B = rng.standard_normal((K, N)) * 10.0 ** rng.uniform(-spread, spread, (K, N))
