@@ -11,8 +11,8 @@
 // most 8 digit pairs per level and at most 128 terms, its magnitude stays below
 // 8 * 127^2 * 128 < 2^24, so the tensor core's FP32 accumulation of a level is
 // exact.  The epilogue combines the 8 levels exactly in a 64-bit integer scaled
-// by 2^52 (the lowest level pair keeps its bits down to 2^-52 of the scale) and
-// converts once to FP64.  The dropped pairs (p + q > 9: at most ~2^-53.2 of
+// by 2^52 (the lowest level pair keeps its bits down to 2^-52 of the scale),
+// sums the runs of one output tile in that integer and converts once to FP64.  The dropped pairs (p + q > 9: at most ~2^-53.2 of
 // 2^(e_m + e_n) per term), the truncation below 2^-56 and the lowest level
 // pair's rounding (1 unit of 2^-52) bound the error by (K + 4) 2^-52 of
 // 2^(e_m + e_n), the size of FP64 rounding over K terms of that magnitude.
@@ -318,15 +318,17 @@ __device__ __forceinline__ void em_store(const EmParams& p, int64_t m, int64_t n
   }
 }
 
-// Persistent: CTA b takes the work units b, b + gridDim.x, ... (unit = K chunk
+// Persistent: CTA b takes the work units b, b + gridDim.x, ... (unit = K part
 // fastest, then the 128-row tile, then the 64-column tile, so that the CTAs
-// running together share B tiles and the K chunks of one output tile run
-// side by side).  Warp 0 loads the 8 digit planes of both operands by TMA
-// into a two-stage ring that runs ahead across tiles; warp 1 issues the 36
-// products of each 16-k step into the 8 level accumulators in tensor memory
-// (level p + q - 2 at columns 64 (p + q - 2)) once the epilogue has drained
-// the previous tile; warps 2 .. 17 combine the levels (warp w: the rows of
-// lane quarter w % 4, columns 16 ((w - 2) / 4) ..).
+// running together share B tiles).  A unit covers p.kin runs of <= 128 k of
+// one output tile (all of K when K <= 1024, else one run, the runs of a tile
+// then being separate units added with atomics).  Warp 0 loads the 8 digit
+// planes of both operands by TMA into a two-stage ring that runs ahead across
+// runs and tiles; warp 1 issues the 36 products of each 16-k step into the 8
+// level accumulators in tensor memory (level p + q - 2 at columns
+// 64 (p + q - 2)) once the epilogue has drained the previous run, and commits
+// after each run; warps 2 .. 17 drain and combine the levels (warp w: the rows
+// of lane quarter w % 4, columns 16 ((w - 2) / 4) ..) and store once per unit.
 __global__ void __launch_bounds__(EM_THREADS, 1)
     emgemm_kernel(const __grid_constant__ EmMaps maps, const EmParams p) {
   extern __shared__ uint8_t smem_raw[];
