@@ -333,3 +333,13 @@ def test_emulated_products_argument_checks(lib):
     assert lib.isdf_vmc_polyak(fake, fake, 0, 1, None) == C.ISDF_E_ARG
     assert lib.isdf_vmc_polyak(fake, fake, 4, 0, None) == C.ISDF_E_ARG
     assert lib.isdf_vmc_objective(fake, 1, fake, None) == C.ISDF_E_ARG
+
+
+def test_vmc_schedule_rejects_bad_window():
+    """The averaging window must lie within the refinement steps (checked on
+    the host before any device work)."""
+    from paper_2607_17314_b300 import api
+    for n_refine, window in ((5, 0), (5, 6), (0, 1)):
+        with pytest.raises(ValueError):
+            api.vmc_schedule(None, None, 1, None, None, None, None, n_warm=1, n_refine=n_refine,
+                             window=window, sweeps=1, sigma=0.5)
