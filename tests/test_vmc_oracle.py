@@ -209,3 +209,55 @@ def test_clipped_residual_jacobian_matches_finite_differences():
         assert np.max(np.abs((rp - rm) / (2 * h) - dr[p])) < 1e-7
         grad = 2.0 / (Nw - 1) * dr[p] @ (Ec - mean)
         assert abs((vp - vm) / (2 * h) - grad) < 1e-7 * max(1.0, abs(grad))
+
+
+def test_energy_jacobian_fd_against_independent_derivatives():
+    """energy_jacobian_fd, the reference for dE_loc/dtheta, against derivatives
+    formed here by setting d, b_t and c_tk on the correlator directly (not through
+    its parameter vector): every row against a five-point stencil (error O(h^4)),
+    and the coefficient block against an exact identity.  u is linear in the
+    coefficients c (Eq. bh-u) and E_loc holds tau at most squared (Eq. Eloc), so
+    along c -> s c the local energy is a quadratic in s and
+    sum_k c_k dE/dc_k = (E(2c) - E(0)) / 2 with no truncation error.  A wrong
+    sign, step divisor or row order fails one of the two."""
+    import copy
+    w = _tiny(n_atom=4, seed=4)
+    c_occ = w.mo_coef[:, :w.n_occ]
+    jas = copy.deepcopy(w.jastrow)
+    jas.coef = jas.coef * 4.0
+    jas.b = np.asarray(jas.b, float) * 1.1
+    nuc, Z = w.xyz, np.ones(len(w.atoms))
+    N = 2 * c_occ.shape[1]
+    R = np.random.default_rng(21).normal(size=(3, N, 3)) * 1.3
+    J = vmc.energy_jacobian_fd(R, w.basis, c_occ, jas, nuc, Z, h=1e-5)
+    T, nt = jas.coef.shape
+
+    def E(j):
+        return vmc.local_energies(R, w.basis, c_occ, j, nuc, Z)
+
+    def moved(row, t):
+        j = copy.deepcopy(jas)
+        j.b = np.array(jas.b, float)
+        j.coef = np.array(jas.coef, float)
+        if row == 0:
+            j.d = jas.d + t
+        elif row <= T:
+            j.b[row - 1] += t
+        else:
+            j.coef[(row - 1 - T) // nt, (row - 1 - T) % nt] += t
+        return j
+
+    assert J.shape == (1 + T + T * nt, R.shape[0])
+    h = 1e-3
+    for row in range(J.shape[0]):
+        five = (-E(moved(row, 2 * h)) + 8 * E(moved(row, h)) - 8 * E(moved(row, -h))
+                + E(moved(row, -2 * h))) / (12 * h)
+        assert np.max(np.abs(J[row] - five)) < 1e-6 * max(1.0, np.max(np.abs(five))), row
+
+    j0, j2 = copy.deepcopy(jas), copy.deepcopy(jas)
+    j0.coef = np.zeros_like(jas.coef)
+    j2.coef = 2.0 * jas.coef
+    euler = (E(j2) - E(j0)) / 2.0
+    got = jas.coef.ravel() @ J[1 + T:]
+    assert np.max(np.abs(got - euler)) < 1e-7 * max(1.0, np.max(np.abs(euler))), (got, euler)
+    assert np.max(np.abs(euler)) > 1e-3  # the correlator's coefficients matter here
