@@ -409,6 +409,35 @@ def test_w_staged_equals_brute_force():
         assert np.max(np.abs(Wst - Wbf)) < 1e-11 * np.max(np.abs(Wbf))
 
 
+def test_stage1_bounded_values_and_bound():
+    """stage1_bounded: its sums equal stage1's (pinned above through W against the
+    brute-force double-grid sum) on ragged row batches, and its bound is fixed as
+    sum_g' |w_g' xi_nu(g')| |K_c(g, g')| by four properties: one nonzero g' gives
+    |calG| itself (a single term), the bound depends on |xi| only (sign flips),
+    it adds over disjoint supports of xi, and it dominates |calG|."""
+    w = wl.tiny_chain(n_atom=2, n_rad=6, n_ang=10, shells=(0, 1), n_mu=10, seed=4)
+    rng = np.random.default_rng(17)
+    n_g = w.grid_xyz.shape[0]
+    rows = np.sort(rng.choice(n_g, 37, replace=False))
+    xi = rng.standard_normal((5, n_g))
+    for jas in (w.jastrow, wl.bh_jastrow(w.atoms, w.xyz, wl.bh_terms_c4(), np.random.default_rng(9), 0.2)):
+        val, bnd = wbuild.stage1_bounded(w.grid_xyz, w.grid_w, xi, jas, rows, batch=8)
+        ref = wbuild.stage1(w.grid_xyz, w.grid_w, xi, jas, g_rows=rows)
+        assert np.max(np.abs(val - ref)) < 1e-13 * np.max(np.abs(ref))
+        assert np.all(bnd >= np.abs(val) * (1 - 1e-14))
+        assert np.any(bnd > 1.5 * np.abs(val))          # mixed signs do cancel
+        flip = xi * rng.choice([-1.0, 1.0], xi.shape)
+        _, bflip = wbuild.stage1_bounded(w.grid_xyz, w.grid_w, flip, jas, rows, batch=8)
+        assert np.max(np.abs(bflip - bnd)) < 1e-13 * np.max(bnd)
+        mask = rng.random(n_g) < 0.5
+        _, b1 = wbuild.stage1_bounded(w.grid_xyz, w.grid_w, xi * mask, jas, rows, batch=8)
+        _, b2 = wbuild.stage1_bounded(w.grid_xyz, w.grid_w, xi * ~mask, jas, rows, batch=8)
+        assert np.max(np.abs(b1 + b2 - bnd)) < 1e-13 * np.max(bnd)
+        one = np.zeros_like(xi)
+        one[:, 3] = xi[:, 3]
+        v1, b1 = wbuild.stage1_bounded(w.grid_xyz, w.grid_w, one, jas, rows, batch=8)
+        assert np.array_equal(b1, np.abs(v1))
+
 def test_zero_jastrow_gives_zero(h6):
     w, phi, dphi = h6
     res = pivots.select(phi, dphi, w.grid_w, 24)
