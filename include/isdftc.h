@@ -599,7 +599,8 @@ int isdf_vmc_objective(const double* E, int64_t n_walkers, double* stats, isdf_s
 /* Polyak-Ruppert averaging of the parameters (Sec. II.C: the production
  * correlator averages the stationary tail of the refinement trajectory):
  * avg[p] += (theta[p] - avg[p]) / k for the k-th averaged iterate (k >= 1; k = 1
- * copies theta).  theta, avg: device [n_par].  Asynchronous. */
+ * copies theta without reading avg, so avg needs no initial value).  theta, avg:
+ * device [n_par].  Asynchronous. */
 int isdf_vmc_polyak(const double* theta, double* avg, int n_par, int64_t k, isdf_stream_t stream);
 int isdf_vmc_gn_step(const double* E, const double* dE, int64_t n_walkers, int n_par,
                      double lambda, double eta, double* theta, double* step, double* stats,

@@ -544,7 +544,10 @@ class VmcOptimizer:
 
 
 def isdf_vmc_polyak(theta, avg, k: int):
-    """avg += (theta - avg) / k in place (the k-th Polyak-Ruppert iterate)."""
+    """avg += (theta - avg) / k in place (the k-th Polyak-Ruppert iterate; at
+    k = 1 avg becomes theta whatever it held)."""
+    if avg.numel() != theta.numel():
+        raise ValueError(f"avg has {avg.numel()} values, theta {theta.numel()}")
     lib = C.load()
     _req(theta, f64, "theta"); _req(avg, f64, "avg")
     C.check("isdf_vmc_polyak", lib.isdf_vmc_polyak(_ptr(theta), _ptr(avg), theta.numel(), int(k),

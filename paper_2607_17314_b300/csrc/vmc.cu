@@ -799,10 +799,12 @@ __global__ void gn_finish_kernel(const double* __restrict__ x, int P, double eta
 }
 
 // Polyak-Ruppert running mean: avg += (theta - avg) / k (k = 1, 2, ...).
+// The first averaged iterate is theta itself: avg is not read then, so it may hold
+// anything (an uninitialised buffer, NaN) before the first call.
 __global__ void polyak_kernel(const double* __restrict__ theta, double* __restrict__ avg, int P,
-                              double inv_k) {
+                              double inv_k, int first) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < P) avg[p] += (theta[p] - avg[p]) * inv_k;
+  if (p < P) avg[p] = first ? theta[p] : avg[p] + (theta[p] - avg[p]) * inv_k;
 }
 
 struct ElocWs {
@@ -945,7 +947,8 @@ int vmc_objective(const double* E, int64_t n_w, double* stats, cudaStream_t s) {
 int vmc_polyak(const double* theta, double* avg, int P, int64_t k, cudaStream_t s) {
   ISDF_ARG(theta && avg, "null pointer argument");
   ISDF_ARG(P >= 1 && k >= 1, "need n_par >= 1 and k >= 1");
-  polyak_kernel<<<(unsigned)ceil_div(P, 128), 128, 0, s>>>(theta, avg, P, 1.0 / (double)k);
+  polyak_kernel<<<(unsigned)ceil_div(P, 128), 128, 0, s>>>(theta, avg, P, 1.0 / (double)k,
+                                                            k == 1 ? 1 : 0);
   ISDF_LAUNCH_CHECK();
   return ISDF_OK;
 }

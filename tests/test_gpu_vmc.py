@@ -221,9 +221,13 @@ def test_optimisation_lowers_the_sampled_variance(api):
 
 
 def test_polyak_running_mean(api):
+    """The running mean of six iterates; the first call copies theta without
+    reading avg, so avg may start as anything (NaN, 1e300 here)."""
     rng = np.random.default_rng(61)
     xs = rng.standard_normal((6, 11))
-    avg = _cu(np.zeros(11))
+    avg = _cu(np.where(np.arange(11) % 2 == 0, np.nan, 1e300))
+    api.isdf_vmc_polyak(_cu(xs[0]), avg, 1)
+    assert np.array_equal(avg.cpu().numpy(), xs[0])
     for k, x in enumerate(xs, 1):
         api.isdf_vmc_polyak(_cu(x), avg, k)
     assert np.allclose(avg.cpu().numpy(), xs.mean(axis=0), rtol=1e-14, atol=1e-15)
