@@ -35,6 +35,58 @@ def _req(t: torch.Tensor, dtype, name: str):
     return t
 
 
+def _shape(t: torch.Tensor, name: str, shape) -> tuple:
+    """t's shape after checking it against `shape` (None entries match any
+    size).  The library reads and writes exactly the sizes it is passed, so a
+    tensor smaller than they say would be accessed out of bounds on the device."""
+    if t.dim() != len(shape) or any(want is not None and got != want
+                                    for got, want in zip(t.shape, shape)):
+        want = tuple("*" if x is None else x for x in shape)
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {want}")
+    return tuple(t.shape)
+
+
+def _dims(t: torch.Tensor, name: str, rank: int) -> tuple:
+    return _shape(t, name, (None,) * rank)
+
+
+def _reqs(*specs):
+    """specs: (tensor, dtype, name, shape or None).  Every shape is checked
+    before any dtype, layout or device, so the host-side size checks run (and
+    are testable) without a GPU; then every tensor must be a contiguous CUDA
+    tensor of its dtype."""
+    for t, _, name, shape in specs:
+        if shape is not None:
+            _shape(t, name, shape)
+    for t, dtype, name, _ in specs:
+        _req(t, dtype, name)
+
+
+def _orbital_planes(phi, dphi, *more):
+    """(n_orb, n_g) of phi [n_orb][n_g]; phi, dphi [3][n_orb][n_g] and the
+    further specs (built from n_g by the caller's lambda) checked."""
+    n_orb, n_g = _dims(phi, "phi", 2)
+    _reqs((phi, f64, "phi", None), (dphi, f64, "dphi", (3, n_orb, n_g)),
+          *[m(n_g) for m in more])
+    return n_orb, n_g
+
+
+def _factors(W, D, Xp, phi_piv, dphi_piv, x_rows_min=None):
+    """(n_mu, n_orb) of the pivot factors, with W [4][n_mu][n_mu], D [n_mu][n_mu],
+    dphi_piv [3][n_mu][n_orb] and the packed X [rows][n_mu] checked: at least
+    x_rows_min rows when given, else the full X of all n_orb orbitals."""
+    n_mu, n_orb = _dims(phi_piv, "phi_piv", 2)
+    _shape(Xp, "Xp", (None, n_mu))
+    full = n_orb * (n_orb + 1) // 2
+    if x_rows_min is not None and Xp.shape[0] < x_rows_min:
+        raise ValueError(f"Xp has {Xp.shape[0]} rows, needs at least {x_rows_min}")
+    if x_rows_min is None and Xp.shape[0] != full:
+        raise ValueError(f"Xp has {Xp.shape[0]} rows; the full X of {n_orb} orbitals has {full}")
+    _reqs((phi_piv, f64, "phi_piv", None), (dphi_piv, f64, "dphi_piv", (3, n_mu, n_orb)),
+          (W, f64, "W", (4, n_mu, n_mu)), (D, f64, "D", (n_mu, n_mu)), (Xp, f64, "Xp", None))
+    return n_mu, n_orb
+
+
 def jastrow_struct(nuc_xyz, nuc_type, mno, coef, b, d: float, cusp: bool = True,
                    chi_a=None, chi_b=None, n_elec: int = 0) -> C.IsdfJastrow:
     """Fill the host isdf_jastrow struct from arrays (see include/isdftc.h);
@@ -85,14 +137,11 @@ def isdf_eval_orbitals(center, powers, exps, coefs, mo_coef, grid_xyz,
     the contractions as FP64 products emulated on the tensor cores."""
     lib = C.load()
     dev = grid_xyz.device
-    for t, n, dt in ((center, "center", f64), (exps, "exps", f64), (coefs, "coefs", f64),
-                     (mo_coef, "mo_coef", f64), (grid_xyz, "grid_xyz", f64),
-                     (powers, "powers", torch.int32)):
-        _req(t, dt, n)
-    n_bf, n_prim = exps.shape
-    n_orb = mo_coef.shape[1]
-    n_g = grid_xyz.shape[0]
-    basis = C.IsdfBasis(n_bf, n_prim, _ptr(center), _ptr(powers), _ptr(exps), _ptr(coefs))
+    n_bf = _dims(exps, "exps", 2)[0]
+    n_orb = _shape(mo_coef, "mo_coef", (n_bf, None))[1]
+    n_g = _shape(grid_xyz, "grid_xyz", (None, 3))[0]
+    basis = _basis(center, powers, exps, coefs, (mo_coef, f64, "mo_coef", None),
+                   (grid_xyz, f64, "grid_xyz", None))
     phi = torch.empty((n_orb, n_g), dtype=f64, device=dev)
     dphi = torch.empty((3, n_orb, n_g), dtype=f64, device=dev)
     if mode == 0:
@@ -112,8 +161,7 @@ def isdf_points(phi, dphi, w, n_mu: int, mode: int = 0, allow_rank: bool = False
     """Interpolation points (Alg. 1 + fusion): int32 tensor of length n_mu_out."""
     lib = C.load()
     dev = phi.device
-    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(w, f64, "w")
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda n_g: (w, f64, "w", (n_g,)))
     piv = torch.empty(n_mu, dtype=torch.int32, device=dev)
     out = C.INT(0)
     ws = _ws(lib.isdf_points_workspace(n_g, n_mu), dev)
@@ -129,8 +177,7 @@ def isdf_points_fixed_rank(phi, dphi, w, n_ch_phi: int, n_ch_grad: int,
     the union (scalar pivots first).  int32 tensor of length n_mu_out."""
     lib = C.load()
     dev = phi.device
-    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(w, f64, "w")
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda n_g: (w, f64, "w", (n_g,)))
     piv = torch.empty(max(n_ch_phi + n_ch_grad, 1), dtype=torch.int32, device=dev)
     out = C.INT(0)
     ws = _ws(lib.isdf_points_fixed_rank_workspace(n_g, n_ch_phi, n_ch_grad), dev)
@@ -150,8 +197,7 @@ def isdf_fit(phi, dphi, pivots, jitter_init: float = 0.0, jitter_growth: float =
     emulated on the tensor cores."""
     lib = C.load()
     dev = phi.device
-    _req(phi, f64, "phi"); _req(dphi, f64, "dphi"); _req(pivots, torch.int32, "pivots")
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda _: (pivots, torch.int32, "pivots", (None,)))
     n_mu = pivots.numel()
     xi = torch.empty((n_mu, n_g), dtype=f64, device=dev)
     xig = torch.empty((3, n_mu, n_g), dtype=f64, device=dev)
@@ -169,17 +215,16 @@ def isdf_dgemm_emulated(A, B, alpha: float = 1.0, out=None):
     """alpha A B, added in place to `out` when given, with the FP64 products
     emulated on the tensor cores; A [M][K], B [K][N] FP64."""
     lib = C.load()
-    _req(A, f64, "A"); _req(B, f64, "B")
-    M, K = A.shape
-    if B.shape[0] != K:
-        raise ValueError("inner dimensions differ")
-    N = B.shape[1]
+    M, K = _dims(A, "A", 2)
+    N = _shape(B, "B", (K, None))[1]
+    specs = [(A, f64, "A", None), (B, f64, "B", None)]
     beta = 0.0
+    if out is not None:
+        specs.append((out, f64, "out", (M, N)))
+        beta = 1.0
+    _reqs(*specs)
     if out is None:
         out = torch.empty((M, N), dtype=f64, device=A.device)
-    else:
-        _req(out, f64, "out")
-        beta = 1.0
     ws = _ws(lib.isdf_dgemm_emulated_workspace(M, N, K), A.device)
     C.check("isdf_dgemm_emulated", lib.isdf_dgemm_emulated(
         M, N, K, _ptr(A), K, _ptr(B), N, float(alpha), beta, _ptr(out), N, _ptr(ws), ws.numel(),
@@ -191,7 +236,7 @@ def isdf_gather_pivots(phi, dphi, pivots):
     """phi_p(r_mu) [n_mu][n_orb] and d_c phi_p(r_mu) [3][n_mu][n_orb] at the
     pivots: the factors of the pivot tensors C^p_q(r_mu) of Eq. isdf-rho."""
     lib = C.load()
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda _: (pivots, torch.int32, "pivots", (None,)))
     n_mu = pivots.numel()
     phiP = torch.empty((n_mu, n_orb), dtype=f64, device=phi.device)
     dphiP = torch.empty((3, n_mu, n_orb), dtype=f64, device=phi.device)
@@ -220,11 +265,12 @@ class KernelBuilder:
                  s2_kchunk: int = 0, sync_check: bool = True, debug_flags: int = 0,
                  time_stages: bool = False, wait_limit_ms: int = 0):
         lib = C.load()
-        for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad")):
-            _req(t, f64, n)
+        n_mu, n_g = _dims(xi, "xi", 2)
+        _reqs((xi, f64, "xi", None), (xig, f64, "xi_grad", (3, n_mu, n_g)),
+              (grid_xyz, f64, "grid_xyz", (n_g, 3)), (w, f64, "w", (n_g,)))
         self.lib = lib
         self.dev = xi.device
-        self.n_mu, self.n_g = xi.shape
+        self.n_mu, self.n_g = n_mu, n_g
         self.g_begin = int(g_begin)
         self.g_end = int(self.n_g if g_end is None else g_end)
         self.args = (grid_xyz, w, xi, xig)
@@ -271,11 +317,15 @@ def tc_kernel_build_streamed(grid_xyz, w, xi_host, xig_host, jastrow: C.IsdfJast
     held in (pinned) host memory, streamed in bra/ket grid batches with a
     depth-one prefetch (Sec. II.D); grid_xyz and w on the device."""
     lib = C.load()
-    _req(grid_xyz, f64, "grid_xyz"); _req(w, f64, "w")
     for t, n in ((xi_host, "xi_host"), (xig_host, "xig_host")):
         if t.device.type != "cpu" or t.dtype != f64 or not t.is_contiguous():
             raise ValueError(f"{n} must be a contiguous FP64 host tensor")
+    if xi_host.dim() != 2:
+        raise ValueError(f"xi_host has shape {tuple(xi_host.shape)}, expected (n_mu, n_g)")
     n_mu, n_g = xi_host.shape
+    if tuple(xig_host.shape) != (3, n_mu, n_g):
+        raise ValueError(f"xig_host has shape {tuple(xig_host.shape)}, expected {(3, n_mu, n_g)}")
+    _reqs((grid_xyz, f64, "grid_xyz", (n_g, 3)), (w, f64, "w", (n_g,)))
     dev = grid_xyz.device
     opt = options(precision, kchunk)
     W = torch.empty((4, n_mu, n_mu), dtype=f64, device=dev)
@@ -311,8 +361,12 @@ def xtc_density_contract(phi_piv, n_occ: int, xi, w, calG, n_orb_x: int = 0,
     """D [n_mu][n_mu] and (n_orb_x > 0) X packed [n_orb_x(n_orb_x+1)/2][n_mu]."""
     lib = C.load()
     dev = xi.device
-    n_mu, n_g = xi.shape
-    n_orb = phi_piv.shape[1]
+    n_mu, n_g = _dims(xi, "xi", 2)
+    n_orb = _shape(phi_piv, "phi_piv", (n_mu, None))[1]
+    if _shape(calG, "calG", (None, n_mu, n_g))[0] < 3:
+        raise ValueError("calG needs its three gradient channels")
+    _reqs((xi, f64, "xi", None), (phi_piv, f64, "phi_piv", None), (w, f64, "w", (n_g,)),
+          (calG, f64, "calG", None))
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     D = torch.empty((n_mu, n_mu), dtype=f64, device=dev)
     Xp = torch.empty((n_orb_x * (n_orb_x + 1) // 2, n_mu), dtype=f64, device=dev) if n_orb_x > 0 else None
@@ -326,7 +380,7 @@ def xtc_density_contract(phi_piv, n_occ: int, xi, w, calG, n_orb_x: int = 0,
 def tc_energies(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
     """(E_K, E_dU, E0) in Hartree from the factors (occupied block)."""
     lib = C.load()
-    n_mu, n_orb = phi_piv.shape
+    n_mu, n_orb = _factors(W, D, Xp, phi_piv, dphi_piv, n_occ * (n_occ + 1) // 2)
     out = (ctypes.c_double * 3)()
     ws = _ws(lib.tc_energies_workspace(n_mu, n_occ), W.device)
     C.check("tc_energies", lib.tc_energies(_ptr(W), _ptr(D), _ptr(Xp), _ptr(phi_piv), _ptr(dphi_piv),
@@ -339,7 +393,7 @@ def tc_two_body_panel(W, D, Xp, phi_piv, dphi_piv, pr_begin: int, pr_end: int,
     """Rows [pr_begin, pr_end) of the four-index K and DeltaU in composite form
     (row (p,r) = p n_orb + r, column (q,s)); Xp is the full packed X."""
     lib = C.load()
-    n_mu, n_orb = phi_piv.shape
+    n_mu, n_orb = _factors(W, D, Xp, phi_piv, dphi_piv)
     rows = pr_end - pr_begin
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dev = phi_piv.device
@@ -356,7 +410,7 @@ def tc_xtc_one_body(W, D, Xp, phi_piv, dphi_piv, n_occ: int):
     """Delta h [n_orb][n_orb], f^xTC [n_orb][n_orb] and E0 (Eqs. xtc-deltah,
     xtc-fock, xtc-const); Xp is the full packed X."""
     lib = C.load()
-    n_mu, n_orb = phi_piv.shape
+    n_mu, n_orb = _factors(W, D, Xp, phi_piv, dphi_piv)
     dev = phi_piv.device
     dh = torch.empty((n_orb, n_orb), dtype=f64, device=dev)
     f = torch.empty((n_orb, n_orb), dtype=f64, device=dev)
@@ -373,9 +427,10 @@ def tc_kernel_adjoint(grid_xyz, w, xi, xig, jastrow: C.IsdfJastrow, Wbar, precis
     """dL/dtheta for L = sum_c <Wbar^c, W^c>, theta = (d, b, c_0 .. c_{K-1});
     with g_begin/g_end, W over that outer-grid slice only."""
     lib = C.load()
-    for t, n in ((grid_xyz, "grid_xyz"), (w, "w"), (xi, "xi"), (xig, "xi_grad"), (Wbar, "Wbar")):
-        _req(t, f64, n)
-    n_mu, n_g = xi.shape
+    n_mu, n_g = _dims(xi, "xi", 2)
+    _reqs((xi, f64, "xi", None), (xig, f64, "xi_grad", (3, n_mu, n_g)),
+          (grid_xyz, f64, "grid_xyz", (n_g, 3)), (w, f64, "w", (n_g,)),
+          (Wbar, f64, "Wbar", (4, n_mu, n_mu)))
     prec = C.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dtheta = torch.empty(2 + jastrow.n_terms, dtype=f64, device=xi.device)
     ws = _ws(lib.tc_kernel_adjoint_workspace(n_g, n_mu, jastrow.n_nuc, prec), xi.device)
@@ -429,11 +484,12 @@ class TCKernel(torch.autograd.Function):
         return g.to(ctx.theta_device), None, None, None, None, None, None
 
 
-def _basis(center, powers, exps, coefs) -> C.IsdfBasis:
-    for t, n, dt in ((center, "center", f64), (exps, "exps", f64), (coefs, "coefs", f64),
-                     (powers, "powers", torch.int32)):
-        _req(t, dt, n)
-    n_bf, n_prim = exps.shape
+def _basis(center, powers, exps, coefs, *more) -> C.IsdfBasis:
+    """The isdf_basis struct over the four device arrays, checked with the
+    further specs `more` (shapes first)."""
+    n_bf, n_prim = _dims(exps, "exps", 2)
+    _reqs((exps, f64, "exps", None), (coefs, f64, "coefs", (n_bf, n_prim)),
+          (center, f64, "center", (n_bf, 3)), (powers, torch.int32, "powers", (n_bf, 3)), *more)
     return C.IsdfBasis(n_bf, n_prim, _ptr(center), _ptr(powers), _ptr(exps), _ptr(coefs))
 
 
@@ -442,9 +498,12 @@ def isdf_vmc_local_energy(basis, mo_coef, n_occ: int, walkers, jastrow: C.IsdfJa
     """E_loc [n_walkers] of Eq. Eloc and, with grad, dE_loc/dtheta [P][n_walkers]
     (theta = (d, b_t, coef row-major); None = the struct's values).
     basis = (center, powers, exps, coefs) device tensors; charges host [n_nuc]."""
+    if len(charges) != jastrow.n_nuc:
+        raise ValueError(f"charges has {len(charges)} values for {jastrow.n_nuc} nuclei")
     lib = C.load()
-    B = _basis(*basis)
-    _req(mo_coef, f64, "mo_coef"); _req(walkers, f64, "walkers")
+    n_bf = _dims(basis[2], "exps", 2)[0]
+    B = _basis(*basis, (mo_coef, f64, "mo_coef", (n_bf, None)),
+               (walkers, f64, "walkers", (None, 2 * n_occ, 3)))
     dev = walkers.device
     n_walk = walkers.shape[0]
     P = lib.isdf_vmc_n_params(ctypes.byref(jastrow))
@@ -467,11 +526,12 @@ def isdf_vmc_sample(basis, mo_coef, n_occ: int, walkers, normals, uniforms, sigm
     """Metropolis sweeps on |Phi_0|^2, walkers moved in place; returns the
     number of accepted moves (synchronises)."""
     lib = C.load()
-    B = _basis(*basis)
-    for t, n in ((mo_coef, "mo_coef"), (walkers, "walkers"), (normals, "normals"),
-                 (uniforms, "uniforms")):
-        _req(t, f64, n)
-    n_steps = uniforms.shape[0]
+    n_bf = _dims(basis[2], "exps", 2)[0]
+    n_w = _shape(walkers, "walkers", (None, 2 * n_occ, 3))[0]
+    n_steps = _shape(uniforms, "uniforms", (None, 2 * n_occ, n_w))[0]
+    B = _basis(*basis, (mo_coef, f64, "mo_coef", (n_bf, None)), (walkers, f64, "walkers", None),
+               (uniforms, f64, "uniforms", None),
+               (normals, f64, "normals", (n_steps, 2 * n_occ, n_w, 3)))
     acc = torch.zeros(1, dtype=torch.int64, device=walkers.device)
     C.check("isdf_vmc_sample", lib.isdf_vmc_sample(
         ctypes.byref(B), _ptr(mo_coef), mo_coef.shape[1], n_occ, _ptr(walkers), walkers.shape[0],
@@ -484,12 +544,12 @@ def isdf_vmc_gn_step(E, dE, lam: float, eta: float, theta=None):
     mean, variance, raw mean, mean absolute deviation); theta += step in place
     when given."""
     lib = C.load()
-    _req(E, f64, "E"); _req(dE, f64, "dE")
-    P, n_w = dE.shape
+    n_w = _dims(E, "E", 1)[0]
+    P = _shape(dE, "dE", (None, n_w))[0]
+    _reqs((E, f64, "E", None), (dE, f64, "dE", None),
+          *([(theta, f64, "theta", (P,))] if theta is not None else []))
     step = torch.empty(P, dtype=f64, device=E.device)
     stats = torch.empty(4, dtype=f64, device=E.device)
-    if theta is not None:
-        _req(theta, f64, "theta")
     ws = _ws(lib.isdf_vmc_gn_step_workspace(n_w, P), E.device)
     C.check("isdf_vmc_gn_step", lib.isdf_vmc_gn_step(
         _ptr(E), _ptr(dE), n_w, P, float(lam), float(eta), _ptr(theta), _ptr(step), _ptr(stats),

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _capi as C
-from .api import _ptr, _req, _stream, _ws
+from .api import _dims, _orbital_planes, _ptr, _reqs, _shape, _stream, _ws
 
 f32, f64 = torch.float32, torch.float64
 
@@ -28,7 +28,8 @@ def features(phi, dphi, w, grid_xyz, nuc_xyz) -> torch.Tensor:
     """Per-point features [n_g][8] (pivot diagonals of Alg. 1 and its gradient
     branch, weights, densities, nucleus distances) on the device."""
     lib = C.load()
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda n_g: (w, f64, "w", (n_g,)),
+                                 lambda n_g: (grid_xyz, f64, "grid_xyz", (n_g, 3)))
     nuc = np.ascontiguousarray(np.asarray(nuc_xyz, dtype=np.float64).reshape(-1, 3))
     feat = torch.empty((n_g, 8), dtype=f32, device=phi.device)
     C.check("isdf_mlp_features", lib.isdf_mlp_features(
@@ -40,6 +41,8 @@ def features(phi, dphi, w, grid_xyz, nuc_xyz) -> torch.Tensor:
 def forward(params, feat) -> torch.Tensor:
     """Scores [n] of the network with BF16-rounded weights."""
     lib = C.load()
+    _shape(feat, "feat", (None, 8))
+    _reqs((params, f32, "params", (n_params(),)), (feat, f32, "feat", None))
     scores = torch.empty(feat.shape[0], dtype=f32, device=feat.device)
     C.check("isdf_mlp_forward", lib.isdf_mlp_forward(_ptr(params), _ptr(feat), feat.shape[0],
                                                      _ptr(scores), _stream()))
@@ -50,6 +53,9 @@ def backward(params, feat, labels, pos_w: float, n_total: int, grad, loss):
     """Add the weighted-BCE gradient (normalised by n_total) to grad and the
     unnormalised loss sum to loss (device FP64 [1])."""
     lib = C.load()
+    n, P = _shape(feat, "feat", (None, 8))[0], n_params()
+    _reqs((params, f32, "params", (P,)), (feat, f32, "feat", None), (labels, f32, "labels", (n,)),
+          (grad, f32, "grad", (P,)), (loss, f64, "loss", (1,)))
     C.check("isdf_mlp_backward", lib.isdf_mlp_backward(
         _ptr(params), _ptr(feat), _ptr(labels), feat.shape[0], float(pos_w), int(n_total),
         _ptr(grad), _ptr(loss), _stream()))
@@ -58,6 +64,9 @@ def backward(params, feat, labels, pos_w: float, n_total: int, grad, loss):
 def adam(params, grad, m, v, step: int, lr: float):
     """One bias-corrected Adam step on params (1-based step)."""
     lib = C.load()
+    P = n_params()
+    _reqs(*[(t, f32, name, (P,)) for t, name in ((params, "params"), (grad, "grad"), (m, "m"),
+                                                 (v, "v"))])
     C.check("isdf_mlp_adam", lib.isdf_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v),
                                                int(step), float(lr), _stream()))
 
@@ -65,6 +74,7 @@ def adam(params, grad, m, v, step: int, lr: float):
 def topk(scores, k: int) -> torch.Tensor:
     """Indices of the k highest scores, ties by the lower index, ascending."""
     lib = C.load()
+    _reqs((scores, f32, "scores", (None,)))
     out = torch.empty(k, dtype=torch.int32, device=scores.device)
     C.check("isdf_mlp_topk", lib.isdf_mlp_topk(_ptr(scores), scores.shape[0], int(k), _ptr(out),
                                                _stream()))
@@ -75,7 +85,8 @@ def points_restricted(phi, dphi, w, cand, n_mu: int) -> torch.Tensor:
     """Fused pivoted Cholesky (Alg. 1 and Sec. II.D) on the candidate points
     only; grid indices of the selected points (fewer if the rank runs out)."""
     lib = C.load()
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _orbital_planes(phi, dphi, lambda n_g: (w, f64, "w", (n_g,)),
+                                 lambda _: (cand, torch.int32, "cand", (None,)))
     piv = torch.empty(n_mu, dtype=torch.int32, device=phi.device)
     n_out = C.INT(0)
     ws = _ws(lib.isdf_points_restricted_workspace(cand.numel(), n_orb, n_mu), phi.device)
@@ -89,7 +100,8 @@ def points_restricted(phi, dphi, w, cand, n_mu: int) -> torch.Tensor:
 def fit_error(phi, w, pivots) -> float:
     """Scalar-channel weighted ISDF fit error of a pivot set (Eq. isdf-rho)."""
     lib = C.load()
-    n_orb, n_g = phi.shape
+    n_orb, n_g = _dims(phi, "phi", 2)
+    _reqs((phi, f64, "phi", None), (w, f64, "w", (n_g,)), (pivots, torch.int32, "pivots", (None,)))
     eps = ctypes.c_double(0.0)
     ws = _ws(lib.isdf_fit_error_workspace(n_g, n_orb, pivots.numel()), phi.device)
     C.check("isdf_fit_error", lib.isdf_fit_error(_ptr(phi), _ptr(w), n_g, n_orb, _ptr(pivots),

@@ -343,3 +343,75 @@ def test_vmc_schedule_rejects_bad_window():
         with pytest.raises(ValueError):
             api.vmc_schedule(None, None, 1, None, None, None, None, n_warm=1, n_refine=n_refine,
                              window=window, sweeps=1, sigma=0.5)
+
+
+def test_binding_rejects_mismatched_shapes():
+    """The Python binding passes sizes taken from one tensor together with the
+    pointers of the others, so every other tensor is checked against those
+    sizes on the host before anything reaches the library (a smaller tensor
+    would be read or written out of bounds on the device).  CPU tensors reach
+    the shape check, which comes before the device check."""
+    import torch
+    from paper_2607_17314_b300 import api, _capi as C
+    d = torch.float64
+
+    def z(*shape, dtype=d):
+        return torch.zeros(shape, dtype=dtype)
+
+    J = C.IsdfJastrow()
+    J.n_nuc, J.n_types, J.n_terms, J.d = 2, 1, 0, 1.0
+    basis = (z(4, 3), z(4, 3, dtype=torch.int32), z(4, 2), z(4, 2))
+    cases = {
+        "dphi": lambda: api.isdf_points(z(3, 10), z(3, 3, 9), z(10), 4),
+        "w": lambda: api.isdf_points_fixed_rank(z(3, 10), z(3, 3, 10), z(9), 2, 2),
+        "pivots": lambda: api.isdf_fit(z(3, 10), z(3, 3, 10), z(2, 2, dtype=torch.int32)),
+        "B": lambda: api.isdf_dgemm_emulated(z(4, 5), z(6, 3)),
+        "out": lambda: api.isdf_dgemm_emulated(z(4, 5), z(5, 3), out=z(3, 4)),
+        "xi_grad": lambda: api.KernelBuilder(z(10, 3), z(10), z(4, 10), z(3, 4, 9), J),
+        "grid_xyz": lambda: api.tc_kernel_build(z(10, 2), z(10), z(4, 10), z(3, 4, 10), J),
+        "xig_host": lambda: api.tc_kernel_build_streamed(z(10, 3), z(10), z(4, 10), z(4, 4, 10), J),
+        "calG": lambda: api.xtc_density_contract(z(4, 3), 1, z(4, 10), z(10), z(4, 4, 9), 1),
+        "phi_piv": lambda: api.xtc_density_contract(z(5, 3), 1, z(4, 10), z(10), z(4, 4, 10), 1),
+        "W": lambda: api.tc_energies(z(4, 5, 5), z(4, 4), z(3, 4), z(4, 3), z(3, 4, 3), 2),
+        "needs at least 3": lambda: api.tc_energies(z(4, 4, 4), z(4, 4), z(2, 4), z(4, 3),
+                                                    z(3, 4, 3), 2),
+        "full X": lambda: api.tc_two_body_panel(z(4, 4, 4), z(4, 4), z(3, 4), z(4, 3), z(3, 4, 3),
+                                                0, 3),
+        "dphi_piv": lambda: api.tc_xtc_one_body(z(4, 4, 4), z(4, 4), z(6, 4), z(4, 3), z(3, 3, 4),
+                                                1),
+        "Wbar": lambda: api.tc_kernel_adjoint(z(10, 3), z(10), z(4, 10), z(3, 4, 10), J,
+                                              z(4, 4, 3)),
+        "mo_coef": lambda: api.isdf_eval_orbitals(*basis[:1], basis[1], basis[2], basis[3],
+                                                  z(5, 2), z(10, 3)),
+        "coefs": lambda: api.isdf_vmc_sample((z(4, 3), basis[1], z(4, 2), z(4, 3)), z(4, 2), 1,
+                                             z(8, 2, 3), z(2, 2, 8, 3), z(2, 2, 8), 0.5),
+        "walkers": lambda: api.isdf_vmc_local_energy(basis, z(4, 2), 2, z(8, 2, 3), J, [1.0, 1.0]),
+        "charges": lambda: api.isdf_vmc_local_energy(basis, z(4, 2), 1, z(8, 2, 3), J, [1.0]),
+        "normals": lambda: api.isdf_vmc_sample(basis, z(4, 2), 1, z(8, 2, 3), z(2, 2, 8, 2),
+                                               z(2, 2, 8), 0.5),
+        "uniforms": lambda: api.isdf_vmc_sample(basis, z(4, 2), 1, z(8, 2, 3), z(2, 2, 8, 3),
+                                                z(2, 2, 7), 0.5),
+        "dE": lambda: api.isdf_vmc_gn_step(z(8), z(3, 9), 0.0, 1.0),
+        "theta": lambda: api.isdf_vmc_gn_step(z(8), z(3, 8), 0.0, 1.0, theta=z(4)),
+    }
+    from paper_2607_17314_b300 import proposer as PR
+    P = PR.n_params()
+    f32 = torch.float32
+    cases.update({
+        r"grid_xyz has shape \(10, 4\)": lambda: PR.features(z(3, 10), z(3, 3, 10), z(10), z(10, 4),
+                                                             [[0, 0, 0]]),
+        "params": lambda: PR.forward(z(P - 1, dtype=f32), z(5, 8, dtype=f32)),
+        "feat": lambda: PR.forward(z(P, dtype=f32), z(5, 7, dtype=f32)),
+        "labels": lambda: PR.backward(z(P, dtype=f32), z(5, 8, dtype=f32), z(4, dtype=f32), 1.0,
+                                      5, z(P, dtype=f32), z(1)),
+        "loss": lambda: PR.backward(z(P, dtype=f32), z(5, 8, dtype=f32), z(5, dtype=f32), 1.0,
+                                    5, z(P, dtype=f32), z(2)),
+        "m has shape": lambda: PR.adam(z(P, dtype=f32), z(P, dtype=f32), z(3, dtype=f32),
+                                       z(P, dtype=f32), 1, 1e-3),
+        "cand": lambda: PR.points_restricted(z(3, 10), z(3, 3, 10), z(10),
+                                             z(2, 2, dtype=torch.int32), 2),
+        "w has shape": lambda: PR.fit_error(z(3, 10), z(11), z(2, dtype=torch.int32)),
+    })
+    for name, call in cases.items():
+        with pytest.raises(ValueError, match=name):
+            call()
