@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "W_munu build TFLOP/s (algorithmic 8 N_mu N_g^2 + 8 N_mu^2 N_g), tensor-core vs FP64 GPU"
+L2_BYTES = 126e6  # B300's L2; operands above it are not served from L2 between steps
 
 
 def parse():
@@ -275,10 +276,13 @@ def run_config(args, wlw, world):
     """The workload config shared by both arms' lines."""
     n_mu, n_g = wlw.n_mu, wlw.n_g
     limbs = 2 if args.precision == "bf16x3" else 3
+    limb_bytes = limbs * 2 * n_mu * n_g
+    l2 = (f"inputs larger than L2 (w xi limbs {limb_bytes / 1e9:.2f} GB)" if limb_bytes > L2_BYTES
+          else f"inputs fit in L2 (w xi limbs {limb_bytes / 1e6:.1f} MB): not a timing size")
     return {"workload": args.workload, "n_g": n_g, "n_mu": n_mu, "n_orb": wlw.n_orb,
             "n_occ": wlw.n_occ, "jastrow": "radial u=r/(2(1+r))",
             "precision": args.precision,
-            "l2": f"inputs larger than L2 (w xi limbs {limbs * 2 * n_mu * n_g / 1e9:.2f} GB)",
+            "l2": l2,
             "parallelism": f"replicas{world}",
             "fp64_products": ("orbitals and fit: emulated on the tensor cores"
                               if getattr(args, "fit_mode", 0) else "FP64 on CUDA cores"),

@@ -66,3 +66,28 @@ def test_w_flops_counts_both_stages(n_mu, rows, n_g):
     s1 = 4 * 2 * n_mu * rows * n_g
     s2 = 4 * 2 * n_mu * n_mu * rows
     assert bench.w_flops(n_mu, rows, n_g) == s1 + s2
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the oracle on the host (no GPU) and
+    prints one JSON line with the contract's keys; its cpu_baseline and e2e
+    describe the same run, with no host-device copies."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "h6_chain", "--steps", "2", "--warmup", "1",
+                        "--cpu-rows", "4"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "TFLOP/s" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["dtype"] == "f64" and line["config"]["workload"] == "h6_chain"
+    assert line["config"]["l2"].startswith("inputs fit in L2")     # 4800 x 96: a small case
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert "4 of 4800 outer grid points" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
