@@ -84,14 +84,15 @@ def api():
     return api
 
 
-@pytest.mark.parametrize("prec,debug", [("bf16x3", 0), ("bf16x6", 0), ("bf16x3", 2),
-                                        ("tf32x3", 0)])
-@pytest.mark.parametrize("name", ["radial", "benzene", "benzene_chi"])
+# Every supported (correlator, precision, kernel) combination: the TF32 stage 1
+# takes the radial correlator only, and the single-CTA kernel (debug bit 1 of
+# the flags, value 2 here) is checked on the benzene case without the one-body term.
+_COMBOS = ([(n, p, 0) for n in ("radial", "benzene", "benzene_chi") for p in ("bf16x3", "bf16x6")]
+           + [("radial", "bf16x3", 2), ("benzene", "bf16x3", 2), ("radial", "tf32x3", 0)])
+
+
+@pytest.mark.parametrize("name,prec,debug", _COMBOS)
 def test_stage1_and_w_every_element(api, name, prec, debug):
-    if prec == "tf32x3" and name != "radial":
-        pytest.skip("the TF32 stage 1 takes the radial correlator only")
-    if debug and name == "benzene_chi":
-        pytest.skip("the single-CTA multi-centre kernel is checked on the benzene case")
     grid, w, jas, xi, xit, calG, bound, W, Wb = _oracle(name)
     n_g = grid.shape[0]
     c = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
